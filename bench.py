@@ -1,0 +1,309 @@
+"""Benchmark of the FastSimilarityGraph hot path on GB300.
+
+One step = the whole path of Algorithm 2 on one synthetic point set resident
+in HBM: tree rebuild (fsg_tree_update), then fsg_build_graph (bin-pass KDE,
+degrees, descent of all n*L samples, leaf finish with weights, SET edge list).
+
+Workload: Gaussian mixture, n = 100,000, d = 10, 10 equal-weight unit blobs
+with centres uniform in [-10,10]^10, sigma = 1.5 (gamma = 1/(2 sigma^2)),
+L = 64 samples per point, Philox seed 0.
+
+Printed (one JSON line, rank 0): sampled edges/s = n*L / step time (device,
+CUDA events, L2 flushed between steps by writing a 512 MB buffer), the e2e
+figure through the host-buffer entry point (copies inside the timed region),
+the roofline of the dominant kernel (bin pass, ALU bound) and the oracle's
+CPU throughput on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sampled graph edges/s & Gkernel-evals/s vs plain FP32 GPU path; p50/p99 latency"
+UNIT = "sampled edges/s"
+WORKLOAD = dict(workload="gaussian_mixture n=100000 d=10 k=10 box=10 sigma=1.5 L=64 seed=0", n=100_000, d=10,
+                sigma=1.5, L=64, seed=0, edges="SET", self_term="EXCLUDE", l2="flushed (512 MB write) between steps")
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128
+MUFU_EX2_PER_SM = 16
+
+
+def alu_peak_evals(d: int, mhz: float = SM_MAX_MHZ) -> float:
+    """ALU bound of the bin pass, in kernel evaluations/s: per evaluation the
+    FP32 pipe executes d subtractions, d multiply-adds, one scale and one
+    accumulate (2d+2 lane operations) and the MUFU one ex2."""
+    fp32 = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / (2 * d + 2)
+    mufu = SM_COUNT * MUFU_EX2_PER_SM * mhz * 1e6
+    return min(fp32, mufu)
+
+
+def make_points(rank: int = 0):
+    from paper_2310_13870_gb300 import inputs
+    return inputs.gaussian_mixture(n=WORKLOAD["n"], d=WORKLOAD["d"], seed=WORKLOAD["seed"] + rank)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fsg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_throughput(X, n_queries: int, L: int, sigma: float, seed: int):
+    """The oracle (as it stands) on a bounded sample: the descent of every
+    sample of n_queries points plus their degrees, on all host cores.
+    Returns (sampled edges/s, seconds, threads)."""
+    import oracle as ora
+    gam = ora.gamma(sigma)
+    q = np.arange(n_queries, dtype=np.int64) * (X.shape[0] // n_queries)
+    t0 = time.perf_counter()
+    ora.sample(X, gam, L, seed, queries=q)
+    ora.degrees(X, gam, queries=q)
+    dt = time.perf_counter() - t0
+    return n_queries * L / dt, dt, ora.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as ora
+    ora.build()
+    X = make_points(0)
+    L, sigma, seed = WORKLOAD["L"], WORKLOAD["sigma"], WORKLOAD["seed"]
+    nq = args.ref_queries
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, dt, threads = cpu_oracle_throughput(X, nq, L, sigma, seed)
+        if s >= args.warmup:
+            vals.append((v, dt))
+    value = statistics.mean(v for v, _ in vals)
+    ms = statistics.mean(dt for _, dt in vals) * 1e3
+    sample = f"{nq} query points of the n=100000 workload per step (all {L} samples + degrees), extrapolated per edge"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism="oracle on host cores"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2310_13870_gb300 import fsg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(fsg.LIB_PATH):
+        import __graft_entry__ as g
+        g.build()
+    fsg.load()
+    n, d, L, sigma, seed = WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["L"], WORKLOAD["sigma"], WORKLOAD["seed"]
+    X = make_points(rank)
+    stream = torch.cuda.Stream()
+    p = fsg.params(sigma)
+    with torch.cuda.stream(stream):
+        pts = torch.from_numpy(X).cuda()
+        tree = fsg.fsg_build_tree(pts, stream=stream)
+        bufs = fsg.GraphBuffers(n, L, with_aux=False)
+        bufs.deg = torch.empty(n, dtype=torch.float64, device="cuda")
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        fsg.fsg_tree_update(tree, pts, stream=stream)
+        fsg.fsg_build_graph(tree, p, L, seed, bufs=bufs, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    fsg.fsg_sync(tree, stream=stream)
+    fsg.fsg_profile(tree, True)
+    _, launches0 = fsg.fsg_profile_read(tree)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, kde_ms, phase_tot = [], [], {}
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ph, _ = fsg.fsg_profile_read(tree)
+        kde_ms.append(ph["kde_bins"])
+        for k, v in ph.items():
+            phase_tot[k] = phase_tot.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    _, launches1 = fsg.fsg_profile_read(tree)
+    fsg.fsg_profile(tree, False)
+    assert fsg.fsg_sync(tree, stream=stream) == 0
+    ms = statistics.mean(step_ms)
+    st = fsg.stats_dict(bufs)
+    m = int(bufs.m.item())
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * L / (ms * 1e-3)
+    evals_per_step = st["n_evals"]
+    gevals = world * evals_per_step / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (bin pass): algorithmic evaluations n*n
+    kde_avg = statistics.mean(kde_ms)
+    achieved = n * n / (kde_avg * 1e-3) / 1e9
+    peak = alu_peak_evals(d) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "kde_bins_traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        cap = n * L
+        hsrc = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
+        hdst = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
+        hw = torch.empty(cap, dtype=torch.float32).pin_memory().numpy()
+        hX = torch.from_numpy(X).pin_memory().numpy()
+        times, mm = [], 0
+        for r in range(2 + args.e2e_steps):
+            t0 = time.perf_counter()
+            s_, d_, w_ = fsg.fsg_build_graph_host(hX, p, L, seed, out=(hsrc, hdst, hw), stream=stream)
+            dt = time.perf_counter() - t0
+            mm = len(s_)
+            if r >= 2:
+                times.append(dt)
+        e2e_s = statistics.mean(times)
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n * L / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
+               "d2h_bytes_per_step": int(8 + mm * 12), "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.cpu_queries} of the {n} query points (all {L} samples each + their degrees), "
+                         f"{dt:.1f} s, extrapolated per sampled edge"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)"),
+                "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
+                "flagged_samples": st["n_flagged"], "items": st["n_items"],
+                "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
+                "roofline": {"bound": "alu", "kernel": "kde_bins_kernel<10>", "achieved": achieved, "peak": peak,
+                             "unit": "Gkernel-evals/s", "frac": achieved / peak, "traffic": traffic,
+                             "peak_basis": f"{SM_COUNT} SMs x min({FP32_LANES_PER_SM} FP32 lanes/(2d+2), "
+                                           f"{MUFU_EX2_PER_SM} ex2) x {SM_MAX_MHZ:.0f} MHz"},
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches1 - launches0)}
+        print(json.dumps(line), flush=True)
+    tree.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-queries", type=int, default=2048)
+    ap.add_argument("--ref-queries", type=int, default=1024)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * fsg.h -- C ABI of the GB300 (sm_103a) FastSimilarityGraph hot path.
+ *
+ * The library computes, on one GPU, the data-parallel core of the algorithm of
+ * Macgregor & Sun, "Fast Approximation of Similarity Graphs with Kernel
+ * Density Estimation" (NeurIPS 2023):
+ *   - Gaussian kernel k(x_i,x_j) = exp(-gamma ||x_i-x_j||^2)          (Sec. 2.1)
+ *   - KDE sums g_[a,b](y_i) = sum_{j=a..b} k(y_i,x_j), computed exactly   (Eq. 1)
+ *   - degrees g_[1,n](x_i)                                          (Algorithm 2)
+ *   - L neighbour samples per point by recursive halving of the point set,
+ *     moving left with probability g_left/(g_left+g_right)   (Algorithm 1, Sec. 4.1)
+ *   - the re-weighted sparse edge list w = k / p_hat                 (Eq. 2, Algorithm 2)
+ *
+ * Conventions shared by every call
+ *   - Every function returns an int status: FSG_OK (0) or one of FSG_ERR_*.
+ *     fsg_error_string() describes a status.  Invalid arguments are refused
+ *     before anything is enqueued.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued asynchronously on that stream; outputs are
+ *     valid once the stream reaches that point.  Device-side faults of the
+ *     library's own checks (a bounded wait that ran out) are recorded in a
+ *     per-tree status word that fsg_sync() reads and returns.
+ *   - Device pointers (d_*) are CUDA global-memory addresses on the current
+ *     device; host pointers (h_*) are ordinary host memory (pinned memory makes
+ *     the copies of the host entry point asynchronous).
+ *   - Points are float32, row-major [n][d], indexed by ORIGINAL point index.
+ *     Outputs indexed by point use original indices as well.
+ *   - The caller owns every buffer it passes; the library never frees them.
+ *     fsg_tree objects are owned by the library and released by fsg_free_tree.
+ *   - No host fallback exists: without a usable sm_103a GPU every compute call
+ *     fails with FSG_ERR_CUDA.
+ */
+#ifndef FSG_H
+#define FSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FSG_OK 0
+#define FSG_ERR_INVALID_ARG 1   /* bad size, NULL pointer, sigma <= 0, ...      */
+#define FSG_ERR_OOM 2           /* a device allocation failed                     */
+#define FSG_ERR_CUDA 3          /* a CUDA runtime call failed                     */
+#define FSG_ERR_TIMEOUT 4       /* a bounded device wait ran out                  */
+#define FSG_ERR_UNSUPPORTED 5   /* option not implemented for these sizes        */
+#define FSG_ERR_BUSY 6          /* server: no slot or budget for the request      */
+#define FSG_ERR_CAPACITY 7      /* an output buffer is too small                  */
+
+/* ---- option values ----------------------------------------------------- */
+/* Bandwidth convention: gamma = 1/(2 sigma^2) (default) or 1/sigma^2, the form
+ * printed in Sec. 2.1. */
+#define FSG_TWO_SIGMA_SQ 0
+#define FSG_SIGMA_SQ 1
+/* Self term: EXCLUDE omits j == i from every KDE sum (the fully connected
+ * graph of Sec. 2.1 has no self loops, so g_[1,n](x_i) equals the degree);
+ * INCLUDE keeps k(i,i) = 1 as Algorithm 1 literally sums over all of X. */
+#define FSG_SELF_EXCLUDE 0
+#define FSG_SELF_INCLUDE 1
+/* Arithmetic of the kernel evaluations. */
+#define FSG_PREC_AUTO 0         /* FP32 for d <= 16; tensor-core form for large d */
+#define FSG_PREC_FP32 1         /* FP32 direct differences + ex2 on every d       */
+#define FSG_PREC_SPLIT_BF16 2   /* BF16 hi/lo split tcgen05 GEMM, FP32 accumulate */
+#define FSG_PREC_EXACT_INT 3    /* tcgen05 BF16 on data that are k/255 exactly    */
+/* Edge semantics of Algorithm 2's set union. */
+#define FSG_EDGES_SET 0         /* one edge per unordered pair {i,j} sampled      */
+#define FSG_EDGES_MULTI 1       /* one edge per (non-self) sample                 */
+/* Sampling schedule. */
+#define FSG_SCHED_FUSED 0       /* top levels from one bin pass, then leaf finish */
+#define FSG_SCHED_LEVELWISE 1   /* literal per-level KDE of both halves           */
+
+typedef struct fsg_tree fsg_tree; /* opaque */
+
+typedef struct {
+    /* Device int32 [n]: tree position p -> original point index (a
+     * permutation), or NULL for the identity order.  Copied at build time. */
+    const int32_t* d_perm;
+    /* Largest node handled by the leaf-finish kernel (power of two in
+     * [64, 1024]); 0 selects 256.  Smaller values run more levels through the
+     * bin pass. */
+    int32_t leaf_max;
+    int32_t reserved[5];
+} fsg_tree_opts;
+
+typedef struct {
+    double sigma;          /* kernel bandwidth, > 0 and finite                 */
+    int32_t scale_conv;    /* FSG_TWO_SIGMA_SQ | FSG_SIGMA_SQ                   */
+    int32_t self_mode;     /* FSG_SELF_EXCLUDE | FSG_SELF_INCLUDE               */
+    int32_t precision;     /* FSG_PREC_*                                        */
+    int32_t schedule;      /* FSG_SCHED_*                                       */
+    /* Relative error bound eps of the GPU's KDE sums used to flag near-threshold
+     * decisions: a level is flagged when |u - r| < 2 eps r (1-r) + 2^-22 with
+     * r = g_left/(g_left+g_right).  0 selects 2^-13. */
+    float flag_eps;
+    int32_t reserved[5];
+} fsg_params;
+
+/* Device-side statistics of one fsg_build_graph call (all int64). */
+typedef struct {
+    int64_t n_samples;     /* n * L descents run                               */
+    int64_t n_flagged;     /* samples with >= 1 near-threshold decision         */
+    int64_t n_self;        /* samples that returned the query itself (INCLUDE)  */
+    int64_t n_empty;       /* samples of zero-degree queries (index -1)         */
+    int64_t n_evals;       /* kernel evaluations executed                        */
+    int64_t n_items;       /* distinct (query, node) pairs in the leaf finish   */
+    int64_t n_edges;       /* edges written                                     */
+    int64_t status;        /* device status word (FSG_OK or FSG_ERR_TIMEOUT)    */
+} fsg_stats;
+
+/* Library version string and a description of a status code. */
+const char* fsg_version(void);
+const char* fsg_error_string(int status);
+
+/*
+ * Builds the device-resident tree of n points (Sec. 4.1: the point set is split
+ * recursively into a left half of floor(|X|/2) points and a right half).
+ *   d_points : device float32 [n][d] row-major, read only during this call.
+ *   n        : 1 <= n <= 2^31 - 1;  d : 1 <= d <= 4096.
+ *   opts     : may be NULL (identity order, leaf_max 256).
+ * Writes *out.  The tree holds a tree-ordered, padded copy of the points and
+ * grows a workspace on first use; fsg_free_tree releases both.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts,
+                   void* stream, fsg_tree** out);
+void fsg_free_tree(fsg_tree* tree);
+
+/* Number of points, dimension and depth ceil(log2 n) of a tree. */
+int fsg_tree_info(const fsg_tree* tree, int64_t* n, int32_t* d, int32_t* depth);
+
+/*
+ * Replaces the tree's points by new values of the same shape (n, d) in the
+ * same tree order, without allocating (Sec. 4.1's tree is rebuilt in place).
+ *   d_points : device float32 [n][d], read only during this call.
+ * Errors: INVALID_ARG, CUDA.
+ */
+int fsg_tree_update(fsg_tree* tree, const float* d_points, void* stream);
+
+/*
+ * Degrees g_[1,n](x_i) of Algorithm 2 (Eq. 1 over all points) for every point.
+ *   d_deg : device float64 [n], indexed by original point index.
+ * Errors: INVALID_ARG (params), OOM, CUDA, UNSUPPORTED.
+ */
+int fsg_degrees(fsg_tree* tree, const fsg_params* params, double* d_deg, void* stream);
+
+/*
+ * L samples per point by the descent of Algorithm 1 (Sec. 4.1).  The uniform
+ * u of (point i, sample l, level lev) is word (lev mod 4) of Philox4x32-10
+ * (Salmon et al., SC'11) at counter (i, l, lev/4, 0) with key (seed low 32
+ * bits, seed high 32 bits), divided by 2^32; the descent goes left iff
+ * u < g_left/(g_left+g_right).
+ *   L         : 1..64.
+ *   d_samples : device int32 [n][L]: original index of the neighbour, or -1
+ *               when the point has zero degree.
+ *   d_flags   : device uint8 [n][L] or NULL: bit 0 = some decision was within
+ *               the flag tolerance (see fsg_params.flag_eps), bit 1 = some
+ *               node had zero FP32 mass.
+ * Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED.
+ */
+int fsg_sample_edges(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_t seed,
+                     int32_t* d_samples, uint8_t* d_flags, void* stream);
+
+/*
+ * The whole of Algorithm 2: L samples per point, degrees, and the sparse
+ * edge list with weights w(i,j) = k(x_i,x_j) / p_hat(i,j),
+ * p_hat = p_i + p_j - p_i p_j, p_i = min(L k / g_[1,n](x_i), 1)    (Eq. 2).
+ *   edge_mode  : FSG_EDGES_SET or FSG_EDGES_MULTI.
+ *   d_src,d_dst: device int32 [cap] original indices (SET: the point that
+ *                sampled the edge first in (point, sample) order is src).
+ *   d_w        : device float32 [cap].
+ *   cap        : >= n*L (an upper bound of the edge count in either mode).
+ *   d_m_out    : device int64, number of edges written.
+ *   d_deg, d_samples, d_flags, d_stats : optional device outputs (NULL to
+ *                skip): float64 [n], int32 [n][L], uint8 [n][L], fsg_stats.
+ * Errors: INVALID_ARG, CAPACITY, OOM, CUDA, UNSUPPORTED.
+ */
+int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_t seed,
+                    int32_t edge_mode, int32_t* d_src, int32_t* d_dst, float* d_w, int64_t cap,
+                    int64_t* d_m_out, double* d_deg, int32_t* d_samples, uint8_t* d_flags,
+                    fsg_stats* d_stats, void* stream);
+
+/*
+ * Per-phase timing with CUDA events recorded on the call's stream (not part
+ * of the paper's method; used to report kernel durations).
+ * fsg_profile(tree, 1) makes later calls record an event at each phase
+ * boundary; fsg_profile_read() waits for the last profiled call and writes
+ * the duration in milliseconds of each phase into ms[FSG_NUM_PHASES] (0 for
+ * phases that did not run) and the total number of the library's kernel
+ * launches made on this tree since it was built into *launches.
+ */
+#define FSG_PHASE_TREE 0        /* tree build / update                         */
+#define FSG_PHASE_KDE_BINS 1    /* bin pass: every query against every point   */
+#define FSG_PHASE_DESCEND_TOP 2 /* degrees and the top s0 levels               */
+#define FSG_PHASE_BUCKET 3      /* grouping of (query, node) items per node    */
+#define FSG_PHASE_LEAF 4        /* leaf finish: remaining levels and weights   */
+#define FSG_PHASE_EDGES 5       /* edge list                                   */
+#define FSG_PHASE_OUTPUTS 6     /* per-sample outputs and statistics           */
+#define FSG_NUM_PHASES 8
+int fsg_profile(fsg_tree* tree, int enable);
+int fsg_profile_read(fsg_tree* tree, float* ms, int64_t* launches);
+
+/*
+ * Waits for the stream and returns the tree's device status word
+ * (FSG_OK or FSG_ERR_TIMEOUT), then clears it.  Errors: CUDA.
+ */
+int fsg_sync(fsg_tree* tree, void* stream);
+
+/*
+ * End-to-end entry point on HOST buffers: copies h_points to the device,
+ * builds the tree, runs fsg_build_graph, and copies the edge list back.
+ *   h_src, h_dst (int32 [cap]), h_w (float32 [cap]), *h_m_out (edge count).
+ * Blocks until the result is on the host.  The device buffers live in an
+ * internal per-thread cache that grows to the largest (n, d, L) seen.
+ * Errors: as fsg_build_graph, plus CAPACITY when cap < n*L.
+ */
+int fsg_build_graph_host(const float* h_points, int64_t n, int32_t d, const fsg_params* params,
+                         int32_t L, uint64_t seed, int32_t edge_mode, int32_t* h_src,
+                         int32_t* h_dst, float* h_w, int64_t cap, int64_t* h_m_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSG_H */

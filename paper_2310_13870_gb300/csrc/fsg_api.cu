@@ -1,0 +1,498 @@
+// C ABI entry points (include/fsg.h): argument checks, the tree object and
+// its workspace, and the fixed launch sequence of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "fsg_internal.cuh"
+
+namespace fsg {
+
+int leaf_queries_per_tile(const fsg_tree* t);
+
+namespace {
+
+constexpr double kLog2e = 1.4426950408889634073599246810019;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int status_of(cudaError_t e) {
+    if (e == cudaSuccess) return FSG_OK;
+    if (e == cudaErrorMemoryAllocation) return FSG_ERR_OOM;
+    return FSG_ERR_CUDA;
+}
+
+int check_params(const fsg_params* p) {
+    if (!p) return FSG_ERR_INVALID_ARG;
+    if (!(p->sigma > 0.0) || !std::isfinite(p->sigma)) return FSG_ERR_INVALID_ARG;
+    if (p->scale_conv != FSG_TWO_SIGMA_SQ && p->scale_conv != FSG_SIGMA_SQ) return FSG_ERR_INVALID_ARG;
+    if (p->self_mode != FSG_SELF_EXCLUDE && p->self_mode != FSG_SELF_INCLUDE) return FSG_ERR_INVALID_ARG;
+    if (p->precision < FSG_PREC_AUTO || p->precision > FSG_PREC_EXACT_INT) return FSG_ERR_INVALID_ARG;
+    if (p->schedule != FSG_SCHED_FUSED && p->schedule != FSG_SCHED_LEVELWISE) return FSG_ERR_INVALID_ARG;
+    if (!(p->flag_eps >= 0.f) || !std::isfinite(p->flag_eps) || p->flag_eps > 0.25f) return FSG_ERR_INVALID_ARG;
+    return FSG_OK;
+}
+
+KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
+    const double gamma = p->scale_conv == FSG_SIGMA_SQ ? 1.0 / (p->sigma * p->sigma)
+                                                       : 1.0 / (2.0 * p->sigma * p->sigma);
+    KernelParams kp;
+    kp.gamma = (float)gamma;
+    kp.neg_c = (float)(-gamma * kLog2e);
+    kp.self_exclude = p->self_mode == FSG_SELF_EXCLUDE ? 1 : 0;
+    kp.L = L;
+    kp.seed = seed;
+    kp.flag_eps = p->flag_eps > 0.f ? p->flag_eps : 0x1p-13f;
+    return kp;
+}
+
+// Records the start/end event of a phase when profiling is on.
+struct PhaseScope {
+    fsg_tree* t;
+    int phase;
+    cudaStream_t s;
+    PhaseScope(fsg_tree* t_, int phase_, cudaStream_t s_) : t(t_), phase(phase_), s(s_) {
+        if (t->profiling) cudaEventRecord(t->ev_start[phase], s);
+    }
+    ~PhaseScope() {
+        if (t->profiling) {
+            cudaEventRecord(t->ev_end[phase], s);
+            t->ev_used[phase] = true;
+        }
+    }
+};
+
+void begin_call(fsg_tree* t) {
+    for (int k = 0; k < FSG_NUM_PHASES; ++k) t->ev_used[k] = false;
+}
+
+int check_path(const fsg_tree* t, const fsg_params* p) {
+    if (p->precision == FSG_PREC_SPLIT_BF16 || p->precision == FSG_PREC_EXACT_INT) return FSG_ERR_UNSUPPORTED;
+    if (!kde_bins_supported(t)) return FSG_ERR_UNSUPPORTED;
+    if (p->schedule != FSG_SCHED_FUSED) return FSG_ERR_UNSUPPORTED;
+    return FSG_OK;
+}
+
+}  // namespace
+
+int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
+    Workspace& ws = t->ws;
+    if (ws.base && ws.cap_n >= t->n && ws.cap_L >= L) return FSG_OK;
+    const int64_t n = t->n;
+    const int64_t Lc = L > ws.cap_L ? L : ws.cap_L;
+    const int64_t nb = t->nb;
+    const int64_t max_items = n * (Lc < nb ? Lc : nb);
+    const int64_t nblocks = (n + 1023) / 1024 + 2;
+    size_t off = 0;
+    struct Part { void** ptr; size_t bytes; };
+    Part parts[] = {
+        {(void**)&ws.binsum, sizeof(float) * (size_t)n * nb},
+        {(void**)&ws.degf, sizeof(float) * (size_t)n},
+        {(void**)&ws.node_bin, sizeof(int32_t) * (size_t)n * Lc},
+        {(void**)&ws.flags, sizeof(uint8_t) * (size_t)n * Lc},
+        {(void**)&ws.leaf_pos, sizeof(int32_t) * (size_t)n * Lc},
+        {(void**)&ws.wsmp, sizeof(float) * (size_t)n * Lc},
+        {(void**)&ws.bin_count, sizeof(int32_t) * (size_t)nb},
+        {(void**)&ws.bin_cursor, sizeof(int32_t) * (size_t)nb},
+        {(void**)&ws.bin_off, sizeof(int32_t) * (size_t)(nb + 1)},
+        {(void**)&ws.tile_prefix, sizeof(int32_t) * (size_t)(nb + 1)},
+        {(void**)&ws.items_q, sizeof(int32_t) * (size_t)max_items},
+        {(void**)&ws.items_mask, sizeof(uint64_t) * (size_t)max_items},
+        {(void**)&ws.uniq, sizeof(int32_t) * (size_t)n * Lc},
+        {(void**)&ws.uniq_w, sizeof(float) * (size_t)n * Lc},
+        {(void**)&ws.ucnt, sizeof(int32_t) * (size_t)n},
+        {(void**)&ws.emit_mask, sizeof(uint64_t) * (size_t)n},
+        {(void**)&ws.ecount, sizeof(int64_t) * (size_t)(n + 1)},
+        {(void**)&ws.scan_tmp, sizeof(int64_t) * (size_t)nblocks},
+        {(void**)&ws.stats, sizeof(fsg_stats)},
+        {(void**)&ws.misc, sizeof(int32_t) * 8},
+    };
+    size_t offs[sizeof(parts) / sizeof(parts[0])];
+    for (size_t k = 0; k < sizeof(parts) / sizeof(parts[0]); ++k) {
+        offs[k] = off;
+        off = align_up(off + parts[k].bytes, 256);
+    }
+    if (ws.base) {
+        cudaStreamSynchronize(s);
+        cudaFree(ws.base);
+        ws.base = nullptr;
+    }
+    void* base = nullptr;
+    cudaError_t e = cudaMalloc(&base, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ws.cap_n = ws.cap_L = 0;
+        return status_of(e);
+    }
+    ws.base = base;
+    ws.bytes = off;
+    for (size_t k = 0; k < sizeof(parts) / sizeof(parts[0]); ++k)
+        *parts[k].ptr = static_cast<char*>(base) + offs[k];
+    ws.cap_n = n;
+    ws.cap_L = Lc;
+    return FSG_OK;
+}
+
+}  // namespace fsg
+
+using namespace fsg;
+
+extern "C" {
+
+const char* fsg_version(void) { return "fsg-gb300 0.1 (sm_103a)"; }
+
+const char* fsg_error_string(int status) {
+    switch (status) {
+        case FSG_OK: return "ok";
+        case FSG_ERR_INVALID_ARG: return "invalid argument";
+        case FSG_ERR_OOM: return "device allocation failed";
+        case FSG_ERR_CUDA: return "CUDA runtime error";
+        case FSG_ERR_TIMEOUT: return "a bounded device wait ran out";
+        case FSG_ERR_UNSUPPORTED: return "option not supported for these sizes";
+        case FSG_ERR_BUSY: return "no slot or memory budget available";
+        case FSG_ERR_CAPACITY: return "output buffer too small";
+        default: return "unknown status";
+    }
+}
+
+int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts, void* stream,
+                   fsg_tree** out) {
+    if (!out) return FSG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d_points || n < 1 || n > (int64_t)0x7fffffff - 4096 || d < 1 || d > 4096) return FSG_ERR_INVALID_ARG;
+    int leaf_max = opts && opts->leaf_max ? opts->leaf_max : 0;
+    if (leaf_max && (leaf_max < 64 || leaf_max > 1024 || (leaf_max & (leaf_max - 1)))) return FSG_ERR_INVALID_ARG;
+    const bool auto_leaf = leaf_max == 0;
+    if (auto_leaf) leaf_max = 256;
+    auto pick = [&](int lm, int& s0) {
+        s0 = 0;
+        while ((n + (int64_t(1) << s0) - 1) >> s0 > lm) ++s0;
+    };
+    int s0 = 0;
+    pick(leaf_max, s0);
+    while (auto_leaf && s0 > 10 && leaf_max < 1024) { leaf_max *= 2; pick(leaf_max, s0); }
+    if (s0 > 12) return FSG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    fsg_tree* t = new (std::nothrow) fsg_tree();
+    if (!t) return FSG_ERR_OOM;
+    t->n = n;
+    t->d = d;
+    t->dp = (d + 3) & ~3;
+    t->depth = ceil_log2_host(n);
+    t->leaf_max = leaf_max;
+    t->s0 = s0;
+    t->nb = 1 << s0;
+    t->mmax = (int)((n + t->nb - 1) / t->nb);
+    t->dm = ceil_log2_host(t->mmax);
+    t->n_pad = (n + 127) / 128 * 128;
+    cudaGetDevice(&t->device);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&t->Xt, sizeof(float) * (size_t)t->n_pad * t->dp);
+    if (d <= kMaxFmaDim) alloc((void**)&t->Xdup, sizeof(float) * 2 * (size_t)t->n_pad * t->dp);
+    alloc((void**)&t->perm, sizeof(int32_t) * (size_t)n);
+    alloc((void**)&t->inv, sizeof(int32_t) * (size_t)n);
+    alloc((void**)&t->bnd, sizeof(int32_t) * (size_t)(t->nb + 1));
+    alloc((void**)&t->status, sizeof(int32_t) * 8);
+    if (e == cudaSuccess) {
+        e = launch_tree_prep(t, d_points, opts ? opts->d_perm : nullptr, s);
+        t->launches += 2;
+    }
+    int rc = status_of(e);
+    if (rc == FSG_OK && opts && opts->d_perm) {
+        // a caller-given order is validated before the tree is handed out
+        int32_t st[2] = {0, 0};
+        e = cudaMemcpyAsync(st, t->status, sizeof(st), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        rc = status_of(e);
+        if (rc == FSG_OK && st[0] != 0) rc = FSG_ERR_INVALID_ARG;
+    }
+    if (rc != FSG_OK) {
+        cudaGetLastError();
+        fsg_free_tree(t);
+        return rc;
+    }
+    *out = t;
+    return FSG_OK;
+}
+
+void fsg_free_tree(fsg_tree* t) {
+    if (!t) return;
+    for (int k = 0; k < FSG_NUM_PHASES; ++k) {
+        if (t->ev_start[k]) cudaEventDestroy(t->ev_start[k]);
+        if (t->ev_end[k]) cudaEventDestroy(t->ev_end[k]);
+    }
+    cudaFree(t->Xt);
+    cudaFree(t->Xdup);
+    cudaFree(t->perm);
+    cudaFree(t->inv);
+    cudaFree(t->bnd);
+    cudaFree(t->status);
+    cudaFree(t->ws.base);
+    delete t;
+}
+
+int fsg_tree_info(const fsg_tree* t, int64_t* n, int32_t* d, int32_t* depth) {
+    if (!t) return FSG_ERR_INVALID_ARG;
+    if (n) *n = t->n;
+    if (d) *d = t->d;
+    if (depth) *depth = t->depth;
+    return FSG_OK;
+}
+
+int fsg_tree_update(fsg_tree* t, const float* d_points, void* stream) {
+    if (!t || !d_points) return FSG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    begin_call(t);
+    PhaseScope ph(t, FSG_PHASE_TREE, s);
+    // the stored order is reused: tree_prep reads perm[p] before rewriting it
+    cudaError_t e = launch_tree_prep(t, d_points, t->perm, s);
+    t->launches += 2;
+    return status_of(e);
+}
+
+int fsg_profile(fsg_tree* t, int enable) {
+    if (!t) return FSG_ERR_INVALID_ARG;
+    if (enable && !t->ev_start[0]) {
+        for (int k = 0; k < FSG_NUM_PHASES; ++k) {
+            if (cudaEventCreate(&t->ev_start[k]) != cudaSuccess || cudaEventCreate(&t->ev_end[k]) != cudaSuccess)
+                return FSG_ERR_CUDA;
+        }
+    }
+    t->profiling = enable != 0;
+    return FSG_OK;
+}
+
+int fsg_profile_read(fsg_tree* t, float* ms, int64_t* launches) {
+    if (!t) return FSG_ERR_INVALID_ARG;
+    if (launches) *launches = t->launches;
+    if (!ms) return FSG_OK;
+    for (int k = 0; k < FSG_NUM_PHASES; ++k) {
+        ms[k] = 0.f;
+        if (t->ev_used[k] && t->ev_start[k]) {
+            if (cudaEventSynchronize(t->ev_end[k]) != cudaSuccess) return FSG_ERR_CUDA;
+            if (cudaEventElapsedTime(&ms[k], t->ev_start[k], t->ev_end[k]) != cudaSuccess) return FSG_ERR_CUDA;
+        }
+    }
+    return FSG_OK;
+}
+
+static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cudaStream_t s) {
+    Workspace& ws = t->ws;
+    cudaError_t e = cudaMemsetAsync(ws.bin_count, 0, sizeof(int32_t) * t->nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.bin_cursor, 0, sizeof(int32_t) * t->nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
+        e = launch_kde_bins(t, kp, s);
+        t->launches += 1;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_DESCEND_TOP, s);
+        e = launch_descend_top(t, kp, d_deg, 1, s);
+        t->launches += 1;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_BUCKET, s);
+        e = launch_bucket(t, kp, s);
+        t->launches += 2;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_LEAF, s);
+        e = launch_leaf_finish(t, kp, s);
+        t->launches += 1;
+    }
+    return status_of(e);
+}
+
+// Statistics known on the host: samples run, bin-pass evaluations.
+__global__ static void stats_finish_kernel(fsg_stats* st, int64_t n_samples, int64_t bin_evals,
+                                           const int32_t* status, fsg_stats* out) {
+    st->n_samples = n_samples;
+    st->n_evals += bin_evals;
+    st->status = status[0];
+    if (out) *out = *st;
+}
+
+int fsg_degrees(fsg_tree* t, const fsg_params* p, double* d_deg, void* stream) {
+    if (!t || !d_deg) return FSG_ERR_INVALID_ARG;
+    int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    if ((rc = check_path(t, p)) != FSG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_workspace(t, 1, s)) != FSG_OK) return rc;
+    const KernelParams kp = make_kernel_params(p, 1, 0);
+    begin_call(t);
+    cudaError_t e;
+    {
+        PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
+        e = launch_kde_bins(t, kp, s);
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_DESCEND_TOP, s);
+        e = launch_descend_top(t, kp, d_deg, 0, s);
+    }
+    t->launches += 2;
+    return status_of(e);
+}
+
+int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t* d_samples,
+                     uint8_t* d_flags, void* stream) {
+    if (!t || !d_samples || L < 1 || L > kMaxL) return FSG_ERR_INVALID_ARG;
+    int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    if ((rc = check_path(t, p)) != FSG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    const KernelParams kp = make_kernel_params(p, L, seed);
+    begin_call(t);
+    if ((rc = run_sampling(t, kp, nullptr, s)) != FSG_OK) return rc;
+    cudaError_t e;
+    {
+        PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
+        e = launch_outputs(t, kp, d_samples, d_flags, nullptr, s);
+        if (e == cudaSuccess) {
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, t->n * t->n, t->status, nullptr);
+            e = cudaGetLastError();
+        }
+        t->launches += 2;
+    }
+    return status_of(e);
+}
+
+int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t edge_mode, int32_t* d_src,
+                    int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, double* d_deg, int32_t* d_samples,
+                    uint8_t* d_flags, fsg_stats* d_stats, void* stream) {
+    if (!t || L < 1 || L > kMaxL || !d_src || !d_dst || !d_w || !d_m_out) return FSG_ERR_INVALID_ARG;
+    if (edge_mode != FSG_EDGES_SET && edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
+    if (cap < t->n * (int64_t)L) return FSG_ERR_CAPACITY;
+    int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    if ((rc = check_path(t, p)) != FSG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    const KernelParams kp = make_kernel_params(p, L, seed);
+    begin_call(t);
+    if ((rc = run_sampling(t, kp, d_deg, s)) != FSG_OK) return rc;
+    cudaError_t e;
+    {
+        PhaseScope ph(t, FSG_PHASE_EDGES, s);
+        e = launch_edges(t, kp, edge_mode, d_src, d_dst, d_w, cap, d_m_out, s);
+        t->launches += edge_mode == FSG_EDGES_SET ? 6 : 5;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
+        e = launch_outputs(t, kp, d_samples, d_flags, d_stats, s);
+        if (e == cudaSuccess) {
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, t->n * t->n, t->status, d_stats);
+            e = cudaGetLastError();
+        }
+        t->launches += 2;
+    }
+    return status_of(e);
+}
+
+int fsg_sync(fsg_tree* t, void* stream) {
+    if (!t) return FSG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return status_of(e);
+    if (st != 0) {
+        cudaMemsetAsync(t->status, 0, sizeof(int32_t), s);
+        cudaStreamSynchronize(s);
+        return st;
+    }
+    return FSG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-buffer entry point: device buffers cached per calling thread.
+// ---------------------------------------------------------------------------
+namespace {
+struct HostCache {
+    float* d_points = nullptr;
+    int32_t* d_src = nullptr;
+    int32_t* d_dst = nullptr;
+    float* d_w = nullptr;
+    int64_t* d_m = nullptr;
+    int64_t cap_pts = 0, cap_edges = 0;
+    fsg_tree* tree = nullptr;  // reused while (n, d) stay the same
+    ~HostCache() {
+        fsg_free_tree(tree);
+        cudaFree(d_points); cudaFree(d_src); cudaFree(d_dst); cudaFree(d_w); cudaFree(d_m);
+    }
+};
+thread_local HostCache g_host_cache;
+}  // namespace
+
+int fsg_build_graph_host(const float* h_points, int64_t n, int32_t d, const fsg_params* p, int32_t L, uint64_t seed,
+                         int32_t edge_mode, int32_t* h_src, int32_t* h_dst, float* h_w, int64_t cap,
+                         int64_t* h_m_out, void* stream) {
+    if (!h_points || !h_src || !h_dst || !h_w || !h_m_out || n < 1 || d < 1 || L < 1 || L > kMaxL)
+        return FSG_ERR_INVALID_ARG;
+    if (cap < n * (int64_t)L) return FSG_ERR_CAPACITY;
+    int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    HostCache& hc = g_host_cache;
+    cudaError_t e = cudaSuccess;
+    if (hc.cap_pts < n * (int64_t)d) {
+        cudaFree(hc.d_points);
+        hc.d_points = nullptr;
+        hc.cap_pts = 0;
+        e = cudaMalloc(&hc.d_points, sizeof(float) * (size_t)n * d);
+        if (e != cudaSuccess) return status_of(e);
+        hc.cap_pts = n * (int64_t)d;
+    }
+    const int64_t ecap = n * (int64_t)L;
+    if (hc.cap_edges < ecap) {
+        cudaFree(hc.d_src); cudaFree(hc.d_dst); cudaFree(hc.d_w); cudaFree(hc.d_m);
+        hc.d_src = hc.d_dst = nullptr; hc.d_w = nullptr; hc.d_m = nullptr; hc.cap_edges = 0;
+        e = cudaMalloc(&hc.d_src, sizeof(int32_t) * (size_t)ecap);
+        if (e == cudaSuccess) e = cudaMalloc(&hc.d_dst, sizeof(int32_t) * (size_t)ecap);
+        if (e == cudaSuccess) e = cudaMalloc(&hc.d_w, sizeof(float) * (size_t)ecap);
+        if (e == cudaSuccess) e = cudaMalloc(&hc.d_m, sizeof(int64_t));
+        if (e != cudaSuccess) return status_of(e);
+        hc.cap_edges = ecap;
+    }
+    e = cudaMemcpyAsync(hc.d_points, h_points, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return status_of(e);
+    fsg_tree* t = hc.tree;
+    if (t && t->n == n && t->d == d) {
+        rc = fsg_tree_update(t, hc.d_points, stream);
+        if (rc != FSG_OK) return rc;
+    } else {
+        fsg_free_tree(hc.tree);
+        hc.tree = nullptr;
+        rc = fsg_build_tree(hc.d_points, n, d, nullptr, stream, &t);
+        if (rc != FSG_OK) return rc;
+        hc.tree = t;
+    }
+    rc = fsg_build_graph(t, p, L, seed, edge_mode, hc.d_src, hc.d_dst, hc.d_w, ecap, hc.d_m, nullptr, nullptr,
+                         nullptr, nullptr, stream);
+    int64_t m = 0;
+    if (rc == FSG_OK) {
+        e = cudaMemcpyAsync(&m, hc.d_m, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        rc = status_of(e);
+    }
+    if (rc == FSG_OK) {
+        if (m > cap) m = cap;
+        e = cudaMemcpyAsync(h_src, hc.d_src, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_dst, hc.d_dst, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_w, hc.d_w, sizeof(float) * (size_t)m, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        rc = status_of(e);
+        *h_m_out = m;
+    }
+    if (rc == FSG_OK) rc = fsg_sync(t, stream);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+// Internal declarations of the sm_103a FastSimilarityGraph library.
+// Device helpers shared by the kernels: Philox4x32-10, packed FP32x2
+// arithmetic, ex2, 1-D bulk copies (TMA engine) with mbarriers whose waits are
+// bounded, and the descent decision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fsg.h"
+
+namespace fsg {
+
+constexpr int kMaxL = 64;
+constexpr int kMaxFmaDim = 16;       // FP32 FMA tiles are compiled for d <= 16
+constexpr int kStatusTimeout = FSG_ERR_TIMEOUT;
+// Upper bound on mbarrier polls before a wait gives up (each poll is a
+// try_wait that may itself suspend for a short, hardware-chosen time).
+constexpr uint32_t kMaxPolls = 1u << 24;
+
+// ---------------------------------------------------------------------------
+// Tree and workspace
+// ---------------------------------------------------------------------------
+struct Workspace {
+    size_t bytes = 0;
+    void* base = nullptr;
+    // carve-outs (valid after ensure_workspace)
+    float* binsum = nullptr;        // [n][nb]   bin sums per query (tree order)
+    float* degf = nullptr;          // [n]       FP32 degree per position
+    int32_t* node_bin = nullptr;    // [n][L]    level-s0 bin of each sample
+    uint8_t* flags = nullptr;       // [n][L]    per-sample flags (tree order)
+    int32_t* leaf_pos = nullptr;    // [n][L]    sampled neighbour position or -1
+    float* wsmp = nullptr;          // [n][L]    weight of each sample
+    int32_t* bin_count = nullptr;   // [nb]
+    int32_t* bin_cursor = nullptr;  // [nb]
+    int32_t* bin_off = nullptr;     // [nb+1]
+    int32_t* tile_prefix = nullptr; // [nb+1]
+    int32_t* items_q = nullptr;     // [max_items] query position per item
+    uint64_t* items_mask = nullptr; // [max_items] samples of that query at the bin
+    int32_t* uniq = nullptr;        // [n][L]    per-query sorted distinct neighbours
+    float* uniq_w = nullptr;        // [n][L]
+    int32_t* ucnt = nullptr;        // [n]
+    uint64_t* emit_mask = nullptr;  // [n]
+    int64_t* ecount = nullptr;      // [n+1]     edges per query, scanned in place
+    int64_t* scan_tmp = nullptr;    // [blocks]
+    fsg_stats* stats = nullptr;     // device statistics of the last call
+    int32_t* misc = nullptr;        // [8] n_tiles, ...
+    int64_t cap_n = 0, cap_L = 0;
+};
+
+}  // namespace fsg
+
+struct fsg_tree {
+    int64_t n = 0;
+    int32_t d = 0;
+    int32_t dp = 0;          // padded dimension (multiple of 4)
+    int32_t depth = 0;       // ceil(log2 n)
+    int32_t leaf_max = 256;
+    int32_t s0 = 0;          // levels decided from the bin pass
+    int32_t nb = 1;          // bins = 2^s0
+    int32_t mmax = 1;        // largest bin size = ceil(n / nb)
+    int32_t dm = 0;          // ceil(log2 mmax): levels in the leaf finish
+    int64_t n_pad = 0;       // rows allocated in the point arrays
+    int device = 0;
+    float* Xt = nullptr;     // [n_pad][dp]     tree-ordered points
+    float* Xdup = nullptr;   // [n_pad][dp][2]  same, each coordinate twice (d <= 16)
+    int32_t* perm = nullptr; // [n]  position -> original index
+    int32_t* inv = nullptr;  // [n]  original index -> position
+    int32_t* bnd = nullptr;  // [nb+1] level-s0 node boundaries
+    int32_t* status = nullptr;  // device status word
+    int exact_int = 0;       // points are multiples of 1/255 in [0,1]
+    fsg::Workspace ws;
+    // per-phase timing (fsg_profile) and kernel-launch count
+    bool profiling = false;
+    cudaEvent_t ev_start[FSG_NUM_PHASES] = {};
+    cudaEvent_t ev_end[FSG_NUM_PHASES] = {};
+    bool ev_used[FSG_NUM_PHASES] = {};
+    int64_t launches = 0;
+};
+
+namespace fsg {
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one per .cu file)
+// ---------------------------------------------------------------------------
+struct KernelParams {
+    float neg_c;      // -gamma * log2(e): k = ex2(neg_c * ||x-y||^2)
+    float gamma;
+    int self_exclude;
+    int L;
+    uint64_t seed;
+    float flag_eps;
+};
+
+int ensure_workspace(fsg_tree* t, int L, cudaStream_t s);
+cudaError_t launch_tree_prep(fsg_tree* t, const float* d_points, const int32_t* d_perm, cudaStream_t s);
+cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+bool kde_bins_supported(const fsg_tree* t);
+cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
+                               cudaStream_t s);
+cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
+                         int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
+cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
+                           fsg_stats* d_stats, cudaStream_t s);
+cudaError_t launch_levelwise(const fsg_tree* t, const KernelParams& kp, double* d_deg, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplications whose high halves are xored into the other words and the
+// round key; the key advances by the two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+        const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) { k.x += W0; k.y += W1; }
+    }
+    return c;
+}
+
+// Four consecutive levels (4m .. 4m+3) of one (point, sample) share one block.
+__device__ __forceinline__ uint4 draw_block(uint64_t seed, uint32_t i, uint32_t l, uint32_t level) {
+    return philox4x32_10(make_uint4(i, l, level >> 2, 0u),
+                         make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)));
+}
+__device__ __forceinline__ uint32_t block_word(const uint4& b, uint32_t level) {
+    const uint32_t w = level & 3u;
+    return w == 0 ? b.x : (w == 1 ? b.y : (w == 2 ? b.z : b.w));
+}
+
+// One level of the descent of Algorithm 1: returns 1 for the right half.
+// u is the draw truncated to 24 bits (exact in FP32, at most 2^-24 below the
+// 32-bit value); the comparison is flagged when |u - r| is within the error
+// bound of the FP32 sums, so an unflagged decision equals the exact one.
+__device__ __forceinline__ int descend_decide(float gl, float gr, uint32_t word, float eps, uint8_t& flag) {
+    const float S = gl + gr;
+    if (!(S > 0.f)) { flag |= 2; return 1; }
+    const float r = __fdiv_rn(gl, S);
+    const float u = __uint2float_rz(word >> 8) * 0x1p-24f;
+    const float tau = 2.f * eps * r * (1.f - r) + 0x1p-22f;
+    if (fabsf(u - r) < tau) flag |= 1;
+    return u < r ? 0 : 1;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Packed FP32x2 arithmetic (sm_100+): both lanes rounded to nearest, IEEE.
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t d; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d; asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c)); return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t d; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b)); return d;
+}
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t d; asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi)); return d;
+}
+__device__ __forceinline__ float2 f2_unpack(uint64_t v) {
+    float2 r; asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v)); return r;
+}
+
+// --- mbarrier + 1-D bulk copy (TMA engine) --------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bulk copy of `bytes` (multiple of 16, 16-byte aligned on both sides) from
+// global to this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: returns false (and records FSG_ERR_TIMEOUT) if the phase did
+// not complete within kMaxPolls polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int32_t* status) {
+    for (uint32_t it = 0; it < kMaxPolls; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(status, kStatusTimeout);
+    return false;
+}
+
+__device__ __forceinline__ int ceil_log2_dev(int m) {
+    return m <= 1 ? 0 : 32 - __clz(m - 1);
+}
+
+#endif  // __CUDACC__
+
+inline int ceil_log2_host(int64_t m) {
+    int r = 0;
+    while ((int64_t(1) << r) < m) ++r;
+    return r;
+}
+
+}  // namespace fsg

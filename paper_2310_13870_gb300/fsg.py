@@ -1,0 +1,274 @@
+"""Python binding of libfsg.so (include/fsg.h): argument marshalling only.
+
+Every step of the path runs in the library's sm_103a kernels; this module
+allocates output tensors with PyTorch, passes raw device pointers and the
+current CUDA stream, and turns status codes into exceptions.  There is no
+fallback: if libfsg.so is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfsg.so")
+
+FSG_OK = 0
+FSG_ERR_INVALID_ARG = 1
+FSG_ERR_OOM = 2
+FSG_ERR_CUDA = 3
+FSG_ERR_TIMEOUT = 4
+FSG_ERR_UNSUPPORTED = 5
+FSG_ERR_BUSY = 6
+FSG_ERR_CAPACITY = 7
+
+FSG_TWO_SIGMA_SQ, FSG_SIGMA_SQ = 0, 1
+FSG_SELF_EXCLUDE, FSG_SELF_INCLUDE = 0, 1
+FSG_PREC_AUTO, FSG_PREC_FP32, FSG_PREC_SPLIT_BF16, FSG_PREC_EXACT_INT = 0, 1, 2, 3
+FSG_EDGES_SET, FSG_EDGES_MULTI = 0, 1
+FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE = 0, 1
+
+# Names every build of the library must export (checked by the CPU tests
+# against include/fsg.h).
+EXPORTED = [
+    "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info",
+    "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
+    "fsg_tree_update", "fsg_profile", "fsg_profile_read",
+]
+FSG_NUM_PHASES = 8
+PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "unused"]
+
+
+class FsgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib_or_none().fsg_error_string(status).decode() if _lib_or_none() else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+class fsg_params(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("scale_conv", ctypes.c_int32), ("self_mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flag_eps", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class fsg_tree_opts(ctypes.Structure):
+    _fields_ = [("d_perm", ctypes.c_void_p), ("leaf_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+STATS_FIELDS = ["n_samples", "n_flagged", "n_self", "n_empty", "n_evals", "n_items", "n_edges", "status"]
+
+
+class fsg_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in STATS_FIELDS]
+
+
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def load(path: str = LIB_PATH):
+    """Loads libfsg.so (built by paper_2310_13870_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    lib.fsg_version.restype = ctypes.c_char_p
+    lib.fsg_version.argtypes = []
+    lib.fsg_error_string.restype = ctypes.c_char_p
+    lib.fsg_error_string.argtypes = [ctypes.c_int]
+    lib.fsg_build_tree.argtypes = [P, I64, I32, P, P, ctypes.POINTER(P)]
+    lib.fsg_free_tree.argtypes = [P]
+    lib.fsg_free_tree.restype = None
+    lib.fsg_tree_info.argtypes = [P, P, P, P]
+    lib.fsg_degrees.argtypes = [P, P, P, P]
+    lib.fsg_sample_edges.argtypes = [P, P, I32, U64, P, P, P]
+    lib.fsg_build_graph.argtypes = [P, P, I32, U64, I32, P, P, P, I64, P, P, P, P, P, P]
+    lib.fsg_sync.argtypes = [P, P]
+    lib.fsg_build_graph_host.argtypes = [P, I64, I32, P, I32, U64, I32, P, P, P, I64, P, P]
+    lib.fsg_tree_update.argtypes = [P, P, P]
+    lib.fsg_profile.argtypes = [P, ctypes.c_int]
+    lib.fsg_profile_read.argtypes = [P, P, P]
+    for name in EXPORTED:
+        if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != FSG_OK:
+        raise FsgError(rc, where)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FSG_SELF_EXCLUDE,
+           precision: int = FSG_PREC_AUTO, schedule: int = FSG_SCHED_FUSED, flag_eps: float = 0.0) -> fsg_params:
+    p = fsg_params()
+    p.sigma = float(sigma)
+    p.scale_conv = scale_conv
+    p.self_mode = self_mode
+    p.precision = precision
+    p.schedule = schedule
+    p.flag_eps = float(flag_eps)
+    return p
+
+
+class Tree:
+    """Owns an fsg_tree*; freed on close() or garbage collection."""
+
+    def __init__(self, handle: ctypes.c_void_p, n: int, d: int):
+        self.handle = handle
+        self.n = n
+        self.d = d
+
+    def close(self):
+        if self.handle is not None and _lib is not None:
+            _lib.fsg_free_tree(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def depth(self) -> int:
+        n, d, dep = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().fsg_tree_info(self.handle, ctypes.byref(n), ctypes.byref(d), ctypes.byref(dep)), "fsg_tree_info")
+        return int(dep.value)
+
+
+def fsg_build_tree(points, perm=None, leaf_max: int = 0, stream=None) -> Tree:
+    """points: CUDA float32 [n][d] contiguous; perm: optional CUDA int32 [n]."""
+    import torch
+    lib = load()
+    if not (points.is_cuda and points.dtype == torch.float32 and points.dim() == 2):
+        raise ValueError("points must be a CUDA float32 [n][d] tensor")
+    points = points.contiguous()
+    opts = fsg_tree_opts()
+    opts.d_perm = None if perm is None else perm.contiguous().data_ptr()
+    opts.leaf_max = leaf_max
+    h = ctypes.c_void_p()
+    _check(lib.fsg_build_tree(_dptr(points), points.shape[0], points.shape[1], ctypes.byref(opts),
+                              _stream_ptr(stream), ctypes.byref(h)), "fsg_build_tree")
+    return Tree(h, points.shape[0], points.shape[1])
+
+
+def fsg_tree_update(tree: Tree, points, stream=None):
+    """Refills the tree with new points of the same shape (no allocation)."""
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float32 and tuple(points.shape) == (tree.n, tree.d)):
+        raise ValueError("points must be a CUDA float32 tensor of the tree's shape")
+    points = points.contiguous()
+    _check(load().fsg_tree_update(tree.handle, _dptr(points), _stream_ptr(stream)), "fsg_tree_update")
+
+
+def fsg_profile(tree: Tree, enable: bool = True):
+    _check(load().fsg_profile(tree.handle, int(enable)), "fsg_profile")
+
+
+def fsg_profile_read(tree: Tree):
+    """Returns ({phase: ms} of the last profiled call, total kernel launches)."""
+    ms = (ctypes.c_float * FSG_NUM_PHASES)()
+    launches = ctypes.c_int64()
+    _check(load().fsg_profile_read(tree.handle, ms, ctypes.byref(launches)), "fsg_profile_read")
+    return dict(zip(PHASES, list(ms))), int(launches.value)
+
+
+def fsg_degrees(tree: Tree, p: fsg_params, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(tree.n, dtype=torch.float64, device="cuda")
+    _check(load().fsg_degrees(tree.handle, ctypes.byref(p), _dptr(out), _stream_ptr(stream)), "fsg_degrees")
+    return out
+
+
+def fsg_sample_edges(tree: Tree, p: fsg_params, L: int, seed: int, samples=None, flags=None, stream=None):
+    import torch
+    if samples is None:
+        samples = torch.empty((tree.n, L), dtype=torch.int32, device="cuda")
+    if flags is None:
+        flags = torch.empty((tree.n, L), dtype=torch.uint8, device="cuda")
+    _check(load().fsg_sample_edges(tree.handle, ctypes.byref(p), L, ctypes.c_uint64(seed), _dptr(samples),
+                                   _dptr(flags), _stream_ptr(stream)), "fsg_sample_edges")
+    return samples, flags
+
+
+class GraphBuffers:
+    """Device output buffers of fsg_build_graph, reusable across calls."""
+
+    def __init__(self, n: int, L: int, with_aux: bool = True):
+        import torch
+        cap = n * L
+        self.cap = cap
+        self.src = torch.empty(cap, dtype=torch.int32, device="cuda")
+        self.dst = torch.empty(cap, dtype=torch.int32, device="cuda")
+        self.w = torch.empty(cap, dtype=torch.float32, device="cuda")
+        self.m = torch.zeros(1, dtype=torch.int64, device="cuda")
+        self.stats = torch.zeros(len(STATS_FIELDS), dtype=torch.int64, device="cuda")
+        self.deg = torch.empty(n, dtype=torch.float64, device="cuda") if with_aux else None
+        self.samples = torch.empty((n, L), dtype=torch.int32, device="cuda") if with_aux else None
+        self.flags = torch.empty((n, L), dtype=torch.uint8, device="cuda") if with_aux else None
+
+
+def fsg_build_graph(tree: Tree, p: fsg_params, L: int, seed: int, edge_mode: int = FSG_EDGES_SET,
+                    bufs: Optional[GraphBuffers] = None, stream=None) -> GraphBuffers:
+    if bufs is None:
+        bufs = GraphBuffers(tree.n, L)
+    _check(load().fsg_build_graph(tree.handle, ctypes.byref(p), L, ctypes.c_uint64(seed), edge_mode,
+                                  _dptr(bufs.src), _dptr(bufs.dst), _dptr(bufs.w), bufs.cap, _dptr(bufs.m),
+                                  _dptr(bufs.deg), _dptr(bufs.samples), _dptr(bufs.flags), _dptr(bufs.stats),
+                                  _stream_ptr(stream)), "fsg_build_graph")
+    return bufs
+
+
+def stats_dict(bufs: GraphBuffers) -> dict:
+    v = bufs.stats.cpu().tolist()
+    return dict(zip(STATS_FIELDS, v))
+
+
+def fsg_sync(tree: Tree, stream=None) -> int:
+    rc = load().fsg_sync(tree.handle, _stream_ptr(stream))
+    _check(rc, "fsg_sync")
+    return rc
+
+
+def fsg_build_graph_host(points: np.ndarray, p: fsg_params, L: int, seed: int, edge_mode: int = FSG_EDGES_SET,
+                         out=None, stream=None):
+    """End to end on host arrays: returns (src, dst, w) numpy views of `out`.
+    `out` = (src int32 [cap], dst int32 [cap], w float32 [cap]) host arrays
+    (pinned recommended) with cap >= n*L."""
+    X = np.ascontiguousarray(points, dtype=np.float32)
+    n, d = X.shape
+    if out is None:
+        cap = n * L
+        out = (np.empty(cap, np.int32), np.empty(cap, np.int32), np.empty(cap, np.float32))
+    src, dst, w = out
+    m = ctypes.c_int64()
+    _check(load().fsg_build_graph_host(X.ctypes.data_as(ctypes.c_void_p), n, d, ctypes.byref(p), L,
+                                       ctypes.c_uint64(seed), edge_mode, src.ctypes.data_as(ctypes.c_void_p),
+                                       dst.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                                       src.shape[0], ctypes.byref(m), _stream_ptr(stream)), "fsg_build_graph_host")
+    k = int(m.value)
+    return src[:k], dst[:k], w[:k]

@@ -1,0 +1,79 @@
+"""CPU checks of the C ABI: the library loads, exports every function that
+include/fsg.h declares, and refuses bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2310_13870_gb300 import fsg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "fsg.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fsg_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(fsg.LIB_PATH):
+        import __graft_entry__ as g
+        g.build()
+    return fsg.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("fsg_build_tree", "fsg_degrees", "fsg_sample_edges", "fsg_build_graph"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert sorted(fsg.EXPORTED) == _declared()
+
+
+def test_version_and_error_strings(lib):
+    assert b"sm_103a" in lib.fsg_version()
+    for code in range(0, 8):
+        assert lib.fsg_error_string(code)
+    assert lib.fsg_error_string(fsg.FSG_ERR_CAPACITY) == b"output buffer too small"
+
+
+def test_bad_arguments_are_refused_without_gpu(lib):
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.fsg_build_tree(None, 10, 2, None, None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_build_tree(fake, 0, 2, None, None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_build_tree(fake, 10, 0, None, None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_build_tree(fake, 10, 4097, None, None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    opts = fsg.fsg_tree_opts()
+    opts.leaf_max = 100  # not a power of two
+    assert lib.fsg_build_tree(fake, 10, 2, ctypes.byref(opts), None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_build_tree(fake, 10, 2, None, None, None) == fsg.FSG_ERR_INVALID_ARG
+    p = fsg.params(0.1)
+    assert lib.fsg_degrees(None, ctypes.byref(p), fake, None) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_sample_edges(None, ctypes.byref(p), 8, 0, fake, None, None) == fsg.FSG_ERR_INVALID_ARG
+    m = ctypes.c_int64()
+    buf = (ctypes.c_float * 8)()
+    for bad in (fsg.params(0.0), fsg.params(float("nan")), fsg.params(-1.0), fsg.params(0.1, self_mode=3),
+                fsg.params(0.1, scale_conv=7), fsg.params(0.1, precision=9), fsg.params(0.1, flag_eps=-1.0)):
+        rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(bad), 2, 0, 0, buf, buf, buf, 8, ctypes.byref(m), None)
+        assert rc == fsg.FSG_ERR_INVALID_ARG
+    # capacity below n*L is refused
+    rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(p), 4, 0, 0, buf, buf, buf, 8, ctypes.byref(m), None)
+    assert rc == fsg.FSG_ERR_CAPACITY
+    # L outside 1..64
+    rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(p), 65, 0, 0, buf, buf, buf, 1000, ctypes.byref(m), None)
+    assert rc == fsg.FSG_ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(fsg.fsg_params) == 48
+    assert ctypes.sizeof(fsg.fsg_tree_opts) == 32
+    assert ctypes.sizeof(fsg.fsg_stats) == 64
