@@ -56,6 +56,12 @@ def make_points(rank: int = 0):
     return inputs.gaussian_mixture(n=WORKLOAD["n"], d=WORKLOAD["d"], seed=WORKLOAD["seed"] + rank)
 
 
+def set_size(n: int):
+    """Smaller instance of the same workload (used for profiler captures)."""
+    WORKLOAD["n"] = n
+    WORKLOAD["workload"] = WORKLOAD["workload"].replace("n=100000", f"n={n}")
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -297,7 +303,10 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="smaller point count (profiler captures only)")
     args = ap.parse_args()
+    if args.n:
+        set_size(args.n)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
