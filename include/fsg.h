@@ -78,8 +78,8 @@ typedef struct {
      * permutation), or NULL for the identity order.  Copied at build time. */
     const int32_t* d_perm;
     /* Largest node handled by the leaf-finish kernel (power of two in
-     * [64, 1024]); 0 selects 256.  Smaller values run more levels through the
-     * bin pass. */
+     * [64, 1024]); 0 selects 128 (raised automatically for very large n).
+     * Smaller values run more levels through the bin pass. */
     int32_t leaf_max;
     int32_t reserved[5];
 } fsg_tree_opts;
@@ -118,7 +118,7 @@ const char* fsg_error_string(int status);
  * recursively into a left half of floor(|X|/2) points and a right half).
  *   d_points : device float32 [n][d] row-major, read only during this call.
  *   n        : 1 <= n <= 2^31 - 1;  d : 1 <= d <= 4096.
- *   opts     : may be NULL (identity order, leaf_max 256).
+ *   opts     : may be NULL (identity order, automatic leaf_max).
  * Writes *out.  The tree holds a tree-ordered, padded copy of the points and
  * grows a workspace on first use; fsg_free_tree releases both.
  * Errors: INVALID_ARG, OOM, CUDA.
@@ -193,7 +193,7 @@ int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_
 #define FSG_PHASE_TREE 0        /* tree build / update                         */
 #define FSG_PHASE_KDE_BINS 1    /* bin pass: every query against every point   */
 #define FSG_PHASE_DESCEND_TOP 2 /* degrees and the top s0 levels               */
-#define FSG_PHASE_BUCKET 3      /* grouping of (query, node) items per node    */
+#define FSG_PHASE_BUCKET 3      /* reserved (items are grouped in descend_top) */
 #define FSG_PHASE_LEAF 4        /* leaf finish: remaining levels and weights   */
 #define FSG_PHASE_EDGES 5       /* edge list                                   */
 #define FSG_PHASE_OUTPUTS 6     /* per-sample outputs and statistics           */

@@ -5,9 +5,9 @@
 //                 shared memory); the root is the degree g_[1,n] (Algorithm 2).
 //                 Each sample then takes its first s0 decisions, comparing the
 //                 Philox draw with g_left/(g_left+g_right) at every level.
-//  bucket       : the distinct (query, bin) pairs reached are counted per bin,
-//                 scanned, and scattered into per-bin item lists, each item
-//                 carrying the 64-bit mask of the query's samples at that bin.
+//                 The distinct (query, bin) pairs reached go straight into
+//                 per-bin item lists (bin-major, capacity n per bin), each
+//                 item carrying the 64-bit mask of the query's samples there.
 //  leaf_finish  : per (bin, batch of items): the kernel value of every (query,
 //                 point) pair of the bin, the query's segment tree over the
 //                 bin's sub-nodes, and the remaining decisions of every
@@ -20,33 +20,22 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Group the warp's (up to 64) samples by bin: returns the mask of samples at
-// the same bin as sample `lane` (Ma) and as sample `lane + 32` (Mb).
-__device__ __forceinline__ void sample_groups(int a, int b, int lane, uint64_t& Ma, uint64_t& Mb) {
-    const uint32_t ma = __match_any_sync(kFull, a);
-    const uint32_t mb = __match_any_sync(kFull, b);
-    uint32_t xa = 0, xb = 0;
-#pragma unroll 4
-    for (int m = 0; m < 32; ++m) {
-        const int bm = __shfl_sync(kFull, b, m);
-        const int am = __shfl_sync(kFull, a, m);
-        if (bm == a) xa |= 1u << m;
-        if (am == b) xb |= 1u << m;
-    }
-    Ma = (uint64_t)ma | ((uint64_t)xa << 32);
-    Mb = (uint64_t)xb | ((uint64_t)mb << 32);
-    (void)lane;
-}
-
-__global__ void __launch_bounds__(128)
+// Per query (one warp): segment tree of the query's node sums over levels
+// 0..s0 built from its bin sums, the degree (the root), the first s0
+// decisions of each of the query's L samples, and the compact list of the
+// distinct bins its samples reached with the mask of samples at each.
+__global__ void __launch_bounds__(256)
 descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, const int32_t* __restrict__ perm,
                    KernelParams kp, int with_samples, double* __restrict__ d_deg, float* __restrict__ degf,
-                   int32_t* __restrict__ node_bin, uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos,
-                   float* __restrict__ wsmp, int32_t* __restrict__ bin_count) {
-    extern __shared__ float tree_s[];
+                   uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos, float* __restrict__ wsmp,
+                   int32_t* __restrict__ bin_count, int32_t* __restrict__ items_q,
+                   uint64_t* __restrict__ items_mask) {
+    extern __shared__ __align__(16) unsigned char smem_b[];
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* tree = tree_s + (size_t)w * 2 * nb;
+    int32_t* sbin = reinterpret_cast<int32_t*>(smem_b) + (size_t)w * 64;             // [64] per warp
+    float* tree = reinterpret_cast<float*>(reinterpret_cast<int32_t*>(smem_b) + (size_t)warps * 64) +
+                  (size_t)w * 2 * nb;                                                 // [2 nb] per warp
     const int L = kp.L;
     for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
         const float* row = binsum + (size_t)q * nb;
@@ -63,15 +52,13 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
             if (d_deg) d_deg[i] = (double)root;
         }
         if (with_samples) {
-            int binv[2];
+            int binv[2] = {-1, -1};
+            if (root > 0.f) {
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int l = lane + 32 * r;
-                binv[r] = -1;
-                if (l < L) {
-                    uint8_t f = 0;
-                    int bin = -1;
-                    if (root > 0.f) {
+                for (int r = 0; r < 2; ++r) {
+                    const int l = lane + 32 * r;
+                    if (l < L) {
+                        uint8_t f = 0;
                         int h = 1;
                         uint4 blk = make_uint4(0, 0, 0, 0);
                         for (int t = 0; t < s0; ++t) {
@@ -79,106 +66,75 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                             h = 2 * h + descend_decide(tree[2 * h], tree[2 * h + 1], block_word(blk, (uint32_t)t),
                                                        kp.flag_eps, f);
                         }
-                        bin = h - nb;
-                    } else {
-                        // zero FP32 mass: no sample; flag unless no other point exists
-                        if (n > 1 || !kp.self_exclude) f |= 2;
-                        leaf_pos[(size_t)q * L + l] = -1;
-                        wsmp[(size_t)q * L + l] = 0.f;
+                        binv[r] = h - nb;
+                        flags[(size_t)q * L + l] = f;
                     }
-                    node_bin[(size_t)q * L + l] = bin;
+                    sbin[l] = binv[r];
+                }
+                __syncwarp();
+                // Group the samples by bin: sample l's mask holds every sample at its bin.
+                uint64_t M[2] = {0ull, 0ull};
+                for (int e = 0; e < 64; e += 4) {
+                    const int4 v = *reinterpret_cast<const int4*>(sbin + e);
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        M[r] |= (uint64_t)(v.x == binv[r]) << e;
+                        M[r] |= (uint64_t)(v.y == binv[r]) << (e + 1);
+                        M[r] |= (uint64_t)(v.z == binv[r]) << (e + 2);
+                        M[r] |= (uint64_t)(v.w == binv[r]) << (e + 3);
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int l = lane + 32 * r;
+                    // the lowest sample of each bin writes the (query, mask) item
+                    if (binv[r] >= 0 && (M[r] & ((1ull << l) - 1ull)) == 0ull) {
+                        const int b = binv[r];
+                        const int slot = atomicAdd(&bin_count[b], 1);
+                        items_q[(size_t)b * n + slot] = q;
+                        items_mask[(size_t)b * n + slot] = M[r];
+                    }
+                }
+            } else {
+                // zero FP32 mass: no sample; flag unless no other point exists
+                const uint8_t f = (n > 1 || !kp.self_exclude) ? 2 : 0;
+                for (int l = lane; l < L; l += 32) {
+                    leaf_pos[(size_t)q * L + l] = -1;
+                    wsmp[(size_t)q * L + l] = 0.f;
                     flags[(size_t)q * L + l] = f;
-                    binv[r] = bin;
                 }
             }
-            uint64_t Ma, Mb;
-            sample_groups(binv[0], binv[1], lane, Ma, Mb);
-            if (binv[0] >= 0 && (Ma & ((1ull << lane) - 1ull)) == 0ull) atomicAdd(&bin_count[binv[0]], 1);
-            if (binv[1] >= 0 && (Mb & ((1ull << (lane + 32)) - 1ull)) == 0ull) atomicAdd(&bin_count[binv[1]], 1);
         }
         __syncwarp();
     }
 }
 
-// Exclusive scan of the per-bin item counts (single CTA), tile counts per bin.
-__global__ void __launch_bounds__(1024)
-scan_bins_kernel(const int32_t* __restrict__ bin_count, int nb, int qt, int32_t* __restrict__ bin_off,
-                 int32_t* __restrict__ tile_prefix, int32_t* __restrict__ misc, fsg_stats* __restrict__ stats) {
-    __shared__ int32_t s_items[1024], s_tiles[1024];
-    const int tid = threadIdx.x;
-    const int per = (nb + 1023) / 1024;
-    int ci = 0, ct = 0;
-    for (int u = 0; u < per; ++u) {
-        const int b = tid * per + u;
-        if (b < nb) { ci += bin_count[b]; ct += (bin_count[b] + qt - 1) / qt; }
-    }
-    s_items[tid] = ci;
-    s_tiles[tid] = ct;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int vi = tid >= off ? s_items[tid - off] : 0;
-        const int vt = tid >= off ? s_tiles[tid - off] : 0;
-        __syncthreads();
-        s_items[tid] += vi;
-        s_tiles[tid] += vt;
-        __syncthreads();
-    }
-    int ri = s_items[tid] - ci, rt = s_tiles[tid] - ct;  // exclusive prefix of this thread's range
-    for (int u = 0; u < per; ++u) {
-        const int b = tid * per + u;
-        if (b < nb) {
-            bin_off[b] = ri;
-            tile_prefix[b] = rt;
-            ri += bin_count[b];
-            rt += (bin_count[b] + qt - 1) / qt;
-        }
-    }
-    if (tid == 1023) {
-        bin_off[nb] = s_items[1023];
-        tile_prefix[nb] = s_tiles[1023];
-        misc[0] = s_tiles[1023];
-        stats->n_items = s_items[1023];
-    }
-}
-
-__global__ void __launch_bounds__(128)
-scatter_items_kernel(const int32_t* __restrict__ node_bin, int n, int L, const int32_t* __restrict__ bin_off,
-                     int32_t* __restrict__ bin_cursor, int32_t* __restrict__ items_q,
-                     uint64_t* __restrict__ items_mask) {
-    const int warps = blockDim.x >> 5;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
-        const int a = lane < L ? node_bin[(size_t)q * L + lane] : -1;
-        const int b = lane + 32 < L ? node_bin[(size_t)q * L + lane + 32] : -1;
-        uint64_t Ma, Mb;
-        sample_groups(a, b, lane, Ma, Mb);
-        if (a >= 0 && (Ma & ((1ull << lane) - 1ull)) == 0ull) {
-            const int slot = bin_off[a] + atomicAdd(&bin_cursor[a], 1);
-            items_q[slot] = q;
-            items_mask[slot] = Ma;
-        }
-        if (b >= 0 && (Mb & ((1ull << (lane + 32)) - 1ull)) == 0ull) {
-            const int slot = bin_off[b] + atomicAdd(&bin_cursor[b], 1);
-            items_q[slot] = q;
-            items_mask[slot] = Mb;
-        }
-    }
-}
-
 constexpr int kThreadsC = 256;
 
-template <int D, int PPT>
+// Leaf finish: CTA (b, y) handles chunks y, y + gridDim.y, ... of bin b's
+// item list, qt items per chunk.  Thread t owns leaf slots t, t + 256, ... of
+// the bin's perfect binary tree (slot = the path bits of the halving descent;
+// slots of empty nodes hold 0) -- or, when the tree has fewer than 256
+// leaves, slot t mod 2^dm for every G-th query.  Each chunk: kernel value of
+// every (query, slot), per-query trees summed upwards in shared memory, then
+// one thread per (query, sample) takes the remaining decisions and forms the
+// weight w = k / p_hat of Eq. 2.
+template <int D, int SPT>
 __global__ void __launch_bounds__(kThreadsC)
 leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
-                   int nb, int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ bin_count,
-                   const int32_t* __restrict__ tile_prefix, const int32_t* __restrict__ misc,
-                   const int32_t* __restrict__ items_q, const uint64_t* __restrict__ items_mask,
-                   const float* __restrict__ degf, KernelParams kp, int qt, int dm_max,
-                   int32_t* __restrict__ leaf_pos, float* __restrict__ wsmp, uint8_t* __restrict__ flags,
-                   unsigned long long* __restrict__ n_evals) {
+                   int n, int s0, const int32_t* __restrict__ bin_count, const int32_t* __restrict__ items_q,
+                   const uint64_t* __restrict__ items_mask, const float* __restrict__ degf, KernelParams kp, int qt,
+                   int dm_max, int32_t* __restrict__ leaf_pos, float* __restrict__ wsmp, uint8_t* __restrict__ flags,
+                   unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items) {
     constexpr int DP = (D + 3) & ~3;
+    const int b = blockIdx.x;
+    const int cnt = bin_count[b];
+    const int nchunks = (cnt + qt - 1) / qt;
+    if ((int)blockIdx.y >= nchunks) return;
+
     extern __shared__ __align__(16) unsigned char smem_c[];
-    const int vs = 2 << dm_max;  // row stride of the per-query segment trees
+    const int vs = 2 << dm_max;  // row stride of the per-query trees
     float* V = reinterpret_cast<float*>(smem_c);
     float* qs = V + (size_t)qt * vs;
     uint64_t* qmask = reinterpret_cast<uint64_t*>(qs + (size_t)qt * DP);
@@ -189,88 +145,74 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
     int32_t* list = loff + qt + 1;                            // qt * 64
 
     const int tid = threadIdx.x;
-    const int ntiles = misc[0];
     const int L = kp.L;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int lo = 0, hi = nb;  // largest b with tile_prefix[b] <= tile
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (tile_prefix[mid] <= tile) lo = mid; else hi = mid;
+    const int p_lo = bnd[b];
+    const int m = bnd[b + 1] - p_lo;
+    const int dm = ceil_log2_dev(m);
+    const int leaf0 = 1 << dm;
+    const int G = leaf0 >= kThreadsC ? 1 : kThreadsC / leaf0;
+    const int g = leaf0 >= kThreadsC ? 0 : tid / leaf0;
+    const int s_first = leaf0 >= kThreadsC ? tid : tid % leaf0;
+    // This thread's slots: point coordinates kept in registers for every chunk.
+    float pc[SPT][D];
+    int ppos[SPT];
+#pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+        const int sl = s_first + u * kThreadsC;
+        ppos[u] = -1;
+        if (sl < leaf0) {
+            int a = 0, c = m;  // walk the slot's path bits from the root
+            for (int t = dm - 1; t >= 0; --t) {
+                const int mid = a + (c - a) / 2;
+                if ((sl >> t) & 1) a = mid; else c = mid;
+            }
+            if (c - a == 1) ppos[u] = p_lo + a;
         }
-        const int b = lo;
-        const int j0 = (tile - tile_prefix[b]) * qt;
-        const int qcnt = min(qt, bin_count[b] - j0);
-        const int it0 = bin_off[b] + j0;
-        const int p_lo = bnd[b];
-        const int m = bnd[b + 1] - p_lo;
-        const int dm = ceil_log2_dev(m);
-        const int leaf0 = 1 << dm;
-
+#pragma unroll
+        for (int t = 0; t < D; ++t) pc[u][t] = ppos[u] >= 0 ? Xt[(size_t)ppos[u] * DP + t] : 0.f;
+    }
+    const size_t base = (size_t)b * n;
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        const int it0 = chunk * qt;
+        const int qcnt = min(qt, cnt - it0);
         for (int e = tid; e < qcnt; e += kThreadsC) {
-            const int q = items_q[it0 + e];
+            const int q = items_q[base + it0 + e];
             qpos[e] = q;
             qidx[e] = perm[q];
-            qmask[e] = items_mask[it0 + e];
+            qmask[e] = items_mask[base + it0 + e];
             qdeg[e] = degf[q];
         }
         for (int e = tid; e < qcnt * DP; e += kThreadsC) {
             const int qq = e / DP;
-            qs[e] = Xt[(size_t)items_q[it0 + qq] * DP + (e - qq * DP)];
-        }
-        for (int e = tid; e < qcnt * leaf0; e += kThreadsC) {
-            const int qq = e >> dm;
-            V[(size_t)qq * vs + leaf0 + (e & (leaf0 - 1))] = 0.f;
-        }
-        // This thread's points and their leaf slots (path bits, 1 = right half).
-        float pc[PPT][D];
-        int slot[PPT];
-#pragma unroll
-        for (int u = 0; u < PPT; ++u) {
-            const int p = tid + u * kThreadsC;
-            slot[u] = -1;
-            if (p < m) {
-#pragma unroll
-                for (int t = 0; t < D; ++t) pc[u][t] = Xt[(size_t)(p_lo + p) * DP + t];
-                int a = 0, c = m, sl = 0;
-                for (int t = 0; t < dm; ++t) {
-                    const int mid = a + (c - a) / 2;
-                    const int right = p >= mid ? 1 : 0;
-                    if (right) a = mid; else c = mid;
-                    sl = 2 * sl + right;
-                }
-                slot[u] = sl;
-            } else {
-#pragma unroll
-                for (int t = 0; t < D; ++t) pc[u][t] = 0.f;
-            }
+            qs[e] = Xt[(size_t)items_q[base + it0 + qq] * DP + (e - qq * DP)];
         }
         __syncthreads();
-        // Kernel values of every (query, point) pair of the tile.
-        for (int qq = 0; qq < qcnt; ++qq) {
-            float qc[D];
 #pragma unroll
-            for (int t = 0; t < D; ++t) qc[t] = qs[qq * DP + t];
-            const int qp = qpos[qq];
+        for (int u = 0; u < SPT; ++u) {
+            const int sl = s_first + u * kThreadsC;
+            if (sl < leaf0) {
+                for (int qq = g; qq < qcnt; qq += G) {
+                    float k = 0.f;
+                    if (ppos[u] >= 0) {
+                        const float* qc = qs + qq * DP;
+                        float dd = qc[0] - pc[u][0];
+                        float acc = dd * dd;
 #pragma unroll
-            for (int u = 0; u < PPT; ++u) {
-                if (slot[u] >= 0) {
-                    float dd = qc[0] - pc[u][0];
-                    float s = dd * dd;
-#pragma unroll
-                    for (int t = 1; t < D; ++t) {
-                        dd = qc[t] - pc[u][t];
-                        s = fmaf(dd, dd, s);
+                        for (int t = 1; t < D; ++t) {
+                            dd = qc[t] - pc[u][t];
+                            acc = fmaf(dd, dd, acc);
+                        }
+                        k = ex2_approx(acc * kp.neg_c);
+                        if (kp.self_exclude && ppos[u] == qpos[qq]) k = 0.f;
                     }
-                    float k = ex2_approx(s * kp.neg_c);
-                    if (kp.self_exclude && p_lo + tid + u * kThreadsC == qp) k = 0.f;
-                    V[(size_t)qq * vs + leaf0 + slot[u]] = k;
+                    V[(size_t)qq * vs + leaf0 + sl] = k;
                 }
             }
         }
         __syncthreads();
         for (int lev = dm - 1; lev >= 0; --lev) {
-            const int cnt = qcnt << lev;
-            for (int e = tid; e < cnt; e += kThreadsC) {
+            const int cn = qcnt << lev;
+            for (int e = tid; e < cn; e += kThreadsC) {
                 const int qq = e >> lev;
                 const int h = (1 << lev) + (e & ((1 << lev) - 1));
                 float* row = V + (size_t)qq * vs;
@@ -278,11 +220,22 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
             }
             __syncthreads();
         }
-        // List of (query, sample) pairs of this tile.
-        if (tid == 0) {
-            int acc = 0;
-            for (int qq = 0; qq < qcnt; ++qq) { loff[qq] = acc; acc += __popcll(qmask[qq]); }
-            loff[qcnt] = acc;
+        // List of (query, sample) pairs of this chunk (warp 0: popcount prefix).
+        if (tid < 32) {
+            int c0 = 0, c1 = 0;
+            if (tid < qcnt) c0 = __popcll(qmask[tid]);
+            if (tid + 32 < qcnt) c1 = __popcll(qmask[tid + 32]);
+            int s0v = c0, s1v = c1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y0 = __shfl_up_sync(0xffffffffu, s0v, o);
+                const int y1 = __shfl_up_sync(0xffffffffu, s1v, o);
+                if (tid >= o) { s0v += y0; s1v += y1; }
+            }
+            const int tot0 = __shfl_sync(0xffffffffu, s0v, 31);
+            if (tid < qcnt) loff[tid] = s0v - c0;
+            if (tid + 32 < qcnt) loff[tid + 32] = tot0 + s1v - c1;
+            if (tid == 31) loff[qcnt] = tot0 + s1v;
         }
         __syncthreads();
         for (int e = tid; e < qcnt * 64; e += kThreadsC) {
@@ -326,45 +279,55 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
             wsmp[o] = k > 0.f ? __fdiv_rn(k, ph) : 0.f;
             flags[o] |= f;
         }
-        if (tid == 0) atomicAdd(n_evals, (unsigned long long)qcnt * (unsigned long long)m);
+        if (tid == 0) {
+            atomicAdd(n_evals, (unsigned long long)qcnt * (unsigned long long)m);
+            atomicAdd(n_items, (unsigned long long)qcnt);
+        }
         __syncthreads();
     }
 }
 
-template <int D>
-cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qt, cudaStream_t s) {
+template <int D, int SPT>
+cudaError_t launch_leaf_ds(const fsg_tree* t, const KernelParams& kp, int qt, cudaStream_t s) {
     constexpr int DP = (D + 3) & ~3;
     const int vs = 2 << t->dm;
     const size_t smem = (size_t)qt * vs * 4 + (size_t)qt * DP * 4 + (size_t)qt * 8 + (size_t)qt * 12 +
                         (size_t)(qt + 1) * 4 + (size_t)qt * 64 * 4;
-    const int ppt = (t->mmax + kThreadsC - 1) / kThreadsC;
-    int64_t max_items = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
-    int64_t tiles_ub = (max_items + qt - 1) / qt + t->nb;
-    int grid = 152 * 3;
-    if (tiles_ub < grid) grid = (int)tiles_ub;
-    if (grid < 1) grid = 1;
-    auto* ws = &t->ws;
-#define FSG_LEAF_LAUNCH(PPT)                                                                                      \
-    {                                                                                                             \
-        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D, PPT>,                                          \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);            \
-        if (e != cudaSuccess) return e;                                                                           \
-        leaf_finish_kernel<D, PPT><<<grid, kThreadsC, smem, s>>>(                                                 \
-            t->Xt, t->perm, t->bnd, t->nb, t->s0, ws->bin_off, ws->bin_count, ws->tile_prefix, ws->misc,           \
-            ws->items_q, ws->items_mask, ws->degf, kp, qt, t->dm, ws->leaf_pos, ws->wsmp, ws->flags,               \
-            reinterpret_cast<unsigned long long*>(&ws->stats->n_evals));                                          \
-        return cudaGetLastError();                                                                                \
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D, SPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
-    if (ppt <= 1) FSG_LEAF_LAUNCH(1)
-    if (ppt <= 2) FSG_LEAF_LAUNCH(2)
-    FSG_LEAF_LAUNCH(4)
-#undef FSG_LEAF_LAUNCH
+    // Splits per bin: about 8 waves of CTAs over the expected items.
+    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
+    const int64_t chunks_per_bin = (items_est / t->nb + qt - 1) / qt + 1;
+    int64_t S = (152 * 4 * 8 + t->nb - 1) / t->nb;
+    if (S > chunks_per_bin) S = chunks_per_bin;
+    if (S < 1) S = 1;
+    if (S > 65535) S = 65535;
+    dim3 grid(t->nb, (unsigned)S);
+    const auto& ws = t->ws;
+    leaf_finish_kernel<D, SPT><<<grid, kThreadsC, smem, s>>>(
+        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_count, ws.items_q, ws.items_mask, ws.degf, kp, qt, t->dm,
+        ws.leaf_pos, ws.wsmp, ws.flags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+        reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qt, cudaStream_t s) {
+    const int leaf0 = 1 << t->dm;
+    if (leaf0 <= kThreadsC) return launch_leaf_ds<D, 1>(t, kp, qt, s);
+    if (leaf0 <= 2 * kThreadsC) return launch_leaf_ds<D, 2>(t, kp, qt, s);
+    return launch_leaf_ds<D, 4>(t, kp, qt, s);
 }
 
 }  // namespace
 
 int leaf_queries_per_tile(const fsg_tree* t) {
-    int qt = 16384 / (2 << t->dm);
+    int qt = 8192 / (2 << t->dm);  // 32 KB of per-query trees
     if (qt > 64) qt = 64;
     if (qt < 4) qt = 4;
     return qt;
@@ -372,31 +335,22 @@ int leaf_queries_per_tile(const fsg_tree* t) {
 
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
                                cudaStream_t s) {
-    int warps = 4;
-    while (warps > 1 && (size_t)warps * 2 * t->nb * 4 > 64 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * 2 * t->nb * 4;
-    cudaError_t e = cudaFuncSetAttribute(descend_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
-    if (e != cudaSuccess) return e;
+    int warps = 8;
+    while (warps > 1 && (size_t)warps * (256 + 8 * t->nb) > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * (256 + 8 * t->nb);  // per warp: 64 sample bins + 2 nb tree nodes
+    static size_t attr = 0;
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(descend_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
     int64_t blocks = (t->n + warps - 1) / warps;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > 152 * 16) blocks = 152 * 16;
     const auto& ws = t->ws;
     descend_top_kernel<<<(int)blocks, warps * 32, smem, s>>>(ws.binsum, (int)t->n, t->nb, t->s0, t->perm, kp,
-                                                            with_samples, d_deg, ws.degf, ws.node_bin, ws.flags,
-                                                            ws.leaf_pos, ws.wsmp, ws.bin_count);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    const auto& ws = t->ws;
-    const int qt = leaf_queries_per_tile(t);
-    scan_bins_kernel<<<1, 1024, 0, s>>>(ws.bin_count, t->nb, qt, ws.bin_off, ws.tile_prefix, ws.misc, ws.stats);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int64_t blocks = (t->n + 3) / 4;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    scatter_items_kernel<<<(int)blocks, 128, 0, s>>>(ws.node_bin, (int)t->n, kp.L, ws.bin_off, ws.bin_cursor,
-                                                     ws.items_q, ws.items_mask);
+                                                            with_samples, d_deg, ws.degf, ws.flags, ws.leaf_pos,
+                                                            ws.wsmp, ws.bin_count, ws.items_q, ws.items_mask);
     return cudaGetLastError();
 }
 

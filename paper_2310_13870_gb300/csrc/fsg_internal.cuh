@@ -27,16 +27,12 @@ struct Workspace {
     // carve-outs (valid after ensure_workspace)
     float* binsum = nullptr;        // [n][nb]   bin sums per query (tree order)
     float* degf = nullptr;          // [n]       FP32 degree per position
-    int32_t* node_bin = nullptr;    // [n][L]    level-s0 bin of each sample
     uint8_t* flags = nullptr;       // [n][L]    per-sample flags (tree order)
     int32_t* leaf_pos = nullptr;    // [n][L]    sampled neighbour position or -1
     float* wsmp = nullptr;          // [n][L]    weight of each sample
-    int32_t* bin_count = nullptr;   // [nb]
-    int32_t* bin_cursor = nullptr;  // [nb]
-    int32_t* bin_off = nullptr;     // [nb+1]
-    int32_t* tile_prefix = nullptr; // [nb+1]
-    int32_t* items_q = nullptr;     // [max_items] query position per item
-    uint64_t* items_mask = nullptr; // [max_items] samples of that query at the bin
+    int32_t* bin_count = nullptr;   // [nb]       items per bin
+    int32_t* items_q = nullptr;     // [nb][n]    per-bin lists: query position
+    uint64_t* items_mask = nullptr; // [nb][n]    per-bin lists: samples of that query there
     int32_t* uniq = nullptr;        // [n][L]    per-query sorted distinct neighbours
     float* uniq_w = nullptr;        // [n][L]
     int32_t* ucnt = nullptr;        // [n]
@@ -98,7 +94,6 @@ cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStrea
 bool kde_bins_supported(const fsg_tree* t);
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
                                cudaStream_t s);
-cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
                          int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
@@ -138,17 +133,21 @@ __device__ __forceinline__ uint32_t block_word(const uint4& b, uint32_t level) {
 }
 
 // One level of the descent of Algorithm 1: returns 1 for the right half.
-// u is the draw truncated to 24 bits (exact in FP32, at most 2^-24 below the
-// 32-bit value); the comparison is flagged when |u - r| is within the error
-// bound of the FP32 sums, so an unflagged decision equals the exact one.
+// The exact rule is "left iff u < g_left / (g_left + g_right)", i.e.
+// u * S - g_left < 0 with S = g_left + g_right, evaluated here with one fused
+// multiply-add.  u is the draw truncated to 24 bits (exact in FP32, at most
+// 2^-24 below the 32-bit value).  The decision is flagged when
+// |u S - g_left| < 2 eps min(g_left, g_right) + 2^-22 S: with both sums
+// within relative error eps of the exact ones, an unflagged decision equals
+// the exact one (min(r, 1-r) >= r (1-r) bounds the ratio's error).
 __device__ __forceinline__ int descend_decide(float gl, float gr, uint32_t word, float eps, uint8_t& flag) {
     const float S = gl + gr;
     if (!(S > 0.f)) { flag |= 2; return 1; }
-    const float r = __fdiv_rn(gl, S);
     const float u = __uint2float_rz(word >> 8) * 0x1p-24f;
-    const float tau = 2.f * eps * r * (1.f - r) + 0x1p-22f;
-    if (fabsf(u - r) < tau) flag |= 1;
-    return u < r ? 0 : 1;
+    const float dlt = fmaf(u, S, -gl);
+    const float tol = 2.f * eps * fminf(gl, gr) + 0x1p-22f * S;
+    if (fabsf(dlt) < tol) flag |= 1;
+    return dlt < 0.f ? 0 : 1;
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
