@@ -41,6 +41,7 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     KernelParams kp;
     kp.gamma = (float)gamma;
     kp.neg_c = (float)(-gamma * kLog2e);
+    if (kp.neg_c > -1e-30f) kp.neg_c = -1e-30f;  // keeps far-away padding at exactly 0
     kp.self_exclude = p->self_mode == FSG_SELF_EXCLUDE ? 1 : 0;
     kp.L = L;
     kp.seed = seed;
@@ -68,6 +69,12 @@ void begin_call(fsg_tree* t) {
     for (int k = 0; k < FSG_NUM_PHASES; ++k) t->ev_used[k] = false;
 }
 
+// Bin pass: the symmetric kernel (each pair once) when bins hold <= 128 points.
+cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (kde_bins_sym_supported(t)) return launch_kde_bins_sym(t, kp, s);
+    return launch_kde_bins(t, kp, s);
+}
+
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 || p->precision == FSG_PREC_EXACT_INT) return FSG_ERR_UNSUPPORTED;
     if (!kde_bins_supported(t)) return FSG_ERR_UNSUPPORTED;
@@ -92,7 +99,8 @@ int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
         {(void**)&ws.degf, sizeof(float) * (size_t)n},
         {(void**)&ws.flags, sizeof(uint8_t) * (size_t)n * Lc},
         {(void**)&ws.leaf_pos, sizeof(int32_t) * (size_t)n * Lc},
-        {(void**)&ws.wsmp, sizeof(float) * (size_t)n * Lc},
+        {(void**)&ws.ksmp, sizeof(float) * (size_t)n * Lc},
+        {(void**)&ws.lflags, sizeof(uint8_t) * (size_t)n * Lc},
         {(void**)&ws.bin_count, sizeof(int32_t) * (size_t)nb},
         {(void**)&ws.items_q, sizeof(int32_t) * (size_t)list_cap},
         {(void**)&ws.items_mask, sizeof(uint64_t) * (size_t)list_cap},
@@ -168,7 +176,7 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
     };
     int s0 = 0;
     pick(leaf_max, s0);
-    while (auto_leaf && s0 > 10 && leaf_max < 1024) { leaf_max *= 2; pick(leaf_max, s0); }
+    while (auto_leaf && s0 > 11 && leaf_max < 1024) { leaf_max *= 2; pick(leaf_max, s0); }
     if (s0 > 12) return FSG_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     fsg_tree* t = new (std::nothrow) fsg_tree();
@@ -283,7 +291,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
-        e = launch_kde_bins(t, kp, s);
+        e = run_kde_bins(t, kp, s);
         t->launches += 1;
     }
     if (e == cudaSuccess) {
@@ -320,7 +328,7 @@ int fsg_degrees(fsg_tree* t, const fsg_params* p, double* d_deg, void* stream) {
     cudaError_t e;
     {
         PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
-        e = launch_kde_bins(t, kp, s);
+        e = run_kde_bins(t, kp, s);
     }
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_DESCEND_TOP, s);

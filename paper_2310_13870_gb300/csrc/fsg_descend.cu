@@ -11,14 +11,12 @@
 //  leaf_finish  : per (bin, batch of items): the kernel value of every (query,
 //                 point) pair of the bin, the query's segment tree over the
 //                 bin's sub-nodes, and the remaining decisions of every
-//                 sample down to a single point; the sample's weight
-//                 w = k / p_hat of Eq. 2 is formed from that point's value.
+//                 sample down to a single point, whose kernel value is kept
+//                 for the weight of Eq. 2 (formed by the edge kernels).
 #include "fsg_internal.cuh"
 
 namespace fsg {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // Per query (one warp): segment tree of the query's node sums over levels
 // 0..s0 built from its bin sums, the degree (the root), the first s0
@@ -27,7 +25,7 @@ constexpr unsigned kFull = 0xffffffffu;
 __global__ void __launch_bounds__(256)
 descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, const int32_t* __restrict__ perm,
                    KernelParams kp, int with_samples, double* __restrict__ d_deg, float* __restrict__ degf,
-                   uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos, float* __restrict__ wsmp,
+                   uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp,
                    int32_t* __restrict__ bin_count, int32_t* __restrict__ items_q,
                    uint64_t* __restrict__ items_mask) {
     extern __shared__ __align__(16) unsigned char smem_b[];
@@ -101,7 +99,7 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                 const uint8_t f = (n > 1 || !kp.self_exclude) ? 2 : 0;
                 for (int l = lane; l < L; l += 32) {
                     leaf_pos[(size_t)q * L + l] = -1;
-                    wsmp[(size_t)q * L + l] = 0.f;
+                    ksmp[(size_t)q * L + l] = 0.f;
                     flags[(size_t)q * L + l] = f;
                 }
             }
@@ -112,139 +110,225 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
 
 constexpr int kThreadsC = 256;
 
+constexpr int kLeafWords = 512;   // Philox blocks precomputed per chunk (more: computed inline)
+
+// Shared-memory layout of the leaf finish (same arithmetic on host and device).
+struct LeafSmem {
+    size_t P, spos, V, qmask, qpos, qidx, qdeg, loff, list, W, total;
+    __host__ __device__ static size_t up16(size_t x) { return (x + 15) & ~size_t(15); }
+    __host__ __device__ LeafSmem(int leafmax, int dh, int qc) {
+        const size_t vs = 2 * (size_t)leafmax + 1;
+        P = 0;
+        spos = up16(P + (size_t)(leafmax / 2 + 2) * dh * 16);
+        V = up16(spos + (size_t)(leafmax + 4) * 4);
+        qmask = up16(V + (size_t)qc * vs * 4);
+        qpos = up16(qmask + (size_t)qc * 8);
+        qidx = up16(qpos + (size_t)qc * 4);
+        qdeg = up16(qidx + (size_t)qc * 4);            // query coordinates [qc][16]
+        loff = up16(qdeg + (size_t)qc * 16 * 4);
+        list = up16(loff + (size_t)(qc + 1) * 4);
+        W = up16(list + (size_t)qc * 64 * 4);
+        total = up16(W + (size_t)kLeafWords * 16);
+    }
+};
+
 // Leaf finish: CTA (b, y) handles chunks y, y + gridDim.y, ... of bin b's
-// item list, qt items per chunk.  Thread t owns leaf slots t, t + 256, ... of
-// the bin's perfect binary tree (slot = the path bits of the halving descent;
-// slots of empty nodes hold 0) -- or, when the tree has fewer than 256
-// leaves, slot t mod 2^dm for every G-th query.  Each chunk: kernel value of
-// every (query, slot), per-query trees summed upwards in shared memory, then
-// one thread per (query, sample) takes the remaining decisions and forms the
-// weight w = k / p_hat of Eq. 2.
-template <int D, int SPT>
+// item list, qc <= 32 items (queries) per chunk, lane = query.  The bin's
+// points are laid out in shared memory by leaf slot of the bin's perfect
+// binary tree (slot = path bits of the halving descent), two slots
+// interleaved per 16-byte word so that one load yields FP32x2 operands for
+// two slots; empty slots hold coordinate 1e19 and evaluate to exactly 0.
+// Warp w evaluates slot pairs w, w+8, ... for every query of the chunk; the
+// per-query trees are summed upwards in shared memory (rows of odd stride, so
+// the lanes' stores hit distinct banks); then one thread per (query, sample)
+// takes the remaining decisions and forms the weight w = k / p_hat (Eq. 2).
+template <int D>
 __global__ void __launch_bounds__(kThreadsC)
 leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
                    int n, int s0, const int32_t* __restrict__ bin_count, const int32_t* __restrict__ items_q,
-                   const uint64_t* __restrict__ items_mask, const float* __restrict__ degf, KernelParams kp, int qt,
-                   int dm_max, int32_t* __restrict__ leaf_pos, float* __restrict__ wsmp, uint8_t* __restrict__ flags,
+                   const uint64_t* __restrict__ items_mask, KernelParams kp, int qc_max, int dm_max,
+                   int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp, uint8_t* __restrict__ lflags,
                    unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items) {
     constexpr int DP = (D + 3) & ~3;
+    constexpr int DH = (D + 1) / 2;  // 16-byte words per slot pair
     const int b = blockIdx.x;
     const int cnt = bin_count[b];
-    const int nchunks = (cnt + qt - 1) / qt;
+    const int nchunks = (cnt + qc_max - 1) / qc_max;
     if ((int)blockIdx.y >= nchunks) return;
 
     extern __shared__ __align__(16) unsigned char smem_c[];
-    const int vs = 2 << dm_max;  // row stride of the per-query trees
-    float* V = reinterpret_cast<float*>(smem_c);
-    float* qs = V + (size_t)qt * vs;
-    uint64_t* qmask = reinterpret_cast<uint64_t*>(qs + (size_t)qt * DP);
-    int32_t* qpos = reinterpret_cast<int32_t*>(qmask + qt);
-    int32_t* qidx = qpos + qt;
-    float* qdeg = reinterpret_cast<float*>(qidx + qt);
-    int32_t* loff = reinterpret_cast<int32_t*>(qdeg + qt);   // qt + 1
-    int32_t* list = loff + qt + 1;                            // qt * 64
+    const int leafmax = 1 << dm_max;
+    const int vs = 2 * leafmax + 1;  // odd row stride
+    const LeafSmem lay(leafmax, DH, qc_max);
+    float4* P = reinterpret_cast<float4*>(smem_c + lay.P);           // [leafmax/2 + 2][DH] slot pairs
+    int32_t* spos = reinterpret_cast<int32_t*>(smem_c + lay.spos);   // [leafmax + 4] slot -> position
+    float* V = reinterpret_cast<float*>(smem_c + lay.V);             // [qc_max][vs] per-query trees
+    uint64_t* qmask = reinterpret_cast<uint64_t*>(smem_c + lay.qmask);
+    int32_t* qpos = reinterpret_cast<int32_t*>(smem_c + lay.qpos);
+    int32_t* qidx = reinterpret_cast<int32_t*>(smem_c + lay.qidx);
+    float* qco = reinterpret_cast<float*>(smem_c + lay.qdeg);        // [qc_max][DP] query coordinates
+    int32_t* loff = reinterpret_cast<int32_t*>(smem_c + lay.loff);   // qc_max + 1
+    int32_t* list = reinterpret_cast<int32_t*>(smem_c + lay.list);   // qc_max * 64
+    uint4* W = reinterpret_cast<uint4*>(smem_c + lay.W);              // [kLeafWords] Philox blocks
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const int L = kp.L;
     const int p_lo = bnd[b];
     const int m = bnd[b + 1] - p_lo;
     const int dm = ceil_log2_dev(m);
     const int leaf0 = 1 << dm;
-    const int G = leaf0 >= kThreadsC ? 1 : kThreadsC / leaf0;
-    const int g = leaf0 >= kThreadsC ? 0 : tid / leaf0;
-    const int s_first = leaf0 >= kThreadsC ? tid : tid % leaf0;
-    // This thread's slots: point coordinates kept in registers for every chunk.
-    float pc[SPT][D];
-    int ppos[SPT];
+    // Slot table and pair-interleaved point coordinates.
+    for (int sl = tid; sl < 4 * ((leaf0 + 3) / 4); sl += kThreadsC) {
+        int a = 0, c = m;  // walk the slot's path bits from the root
+        for (int t = dm - 1; t >= 0; --t) {
+            const int mid = a + (c - a) / 2;
+            if ((sl >> t) & 1) a = mid; else c = mid;
+        }
+        const int pos = (sl < leaf0 && c - a == 1) ? p_lo + a : -1;
+        spos[sl] = pos;
+        float* Pw = reinterpret_cast<float*>(P + (size_t)(sl >> 1) * DH);
 #pragma unroll
-    for (int u = 0; u < SPT; ++u) {
-        const int sl = s_first + u * kThreadsC;
-        ppos[u] = -1;
-        if (sl < leaf0) {
-            int a = 0, c = m;  // walk the slot's path bits from the root
-            for (int t = dm - 1; t >= 0; --t) {
-                const int mid = a + (c - a) / 2;
-                if ((sl >> t) & 1) a = mid; else c = mid;
+        for (int u = 0; u < DH; ++u) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = 2 * u + h;
+                const float v = (t < D) ? (pos >= 0 ? Xt[(size_t)pos * DP + t] : 1e19f) : 0.f;
+                Pw[4 * u + 2 * h + (sl & 1)] = v;
             }
-            if (c - a == 1) ppos[u] = p_lo + a;
         }
-#pragma unroll
-        for (int t = 0; t < D; ++t) pc[u][t] = ppos[u] >= 0 ? Xt[(size_t)ppos[u] * DP + t] : 0.f;
     }
+    const uint64_t nc2 = f2_pack(kp.neg_c, kp.neg_c);
     const size_t base = (size_t)b * n;
-    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
-        const int it0 = chunk * qt;
-        const int qcnt = min(qt, cnt - it0);
-        for (int e = tid; e < qcnt; e += kThreadsC) {
-            const int q = items_q[base + it0 + e];
-            qpos[e] = q;
-            qidx[e] = perm[q];
-            qmask[e] = items_mask[base + it0 + e];
-            qdeg[e] = degf[q];
+    // Warp 0 holds the next chunk's items (query, mask, index, coordinates) in
+    // registers: their global loads overlap the current chunk's work.
+    int nx_q = -1, nx_i = 0;
+    uint64_t nx_m = 0ull;
+    float nx_x[D];
+    auto fetch = [&](int chunk) {
+        const int it = chunk * qc_max + lane;
+        nx_q = -1;
+        if (chunk < nchunks && lane < qc_max && it < cnt) {
+            nx_q = items_q[base + it];
+            nx_m = items_mask[base + it];
+            nx_i = perm[nx_q];
+#pragma unroll
+            for (int t = 0; t < D; ++t) nx_x[t] = Xt[(size_t)nx_q * DP + t];
         }
-        for (int e = tid; e < qcnt * DP; e += kThreadsC) {
-            const int qq = e / DP;
-            qs[e] = Xt[(size_t)items_q[base + it0 + qq] * DP + (e - qq * DP)];
+    };
+    if (tid < 32) fetch(blockIdx.y);
+    unsigned long long ev_acc = 0, it_acc = 0;
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        const int it0 = chunk * qc_max;
+        const int qcnt = min(qc_max, cnt - it0);
+        if (tid < 32) {
+            if (lane < qcnt) {
+                qpos[lane] = nx_q;
+                qidx[lane] = nx_i;
+                qmask[lane] = nx_m;
+#pragma unroll
+                for (int t = 0; t < D; ++t) qco[lane * DP + t] = nx_x[t];
+            }
+            fetch(chunk + gridDim.y);
         }
         __syncthreads();
+        // Kernel values: lane = query, warp w = slot pairs w, w + 8, ...
+        if (lane < qc_max) {
+            const bool qv = lane < qcnt;
+            const int my_pos = qv ? qpos[lane] : -2;
+            uint64_t qd[D];
 #pragma unroll
-        for (int u = 0; u < SPT; ++u) {
-            const int sl = s_first + u * kThreadsC;
-            if (sl < leaf0) {
-                for (int qq = g; qq < qcnt; qq += G) {
-                    float k = 0.f;
-                    if (ppos[u] >= 0) {
-                        const float* qc = qs + qq * DP;
-                        float dd = qc[0] - pc[u][0];
-                        float acc = dd * dd;
+            for (int t = 0; t < D; ++t) {
+                const float x = qv ? qco[lane * DP + t] : 1e19f;
+                qd[t] = f2_pack(x, x);
+            }
+            float* row = V + (size_t)lane * vs;
+            // Quads of 4 consecutive slots (two slot pairs): leaves, their two
+            // parents and their grandparent are formed here, in registers.
+            const int nquad = (leaf0 + 3) / 4;
+            for (int j = w; j < nquad; j += kThreadsC / 32) {
+                float kq[4];
 #pragma unroll
-                        for (int t = 1; t < D; ++t) {
-                            dd = qc[t] - pc[u][t];
-                            acc = fmaf(dd, dd, acc);
+                for (int hp = 0; hp < 2; ++hp) {
+                    const int pp = 2 * j + hp;
+                    const float4* Pp = P + (size_t)pp * DH;
+                    uint64_t s2 = 0ull, s3 = 0ull;
+#pragma unroll
+                    for (int u = 0; u < DH; ++u) {
+                        const float4 c4 = Pp[u];
+                        const uint64_t ca = f2_pack(c4.x, c4.y), cb = f2_pack(c4.z, c4.w);
+                        uint64_t dd = f2_sub(qd[2 * u], ca);
+                        s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
+                        if (2 * u + 1 < D) {
+                            dd = f2_sub(qd[2 * u + 1], cb);
+                            s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
                         }
-                        k = ex2_approx(acc * kp.neg_c);
-                        if (kp.self_exclude && ppos[u] == qpos[qq]) k = 0.f;
                     }
-                    V[(size_t)qq * vs + leaf0 + sl] = k;
+                    if (D > 1) s2 = f2_add(s2, s3);
+                    const float2 sv = f2_unpack(f2_mul(s2, nc2));
+                    float k0 = ex2_approx(sv.x), k1 = ex2_approx(sv.y);
+                    if (kp.self_exclude) {
+                        if (spos[2 * pp] == my_pos) k0 = 0.f;
+                        if (spos[2 * pp + 1] == my_pos) k1 = 0.f;
+                    }
+                    kq[2 * hp] = k0;
+                    kq[2 * hp + 1] = k1;
+                }
+                const int s4 = 4 * j;
+                if (leaf0 >= 4) {
+                    row[leaf0 + s4] = kq[0];
+                    row[leaf0 + s4 + 1] = kq[1];
+                    row[leaf0 + s4 + 2] = kq[2];
+                    row[leaf0 + s4 + 3] = kq[3];
+                    const float p0 = kq[0] + kq[1], p1 = kq[2] + kq[3];
+                    row[(leaf0 + s4) / 2] = p0;
+                    row[(leaf0 + s4) / 2 + 1] = p1;
+                    row[(leaf0 + s4) / 4] = p0 + p1;
+                } else {
+                    for (int x = 0; x < leaf0; ++x) row[leaf0 + x] = kq[x];
+                    if (leaf0 == 2) row[1] = kq[0] + kq[1];
                 }
             }
         }
         __syncthreads();
-        for (int lev = dm - 1; lev >= 0; --lev) {
+        for (int lev = dm - 3; lev >= 0; --lev) {
             const int cn = qcnt << lev;
             for (int e = tid; e < cn; e += kThreadsC) {
                 const int qq = e >> lev;
                 const int h = (1 << lev) + (e & ((1 << lev) - 1));
-                float* row = V + (size_t)qq * vs;
-                row[h] = row[2 * h] + row[2 * h + 1];
+                float* r = V + (size_t)qq * vs;
+                r[h] = r[2 * h] + r[2 * h + 1];
             }
             __syncthreads();
         }
-        // List of (query, sample) pairs of this chunk (warp 0: popcount prefix).
+        // List of (query, sample) pairs of this chunk: warp 0, lane = query.
         if (tid < 32) {
-            int c0 = 0, c1 = 0;
-            if (tid < qcnt) c0 = __popcll(qmask[tid]);
-            if (tid + 32 < qcnt) c1 = __popcll(qmask[tid + 32]);
-            int s0v = c0, s1v = c1;
+            const uint64_t mk0 = tid < qcnt ? qmask[tid] : 0ull;
+            const int c0 = __popcll(mk0);
+            int sv = c0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y0 = __shfl_up_sync(0xffffffffu, s0v, o);
-                const int y1 = __shfl_up_sync(0xffffffffu, s1v, o);
-                if (tid >= o) { s0v += y0; s1v += y1; }
+                const int y = __shfl_up_sync(0xffffffffu, sv, o);
+                if (tid >= o) sv += y;
             }
-            const int tot0 = __shfl_sync(0xffffffffu, s0v, 31);
-            if (tid < qcnt) loff[tid] = s0v - c0;
-            if (tid + 32 < qcnt) loff[tid + 32] = tot0 + s1v - c1;
-            if (tid == 31) loff[qcnt] = tot0 + s1v;
+            int off = sv - c0;
+            if (tid < qcnt) loff[tid] = off;
+            if (tid == 31) loff[qcnt] = sv;
+            for (uint64_t mk = mk0; mk; mk &= mk - 1ull) list[off++] = (tid << 6) | (__ffsll((long long)mk) - 1);
         }
         __syncthreads();
-        for (int e = tid; e < qcnt * 64; e += kThreadsC) {
-            const int qq = e >> 6, l = e & 63;
-            const uint64_t mk = qmask[qq];
-            if ((mk >> l) & 1ull) list[loff[qq] + __popcll(mk & ((1ull << l) - 1ull))] = (qq << 6) | l;
-        }
-        __syncthreads();
+        // Philox blocks of every sample's remaining levels, one per thread.
         const int nsamp = loff[qcnt];
+        const int blk0 = s0 >> 2;
+        const int nblk = dm > 0 ? ((s0 + dm - 1) >> 2) - blk0 + 1 : 0;
+        const bool pre = nsamp * nblk <= kLeafWords;
+        if (pre) {
+            for (int e = tid; e < nsamp * nblk; e += kThreadsC) {
+                const int sidx = e / nblk, jb = e - sidx * nblk;
+                const int qq = list[sidx] >> 6, l = list[sidx] & 63;
+                W[e] = draw_block(kp.seed, (uint32_t)qidx[qq], (uint32_t)l, (uint32_t)(4 * (blk0 + jb)));
+            }
+            __syncthreads();
+        }
         for (int e = tid; e < nsamp; e += kThreadsC) {
             const int qq = list[e] >> 6, l = list[e] & 63;
             const float* row = V + (size_t)qq * vs;
@@ -257,8 +341,8 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 if (c - a >= 2) {
                     const uint32_t lev = (uint32_t)(s0 + t);
                     if ((int)(lev >> 2) != blk_id) {
-                        blk = draw_block(kp.seed, i, (uint32_t)l, lev);
                         blk_id = (int)(lev >> 2);
+                        blk = pre ? W[e * nblk + (blk_id - blk0)] : draw_block(kp.seed, i, (uint32_t)l, lev);
                     }
                     const int mid = a + (c - a) / 2;
                     const int right = descend_decide(row[2 * h], row[2 * h + 1], block_word(blk, lev), kp.flag_eps, f);
@@ -268,69 +352,55 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                     h = 2 * h + 1;  // a single point sits in the right half
                 }
             }
-            const int pos = p_lo + a;
-            const float k = row[h];
-            const float Lk = (float)L * k;
-            const float pi = fminf(__fdiv_rn(Lk, qdeg[qq]), 1.f);
-            const float pj = fminf(__fdiv_rn(Lk, degf[pos]), 1.f);
-            const float ph = pi + pj - pi * pj;
             const size_t o = (size_t)qpos[qq] * L + l;
-            leaf_pos[o] = pos;
-            wsmp[o] = k > 0.f ? __fdiv_rn(k, ph) : 0.f;
-            flags[o] |= f;
+            leaf_pos[o] = p_lo + a;
+            ksmp[o] = row[h];
+            lflags[o] = f;
         }
-        if (tid == 0) {
-            atomicAdd(n_evals, (unsigned long long)qcnt * (unsigned long long)m);
-            atomicAdd(n_items, (unsigned long long)qcnt);
-        }
+        ev_acc += (unsigned long long)qcnt * (unsigned long long)m;
+        it_acc += (unsigned long long)qcnt;
         __syncthreads();
+    }
+    if (tid == 0) {
+        atomicAdd(n_evals, ev_acc);
+        atomicAdd(n_items, it_acc);
     }
 }
 
-template <int D, int SPT>
-cudaError_t launch_leaf_ds(const fsg_tree* t, const KernelParams& kp, int qt, cudaStream_t s) {
-    constexpr int DP = (D + 3) & ~3;
-    const int vs = 2 << t->dm;
-    const size_t smem = (size_t)qt * vs * 4 + (size_t)qt * DP * 4 + (size_t)qt * 8 + (size_t)qt * 12 +
-                        (size_t)(qt + 1) * 4 + (size_t)qt * 64 * 4;
+template <int D>
+cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cudaStream_t s) {
+    constexpr int DH = (D + 1) / 2;
+    const size_t smem = LeafSmem(1 << t->dm, DH, qc).total;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D, SPT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     // Splits per bin: about 8 waves of CTAs over the expected items.
     const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
-    const int64_t chunks_per_bin = (items_est / t->nb + qt - 1) / qt + 1;
+    const int64_t chunks_per_bin = (items_est / t->nb + qc - 1) / qc + 1;
     int64_t S = (152 * 4 * 8 + t->nb - 1) / t->nb;
     if (S > chunks_per_bin) S = chunks_per_bin;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
-    leaf_finish_kernel<D, SPT><<<grid, kThreadsC, smem, s>>>(
-        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_count, ws.items_q, ws.items_mask, ws.degf, kp, qt, t->dm,
-        ws.leaf_pos, ws.wsmp, ws.flags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+    leaf_finish_kernel<D><<<grid, kThreadsC, smem, s>>>(
+        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_count, ws.items_q, ws.items_mask, kp, qc, t->dm,
+        ws.leaf_pos, ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
     return cudaGetLastError();
-}
-
-template <int D>
-cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qt, cudaStream_t s) {
-    const int leaf0 = 1 << t->dm;
-    if (leaf0 <= kThreadsC) return launch_leaf_ds<D, 1>(t, kp, qt, s);
-    if (leaf0 <= 2 * kThreadsC) return launch_leaf_ds<D, 2>(t, kp, qt, s);
-    return launch_leaf_ds<D, 4>(t, kp, qt, s);
 }
 
 }  // namespace
 
 int leaf_queries_per_tile(const fsg_tree* t) {
-    int qt = 8192 / (2 << t->dm);  // 32 KB of per-query trees
-    if (qt > 64) qt = 64;
-    if (qt < 4) qt = 4;
-    return qt;
+    int qc = 8192 / (2 << t->dm);  // <= 32 KB of per-query trees, one query per lane
+    if (qc > 32) qc = 32;
+    if (qc < 1) qc = 1;
+    return qc;
 }
 
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
@@ -350,7 +420,7 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
     const auto& ws = t->ws;
     descend_top_kernel<<<(int)blocks, warps * 32, smem, s>>>(ws.binsum, (int)t->n, t->nb, t->s0, t->perm, kp,
                                                             with_samples, d_deg, ws.degf, ws.flags, ws.leaf_pos,
-                                                            ws.wsmp, ws.bin_count, ws.items_q, ws.items_mask);
+                                                            ws.ksmp, ws.bin_count, ws.items_q, ws.items_mask);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,7 @@
 // Edge list of Algorithm 2: the union over all points of the sampled pairs,
-// with the weights of Eq. 2 computed per sample by the leaf finish.
+// with the weights of Eq. 2, w = k / p_hat, p_hat = p_i + p_j - p_i p_j,
+// p_i = min(L k / g_[1,n](x_i), 1), formed here from each sample's kernel
+// value k (kept by the leaf finish) and the two endpoints' degrees.
 //
 //   SET   : each unordered pair {i,j} (i != j) appears once.  Per query, the
 //           distinct sampled neighbours are sorted in-warp (bitonic network);
@@ -15,6 +17,15 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int32_t kSentinel = 0x7fffffff;
+
+// Weight of Eq. 2 in FP32; symmetric in (i, j) bit for bit.
+__device__ __forceinline__ float edge_weight(float k, float deg_i, float deg_j, int L) {
+    if (!(k > 0.f)) return 0.f;
+    const float Lk = (float)L * k;
+    const float pi = fminf(__fdiv_rn(Lk, deg_i), 1.f);
+    const float pj = fminf(__fdiv_rn(Lk, deg_j), 1.f);
+    return __fdiv_rn(k, pi + pj - pi * pj);
+}
 
 // Bitonic sort of the warp's 64 (key, value) pairs: element index lane holds
 // (k0, v0), index lane+32 holds (k1, v1).  Ascending by key.
@@ -46,20 +57,22 @@ __device__ __forceinline__ void warp_sort64(int32_t& k0, float& v0, int32_t& k1,
 
 // SET, step 1: per query, the sorted distinct neighbours (self and -1 dropped).
 __global__ void __launch_bounds__(128)
-unique_neighbours_kernel(const int32_t* __restrict__ leaf_pos, const float* __restrict__ wsmp, int n, int L,
-                         int32_t* __restrict__ uniq, float* __restrict__ uniq_w, int32_t* __restrict__ ucnt) {
+unique_neighbours_kernel(const int32_t* __restrict__ leaf_pos, const float* __restrict__ ksmp,
+                         const float* __restrict__ degf, int n, int L, int32_t* __restrict__ uniq,
+                         float* __restrict__ uniq_w, int32_t* __restrict__ ucnt) {
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
         int32_t k0 = kSentinel, k1 = kSentinel;
         float v0 = 0.f, v1 = 0.f;
+        const float dq = degf[q];
         if (lane < L) {
             const int32_t j = leaf_pos[(size_t)q * L + lane];
-            if (j >= 0 && j != q) { k0 = j; v0 = wsmp[(size_t)q * L + lane]; }
+            if (j >= 0 && j != q) { k0 = j; v0 = edge_weight(ksmp[(size_t)q * L + lane], dq, degf[j], L); }
         }
         if (lane + 32 < L) {
             const int32_t j = leaf_pos[(size_t)q * L + lane + 32];
-            if (j >= 0 && j != q) { k1 = j; v1 = wsmp[(size_t)q * L + lane + 32]; }
+            if (j >= 0 && j != q) { k1 = j; v1 = edge_weight(ksmp[(size_t)q * L + lane + 32], dq, degf[j], L); }
         }
         warp_sort64(k0, v0, k1, v1, lane);
         // previous element of index lane (k0) and lane+32 (k1)
@@ -232,8 +245,9 @@ set_write_kernel(const int32_t* __restrict__ uniq, const float* __restrict__ uni
     }
 }
 
-__global__ void multi_write_kernel(const int32_t* __restrict__ leaf_pos, const float* __restrict__ wsmp,
-                                   const int64_t* __restrict__ eoff, const int32_t* __restrict__ perm, int n, int L,
+__global__ void multi_write_kernel(const int32_t* __restrict__ leaf_pos, const float* __restrict__ ksmp,
+                                   const float* __restrict__ degf, const int64_t* __restrict__ eoff,
+                                   const int32_t* __restrict__ perm, int n, int L,
                                    int64_t cap, int32_t* __restrict__ src, int32_t* __restrict__ dst,
                                    float* __restrict__ wout) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -245,7 +259,7 @@ __global__ void multi_write_kernel(const int32_t* __restrict__ leaf_pos, const f
                 if (o < cap) {
                     src[o] = iq;
                     dst[o] = perm[j];
-                    wout[o] = wsmp[(size_t)q * L + l];
+                    wout[o] = edge_weight(ksmp[(size_t)q * L + l], degf[q], degf[j], L);
                 }
                 ++o;
             }
@@ -255,7 +269,8 @@ __global__ void multi_write_kernel(const int32_t* __restrict__ leaf_pos, const f
 
 // Per-sample outputs in original index order, and sample statistics.
 __global__ void outputs_kernel(const int32_t* __restrict__ leaf_pos, const uint8_t* __restrict__ flags,
-                               const int32_t* __restrict__ perm, int n, int L, int32_t* __restrict__ d_samples,
+                               const uint8_t* __restrict__ lflags, const int32_t* __restrict__ perm, int n, int L,
+                               int32_t* __restrict__ d_samples,
                                uint8_t* __restrict__ d_flags, fsg_stats* __restrict__ stats) {
     const int64_t total = (int64_t)n * L;
     unsigned long long fl = 0, sf = 0, em = 0;
@@ -263,7 +278,7 @@ __global__ void outputs_kernel(const int32_t* __restrict__ leaf_pos, const uint8
         const int q = (int)(e / L);
         const int l = (int)(e - (int64_t)q * L);
         const int32_t pos = leaf_pos[e];
-        const uint8_t f = flags[e];
+        const uint8_t f = flags[e] | (pos >= 0 ? lflags[e] : (uint8_t)0);
         const size_t o = (size_t)perm[q] * L + l;
         if (d_samples) d_samples[o] = pos >= 0 ? perm[pos] : -1;
         if (d_flags) d_flags[o] = f;
@@ -298,8 +313,8 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
     const auto& ws = t->ws;
     const int n = (int)t->n, L = kp.L;
     if (edge_mode == FSG_EDGES_SET) {
-        unique_neighbours_kernel<<<grid_for(n, 4), 128, 0, s>>>(ws.leaf_pos, ws.wsmp, n, L, ws.uniq, ws.uniq_w,
-                                                               ws.ucnt);
+        unique_neighbours_kernel<<<grid_for(n, 4), 128, 0, s>>>(ws.leaf_pos, ws.ksmp, ws.degf, n, L, ws.uniq,
+                                                               ws.uniq_w, ws.ucnt);
         owner_kernel<<<grid_for(n, 4), 128, 0, s>>>(ws.uniq, ws.ucnt, t->perm, n, L, ws.emit_mask, ws.ecount);
     } else {
         multi_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(ws.leaf_pos, n, L, ws.ecount);
@@ -314,8 +329,8 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
         set_write_kernel<<<grid_for(n, 4), 128, 0, s>>>(ws.uniq, ws.uniq_w, ws.emit_mask, ws.ecount, t->perm, n, L,
                                                        cap, d_src, d_dst, d_w);
     } else {
-        multi_write_kernel<<<grid_for(n, 256), 256, 0, s>>>(ws.leaf_pos, ws.wsmp, ws.ecount, t->perm, n, L, cap,
-                                                           d_src, d_dst, d_w);
+        multi_write_kernel<<<grid_for(n, 256), 256, 0, s>>>(ws.leaf_pos, ws.ksmp, ws.degf, ws.ecount, t->perm, n, L,
+                                                           cap, d_src, d_dst, d_w);
     }
     return cudaGetLastError();
 }
@@ -324,8 +339,8 @@ cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d
                            fsg_stats* d_stats, cudaStream_t s) {
     (void)d_stats;
     const auto& ws = t->ws;
-    outputs_kernel<<<grid_for(t->n * kp.L, 256), 256, 0, s>>>(ws.leaf_pos, ws.flags, t->perm, (int)t->n, kp.L,
-                                                              d_samples, d_flags, ws.stats);
+    outputs_kernel<<<grid_for(t->n * kp.L, 256), 256, 0, s>>>(ws.leaf_pos, ws.flags, ws.lflags, t->perm, (int)t->n,
+                                                              kp.L, d_samples, d_flags, ws.stats);
     return cudaGetLastError();
 }
 

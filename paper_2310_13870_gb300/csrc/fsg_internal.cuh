@@ -29,7 +29,8 @@ struct Workspace {
     float* degf = nullptr;          // [n]       FP32 degree per position
     uint8_t* flags = nullptr;       // [n][L]    per-sample flags (tree order)
     int32_t* leaf_pos = nullptr;    // [n][L]    sampled neighbour position or -1
-    float* wsmp = nullptr;          // [n][L]    weight of each sample
+    float* ksmp = nullptr;          // [n][L]    kernel value k(x_i, x_j) of each sample
+    uint8_t* lflags = nullptr;      // [n][L]    flags of the leaf-finish decisions
     int32_t* bin_count = nullptr;   // [nb]       items per bin
     int32_t* items_q = nullptr;     // [nb][n]    per-bin lists: query position
     uint64_t* items_mask = nullptr; // [nb][n]    per-bin lists: samples of that query there
@@ -92,6 +93,8 @@ int ensure_workspace(fsg_tree* t, int L, cudaStream_t s);
 cudaError_t launch_tree_prep(fsg_tree* t, const float* d_points, const int32_t* d_perm, cudaStream_t s);
 cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 bool kde_bins_supported(const fsg_tree* t);
+cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+bool kde_bins_sym_supported(const fsg_tree* t);
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
                                cudaStream_t s);
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
