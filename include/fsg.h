@@ -48,6 +48,7 @@ extern "C" {
 #define FSG_ERR_UNSUPPORTED 5   /* option not implemented for these sizes        */
 #define FSG_ERR_BUSY 6          /* server: no slot or budget for the request      */
 #define FSG_ERR_CAPACITY 7      /* an output buffer is too small                  */
+#define FSG_ERR_SCRATCH 8       /* problem too large for fsg_degrees_noalloc      */
 
 /* ---- option values ----------------------------------------------------- */
 /* Bandwidth convention: gamma = 1/(2 sigma^2) (default) or 1/sigma^2, the form
@@ -144,6 +145,37 @@ int fsg_tree_update(fsg_tree* tree, const float* d_points, void* stream);
  * Errors: INVALID_ARG (params), OOM, CUDA, UNSUPPORTED.
  */
 int fsg_degrees(fsg_tree* tree, const fsg_params* params, double* d_deg, void* stream);
+
+/*
+ * Degrees without any device allocation.  (The paper has no counterpart:
+ * this is a service for callers, computing the same values as fsg_degrees.)
+ *
+ * Some callers cannot call cudaMalloc: an application whose device memory is
+ * owned entirely by its own pool allocator (a framework's caching allocator,
+ * a serving runtime that reserves its HBM budget up front) must not have a
+ * library allocate behind its back, and latency-critical callers cannot pay
+ * for cudaMalloc/cudaFree, which may synchronize the device.  This entry
+ * point needs no tree object and no workspace: its scratch (a tree-ordered
+ * copy of the points, bin boundaries, per-bin partial sums) lives in one
+ * statically sized array in the library's device memory, which every GPU
+ * that loads the library holds until the process exits.
+ *   d_points : device float32 [n][d] row-major, read only.
+ *   d_deg    : device float64 [n], original index order (same values as
+ *              fsg_degrees to FP32 accuracy).
+ *   Limits   : 1 <= d <= 16, and the scratch (about 270 bytes per point at
+ *              d = 16) must fit FSG_NOALLOC_SCRATCH_BYTES; larger problems are
+ *              refused with FSG_ERR_SCRATCH before anything is enqueued.
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call, on any stream, shares the one
+ * array and leaves its contents behind: calls that overlap on the GPU race
+ * and give wrong results, so serialize them (one stream, or events).
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * Errors: INVALID_ARG, UNSUPPORTED (d > 16), SCRATCH, CUDA.
+ */
+#define FSG_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int fsg_degrees_noalloc(const float* d_points, int64_t n, int32_t d, const fsg_params* params, double* d_deg,
+                        void* stream);
 
 /*
  * L samples per point by the descent of Algorithm 1 (Sec. 4.1).  The uniform

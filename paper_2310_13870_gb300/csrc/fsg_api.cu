@@ -157,6 +157,7 @@ const char* fsg_error_string(int status) {
         case FSG_ERR_UNSUPPORTED: return "option not supported for these sizes";
         case FSG_ERR_BUSY: return "no slot or memory budget available";
         case FSG_ERR_CAPACITY: return "output buffer too small";
+        case FSG_ERR_SCRATCH: return "problem too large for the fixed scratch of fsg_degrees_noalloc";
         default: return "unknown status";
     }
 }

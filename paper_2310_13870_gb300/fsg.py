@@ -24,6 +24,7 @@ FSG_ERR_TIMEOUT = 4
 FSG_ERR_UNSUPPORTED = 5
 FSG_ERR_BUSY = 6
 FSG_ERR_CAPACITY = 7
+FSG_ERR_SCRATCH = 8
 
 FSG_TWO_SIGMA_SQ, FSG_SIGMA_SQ = 0, 1
 FSG_SELF_EXCLUDE, FSG_SELF_INCLUDE = 0, 1
@@ -36,7 +37,7 @@ FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE = 0, 1
 EXPORTED = [
     "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info",
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
-    "fsg_tree_update", "fsg_profile", "fsg_profile_read",
+    "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
 ]
 FSG_NUM_PHASES = 8
 PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "unused"]
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH):
     lib.fsg_tree_update.argtypes = [P, P, P]
     lib.fsg_profile.argtypes = [P, ctypes.c_int]
     lib.fsg_profile_read.argtypes = [P, P, P]
+    lib.fsg_degrees_noalloc.argtypes = [P, I64, I32, P, P, P]
     for name in EXPORTED:
         if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree"):
             getattr(lib, name).restype = ctypes.c_int
@@ -201,6 +203,20 @@ def fsg_degrees(tree: Tree, p: fsg_params, out=None, stream=None):
     if out is None:
         out = torch.empty(tree.n, dtype=torch.float64, device="cuda")
     _check(load().fsg_degrees(tree.handle, ctypes.byref(p), _dptr(out), _stream_ptr(stream)), "fsg_degrees")
+    return out
+
+
+def fsg_degrees_noalloc(points, p: fsg_params, out=None, stream=None):
+    """Degrees through the allocation-free entry point (no tree object; the
+    library's fixed device scratch is used; see include/fsg.h)."""
+    import torch
+    if not (points.is_cuda and points.dtype == torch.float32 and points.dim() == 2):
+        raise ValueError("points must be a CUDA float32 [n][d] tensor")
+    points = points.contiguous()
+    if out is None:
+        out = torch.empty(points.shape[0], dtype=torch.float64, device=points.device)
+    _check(load().fsg_degrees_noalloc(_dptr(points), points.shape[0], points.shape[1], ctypes.byref(p), _dptr(out),
+                                      _stream_ptr(stream)), "fsg_degrees_noalloc")
     return out
 
 
