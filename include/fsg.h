@@ -225,13 +225,50 @@ int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_
 #define FSG_PHASE_TREE 0        /* tree build / update                         */
 #define FSG_PHASE_KDE_BINS 1    /* bin pass: every query against every point   */
 #define FSG_PHASE_DESCEND_TOP 2 /* degrees and the top s0 levels               */
-#define FSG_PHASE_BUCKET 3      /* reserved (items are grouped in descend_top) */
+#define FSG_PHASE_BUCKET 3      /* grouping of (query, node) items per node    */
 #define FSG_PHASE_LEAF 4        /* leaf finish: remaining levels and weights   */
 #define FSG_PHASE_EDGES 5       /* edge list                                   */
 #define FSG_PHASE_OUTPUTS 6     /* per-sample outputs and statistics           */
 #define FSG_NUM_PHASES 8
 int fsg_profile(fsg_tree* tree, int enable);
 int fsg_profile_read(fsg_tree* tree, float* ms, int64_t* launches);
+
+/*
+ * Batched graph construction over many independent point sets (for example
+ * the pixel features of many images): every set runs the whole of
+ * Algorithm 2 with its own parameters.  fsg_batch_create builds one tree per
+ * set (allocating); fsg_batch_run refreshes every tree from its d_points and
+ * enqueues every set's graph build on `streams` internal streams forked from
+ * (and joined back into) the caller's stream.  With capture != 0 the first run
+ * records the whole launch sequence into a CUDA graph and later runs replay
+ * it (inputs and outputs are read and written through the pointers given at
+ * creation, so new point values of the same shapes are picked up).
+ */
+typedef struct {
+    const float* d_points;  /* device float32 [n][d], read at every run       */
+    int64_t n;
+    int32_t d;
+    int32_t L;              /* 1..64                                          */
+    fsg_params params;
+    uint64_t seed;
+    int32_t edge_mode;      /* FSG_EDGES_SET | FSG_EDGES_MULTI                */
+    int32_t reserved0;
+    int32_t* d_src;         /* device int32 [cap]                             */
+    int32_t* d_dst;         /* device int32 [cap]                             */
+    float* d_w;             /* device float32 [cap]                           */
+    int64_t cap;            /* >= n * L                                       */
+    int64_t* d_m_out;       /* device int64: edges written                    */
+    double* d_deg;          /* optional device float64 [n]                    */
+    fsg_stats* d_stats;     /* optional device statistics                     */
+} fsg_batch_item;
+
+typedef struct fsg_batch fsg_batch; /* opaque */
+
+/* Errors: INVALID_ARG (any item), OOM, CUDA, UNSUPPORTED, CAPACITY. */
+int fsg_batch_create(const fsg_batch_item* items, int32_t count, int32_t streams, int32_t capture,
+                     void* stream, fsg_batch** out);
+int fsg_batch_run(fsg_batch* batch, void* stream);
+void fsg_batch_destroy(fsg_batch* batch);
 
 /*
  * Waits for the stream and returns the tree's device status word

@@ -90,7 +90,7 @@ int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
     const int64_t n = t->n;
     const int64_t Lc = L > ws.cap_L ? L : ws.cap_L;
     const int64_t nb = t->nb;
-    const int64_t list_cap = n * nb;  // per-bin item lists: capacity n each
+    const int64_t max_items = n * (Lc < nb ? Lc : nb);  // distinct (query, bin) pairs
     const int64_t nblocks = (n + 1023) / 1024 + 2;
     size_t off = 0;
     struct Part { void** ptr; size_t bytes; };
@@ -101,9 +101,14 @@ int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
         {(void**)&ws.leaf_pos, sizeof(int32_t) * (size_t)n * Lc},
         {(void**)&ws.ksmp, sizeof(float) * (size_t)n * Lc},
         {(void**)&ws.lflags, sizeof(uint8_t) * (size_t)n * Lc},
-        {(void**)&ws.bin_count, sizeof(int32_t) * (size_t)nb},
-        {(void**)&ws.items_q, sizeof(int32_t) * (size_t)list_cap},
-        {(void**)&ws.items_mask, sizeof(uint64_t) * (size_t)list_cap},
+        {(void**)&ws.qitem_bin, sizeof(int32_t) * (size_t)n * Lc},
+        {(void**)&ws.qitem_mask, sizeof(uint64_t) * (size_t)n * Lc},
+        {(void**)&ws.qitem_cnt, sizeof(int32_t) * (size_t)n},
+        {(void**)&ws.bin_count, sizeof(int32_t) * (size_t)nb * kBinSlots},
+        {(void**)&ws.bin_cursor, sizeof(int32_t) * (size_t)nb * kBinSlots},
+        {(void**)&ws.bin_off, sizeof(int32_t) * (size_t)(nb * kBinSlots + 1)},
+        {(void**)&ws.items_q, sizeof(int32_t) * (size_t)max_items},
+        {(void**)&ws.items_mask, sizeof(uint64_t) * (size_t)max_items},
         {(void**)&ws.uniq, sizeof(int32_t) * (size_t)n * Lc},
         {(void**)&ws.uniq_w, sizeof(float) * (size_t)n * Lc},
         {(void**)&ws.ucnt, sizeof(int32_t) * (size_t)n},
@@ -288,7 +293,8 @@ int fsg_profile_read(fsg_tree* t, float* ms, int64_t* launches) {
 
 static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cudaStream_t s) {
     Workspace& ws = t->ws;
-    cudaError_t e = cudaMemsetAsync(ws.bin_count, 0, sizeof(int32_t) * t->nb, s);
+    cudaError_t e = cudaMemsetAsync(ws.bin_count, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.bin_cursor, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
@@ -299,6 +305,11 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cuda
         PhaseScope ph(t, FSG_PHASE_DESCEND_TOP, s);
         e = launch_descend_top(t, kp, d_deg, 1, s);
         t->launches += 1;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_BUCKET, s);
+        e = launch_bucket(t, kp, s);
+        t->launches += 2;
     }
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_LEAF, s);

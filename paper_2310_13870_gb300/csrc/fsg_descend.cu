@@ -26,8 +26,8 @@ __global__ void __launch_bounds__(256)
 descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, const int32_t* __restrict__ perm,
                    KernelParams kp, int with_samples, double* __restrict__ d_deg, float* __restrict__ degf,
                    uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp,
-                   int32_t* __restrict__ bin_count, int32_t* __restrict__ items_q,
-                   uint64_t* __restrict__ items_mask) {
+                   int32_t* __restrict__ bin_count, int32_t* __restrict__ qitem_bin,
+                   uint64_t* __restrict__ qitem_mask, int32_t* __restrict__ qitem_cnt) {
     extern __shared__ __align__(16) unsigned char smem_b[];
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -83,17 +83,26 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                     }
                 }
                 __syncwarp();
+                // The lowest sample of each bin writes the (bin, mask) item of
+                // this query; items are packed per query and counted per bin.
+                bool lead[2];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const int l = lane + 32 * r;
-                    // the lowest sample of each bin writes the (query, mask) item
-                    if (binv[r] >= 0 && (M[r] & ((1ull << l) - 1ull)) == 0ull) {
-                        const int b = binv[r];
-                        const int slot = atomicAdd(&bin_count[b], 1);
-                        items_q[(size_t)b * n + slot] = q;
-                        items_mask[(size_t)b * n + slot] = M[r];
+                    lead[r] = binv[r] >= 0 && (M[r] & ((1ull << l) - 1ull)) == 0ull;
+                }
+                const uint32_t b0 = __ballot_sync(0xffffffffu, lead[0]), b1 = __ballot_sync(0xffffffffu, lead[1]);
+                const uint32_t below = (1u << lane) - 1u;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    if (lead[r]) {
+                        const int k = r == 0 ? __popc(b0 & below) : __popc(b0) + __popc(b1 & below);
+                        qitem_bin[(size_t)q * L + k] = binv[r];
+                        qitem_mask[(size_t)q * L + k] = M[r];
+                        atomicAdd(&bin_count[binv[r] * kBinSlots + (q & (kBinSlots - 1))], 1);
                     }
                 }
+                if (lane == 0) qitem_cnt[q] = __popc(b0) + __popc(b1);
             } else {
                 // zero FP32 mass: no sample; flag unless no other point exists
                 const uint8_t f = (n > 1 || !kp.self_exclude) ? 2 : 0;
@@ -102,9 +111,60 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                     ksmp[(size_t)q * L + l] = 0.f;
                     flags[(size_t)q * L + l] = f;
                 }
+                if (lane == 0) qitem_cnt[q] = 0;
             }
         }
         __syncwarp();
+    }
+}
+
+// Exclusive scan of the per-(bin, sub-slot) item counts (single CTA).  Bin b's
+// segment is [bin_off[b * kBinSlots], bin_off[(b + 1) * kBinSlots]).
+__global__ void __launch_bounds__(1024)
+scan_bins_kernel(const int32_t* __restrict__ bin_count, int nb, int32_t* __restrict__ bin_off) {
+    __shared__ int32_t s_items[1024];
+    const int tid = threadIdx.x;
+    const int per = (nb + 1023) / 1024;
+    int ci = 0;
+    for (int u = 0; u < per; ++u) {
+        const int b = tid * per + u;
+        if (b < nb) ci += bin_count[b];
+    }
+    s_items[tid] = ci;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int vi = tid >= off ? s_items[tid - off] : 0;
+        __syncthreads();
+        s_items[tid] += vi;
+        __syncthreads();
+    }
+    int ri = s_items[tid] - ci;
+    for (int u = 0; u < per; ++u) {
+        const int b = tid * per + u;
+        if (b < nb) {
+            bin_off[b] = ri;
+            ri += bin_count[b];
+        }
+    }
+    if (tid == 1023) bin_off[nb] = s_items[1023];
+}
+
+// Items of every query into their bin's segment [bin_off[b], bin_off[b+1]).
+__global__ void __launch_bounds__(128)
+scatter_items_kernel(const int32_t* __restrict__ qitem_bin, const uint64_t* __restrict__ qitem_mask,
+                     const int32_t* __restrict__ qitem_cnt, int n, int L, const int32_t* __restrict__ bin_off,
+                     int32_t* __restrict__ bin_cursor, int32_t* __restrict__ items_q,
+                     uint64_t* __restrict__ items_mask) {
+    const int warps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
+        const int cnt = qitem_cnt[q];
+        for (int k = lane; k < cnt; k += 32) {
+            const int b = qitem_bin[(size_t)q * L + k] * kBinSlots + (q & (kBinSlots - 1));
+            const int slot = bin_off[b] + atomicAdd(&bin_cursor[b], 1);
+            items_q[slot] = q;
+            items_mask[slot] = qitem_mask[(size_t)q * L + k];
+        }
     }
 }
 
@@ -145,14 +205,14 @@ struct LeafSmem {
 template <int D>
 __global__ void __launch_bounds__(kThreadsC)
 leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
-                   int n, int s0, const int32_t* __restrict__ bin_count, const int32_t* __restrict__ items_q,
+                   int n, int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
                    const uint64_t* __restrict__ items_mask, KernelParams kp, int qc_max, int dm_max,
                    int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp, uint8_t* __restrict__ lflags,
                    unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items) {
     constexpr int DP = (D + 3) & ~3;
     constexpr int DH = (D + 1) / 2;  // 16-byte words per slot pair
     const int b = blockIdx.x;
-    const int cnt = bin_count[b];
+    const int cnt = bin_off[(b + 1) * kBinSlots] - bin_off[b * kBinSlots];
     const int nchunks = (cnt + qc_max - 1) / qc_max;
     if ((int)blockIdx.y >= nchunks) return;
 
@@ -198,7 +258,7 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
         }
     }
     const uint64_t nc2 = f2_pack(kp.neg_c, kp.neg_c);
-    const size_t base = (size_t)b * n;
+    const size_t base = (size_t)bin_off[b * kBinSlots];
     // Warp 0 holds the next chunk's items (query, mask, index, coordinates) in
     // registers: their global loads overlap the current chunk's work.
     int nx_q = -1, nx_i = 0;
@@ -388,7 +448,7 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
     leaf_finish_kernel<D><<<grid, kThreadsC, smem, s>>>(
-        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_count, ws.items_q, ws.items_mask, kp, qc, t->dm,
+        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_off, ws.items_q, ws.items_mask, kp, qc, t->dm,
         ws.leaf_pos, ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
     return cudaGetLastError();
@@ -420,7 +480,20 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
     const auto& ws = t->ws;
     descend_top_kernel<<<(int)blocks, warps * 32, smem, s>>>(ws.binsum, (int)t->n, t->nb, t->s0, t->perm, kp,
                                                             with_samples, d_deg, ws.degf, ws.flags, ws.leaf_pos,
-                                                            ws.ksmp, ws.bin_count, ws.items_q, ws.items_mask);
+                                                            ws.ksmp, ws.bin_count, ws.qitem_bin, ws.qitem_mask,
+                                                            ws.qitem_cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const auto& ws = t->ws;
+    scan_bins_kernel<<<1, 1024, 0, s>>>(ws.bin_count, t->nb * kBinSlots, ws.bin_off);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (t->n + 3) / 4;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    scatter_items_kernel<<<(int)blocks, 128, 0, s>>>(ws.qitem_bin, ws.qitem_mask, ws.qitem_cnt, (int)t->n, kp.L,
+                                                     ws.bin_off, ws.bin_cursor, ws.items_q, ws.items_mask);
     return cudaGetLastError();
 }
 

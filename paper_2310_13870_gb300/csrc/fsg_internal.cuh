@@ -12,6 +12,9 @@
 namespace fsg {
 
 constexpr int kMaxL = 64;
+// Item counters/cursors per bin are split into this many sub-slots (chosen by
+// the query index) so that concurrent atomics spread over more addresses.
+constexpr int kBinSlots = 16;
 constexpr int kMaxFmaDim = 16;       // FP32 FMA tiles are compiled for d <= 16
 constexpr int kStatusTimeout = FSG_ERR_TIMEOUT;
 // Upper bound on mbarrier polls before a wait gives up (each poll is a
@@ -31,9 +34,14 @@ struct Workspace {
     int32_t* leaf_pos = nullptr;    // [n][L]    sampled neighbour position or -1
     float* ksmp = nullptr;          // [n][L]    kernel value k(x_i, x_j) of each sample
     uint8_t* lflags = nullptr;      // [n][L]    flags of the leaf-finish decisions
-    int32_t* bin_count = nullptr;   // [nb]       items per bin
-    int32_t* items_q = nullptr;     // [nb][n]    per-bin lists: query position
-    uint64_t* items_mask = nullptr; // [nb][n]    per-bin lists: samples of that query there
+    int32_t* qitem_bin = nullptr;   // [n][L]     per query: distinct bins its samples reached
+    uint64_t* qitem_mask = nullptr; // [n][L]     per query: mask of its samples at each
+    int32_t* qitem_cnt = nullptr;   // [n]        per query: number of such bins
+    int32_t* bin_count = nullptr;   // [nb][kBinSlots]   items per (bin, sub-slot)
+    int32_t* bin_cursor = nullptr;  // [nb][kBinSlots]   scatter cursors
+    int32_t* bin_off = nullptr;     // [nb*kBinSlots+1]  segment offsets
+    int32_t* items_q = nullptr;     // [max_items] query position, grouped by bin
+    uint64_t* items_mask = nullptr; // [max_items] samples of that query at the bin
     int32_t* uniq = nullptr;        // [n][L]    per-query sorted distinct neighbours
     float* uniq_w = nullptr;        // [n][L]
     int32_t* ucnt = nullptr;        // [n]
@@ -97,6 +105,7 @@ cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaS
 bool kde_bins_sym_supported(const fsg_tree* t);
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
                                cudaStream_t s);
+cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
                          int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);

@@ -38,6 +38,7 @@ EXPORTED = [
     "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info",
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
+    "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
 ]
 FSG_NUM_PHASES = 8
 PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "unused"]
@@ -58,6 +59,14 @@ class fsg_params(ctypes.Structure):
 
 class fsg_tree_opts(ctypes.Structure):
     _fields_ = [("d_perm", ctypes.c_void_p), ("leaf_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class fsg_batch_item(ctypes.Structure):
+    _fields_ = [("d_points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("params", fsg_params), ("seed", ctypes.c_uint64), ("edge_mode", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p),
+                ("d_w", ctypes.c_void_p), ("cap", ctypes.c_int64), ("d_m_out", ctypes.c_void_p),
+                ("d_deg", ctypes.c_void_p), ("d_stats", ctypes.c_void_p)]
 
 
 STATS_FIELDS = ["n_samples", "n_flagged", "n_self", "n_empty", "n_evals", "n_items", "n_edges", "status"]
@@ -100,8 +109,12 @@ def load(path: str = LIB_PATH):
     lib.fsg_profile.argtypes = [P, ctypes.c_int]
     lib.fsg_profile_read.argtypes = [P, P, P]
     lib.fsg_degrees_noalloc.argtypes = [P, I64, I32, P, P, P]
+    lib.fsg_batch_create.argtypes = [P, I32, I32, I32, P, ctypes.POINTER(P)]
+    lib.fsg_batch_run.argtypes = [P, P]
+    lib.fsg_batch_destroy.argtypes = [P]
+    lib.fsg_batch_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree"):
+        if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -288,3 +301,51 @@ def fsg_build_graph_host(points: np.ndarray, p: fsg_params, L: int, seed: int, e
                                        src.shape[0], ctypes.byref(m), _stream_ptr(stream)), "fsg_build_graph_host")
     k = int(m.value)
     return src[:k], dst[:k], w[:k]
+
+
+class Batch:
+    """Graph builds of many point sets (fsg_batch_*).  `sets` is a list of
+    (points CUDA float32 [n][d], fsg_params, L, seed); output buffers are
+    allocated here and reused by every run()."""
+
+    def __init__(self, sets, edge_mode: int = FSG_EDGES_SET, streams: int = 4, capture: bool = True, stream=None):
+        lib = load()
+        self.sets = sets
+        self.bufs = []
+        arr = (fsg_batch_item * len(sets))()
+        for i, (pts, p, L, seed) in enumerate(sets):
+            b = GraphBuffers(pts.shape[0], L, with_aux=False)
+            b.deg = __import__("torch").empty(pts.shape[0], dtype=__import__("torch").float64, device="cuda")
+            self.bufs.append(b)
+            it = arr[i]
+            it.d_points = pts.data_ptr()
+            it.n = pts.shape[0]
+            it.d = pts.shape[1]
+            it.L = L
+            it.params = p
+            it.seed = seed
+            it.edge_mode = edge_mode
+            it.d_src, it.d_dst, it.d_w = b.src.data_ptr(), b.dst.data_ptr(), b.w.data_ptr()
+            it.cap = b.cap
+            it.d_m_out = b.m.data_ptr()
+            it.d_deg = b.deg.data_ptr()
+            it.d_stats = b.stats.data_ptr()
+        self._items = arr
+        h = ctypes.c_void_p()
+        _check(lib.fsg_batch_create(arr, len(sets), streams, int(capture), _stream_ptr(stream), ctypes.byref(h)),
+               "fsg_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(load().fsg_batch_run(self.handle, _stream_ptr(stream)), "fsg_batch_run")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.fsg_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
