@@ -71,13 +71,13 @@ void begin_call(fsg_tree* t) {
 
 // Bin pass: the symmetric kernel (each pair once) when bins hold <= 128 points.
 cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (t->d > kMaxFmaDim) return launch_kde_bins_generic(t, kp, s);
     if (kde_bins_sym_supported(t)) return launch_kde_bins_sym(t, kp, s);
     return launch_kde_bins(t, kp, s);
 }
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 || p->precision == FSG_PREC_EXACT_INT) return FSG_ERR_UNSUPPORTED;
-    if (!kde_bins_supported(t)) return FSG_ERR_UNSUPPORTED;
     if (p->schedule != FSG_SCHED_FUSED) return FSG_ERR_UNSUPPORTED;
     return FSG_OK;
 }
@@ -109,6 +109,7 @@ int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
         {(void**)&ws.bin_off, sizeof(int32_t) * (size_t)(nb * kBinSlots + 1)},
         {(void**)&ws.items_q, sizeof(int32_t) * (size_t)max_items},
         {(void**)&ws.items_mask, sizeof(uint64_t) * (size_t)max_items},
+        {(void**)&ws.leafv, t->d > kMaxFmaDim ? sizeof(float) * (size_t)max_items * ((size_t)1 << t->dm) : 0},
         {(void**)&ws.uniq, sizeof(int32_t) * (size_t)n * Lc},
         {(void**)&ws.uniq_w, sizeof(float) * (size_t)n * Lc},
         {(void**)&ws.ucnt, sizeof(int32_t) * (size_t)n},
@@ -176,6 +177,7 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
     if (leaf_max && (leaf_max < 64 || leaf_max > 1024 || (leaf_max & (leaf_max - 1)))) return FSG_ERR_INVALID_ARG;
     const bool auto_leaf = leaf_max == 0;
     if (auto_leaf) leaf_max = 128;
+    if (d > kMaxFmaDim && leaf_max < 128) leaf_max = 128;  // the d > 16 tiles assume bins of > 64 points
     auto pick = [&](int lm, int& s0) {
         s0 = 0;
         while ((n + (int64_t(1) << s0) - 1) >> s0 > lm) ++s0;
@@ -313,7 +315,11 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cuda
     }
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_LEAF, s);
-        e = launch_leaf_finish(t, kp, s);
+        if (t->d > kMaxFmaDim) {
+            e = launch_leaf_values_generic(t, kp, s);
+            t->launches += 1;
+        }
+        if (e == cudaSuccess) e = launch_leaf_finish(t, kp, s);
         t->launches += 1;
     }
     return status_of(e);

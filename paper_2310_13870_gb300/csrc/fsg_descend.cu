@@ -202,11 +202,14 @@ struct LeafSmem {
 // per-query trees are summed upwards in shared memory (rows of odd stride, so
 // the lanes' stores hit distinct banks); then one thread per (query, sample)
 // takes the remaining decisions and forms the weight w = k / p_hat (Eq. 2).
-template <int D>
+// FROM_GLOBAL: the leaf values were computed by another kernel (any d) and
+// are read from leafv[item][slot] instead of being evaluated here.
+template <int D, bool FROM_GLOBAL>
 __global__ void __launch_bounds__(kThreadsC)
 leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
                    int n, int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
-                   const uint64_t* __restrict__ items_mask, KernelParams kp, int qc_max, int dm_max,
+                   const uint64_t* __restrict__ items_mask, const float* __restrict__ leafv, KernelParams kp,
+                   int qc_max, int dm_max,
                    int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp, uint8_t* __restrict__ lflags,
                    unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items) {
     constexpr int DP = (D + 3) & ~3;
@@ -238,7 +241,7 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
     const int dm = ceil_log2_dev(m);
     const int leaf0 = 1 << dm;
     // Slot table and pair-interleaved point coordinates.
-    for (int sl = tid; sl < 4 * ((leaf0 + 3) / 4); sl += kThreadsC) {
+    for (int sl = tid; !FROM_GLOBAL && sl < 4 * ((leaf0 + 3) / 4); sl += kThreadsC) {
         int a = 0, c = m;  // walk the slot's path bits from the root
         for (int t = dm - 1; t >= 0; --t) {
             const int mid = a + (c - a) / 2;
@@ -271,8 +274,10 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
             nx_q = items_q[base + it];
             nx_m = items_mask[base + it];
             nx_i = perm[nx_q];
+            if (!FROM_GLOBAL) {
 #pragma unroll
-            for (int t = 0; t < D; ++t) nx_x[t] = Xt[(size_t)nx_q * DP + t];
+                for (int t = 0; t < D; ++t) nx_x[t] = Xt[(size_t)nx_q * DP + t];
+            }
         }
     };
     if (tid < 32) fetch(blockIdx.y);
@@ -285,14 +290,22 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 qpos[lane] = nx_q;
                 qidx[lane] = nx_i;
                 qmask[lane] = nx_m;
+                if (!FROM_GLOBAL) {
 #pragma unroll
-                for (int t = 0; t < D; ++t) qco[lane * DP + t] = nx_x[t];
+                    for (int t = 0; t < D; ++t) qco[lane * DP + t] = nx_x[t];
+                }
             }
             fetch(chunk + gridDim.y);
         }
         __syncthreads();
+        if (FROM_GLOBAL) {
+            for (int e = tid; e < qcnt * leaf0; e += kThreadsC) {
+                const int qq = e >> dm, sl = e & (leaf0 - 1);
+                V[(size_t)qq * vs + leaf0 + sl] = leafv[(base + it0 + qq) * (size_t)leafmax + sl];
+            }
+        }
         // Kernel values: lane = query, warp w = slot pairs w, w + 8, ...
-        if (lane < qc_max) {
+        if (!FROM_GLOBAL && lane < qc_max) {
             const bool qv = lane < qcnt;
             const int my_pos = qv ? qpos[lane] : -2;
             uint64_t qd[D];
@@ -350,7 +363,7 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
             }
         }
         __syncthreads();
-        for (int lev = dm - 3; lev >= 0; --lev) {
+        for (int lev = FROM_GLOBAL ? dm - 1 : dm - 3; lev >= 0; --lev) {
             const int cn = qcnt << lev;
             for (int e = tid; e < cn; e += kThreadsC) {
                 const int qq = e >> lev;
@@ -427,14 +440,14 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
     }
 }
 
-template <int D>
+template <int D, bool FROM_GLOBAL = false>
 cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cudaStream_t s) {
     constexpr int DH = (D + 1) / 2;
     const size_t smem = LeafSmem(1 << t->dm, DH, qc).total;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D, FROM_GLOBAL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -447,8 +460,8 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
-    leaf_finish_kernel<D><<<grid, kThreadsC, smem, s>>>(
-        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_off, ws.items_q, ws.items_mask, kp, qc, t->dm,
+    leaf_finish_kernel<D, FROM_GLOBAL><<<grid, kThreadsC, smem, s>>>(
+        t->Xt, t->perm, t->bnd, (int)t->n, t->s0, ws.bin_off, ws.items_q, ws.items_mask, ws.leafv, kp, qc, t->dm,
         ws.leaf_pos, ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
     return cudaGetLastError();
@@ -516,7 +529,7 @@ cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaSt
         case 14: return launch_leaf_d<14>(t, kp, qt, s);
         case 15: return launch_leaf_d<15>(t, kp, qt, s);
         case 16: return launch_leaf_d<16>(t, kp, qt, s);
-        default: return cudaErrorInvalidValue;
+        default: return launch_leaf_d<1, true>(t, kp, qt, s);  // d > 16: values from leaf_values_generic
     }
 }
 

@@ -42,6 +42,7 @@ struct Workspace {
     int32_t* bin_off = nullptr;     // [nb*kBinSlots+1]  segment offsets
     int32_t* items_q = nullptr;     // [max_items] query position, grouped by bin
     uint64_t* items_mask = nullptr; // [max_items] samples of that query at the bin
+    float* leafv = nullptr;         // [max_items][2^dm] leaf values (d > 16 only)
     int32_t* uniq = nullptr;        // [n][L]    per-query sorted distinct neighbours
     float* uniq_w = nullptr;        // [n][L]
     int32_t* ucnt = nullptr;        // [n]
@@ -111,7 +112,8 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
                          int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
                            fsg_stats* d_stats, cudaStream_t s);
-cudaError_t launch_levelwise(const fsg_tree* t, const KernelParams& kp, double* d_deg, cudaStream_t s);
+cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -144,7 +144,7 @@ def test_leaf_sizes_give_identical_samples(fsg, leaf_max):
     check_degrees(g["deg"][q], ora.degrees(X, gam, queries=q), 3001)
 
 
-@pytest.mark.parametrize("d", [1, 4, 7, 16])
+@pytest.mark.parametrize("d", [1, 4, 7, 16, 17, 33, 64])
 def test_dimensions(fsg, d):
     X = inputs.gaussian_mixture(n=900, d=d, k=3, box=2.0, seed=d)
     sigma = 0.4 * math.sqrt(d)
@@ -153,6 +153,18 @@ def test_dimensions(fsg, d):
     o = ora.build_graph(X, gam, 10, d)
     check_degrees(g["deg"], o["deg"], 900)
     check_samples(g["samples"], g["flags"], o["samples"])
+
+
+def test_digit_like_d784(fsg):
+    # 784-dimensional 8-bit images, sigma = median pairwise distance / 2.
+    X = inputs.digit_like(n=2500, seed=3)
+    sigma = inputs.median_pair_distance(X, m=1024) / 2
+    gam = ora.gamma(sigma)
+    g = gpu_graph(fsg, X, sigma, 16, 5)
+    q = np.arange(0, 2500, 11)
+    check_degrees(g["deg"][q], ora.degrees(X, gam, queries=q), 2500)
+    smp, _, _ = ora.sample(X, gam, 16, 5, queries=q)
+    check_samples(g["samples"][q], g["flags"][q], smp)
 
 
 # ----------------------------------------------------------------------------
