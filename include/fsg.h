@@ -49,6 +49,7 @@ extern "C" {
 #define FSG_ERR_BUSY 6          /* server: no slot or budget for the request      */
 #define FSG_ERR_CAPACITY 7      /* an output buffer is too small                  */
 #define FSG_ERR_SCRATCH 8       /* problem too large for fsg_degrees_noalloc      */
+#define FSG_ERR_CANCELLED 9     /* server: the request was cancelled              */
 
 /* ---- option values ----------------------------------------------------- */
 /* Bandwidth convention: gamma = 1/(2 sigma^2) (default) or 1/sigma^2, the form
@@ -269,6 +270,67 @@ int fsg_batch_create(const fsg_batch_item* items, int32_t count, int32_t streams
                      void* stream, fsg_batch** out);
 int fsg_batch_run(fsg_batch* batch, void* stream);
 void fsg_batch_destroy(fsg_batch* batch);
+
+/*
+ * Serving: a request loop inside the library.  Graph-build requests (host
+ * points, host outputs) of different n and d are queued; a worker thread
+ * admits them in arrival order whenever a slot (a stream) is free and the
+ * request's device memory estimate fits the HBM budget next to the requests
+ * in flight.  Admitted requests run concurrently on their slots' streams, so
+ * their kernels overlap on the GPU; device memory comes from the server's own
+ * stream-ordered pool, so admitting and retiring requests never synchronizes
+ * the device.  A request's result (edge list in its host buffers, latency) is
+ * reported by fsg_server_poll once its edges are on the host.  Each result is
+ * the one fsg_build_graph_host gives for the same request alone.
+ */
+typedef struct {
+    int64_t hbm_budget_bytes;        /* device bytes for requests in flight (> 0)    */
+    int32_t max_slots;               /* requests in flight at once, 1..64            */
+    int32_t queue_cap;               /* pending requests before BUSY (0 = 65536)     */
+    int32_t inject_alloc_fail_every; /* testing: every k-th admission fails with OOM */
+    int32_t reserved[5];
+} fsg_server_opts;
+
+typedef struct {
+    const float* h_points;  /* host float32 [n][d]; valid until the result is polled */
+    int64_t n;
+    int32_t d;
+    int32_t L;              /* 1..64                                          */
+    fsg_params params;
+    uint64_t seed;
+    int32_t edge_mode;
+    int32_t reserved0;
+    int32_t* h_src;         /* host int32 [cap] (pinned memory is faster)     */
+    int32_t* h_dst;         /* host int32 [cap]                               */
+    float* h_w;             /* host float32 [cap]                             */
+    int64_t cap;            /* >= n * L                                       */
+} fsg_request;
+
+typedef struct {
+    uint64_t id;
+    int32_t status;         /* FSG_OK or an FSG_ERR_* code                     */
+    int32_t reserved0;
+    int64_t n_edges;
+    int64_t n_flagged;
+    double latency_ms;      /* submission -> edges on the host                */
+    double queue_ms;        /* submission -> admission                        */
+} fsg_result;
+
+typedef struct fsg_server fsg_server; /* opaque */
+
+/* Errors: INVALID_ARG, OOM, CUDA. */
+int fsg_server_create(const fsg_server_opts* opts, fsg_server** out);
+/* Errors: INVALID_ARG (malformed request), CAPACITY (cap < n L),
+ * BUSY (queue full, or the request alone exceeds the HBM budget). */
+int fsg_server_submit(fsg_server* server, const fsg_request* req, uint64_t* id_out);
+/* Up to max finished results into out; waits up to wait_ms for the first. */
+int fsg_server_poll(fsg_server* server, fsg_result* out, int32_t max, int32_t* count_out, int32_t wait_ms);
+/* A pending request is dropped (its result has status FSG_ERR_CANCELLED); a
+ * request in flight completes and is then reported as cancelled. */
+int fsg_server_cancel(fsg_server* server, uint64_t id);
+int fsg_server_info(fsg_server* server, int64_t* pending, int64_t* in_flight, int64_t* bytes_in_use);
+/* Waits for requests in flight, drops pending ones, frees everything. */
+void fsg_server_destroy(fsg_server* server);
 
 /*
  * Waits for the stream and returns the tree's device status word

@@ -82,55 +82,81 @@ int check_path(const fsg_tree* t, const fsg_params* p) {
     return FSG_OK;
 }
 
+cudaError_t tree_malloc(fsg_tree* t, void** p, size_t bytes, cudaStream_t s) {
+    if (t->pool) return cudaMallocFromPoolAsync(p, bytes, t->pool, s);
+    return cudaMalloc(p, bytes);
+}
+
+void tree_free(fsg_tree* t, void* p) {
+    if (!p) return;
+    if (t->pool) cudaFreeAsync(p, t->alloc_stream);
+    else cudaFree(p);
+}
+
+}  // namespace
+
+// Byte sizes of the workspace carve-outs, in carve order (shared by the
+// allocation and the server's admission estimate).
+namespace {
+constexpr int kWsParts = 23;
+void workspace_sizes(int64_t n, int d, int dm, int nb, int64_t Lc, size_t (&sz)[kWsParts]) {
+    const int64_t max_items = n * (Lc < nb ? Lc : nb);  // distinct (query, bin) pairs
+    const int64_t nblocks = (n + 1023) / 1024 + 2;
+    const size_t v[kWsParts] = {
+        sizeof(float) * (size_t)n * nb,                       // binsum
+        sizeof(float) * (size_t)n,                            // degf
+        sizeof(uint8_t) * (size_t)n * Lc,                     // flags
+        sizeof(int32_t) * (size_t)n * Lc,                     // leaf_pos
+        sizeof(float) * (size_t)n * Lc,                       // ksmp
+        sizeof(uint8_t) * (size_t)n * Lc,                     // lflags
+        sizeof(int32_t) * (size_t)n * Lc,                     // qitem_bin
+        sizeof(uint64_t) * (size_t)n * Lc,                    // qitem_mask
+        sizeof(int32_t) * (size_t)n,                          // qitem_cnt
+        sizeof(int32_t) * (size_t)nb * kBinSlots,             // bin_count
+        sizeof(int32_t) * (size_t)nb * kBinSlots,             // bin_cursor
+        sizeof(int32_t) * (size_t)(nb * kBinSlots + 1),       // bin_off
+        sizeof(int32_t) * (size_t)max_items,                  // items_q
+        sizeof(uint64_t) * (size_t)max_items,                 // items_mask
+        d > kMaxFmaDim ? sizeof(float) * (size_t)max_items * ((size_t)1 << dm) : 0,  // leafv
+        sizeof(int32_t) * (size_t)n * Lc,                     // uniq
+        sizeof(float) * (size_t)n * Lc,                       // uniq_w
+        sizeof(int32_t) * (size_t)n,                          // ucnt
+        sizeof(uint64_t) * (size_t)n,                         // emit_mask
+        sizeof(int64_t) * (size_t)(n + 1),                    // ecount
+        sizeof(int64_t) * (size_t)nblocks,                    // scan_tmp
+        sizeof(fsg_stats),                                    // stats
+        sizeof(int32_t) * 8,                                  // misc
+    };
+    for (int k = 0; k < kWsParts; ++k) sz[k] = v[k];
+}
 }  // namespace
 
 int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
     Workspace& ws = t->ws;
     if (ws.base && ws.cap_n >= t->n && ws.cap_L >= L) return FSG_OK;
-    const int64_t n = t->n;
     const int64_t Lc = L > ws.cap_L ? L : ws.cap_L;
-    const int64_t nb = t->nb;
-    const int64_t max_items = n * (Lc < nb ? Lc : nb);  // distinct (query, bin) pairs
-    const int64_t nblocks = (n + 1023) / 1024 + 2;
-    size_t off = 0;
-    struct Part { void** ptr; size_t bytes; };
-    Part parts[] = {
-        {(void**)&ws.binsum, sizeof(float) * (size_t)n * nb},
-        {(void**)&ws.degf, sizeof(float) * (size_t)n},
-        {(void**)&ws.flags, sizeof(uint8_t) * (size_t)n * Lc},
-        {(void**)&ws.leaf_pos, sizeof(int32_t) * (size_t)n * Lc},
-        {(void**)&ws.ksmp, sizeof(float) * (size_t)n * Lc},
-        {(void**)&ws.lflags, sizeof(uint8_t) * (size_t)n * Lc},
-        {(void**)&ws.qitem_bin, sizeof(int32_t) * (size_t)n * Lc},
-        {(void**)&ws.qitem_mask, sizeof(uint64_t) * (size_t)n * Lc},
-        {(void**)&ws.qitem_cnt, sizeof(int32_t) * (size_t)n},
-        {(void**)&ws.bin_count, sizeof(int32_t) * (size_t)nb * kBinSlots},
-        {(void**)&ws.bin_cursor, sizeof(int32_t) * (size_t)nb * kBinSlots},
-        {(void**)&ws.bin_off, sizeof(int32_t) * (size_t)(nb * kBinSlots + 1)},
-        {(void**)&ws.items_q, sizeof(int32_t) * (size_t)max_items},
-        {(void**)&ws.items_mask, sizeof(uint64_t) * (size_t)max_items},
-        {(void**)&ws.leafv, t->d > kMaxFmaDim ? sizeof(float) * (size_t)max_items * ((size_t)1 << t->dm) : 0},
-        {(void**)&ws.uniq, sizeof(int32_t) * (size_t)n * Lc},
-        {(void**)&ws.uniq_w, sizeof(float) * (size_t)n * Lc},
-        {(void**)&ws.ucnt, sizeof(int32_t) * (size_t)n},
-        {(void**)&ws.emit_mask, sizeof(uint64_t) * (size_t)n},
-        {(void**)&ws.ecount, sizeof(int64_t) * (size_t)(n + 1)},
-        {(void**)&ws.scan_tmp, sizeof(int64_t) * (size_t)nblocks},
-        {(void**)&ws.stats, sizeof(fsg_stats)},
-        {(void**)&ws.misc, sizeof(int32_t) * 8},
+    size_t sz[kWsParts];
+    workspace_sizes(t->n, t->d, t->dm, t->nb, Lc, sz);
+    void** ptrs[kWsParts] = {
+        (void**)&ws.binsum, (void**)&ws.degf, (void**)&ws.flags, (void**)&ws.leaf_pos, (void**)&ws.ksmp,
+        (void**)&ws.lflags, (void**)&ws.qitem_bin, (void**)&ws.qitem_mask, (void**)&ws.qitem_cnt,
+        (void**)&ws.bin_count, (void**)&ws.bin_cursor, (void**)&ws.bin_off, (void**)&ws.items_q,
+        (void**)&ws.items_mask, (void**)&ws.leafv, (void**)&ws.uniq, (void**)&ws.uniq_w, (void**)&ws.ucnt,
+        (void**)&ws.emit_mask, (void**)&ws.ecount, (void**)&ws.scan_tmp, (void**)&ws.stats, (void**)&ws.misc,
     };
-    size_t offs[sizeof(parts) / sizeof(parts[0])];
-    for (size_t k = 0; k < sizeof(parts) / sizeof(parts[0]); ++k) {
+    size_t offs[kWsParts];
+    size_t off = 0;
+    for (int k = 0; k < kWsParts; ++k) {
         offs[k] = off;
-        off = align_up(off + parts[k].bytes, 256);
+        off = align_up(off + sz[k], 256);
     }
     if (ws.base) {
-        cudaStreamSynchronize(s);
-        cudaFree(ws.base);
+        if (!t->pool) cudaStreamSynchronize(s);
+        tree_free(t, ws.base);
         ws.base = nullptr;
     }
     void* base = nullptr;
-    cudaError_t e = cudaMalloc(&base, off);
+    cudaError_t e = tree_malloc(t, &base, off, t->pool ? t->alloc_stream : s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ws.cap_n = ws.cap_L = 0;
@@ -138,11 +164,34 @@ int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
     }
     ws.base = base;
     ws.bytes = off;
-    for (size_t k = 0; k < sizeof(parts) / sizeof(parts[0]); ++k)
-        *parts[k].ptr = static_cast<char*>(base) + offs[k];
-    ws.cap_n = n;
+    for (int k = 0; k < kWsParts; ++k) *ptrs[k] = static_cast<char*>(base) + offs[k];
+    ws.cap_n = t->n;
     ws.cap_L = Lc;
     return FSG_OK;
+}
+
+// Device bytes a tree of n points in d dimensions and its workspace for L
+// samples take (the geometry of build_tree_internal with automatic leaf_max).
+size_t tree_bytes_estimate(int64_t n, int32_t d, int32_t L) {
+    int leaf_max = 128;
+    auto pick = [&](int lm) {
+        int s0 = 0;
+        while ((n + (int64_t(1) << s0) - 1) >> s0 > lm) ++s0;
+        return s0;
+    };
+    int s0 = pick(leaf_max);
+    while (s0 > 11 && leaf_max < 1024) { leaf_max *= 2; s0 = pick(leaf_max); }
+    const int nb = 1 << s0;
+    const int mmax = (int)((n + nb - 1) / nb);
+    const int dm = ceil_log2_host(mmax);
+    const int64_t n_pad = (n + 127) / 128 * 128;
+    const int dp = (d + 3) & ~3;
+    size_t tot = sizeof(float) * (size_t)n_pad * dp * (d <= kMaxFmaDim ? 3 : 1) + sizeof(int32_t) * 2 * (size_t)n +
+                 sizeof(int32_t) * (size_t)(nb + 1) + 64;
+    size_t sz[kWsParts];
+    workspace_sizes(n, d, dm, nb, L, sz);
+    for (int k = 0; k < kWsParts; ++k) tot += align_up(sz[k], 256);
+    return tot + 4096 * 8;
 }
 
 }  // namespace fsg
@@ -164,12 +213,20 @@ const char* fsg_error_string(int status) {
         case FSG_ERR_BUSY: return "no slot or memory budget available";
         case FSG_ERR_CAPACITY: return "output buffer too small";
         case FSG_ERR_SCRATCH: return "problem too large for the fixed scratch of fsg_degrees_noalloc";
+        case FSG_ERR_CANCELLED: return "request cancelled";
         default: return "unknown status";
     }
 }
 
 int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts, void* stream,
                    fsg_tree** out) {
+    return fsg::build_tree_internal(d_points, n, d, opts, (cudaStream_t)stream, nullptr, out);
+}
+
+}  // extern "C"
+
+int fsg::build_tree_internal(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts, cudaStream_t s,
+                             cudaMemPool_t pool, fsg_tree** out) {
     if (!out) return FSG_ERR_INVALID_ARG;
     *out = nullptr;
     if (!d_points || n < 1 || n > (int64_t)0x7fffffff - 4096 || d < 1 || d > 4096) return FSG_ERR_INVALID_ARG;
@@ -186,9 +243,10 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
     pick(leaf_max, s0);
     while (auto_leaf && s0 > 11 && leaf_max < 1024) { leaf_max *= 2; pick(leaf_max, s0); }
     if (s0 > 12) return FSG_ERR_UNSUPPORTED;
-    cudaStream_t s = (cudaStream_t)stream;
     fsg_tree* t = new (std::nothrow) fsg_tree();
     if (!t) return FSG_ERR_OOM;
+    t->pool = pool;
+    t->alloc_stream = s;
     t->n = n;
     t->d = d;
     t->dp = (d + 3) & ~3;
@@ -202,7 +260,7 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
     cudaGetDevice(&t->device);
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+        if (e == cudaSuccess) e = tree_malloc(t, p, bytes, s);
     };
     alloc((void**)&t->Xt, sizeof(float) * (size_t)t->n_pad * t->dp);
     if (d <= kMaxFmaDim) alloc((void**)&t->Xdup, sizeof(float) * 2 * (size_t)t->n_pad * t->dp);
@@ -232,19 +290,21 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
     return FSG_OK;
 }
 
+extern "C" {
+
 void fsg_free_tree(fsg_tree* t) {
     if (!t) return;
     for (int k = 0; k < FSG_NUM_PHASES; ++k) {
         if (t->ev_start[k]) cudaEventDestroy(t->ev_start[k]);
         if (t->ev_end[k]) cudaEventDestroy(t->ev_end[k]);
     }
-    cudaFree(t->Xt);
-    cudaFree(t->Xdup);
-    cudaFree(t->perm);
-    cudaFree(t->inv);
-    cudaFree(t->bnd);
-    cudaFree(t->status);
-    cudaFree(t->ws.base);
+    tree_free(t, t->Xt);
+    tree_free(t, t->Xdup);
+    tree_free(t, t->perm);
+    tree_free(t, t->inv);
+    tree_free(t, t->bnd);
+    tree_free(t, t->status);
+    tree_free(t, t->ws.base);
     delete t;
 }
 

@@ -82,6 +82,11 @@ struct fsg_tree {
     cudaEvent_t ev_end[FSG_NUM_PHASES] = {};
     bool ev_used[FSG_NUM_PHASES] = {};
     int64_t launches = 0;
+    // Stream-ordered allocation (used by the server): when set, every device
+    // buffer of this tree comes from `pool` on `alloc_stream` and is returned
+    // with cudaFreeAsync, so creating and freeing trees never synchronizes.
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t alloc_stream = nullptr;
 };
 
 namespace fsg {
@@ -99,6 +104,9 @@ struct KernelParams {
 };
 
 int ensure_workspace(fsg_tree* t, int L, cudaStream_t s);
+int build_tree_internal(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts, cudaStream_t s,
+                        cudaMemPool_t pool, fsg_tree** out);
+size_t tree_bytes_estimate(int64_t n, int32_t d, int32_t L);
 cudaError_t launch_tree_prep(fsg_tree* t, const float* d_points, const int32_t* d_perm, cudaStream_t s);
 cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 bool kde_bins_supported(const fsg_tree* t);

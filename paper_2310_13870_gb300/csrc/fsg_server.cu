@@ -1,0 +1,366 @@
+// Serving runtime (fsg_server_*): a worker thread admits graph-build requests
+// by slot and HBM budget, runs each on its slot's stream (requests overlap on
+// the device), allocates from a private stream-ordered pool (no device-wide
+// synchronization when requests come and go), and retires them in two stages:
+// (1) graph built and its edge count on the host, (2) the edges on the host.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "fsg_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Pending {
+    uint64_t id;
+    fsg_request req;
+    Clock::time_point t_submit;
+    size_t bytes;
+};
+
+struct Slot {
+    int state = 0;  // 0 idle, 1 building (waiting for ev_built), 2 copying edges (waiting for ev_done)
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_built = nullptr, ev_done = nullptr;
+    int64_t* h_m = nullptr;         // pinned: edge count
+    fsg_stats* h_stats = nullptr;   // pinned: statistics
+    Pending p;
+    Clock::time_point t_admit;
+    bool cancel = false;
+    fsg_tree* tree = nullptr;
+    float* d_points = nullptr;
+    int32_t* d_src = nullptr;
+    int32_t* d_dst = nullptr;
+    float* d_w = nullptr;
+    int64_t* d_m = nullptr;
+    fsg_stats* d_stats = nullptr;
+};
+
+size_t request_bytes(const fsg_request& r) {
+    return fsg::tree_bytes_estimate(r.n, r.d, r.L) + sizeof(float) * (size_t)r.n * r.d +
+           (sizeof(int32_t) * 2 + sizeof(float)) * (size_t)r.n * r.L + 4096;
+}
+
+}  // namespace
+
+struct fsg_server {
+    fsg_server_opts opts{};
+    int device = 0;
+    cudaMemPool_t pool = nullptr;
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Pending> pending;
+    std::deque<fsg_result> done;
+    std::vector<uint64_t> cancel_ids;
+    uint64_t next_id = 1;
+    int64_t bytes_in_use = 0;
+    int64_t admissions = 0;
+    bool stop = false;
+    std::thread worker;
+
+    void finish(const Pending& p, int status, int64_t m, int64_t flagged, Clock::time_point t_admit) {
+        fsg_result r{};
+        r.id = p.id;
+        r.status = status;
+        r.n_edges = m;
+        r.n_flagged = flagged;
+        const auto now = Clock::now();
+        r.latency_ms = ms_since(p.t_submit, now);
+        r.queue_ms = ms_since(p.t_submit, t_admit);
+        std::lock_guard<std::mutex> lock(mu);
+        done.push_back(r);
+        cv_done.notify_all();
+    }
+
+    void release(Slot& s) {
+        if (s.tree) fsg_free_tree(s.tree);
+        s.tree = nullptr;
+        for (void* ptr : {(void*)s.d_points, (void*)s.d_src, (void*)s.d_dst, (void*)s.d_w, (void*)s.d_m,
+                          (void*)s.d_stats})
+            if (ptr) cudaFreeAsync(ptr, s.stream);
+        s.d_points = nullptr;
+        s.d_src = s.d_dst = nullptr;
+        s.d_w = nullptr;
+        s.d_m = nullptr;
+        s.d_stats = nullptr;
+        std::lock_guard<std::mutex> lock(mu);
+        bytes_in_use -= (int64_t)s.p.bytes;
+        s.state = 0;
+    }
+
+    // Enqueues the whole request on the slot's stream.
+    int admit(Slot& s) {
+        const fsg_request& r = s.p.req;
+        ++admissions;
+        if (opts.inject_alloc_fail_every > 0 && admissions % opts.inject_alloc_fail_every == 0) return FSG_ERR_OOM;
+        const size_t cap = (size_t)r.n * r.L;
+        cudaError_t e = cudaMallocFromPoolAsync((void**)&s.d_points, sizeof(float) * (size_t)r.n * r.d, pool, s.stream);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&s.d_src, sizeof(int32_t) * cap, pool, s.stream);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&s.d_dst, sizeof(int32_t) * cap, pool, s.stream);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&s.d_w, sizeof(float) * cap, pool, s.stream);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&s.d_m, sizeof(int64_t), pool, s.stream);
+        if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&s.d_stats, sizeof(fsg_stats), pool, s.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s.d_points, r.h_points, sizeof(float) * (size_t)r.n * r.d, cudaMemcpyHostToDevice,
+                                s.stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? FSG_ERR_OOM : FSG_ERR_CUDA;
+        }
+        int rc = fsg::build_tree_internal(s.d_points, r.n, r.d, nullptr, s.stream, pool, &s.tree);
+        if (rc != FSG_OK) return rc;
+        rc = fsg_build_graph(s.tree, &r.params, r.L, r.seed, r.edge_mode, s.d_src, s.d_dst, s.d_w, (int64_t)cap,
+                             s.d_m, nullptr, nullptr, nullptr, s.d_stats, s.stream);
+        if (rc != FSG_OK) return rc;
+        e = cudaMemcpyAsync(s.h_m, s.d_m, sizeof(int64_t), cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_stats, s.d_stats, sizeof(fsg_stats), cudaMemcpyDeviceToHost, s.stream);
+        if (e == cudaSuccess) e = cudaEventRecord(s.ev_built, s.stream);
+        return e == cudaSuccess ? FSG_OK : FSG_ERR_CUDA;
+    }
+
+    bool cancelled(uint64_t id) {
+        for (uint64_t c : cancel_ids)
+            if (c == id) return true;
+        return false;
+    }
+
+    void run() {
+        cudaSetDevice(device);
+        for (;;) {
+            bool progress = false;
+            for (Slot& s : slots) {
+                if (s.state == 1) {
+                    const cudaError_t q = cudaEventQuery(s.ev_built);
+                    if (q == cudaErrorNotReady) continue;
+                    progress = true;
+                    if (q != cudaSuccess) {
+                        cudaGetLastError();
+                        finish(s.p, FSG_ERR_CUDA, 0, 0, s.t_admit);
+                        release(s);
+                        continue;
+                    }
+                    const int64_t m = *s.h_m;
+                    const fsg_request& r = s.p.req;
+                    if (m > r.cap) {
+                        finish(s.p, FSG_ERR_CAPACITY, m, s.h_stats->n_flagged, s.t_admit);
+                        release(s);
+                        continue;
+                    }
+                    cudaError_t e = cudaSuccess;
+                    if (m > 0) {
+                        e = cudaMemcpyAsync(r.h_src, s.d_src, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s.stream);
+                        if (e == cudaSuccess)
+                            e = cudaMemcpyAsync(r.h_dst, s.d_dst, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s.stream);
+                        if (e == cudaSuccess)
+                            e = cudaMemcpyAsync(r.h_w, s.d_w, sizeof(float) * m, cudaMemcpyDeviceToHost, s.stream);
+                    }
+                    if (e == cudaSuccess) e = cudaEventRecord(s.ev_done, s.stream);
+                    if (e != cudaSuccess) {
+                        cudaGetLastError();
+                        finish(s.p, FSG_ERR_CUDA, 0, 0, s.t_admit);
+                        release(s);
+                        continue;
+                    }
+                    s.state = 2;
+                } else if (s.state == 2) {
+                    const cudaError_t q = cudaEventQuery(s.ev_done);
+                    if (q == cudaErrorNotReady) continue;
+                    progress = true;
+                    int status = q == cudaSuccess ? (int)s.h_stats->status : FSG_ERR_CUDA;
+                    if (q != cudaSuccess) cudaGetLastError();
+                    bool canc;
+                    {
+                        std::lock_guard<std::mutex> lock(mu);
+                        canc = cancelled(s.p.id);
+                    }
+                    if (canc && status == FSG_OK) status = FSG_ERR_CANCELLED;
+                    finish(s.p, status, *s.h_m, s.h_stats->n_flagged, s.t_admit);
+                    release(s);
+                }
+            }
+            // Admission: strict arrival order, slot and budget permitting.
+            for (;;) {
+                Slot* free_slot = nullptr;
+                for (Slot& s : slots)
+                    if (s.state == 0) { free_slot = &s; break; }
+                Pending p;
+                {
+                    std::unique_lock<std::mutex> lock(mu);
+                    if (!free_slot || pending.empty()) break;
+                    if (bytes_in_use + (int64_t)pending.front().bytes > opts.hbm_budget_bytes) break;
+                    p = pending.front();
+                    pending.pop_front();
+                    bytes_in_use += (int64_t)p.bytes;
+                }
+                progress = true;
+                Slot& s = *free_slot;
+                s.p = p;
+                s.t_admit = Clock::now();
+                s.state = 1;
+                const int rc = admit(s);
+                if (rc != FSG_OK) {
+                    // the slot's stream may hold partial work: let it drain before reuse
+                    cudaStreamSynchronize(s.stream);
+                    cudaGetLastError();
+                    finish(s.p, rc, 0, 0, s.t_admit);
+                    release(s);
+                }
+            }
+            {
+                std::unique_lock<std::mutex> lock(mu);
+                bool busy = false;
+                for (Slot& s : slots) busy |= s.state != 0;
+                if (stop && !busy) break;
+                if (!progress) {
+                    if (busy) cv_work.wait_for(lock, std::chrono::microseconds(50));
+                    else cv_work.wait_for(lock, std::chrono::milliseconds(5));
+                }
+            }
+        }
+    }
+};
+
+extern "C" {
+
+int fsg_server_create(const fsg_server_opts* opts, fsg_server** out) {
+    if (!out || !opts || opts->hbm_budget_bytes <= 0 || opts->max_slots < 1 || opts->max_slots > 64 ||
+        opts->queue_cap < 0 || opts->inject_alloc_fail_every < 0)
+        return FSG_ERR_INVALID_ARG;
+    *out = nullptr;
+    fsg_server* sv = new (std::nothrow) fsg_server();
+    if (!sv) return FSG_ERR_OOM;
+    sv->opts = *opts;
+    if (sv->opts.queue_cap == 0) sv->opts.queue_cap = 65536;
+    cudaGetDevice(&sv->device);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = sv->device;
+    cudaError_t e = cudaMemPoolCreate(&sv->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t keep = (uint64_t)opts->hbm_budget_bytes;  // memory stays cached in the pool up to the budget
+        e = cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    sv->slots.resize(opts->max_slots);
+    for (Slot& s : sv->slots) {
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_built, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.h_m, sizeof(int64_t), cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.h_stats, sizeof(fsg_stats), cudaHostAllocDefault);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fsg_server_destroy(sv);
+        return e == cudaErrorMemoryAllocation ? FSG_ERR_OOM : FSG_ERR_CUDA;
+    }
+    sv->worker = std::thread([sv] { sv->run(); });
+    *out = sv;
+    return FSG_OK;
+}
+
+int fsg_server_submit(fsg_server* sv, const fsg_request* r, uint64_t* id_out) {
+    if (!sv || !r || !id_out) return FSG_ERR_INVALID_ARG;
+    if (!r->h_points || r->n < 1 || r->d < 1 || r->d > 4096 || r->L < 1 || r->L > 64 || !r->h_src || !r->h_dst ||
+        !r->h_w)
+        return FSG_ERR_INVALID_ARG;
+    if (r->edge_mode != FSG_EDGES_SET && r->edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
+    const fsg_params& p = r->params;
+    if (!(p.sigma > 0.0) || p.sigma != p.sigma || p.sigma > 1e300) return FSG_ERR_INVALID_ARG;
+    if (r->cap < r->n * (int64_t)r->L) return FSG_ERR_CAPACITY;
+    Pending pd;
+    pd.req = *r;
+    pd.t_submit = Clock::now();
+    pd.bytes = request_bytes(*r);
+    if ((int64_t)pd.bytes > sv->opts.hbm_budget_bytes) return FSG_ERR_BUSY;  // could never be admitted
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        if ((int64_t)sv->pending.size() >= sv->opts.queue_cap) return FSG_ERR_BUSY;
+        pd.id = sv->next_id++;
+        sv->pending.push_back(pd);
+    }
+    sv->cv_work.notify_one();
+    *id_out = pd.id;
+    return FSG_OK;
+}
+
+int fsg_server_poll(fsg_server* sv, fsg_result* out, int32_t max, int32_t* count_out, int32_t wait_ms) {
+    if (!sv || !count_out || max < 0 || (max > 0 && !out)) return FSG_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lock(sv->mu);
+    if (sv->done.empty() && wait_ms > 0)
+        sv->cv_done.wait_for(lock, std::chrono::milliseconds(wait_ms), [sv] { return !sv->done.empty(); });
+    int32_t k = 0;
+    while (k < max && !sv->done.empty()) {
+        out[k++] = sv->done.front();
+        sv->done.pop_front();
+    }
+    *count_out = k;
+    return FSG_OK;
+}
+
+int fsg_server_cancel(fsg_server* sv, uint64_t id) {
+    if (!sv) return FSG_ERR_INVALID_ARG;
+    Pending dropped;
+    bool found = false;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        for (auto it = sv->pending.begin(); it != sv->pending.end(); ++it) {
+            if (it->id == id) {
+                dropped = *it;
+                sv->pending.erase(it);
+                found = true;
+                break;
+            }
+        }
+        if (!found) sv->cancel_ids.push_back(id);
+    }
+    if (found) sv->finish(dropped, FSG_ERR_CANCELLED, 0, 0, Clock::now());
+    return FSG_OK;
+}
+
+int fsg_server_info(fsg_server* sv, int64_t* pending, int64_t* in_flight, int64_t* bytes_in_use) {
+    if (!sv) return FSG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(sv->mu);
+    if (pending) *pending = (int64_t)sv->pending.size();
+    if (in_flight) {
+        int64_t c = 0;
+        for (const Slot& s : sv->slots) c += s.state != 0;
+        *in_flight = c;
+    }
+    if (bytes_in_use) *bytes_in_use = sv->bytes_in_use;
+    return FSG_OK;
+}
+
+void fsg_server_destroy(fsg_server* sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lock(sv->mu);
+        sv->stop = true;
+        sv->pending.clear();
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (Slot& s : sv->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.ev_built) cudaEventDestroy(s.ev_built);
+        if (s.ev_done) cudaEventDestroy(s.ev_done);
+        if (s.h_m) cudaFreeHost(s.h_m);
+        if (s.h_stats) cudaFreeHost(s.h_stats);
+    }
+    if (sv->pool) cudaMemPoolDestroy(sv->pool);
+    delete sv;
+}
+
+}  // extern "C"

@@ -25,6 +25,7 @@ FSG_ERR_UNSUPPORTED = 5
 FSG_ERR_BUSY = 6
 FSG_ERR_CAPACITY = 7
 FSG_ERR_SCRATCH = 8
+FSG_ERR_CANCELLED = 9
 
 FSG_TWO_SIGMA_SQ, FSG_SIGMA_SQ = 0, 1
 FSG_SELF_EXCLUDE, FSG_SELF_INCLUDE = 0, 1
@@ -39,6 +40,8 @@ EXPORTED = [
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
     "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
+    "fsg_server_create", "fsg_server_submit", "fsg_server_poll", "fsg_server_cancel", "fsg_server_info",
+    "fsg_server_destroy",
 ]
 FSG_NUM_PHASES = 8
 PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "unused"]
@@ -67,6 +70,24 @@ class fsg_batch_item(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p),
                 ("d_w", ctypes.c_void_p), ("cap", ctypes.c_int64), ("d_m_out", ctypes.c_void_p),
                 ("d_deg", ctypes.c_void_p), ("d_stats", ctypes.c_void_p)]
+
+
+class fsg_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("queue_cap", ctypes.c_int32),
+                ("inject_alloc_fail_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class fsg_request(ctypes.Structure):
+    _fields_ = [("h_points", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("params", fsg_params), ("seed", ctypes.c_uint64), ("edge_mode", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("h_src", ctypes.c_void_p), ("h_dst", ctypes.c_void_p),
+                ("h_w", ctypes.c_void_p), ("cap", ctypes.c_int64)]
+
+
+class fsg_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("n_edges", ctypes.c_int64), ("n_flagged", ctypes.c_int64), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double)]
 
 
 STATS_FIELDS = ["n_samples", "n_flagged", "n_self", "n_empty", "n_evals", "n_items", "n_edges", "status"]
@@ -113,8 +134,15 @@ def load(path: str = LIB_PATH):
     lib.fsg_batch_run.argtypes = [P, P]
     lib.fsg_batch_destroy.argtypes = [P]
     lib.fsg_batch_destroy.restype = None
+    lib.fsg_server_create.argtypes = [P, ctypes.POINTER(P)]
+    lib.fsg_server_submit.argtypes = [P, P, ctypes.POINTER(ctypes.c_uint64)]
+    lib.fsg_server_poll.argtypes = [P, P, I32, ctypes.POINTER(ctypes.c_int32), I32]
+    lib.fsg_server_cancel.argtypes = [P, ctypes.c_uint64]
+    lib.fsg_server_info.argtypes = [P, P, P, P]
+    lib.fsg_server_destroy.argtypes = [P]
+    lib.fsg_server_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy"):
+        if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy", "fsg_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -342,6 +370,86 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.fsg_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The library's request loop (fsg_server_*).  submit() takes host numpy
+    points and returns an id; the edge list lands in host buffers allocated
+    here (pinned) and is returned by poll() with the result record."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 8, queue_cap: int = 0,
+                 inject_alloc_fail_every: int = 0):
+        o = fsg_server_opts()
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        o.max_slots = max_slots
+        o.queue_cap = queue_cap
+        o.inject_alloc_fail_every = inject_alloc_fail_every
+        h = ctypes.c_void_p()
+        _check(load().fsg_server_create(ctypes.byref(o), ctypes.byref(h)), "fsg_server_create")
+        self.handle = h
+        self.live = {}  # id -> (points, src, dst, w) kept alive until polled
+
+    def submit(self, points: np.ndarray, p: fsg_params, L: int, seed: int, edge_mode: int = FSG_EDGES_SET,
+               pinned: bool = True) -> int:
+        import torch
+        X = np.ascontiguousarray(points, dtype=np.float32)
+        n, d = X.shape
+        cap = n * L
+        if pinned:
+            Xt = torch.from_numpy(X).pin_memory()
+            X = Xt.numpy()
+            src = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
+            dst = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
+            w = torch.empty(cap, dtype=torch.float32).pin_memory().numpy()
+        else:
+            src, dst, w = np.empty(cap, np.int32), np.empty(cap, np.int32), np.empty(cap, np.float32)
+        r = fsg_request()
+        r.h_points = X.ctypes.data
+        r.n, r.d, r.L = n, d, L
+        r.params = p
+        r.seed = seed
+        r.edge_mode = edge_mode
+        r.h_src, r.h_dst, r.h_w = src.ctypes.data, dst.ctypes.data, w.ctypes.data
+        r.cap = cap
+        rid = ctypes.c_uint64()
+        _check(load().fsg_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)), "fsg_server_submit")
+        self.live[rid.value] = (X, src, dst, w)
+        return rid.value
+
+    def poll(self, max_results: int = 256, wait_ms: int = 0):
+        """Returns a list of (result dict, (src, dst, w) numpy views)."""
+        arr = (fsg_result * max_results)()
+        cnt = ctypes.c_int32()
+        _check(load().fsg_server_poll(self.handle, arr, max_results, ctypes.byref(cnt), wait_ms), "fsg_server_poll")
+        out = []
+        for k in range(cnt.value):
+            r = arr[k]
+            rec = dict(id=r.id, status=r.status, n_edges=r.n_edges, n_flagged=r.n_flagged, latency_ms=r.latency_ms,
+                       queue_ms=r.queue_ms)
+            X, src, dst, w = self.live.pop(r.id, (None, None, None, None))
+            m = r.n_edges if r.status == FSG_OK else 0
+            out.append((rec, (src[:m], dst[:m], w[:m]) if src is not None else None))
+        return out
+
+    def cancel(self, rid: int):
+        _check(load().fsg_server_cancel(self.handle, ctypes.c_uint64(rid)), "fsg_server_cancel")
+
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().fsg_server_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "fsg_server_info")
+        return dict(pending=a.value, in_flight=b.value, bytes_in_use=c.value)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.fsg_server_destroy(self.handle)
         self.handle = None
 
     def __del__(self):

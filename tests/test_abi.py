@@ -75,6 +75,9 @@ def test_bad_arguments_are_refused_without_gpu(lib):
 
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(fsg.fsg_batch_item) == 144
+    assert ctypes.sizeof(fsg.fsg_server_opts) == 40
+    assert ctypes.sizeof(fsg.fsg_request) == 120
+    assert ctypes.sizeof(fsg.fsg_result) == 48
     assert ctypes.sizeof(fsg.fsg_params) == 48
     assert ctypes.sizeof(fsg.fsg_tree_opts) == 32
     assert ctypes.sizeof(fsg.fsg_stats) == 64

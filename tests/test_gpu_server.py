@@ -1,0 +1,107 @@
+"""Serving (fsg_server_*): requests of different n, d (2, 10, 64) and L run
+concurrently on the server's slots; every result must equal the same request
+run alone through fsg_build_graph_host, whatever the mix, the admission
+order or the HBM budget.  Host-side failures (an injected allocation failure,
+a cancelled request, malformed or oversized requests) release their slot and
+budget and leave the other results unchanged."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2310_13870_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_13870_gb300 import fsg as _fsg
+    import os
+    if not os.path.exists(_fsg.LIB_PATH):
+        import __graft_entry__ as g
+        g.build()
+    _fsg.load()
+    return _fsg
+
+
+def _requests():
+    rng = np.random.default_rng(0)
+    reqs = []
+    for k in range(10):
+        d = [2, 10, 64][k % 3]
+        n = int(rng.integers(300, 4000))
+        X = inputs.gaussian_mixture(n=n, d=d, k=4, box=4.0, seed=100 + k)
+        reqs.append((X, 1.5 if d > 2 else 0.3, int(rng.choice([8, 16, 32])), 500 + k))
+    return reqs
+
+
+def _alone(fsg, X, sigma, L, seed):
+    src, dst, w = fsg.fsg_build_graph_host(X, fsg.params(sigma), L, seed)
+    return src.copy(), dst.copy(), w.copy()
+
+
+def _drain(server, expect, timeout_s=120):
+    got = {}
+    t0 = time.time()
+    while len(got) < expect and time.time() - t0 < timeout_s:
+        for rec, arrays in server.poll(wait_ms=100):
+            got[rec["id"]] = (rec, arrays)
+    assert len(got) == expect
+    return got
+
+
+@pytest.mark.parametrize("budget_mb,slots", [(8192, 8), (64, 2)])
+def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots):
+    reqs = _requests()
+    want = [_alone(fsg, *r) for r in reqs]
+    server = fsg.Server(hbm_budget_bytes=budget_mb << 20, max_slots=slots)
+    ids = [server.submit(X, fsg.params(s), L, seed) for X, s, L, seed in reqs]
+    got = _drain(server, len(ids))
+    for rid, (src, dst, w) in zip(ids, want):
+        rec, (gs, gd, gw) = got[rid]
+        assert rec["status"] == fsg.FSG_OK
+        assert rec["latency_ms"] >= rec["queue_ms"] >= 0.0
+        np.testing.assert_array_equal(gs, src)
+        np.testing.assert_array_equal(gd, dst)
+        np.testing.assert_array_equal(gw, w)
+    assert server.info() == {"pending": 0, "in_flight": 0, "bytes_in_use": 0}
+    server.close()
+
+
+def test_injected_allocation_failure_and_cancellation(fsg):
+    reqs = _requests()
+    want = [_alone(fsg, *r) for r in reqs]
+    # every 3rd admission fails on the host as if its allocation had failed
+    server = fsg.Server(hbm_budget_bytes=1 << 33, max_slots=1, inject_alloc_fail_every=3)
+    ids = [server.submit(X, fsg.params(s), L, seed) for X, s, L, seed in reqs]
+    server.cancel(ids[-1])
+    got = _drain(server, len(ids))
+    statuses = [got[i][0]["status"] for i in ids]
+    assert statuses.count(fsg.FSG_ERR_OOM) >= 2
+    assert statuses[-1] in (fsg.FSG_ERR_CANCELLED, fsg.FSG_ERR_OOM)
+    for rid, (src, dst, w) in zip(ids, want):
+        rec, arrays = got[rid]
+        if rec["status"] == fsg.FSG_OK:
+            np.testing.assert_array_equal(arrays[0], src)
+            np.testing.assert_array_equal(arrays[2], w)
+    assert server.info()["bytes_in_use"] == 0
+    server.close()
+
+
+def test_malformed_and_oversized_requests_are_refused(fsg):
+    server = fsg.Server(hbm_budget_bytes=1 << 20, max_slots=2)
+    X = inputs.gaussian_mixture(n=50_000, d=10, seed=1)
+    with pytest.raises(fsg.FsgError) as e:
+        server.submit(X, fsg.params(1.5), 32, 0)  # needs far more than 1 MiB
+    assert e.value.status == fsg.FSG_ERR_BUSY
+    with pytest.raises(fsg.FsgError) as e:
+        server.submit(X[:10], fsg.params(-1.0), 8, 0)
+    assert e.value.status == fsg.FSG_ERR_INVALID_ARG
+    with pytest.raises(fsg.FsgError) as e:
+        server.submit(X[:10], fsg.params(1.0), 65, 0)
+    assert e.value.status == fsg.FSG_ERR_INVALID_ARG
+    server.close()
