@@ -397,12 +397,17 @@ class Server:
         self.live = {}  # id -> (points, src, dst, w) kept alive until polled
 
     def submit(self, points: np.ndarray, p: fsg_params, L: int, seed: int, edge_mode: int = FSG_EDGES_SET,
-               pinned: bool = True) -> int:
+               pinned: bool = True, out=None) -> int:
+        """out: optional (src, dst, w) host arrays of >= n*L elements (e.g.
+        pinned buffers reused by the caller); points are then used as given."""
         import torch
         X = np.ascontiguousarray(points, dtype=np.float32)
         n, d = X.shape
         cap = n * L
-        if pinned:
+        if out is not None:
+            src, dst, w = out
+            cap = min(src.shape[0], dst.shape[0], w.shape[0])
+        elif pinned:
             Xt = torch.from_numpy(X).pin_memory()
             X = Xt.numpy()
             src = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
