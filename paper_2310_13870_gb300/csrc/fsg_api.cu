@@ -39,6 +39,7 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     const double gamma = p->scale_conv == FSG_SIGMA_SQ ? 1.0 / (p->sigma * p->sigma)
                                                        : 1.0 / (2.0 * p->sigma * p->sigma);
     KernelParams kp;
+    kp.precision = p->precision;
     kp.gamma = (float)gamma;
     kp.neg_c = (float)(-gamma * kLog2e);
     if (kp.neg_c > -1e-30f) kp.neg_c = -1e-30f;  // keeps far-away padding at exactly 0
@@ -71,13 +72,16 @@ void begin_call(fsg_tree* t) {
 
 // Bin pass: the symmetric kernel (each pair once) when bins hold <= 128 points.
 cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const bool tc = kp.precision == FSG_PREC_EXACT_INT || (kp.precision == FSG_PREC_AUTO && kde_bins_tc_supported(t));
+    if (tc) return launch_kde_bins_tc(t, kp, s);
     if (t->d > kMaxFmaDim) return launch_kde_bins_generic(t, kp, s);
     if (kde_bins_sym_supported(t)) return launch_kde_bins_sym(t, kp, s);
     return launch_kde_bins(t, kp, s);
 }
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
-    if (p->precision == FSG_PREC_SPLIT_BF16 || p->precision == FSG_PREC_EXACT_INT) return FSG_ERR_UNSUPPORTED;
+    if (p->precision == FSG_PREC_SPLIT_BF16) return FSG_ERR_UNSUPPORTED;
+    if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
     if (p->schedule != FSG_SCHED_FUSED) return FSG_ERR_UNSUPPORTED;
     return FSG_OK;
 }
@@ -273,6 +277,17 @@ int fsg::build_tree_internal(const float* d_points, int64_t n, int32_t d, const 
         t->launches += 2;
     }
     int rc = status_of(e);
+    if (rc == FSG_OK && d >= 64 && !pool) {
+        // 8-bit data: prepare the tensor-core path (BF16 copy, norms, TMA maps)
+        int32_t st[2] = {0, 0};
+        e = cudaMemcpyAsync(st, t->status, sizeof(st), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        rc = status_of(e);
+        if (rc == FSG_OK && st[1] == 0) {
+            t->exact_int = 1;
+            rc = tc_prepare(t, s);
+        }
+    }
     if (rc == FSG_OK && opts && opts->d_perm) {
         // a caller-given order is validated before the tree is handed out
         int32_t st[2] = {0, 0};
@@ -305,6 +320,8 @@ void fsg_free_tree(fsg_tree* t) {
     tree_free(t, t->bnd);
     tree_free(t, t->status);
     tree_free(t, t->ws.base);
+    if (t->Xb) cudaFree(t->Xb);
+    if (t->norms) cudaFree(t->norms);
     delete t;
 }
 
@@ -324,7 +341,12 @@ int fsg_tree_update(fsg_tree* t, const float* d_points, void* stream) {
     // the stored order is reused: tree_prep reads perm[p] before rewriting it
     cudaError_t e = launch_tree_prep(t, d_points, t->perm, s);
     t->launches += 2;
-    return status_of(e);
+    int rc = status_of(e);
+    if (rc == FSG_OK && t->Xb) {  // refresh the tensor-core copy (exactness re-checked on the device)
+        rc = tc_prepare(t, s);
+        t->launches += 1;
+    }
+    return rc;
 }
 
 int fsg_profile(fsg_tree* t, int enable) {

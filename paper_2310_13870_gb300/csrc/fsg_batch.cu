@@ -80,7 +80,6 @@ int fsg_batch_create(const fsg_batch_item* items, int32_t count, int32_t streams
     if (!b) return FSG_ERR_OOM;
     b->items.assign(items, items + count);
     b->capture = capture;
-    cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (int32_t k = 0; e == cudaSuccess && k < streams && k < count; ++k) {
         cudaStream_t st = nullptr;
@@ -103,7 +102,6 @@ int fsg_batch_create(const fsg_batch_item* items, int32_t count, int32_t streams
         }
         b->trees.push_back(t);
     }
-    (void)s;
     *out = b;
     return FSG_OK;
 }

@@ -17,9 +17,9 @@ constexpr int kMaxL = 64;
 constexpr int kBinSlots = 16;
 constexpr int kMaxFmaDim = 16;       // FP32 FMA tiles are compiled for d <= 16
 constexpr int kStatusTimeout = FSG_ERR_TIMEOUT;
-// Upper bound on mbarrier polls before a wait gives up (each poll is a
-// try_wait that may itself suspend for a short, hardware-chosen time).
-constexpr uint32_t kMaxPolls = 1u << 24;
+// Time limit of every bounded device wait (an mbarrier phase that does not
+// complete within it is reported as FSG_ERR_TIMEOUT).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------
 // Tree and workspace
@@ -75,6 +75,13 @@ struct fsg_tree {
     int32_t* bnd = nullptr;  // [nb+1] level-s0 node boundaries
     int32_t* status = nullptr;  // device status word
     int exact_int = 0;       // points are multiples of 1/255 in [0,1]
+    // tensor-core path (d >= 64, exact 8-bit data): BF16 copy of 255 x,
+    // squared norms in integer units, TMA descriptors (A: 128 rows, B: 256 rows)
+    void* Xb = nullptr;
+    float* norms = nullptr;
+    int32_t dpad = 0;
+    alignas(64) unsigned char tmap_a[128] = {};
+    alignas(64) unsigned char tmap_b[128] = {};
     fsg::Workspace ws;
     // per-phase timing (fsg_profile) and kernel-launch count
     bool profiling = false;
@@ -95,6 +102,7 @@ namespace fsg {
 // Host-side launchers (one per .cu file)
 // ---------------------------------------------------------------------------
 struct KernelParams {
+    int precision;    // FSG_PREC_*
     float neg_c;      // -gamma * log2(e): k = ex2(neg_c * ||x-y||^2)
     float gamma;
     int self_exclude;
@@ -121,6 +129,9 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
                            fsg_stats* d_stats, cudaStream_t s);
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+int tc_prepare(fsg_tree* t, cudaStream_t s);
+bool kde_bins_tc_supported(const fsg_tree* t);
+cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -231,13 +242,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 // Bounded wait: returns false (and records FSG_ERR_TIMEOUT) if the phase did
-// not complete within kMaxPolls polls.
+// not complete within kWaitLimitNs of wall time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int32_t* status) {
-    for (uint32_t it = 0; it < kMaxPolls; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-    atomicExch(status, kStatusTimeout);
-    return false;
+        if ((it & 31u) == 0u && global_ns() - t0 > kWaitLimitNs) {
+            atomicExch(status, kStatusTimeout);
+            return false;
+        }
+    }
 }
 
 __device__ __forceinline__ int ceil_log2_dev(int m) {

@@ -1,0 +1,368 @@
+// Tensor-core bin pass (tcgen05 + TMEM + TMA) for d >= 64 on data that are
+// exact multiples of 1/255 in [0,1] (8-bit images).  Scaled by 255 the
+// coordinates are integers 0..255, exact in BF16, so every product of the
+// dot-product GEMM is exact and only its FP32 accumulation rounds:
+//   ||x - y||^2 = ||x||^2 + ||y||^2 - 2 x.y   (integer units, exact norms),
+//   k = ex2(neg_c / 255^2 * ||x - y||^2).
+//
+// CTA = one block of 128 queries x one chunk of bins (their points), 6 warps:
+//   warp 0 (one thread): TMA producer, 4-stage ring of {A: 128 query rows,
+//                        B: 256 point rows} x 64 coordinates (128-byte swizzle);
+//   warp 1 (one thread): MMA issuer, tcgen05.mma kind::f16 M=128 N=256 K=16,
+//                        FP32 accumulators in TMEM, two 256-column buffers;
+//                        warp 1 also allocates / frees the 512 TMEM columns;
+//   warps 2..5         : epilogue, one per TMEM lane quadrant: tcgen05.ld of a
+//                        row's 256 dot products, kernel values, per-bin sums.
+// Every mbarrier wait is bounded; on a timeout the CTA records
+// FSG_ERR_TIMEOUT, stops, waits (bounded) for its MMAs and frees TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <climits>
+
+#include "fsg_internal.cuh"
+
+namespace fsg {
+namespace {
+
+constexpr int kTcM = 128;
+constexpr int kTcN = 256;
+constexpr int kTcK = 64;   // BF16 coordinates per 128-byte swizzled row
+constexpr int kTcStages = 4;
+constexpr int kTcThreads = 192;
+constexpr uint32_t kABytes = kTcM * 128;
+constexpr uint32_t kBBytes = kTcN * 128;
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr uint32_t kTmemCols = 512;
+
+// Shared-memory matrix descriptor (tcgen05): K-major, 128-byte swizzle,
+// 8-row groups of 1024 bytes.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;               // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                            ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
+                   int bpc, float neg_c, int self_exclude, float* __restrict__ binsum, int32_t* __restrict__ status) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* tfull = empty + kTcStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* fin = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    int32_t* flags = reinterpret_cast<int32_t*>(tmem_slot + 1);  // [0] abort, [1] stages consumed by MMA
+    int32_t* bnd_s = flags + 2;                                   // bpc + 1
+    float* outs = reinterpret_cast<float*>(bnd_s + ((bpc + 1 + 3) & ~3));  // [128][bpc]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q0 = blockIdx.x * kTcM;
+    const int b0 = blockIdx.y * bpc;
+    const int nbc = min(nb, b0 + bpc) - b0;
+    if (tid <= nbc) bnd_s[tid] = bnd[b0 + tid];
+    for (int e = tid; e < kTcM * bpc; e += kTcThreads) outs[e] = 0.f;
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
+        mbar_init(fin, 1);
+        flags[0] = 0;
+        flags[1] = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int pa = bnd_s[0], pe = bnd_s[nbc];
+    const int ntile = (pe - pa + kTcN - 1) / kTcN;
+    const int total = ntile * kchunks;
+    volatile int32_t* abort_flag = flags;
+    volatile int32_t* consumed = flags + 1;
+    int mma_issued = 0;
+    int issued = 0;  // TMA stages issued (producer thread)
+
+    // The points must be exact 8-bit values (checked when the tree is built or updated).
+    const bool inexact = status[1] != 0;
+
+    if (!inexact && warp == 0 && lane == 0) {
+        // ---- TMA producer
+        for (int it = 0; it < total && !*abort_flag; ++it) {
+            const int s = it % kTcStages;
+            if (!mbar_wait_bounded(&empty[s], ((uint32_t)(it / kTcStages) & 1u) ^ 1u, status)) {
+                *abort_flag = 1;
+                break;
+            }
+            const int tile = it / kchunks, kc = it - tile * kchunks;
+            unsigned char* st = base + s * kStageBytes;
+            mbar_arrive_expect_tx(&full[s], kStageBytes);
+            tma_load_2d(st, &tmA, kc * kTcK, q0, &full[s]);
+            tma_load_2d(st + kABytes, &tmB, kc * kTcK, pa + tile * kTcN, &full[s]);
+            issued = it + 1;
+        }
+    } else if (!inexact && warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        for (int tile = 0; tile < ntile && !*abort_flag; ++tile) {
+            const int a = tile & 1;
+            if (!mbar_wait_bounded(&tempty[a], ((uint32_t)(tile >> 1) & 1u) ^ 1u, status)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dt = tmem + (uint32_t)(a * kTcN);
+            bool ok = true;
+            for (int kc = 0; kc < kchunks; ++kc) {
+                const int it = tile * kchunks + kc;
+                const int s = it % kTcStages;
+                if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kTcStages) & 1u, status)) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(base + s * kStageBytes);
+                const uint64_t da = sdesc(sa), db = sdesc(sa + kABytes);
+#pragma unroll
+                for (int k = 0; k < kTcK / 16; ++k)  // 32 bytes of K per MMA inside the swizzled row
+                    umma_bf16(dt, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), (kc | k) != 0 ? 1u : 0u);
+                mma_issued = 1;
+                umma_commit(&empty[s]);
+                *consumed = it + 1;
+            }
+            if (!ok) break;
+            umma_commit(&tfull[a]);
+        }
+    } else if (!inexact && warp >= 2) {
+        // ---- epilogue: TMEM lane quadrant (warp % 4), row = query
+        const int quad = warp & 3;
+        const int r = 32 * quad + lane;
+        const int q = q0 + r;
+        const float nq = q < n ? norms[q] : 0.f;
+        int bin = 0;
+        int next_b = nbc > 0 ? bnd_s[1] : INT_MAX;
+        float acc = 0.f;
+        for (int tile = 0; tile < ntile; ++tile) {
+            const int a = tile & 1;
+            if (*abort_flag || !mbar_wait_bounded(&tfull[a], (uint32_t)(tile >> 1) & 1u, status)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int t0 = pa + tile * kTcN;
+#pragma unroll 1
+            for (int c = 0; c < kTcN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * kTcN + 32 * c), v);
+                const int pc = t0 + 32 * c;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int p = pc + j;
+                    if (p < pe) {
+                        const float arg = fmaf(-2.f, v[j], nq + norms[p]);
+                        float k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                        if (self_exclude && p == q) k = 0.f;
+                        acc += k;
+                        if (p + 1 == next_b) {
+                            outs[r * bpc + bin] = acc;
+                            acc = 0.f;
+                            ++bin;
+                            next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
+        }
+    }
+    __syncthreads();
+    if (!inexact && !*abort_flag) {
+        const int nq = min(kTcM, n - q0);
+        for (int e = tid; e < nq * nbc; e += kTcThreads) {
+            const int ql = e / nbc, b = e - ql * nbc;
+            binsum[(size_t)(q0 + ql) * nb + b0 + b] = outs[ql * bpc + b];
+        }
+    }
+    if (inexact && tid == 0) atomicExch(status, FSG_ERR_UNSUPPORTED);
+    if (tid == 0) {
+        // after an abort: wait (bounded) for this CTA's own copies still in flight
+        for (int it = *consumed; it < issued; ++it)
+            mbar_wait_bounded(&full[it % kTcStages], (uint32_t)(it / kTcStages) & 1u, status);
+    }
+    if (warp == 1) {
+        if (lane == 0 && mma_issued) {
+            // all MMAs of this CTA must be complete before TMEM is freed
+            umma_commit(fin);
+            mbar_wait_bounded(fin, 0u, status);
+        }
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// BF16 copy of 255 * x (integers 0..255) padded to a multiple of 64
+// coordinates, and exact integer squared norms.
+__global__ void tc_prep_kernel(const float* __restrict__ Xt, int64_t n, int d, int dp, int dpad,
+                               __nv_bfloat16* __restrict__ Xb, float* __restrict__ norms) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; p < n; p += (int64_t)gridDim.x * blockDim.y) {
+        int64_t sq = 0;
+        for (int t = threadIdx.x; t < dpad; t += 32) {
+            const float v = t < d ? rintf(Xt[p * dp + t] * 255.f) : 0.f;
+            Xb[p * dpad + t] = __float2bfloat16_rn(v);
+            const int iv = (int)v;
+            sq += (int64_t)iv * iv;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (threadIdx.x == 0) norms[p] = (float)sq;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+// Allocates and fills the BF16 copy, the norms and the two tensor maps.
+int tc_prepare(fsg_tree* t, cudaStream_t s) {
+    const int dpad = (t->d + kTcK - 1) / kTcK * kTcK;
+    if (!t->Xb) {
+        cudaError_t e = cudaMalloc((void**)&t->Xb, sizeof(__nv_bfloat16) * (size_t)t->n_pad * dpad);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&t->norms, sizeof(float) * (size_t)t->n_pad);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return FSG_ERR_OOM;
+        }
+        cudaMemsetAsync(t->Xb, 0, sizeof(__nv_bfloat16) * (size_t)t->n_pad * dpad, s);
+        PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+        if (!enc) return FSG_ERR_UNSUPPORTED;
+        const cuuint64_t gdim[2] = {(cuuint64_t)dpad, (cuuint64_t)t->n};
+        const cuuint64_t gstride[1] = {(cuuint64_t)dpad * 2};
+        const cuuint32_t estride[2] = {1, 1};
+        const cuuint32_t boxA[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
+        const cuuint32_t boxB[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcN};
+        CUresult r1 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_a), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xb, gdim,
+                          gstride, boxA, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r2 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_b), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xb, gdim,
+                          gstride, boxB, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return FSG_ERR_UNSUPPORTED;
+        t->dpad = dpad;
+    }
+    dim3 block(32, 8);
+    int64_t g = (t->n + 7) / 8;
+    if (g > 152 * 64) g = 152 * 64;
+    tc_prep_kernel<<<(int)g, block, 0, s>>>(t->Xt, t->n, t->d, t->dp, dpad, reinterpret_cast<__nv_bfloat16*>(t->Xb),
+                                            t->norms);
+    return cudaGetLastError() == cudaSuccess ? FSG_OK : FSG_ERR_CUDA;
+}
+
+bool kde_bins_tc_supported(const fsg_tree* t) { return t->Xb != nullptr && t->d >= 64; }
+
+cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const int qblocks = (int)((t->n + kTcM - 1) / kTcM);
+    int chunks = (4 * 152 + qblocks - 1) / qblocks;
+    if (chunks < 1) chunks = 1;
+    if (chunks > t->nb) chunks = t->nb;
+    int bpc = (t->nb + chunks - 1) / chunks;
+    if (bpc > 32) bpc = 32;
+    chunks = (t->nb + bpc - 1) / bpc;
+    const size_t smem = 1024 + (size_t)kTcStages * kStageBytes + 8 * (2 * kTcStages + 5) + 16 +
+                        (size_t)((bpc + 1 + 3) & ~3) * 4 + (size_t)kTcM * bpc * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kde_bins_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(227 * 1024));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    // integer units: ||255 x - 255 y||^2 = 255^2 ||x - y||^2
+    const float nc = kp.neg_c / (255.f * 255.f);
+    dim3 grid(qblocks, chunks);
+    kde_bins_tc_kernel<<<grid, kTcThreads, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(t->tmap_a),
+                                                      *reinterpret_cast<const CUtensorMap*>(t->tmap_b), t->norms,
+                                                      (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc, nc,
+                                                      kp.self_exclude, t->ws.binsum, t->status);
+    return cudaGetLastError();
+}
+
+}  // namespace fsg

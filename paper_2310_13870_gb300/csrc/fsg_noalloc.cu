@@ -104,6 +104,7 @@ extern "C" int fsg_degrees_noalloc(const float* d_points, int64_t n, int32_t d, 
     const double gamma = p->scale_conv == FSG_SIGMA_SQ ? 1.0 / (p->sigma * p->sigma)
                                                        : 1.0 / (2.0 * p->sigma * p->sigma);
     fsg::KernelParams kp;
+    kp.precision = FSG_PREC_FP32;
     kp.gamma = (float)gamma;
     kp.neg_c = (float)(-gamma * 1.4426950408889634073599246810019);
     if (kp.neg_c > -1e-30f) kp.neg_c = -1e-30f;
