@@ -491,6 +491,9 @@ def main():
     if args.workload == "digits":
         WORKLOAD.clear()
         WORKLOAD.update(DIGITS)
+        if args.n:
+            WORKLOAD["n"] = args.n
+            WORKLOAD["workload"] = WORKLOAD["workload"].replace("n=70000", f"n={args.n}")
     return run_ours(args)
 
 

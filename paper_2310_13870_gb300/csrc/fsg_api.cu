@@ -398,7 +398,9 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cuda
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_LEAF, s);
         if (t->d > kMaxFmaDim) {
-            e = launch_leaf_values_generic(t, kp, s);
+            const bool tc = kp.precision == FSG_PREC_EXACT_INT ||
+                            (kp.precision == FSG_PREC_AUTO && kde_bins_tc_supported(t));
+            e = tc && (1 << t->dm) <= 256 ? launch_leaf_values_tc(t, kp, s) : launch_leaf_values_generic(t, kp, s);
             t->launches += 1;
         }
         if (e == cudaSuccess) e = launch_leaf_finish(t, kp, s);

@@ -132,6 +132,7 @@ cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, c
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

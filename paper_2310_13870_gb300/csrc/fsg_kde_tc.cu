@@ -366,3 +366,235 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
 }
 
 }  // namespace fsg
+
+// ---------------------------------------------------------------------------
+// Tensor-core leaf values: for the items (queries) of one bin, the kernel
+// value at every leaf slot of the bin's tree, k = ex2(neg_c (||x||^2 +
+// ||y||^2 - 2 x.y)) in the same integer units as the bin pass.  CTA (b, y)
+// handles chunks of 128 items of bin b: the item rows and the bin's slot rows
+// (zero rows for empty slots) are gathered with cp.async directly into the
+// 128-byte-swizzled K-major layout (3-stage ring), one thread issues
+// tcgen05.mma M=128 x N=slots x K=16, and the four warps read their TMEM lane
+// quadrants and write leafv[item][slot].
+// ---------------------------------------------------------------------------
+namespace fsg {
+namespace {
+
+constexpr int kLvStages = 3;
+constexpr int kLvThreads = 128;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+template <int NS>  // slots (N of the MMA): 64, 128 or 256
+__global__ void __launch_bounds__(kLvThreads, 1)
+leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict__ norms, int dpad,
+                      const int32_t* __restrict__ bnd, const int32_t* __restrict__ bin_off,
+                      const int32_t* __restrict__ items_q, float neg_c, int self_exclude, int leafmax,
+                      float* __restrict__ leafv, int32_t* __restrict__ status) {
+    constexpr uint32_t kA = 128 * 128, kB = NS * 128, kStage = kA + kB;
+    constexpr uint32_t kIdescLv = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NS >> 3) << 17) |
+                                  ((uint32_t)(128 >> 4) << 24);
+    const int b = blockIdx.x;
+    const int seg = bin_off[b * kBinSlots];
+    const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
+    const int nchunks = (cnt + 127) / 128;
+    if ((int)blockIdx.y >= nchunks) return;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* done = reinterpret_cast<uint64_t*>(base + kLvStages * kStage);  // MMAs reading a stage are done
+    uint64_t* accf = done + kLvStages;                                          // accumulator complete
+    uint64_t* fin = accf + 1;                                                   // teardown
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    int32_t* rowpos = reinterpret_cast<int32_t*>(tmem_slot + 4);  // [128] item query positions
+    int32_t* slotpos = rowpos + 128;                              // [NS] slot point positions
+    float* slotnorm = reinterpret_cast<float*>(slotpos + NS);     // [NS]
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;
+    const int dm = ceil_log2_dev(m), leaf0 = 1 << dm;
+    const int kchunks = dpad / 64;
+    if (tid == 0) {
+        for (int s = 0; s < kLvStages; ++s) mbar_init(&done[s], 1);
+        mbar_init(accf, 1);
+        mbar_init(fin, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)NS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // slot table of this bin (the same for every chunk)
+    for (int sl = tid; sl < NS; sl += kLvThreads) {
+        int pos = -1;
+        if (sl < leaf0) {
+            int a = 0, c = m;
+            for (int t = dm - 1; t >= 0; --t) {
+                const int mid = a + (c - a) / 2;
+                if ((sl >> t) & 1) a = mid; else c = mid;
+            }
+            if (c - a == 1) pos = p_lo + a;
+        }
+        slotpos[sl] = pos;
+        slotnorm[sl] = pos >= 0 ? norms[pos] : 0.f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    int g = 0;          // stage uses issued so far (stage g % kLvStages, its use number g / kLvStages)
+    int tiles = 0;      // accumulator tiles completed
+    bool mma_issued = false;
+    bool ok = true;
+    // Gathers K chunk kc (64 coordinates) of the 128 item rows and NS slot rows
+    // into stage s, in the 128-byte-swizzled K-major layout; empty rows are 0.
+    auto fill = [&](int kc, int s) {
+        unsigned char* st = base + s * kStage;
+        for (int e = tid; e < (128 + NS) * 8; e += kLvThreads) {
+            const int r = e >> 3, c = e & 7;
+            const bool is_a = r < 128;
+            const int rr = is_a ? r : r - 128;
+            const int pos = is_a ? rowpos[rr] : slotpos[rr];
+            unsigned char* dst = st + (is_a ? 0u : kA) + (uint32_t)rr * 128u + (uint32_t)((c ^ (rr & 7)) << 4);
+            const __nv_bfloat16* src = Xb + (size_t)(pos >= 0 ? pos : 0) * dpad + kc * 64 + c * 8;
+            cp_async16(dst, src, pos >= 0 ? 16 : 0);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // waits until the MMAs of stage use g2 - kLvStages are done
+    auto stage_free = [&](int g2) -> bool {
+        const int use = g2 / kLvStages;
+        if (use == 0) return true;
+        return mbar_wait_bounded(&done[g2 % kLvStages], (uint32_t)(use - 1) & 1u, status);
+    };
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        const int it0 = chunk * 128;
+        const int qcnt = min(128, cnt - it0);
+        rowpos[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
+        __syncthreads();
+        const int pre = min(kLvStages - 1, kchunks);
+        for (int kc = 0; kc < pre; ++kc) {
+            ok = ok && stage_free(g + kc);
+            fill(kc, (g + kc) % kLvStages);
+        }
+        for (int kc = 0; kc < kchunks; ++kc) {
+            const int s = (g + kc) % kLvStages;
+            if (kc + pre < kchunks) {
+                ok = ok && stage_free(g + kc + pre);
+                fill(kc + pre, (g + kc + pre) % kLvStages);
+                asm volatile("cp.async.wait_group %0;" ::"n"(kLvStages - 1) : "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (__syncthreads_or(!ok)) { ok = false; break; }
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t sa = smem_u32(base + s * kStage);
+                const uint64_t da = sdesc(sa), db = sdesc(sa + kA);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(da + (uint64_t)(2 * k)), "l"(db + (uint64_t)(2 * k)), "r"(kIdescLv),
+                        "r"((kc | k) != 0 ? 1u : 0u)
+                        : "memory");
+                }
+                mma_issued = true;
+                umma_commit(&done[s]);
+                if (kc == kchunks - 1) umma_commit(accf);
+            }
+        }
+        if (!ok) break;
+        g += kchunks;
+        // epilogue: thread = item row = TMEM lane (warp w reads lanes 32 w .. 32 w + 31)
+        ok = mbar_wait_bounded(accf, (uint32_t)tiles & 1u, status);
+        ++tiles;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        tc_fence_after();
+        const int r = tid;
+        const int qp = rowpos[r];
+        const float nq = qp >= 0 ? norms[qp] : 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NS; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            if (r < qcnt && c0 < leaf0) {
+                float* dst = leafv + (size_t)(seg + it0 + r) * leafmax + c0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    float o[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int sl = c0 + j + u;
+                        const int pp = slotpos[sl];
+                        float k = 0.f;
+                        if (pp >= 0 && !(self_exclude && pp == qp)) {
+                            const float arg = fmaf(-2.f, v[j + u], nq + slotnorm[sl]);
+                            k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                        }
+                        o[u] = k;
+                    }
+                    if (c0 + j < leaf0) *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();  // TMEM and rowpos are reused by the next chunk
+    }
+    // teardown: own copies landed, own MMAs complete, then free TMEM
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (tid == 0 && mma_issued) {
+        umma_commit(fin);
+        mbar_wait_bounded(fin, 0u, status);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NS)
+                     : "memory");
+    }
+}
+
+template <int NS>
+cudaError_t launch_lv_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    constexpr uint32_t kStage = 128 * 128 + NS * 128;
+    const size_t smem = 1024 + (size_t)kLvStages * kStage + 8 * (kLvStages + 2) + 16 + 4 * 128 + 8 * NS;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(leaf_values_tc_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
+    const int64_t chunks_per_bin = (items_est / t->nb + 127) / 128 + 1;
+    int64_t S = (152 * 2 * 8 + t->nb - 1) / t->nb;
+    if (S > chunks_per_bin) S = chunks_per_bin;
+    if (S < 1) S = 1;
+    if (S > 65535) S = 65535;
+    dim3 grid(t->nb, (unsigned)S);
+    leaf_values_tc_kernel<NS><<<grid, kLvThreads, smem, s>>>(
+        reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms, t->dpad, t->bnd, t->ws.bin_off, t->ws.items_q,
+        kp.neg_c / (255.f * 255.f), kp.self_exclude, 1 << t->dm, t->ws.leafv, t->status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const int leaf0 = 1 << t->dm;
+    if (leaf0 <= 64) return launch_lv_tc<64>(t, kp, s);
+    if (leaf0 <= 128) return launch_lv_tc<128>(t, kp, s);
+    return launch_lv_tc<256>(t, kp, s);
+}
+
+}  // namespace fsg
