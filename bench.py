@@ -267,6 +267,31 @@ def run_ours(args):
         with open(tfile) as f:
             traffic = json.load(f).get("bytes_per_launch")
 
+    # the plain FP32 exact GPU path (levelwise schedule) on the same input, same clocks regime
+    plain = None
+    if args.plain_steps > 0:
+        pl = fsg.params(sigma, schedule=fsg.FSG_SCHED_LEVELWISE)
+        fsg.fsg_build_graph(tree, pl, L, seed, bufs=bufs, stream=stream)  # warm-up
+        stream.synchronize()
+        pms = []
+        for _ in range(args.plain_steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fsg.fsg_tree_update(tree, pts, stream=stream)
+            fsg.fsg_build_graph(tree, pl, L, seed, bufs=bufs, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            pms.append(e0.elapsed_time(e1))
+        assert fsg.fsg_sync(tree, stream=stream) == 0
+        pst = fsg.stats_dict(bufs)
+        pt = statistics.mean(pms)
+        plain = {"schedule": "levelwise (Algorithm 1 per level, FP32 direct differences, no bin pass)",
+                 "value": n * L / (pt * 1e-3), "unit": UNIT, "ms_per_step": pt, "steps": args.plain_steps,
+                 "evals_per_step": pst["n_evals"], "gkernel_evals_per_s": pst["n_evals"] / (pt * 1e-3) / 1e9,
+                 "flagged_samples": pst["n_flagged"], "speedup_of_fused": (n * L / (ms * 1e-3)) / (n * L / (pt * 1e-3))}
+
     # end to end through the host-buffer entry point
     e2e = None
     if not args.no_e2e:
@@ -306,7 +331,7 @@ def run_ours(args):
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
-                "roofline": dict(roof, traffic=traffic),
+                "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches1 - launches0)}
         print(json.dumps(line), flush=True)
@@ -472,6 +497,7 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP32 levelwise path")
     ap.add_argument("--n", type=int, default=0, help="smaller point count (profiler captures only)")
     ap.add_argument("--workload", choices=["gmm", "digits", "seg-batch", "serving"], default="gmm")
     ap.add_argument("--requests", type=int, default=10_000)

@@ -82,7 +82,9 @@ cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16) return FSG_ERR_UNSUPPORTED;
     if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
-    if (p->schedule != FSG_SCHED_FUSED) return FSG_ERR_UNSUPPORTED;
+    // the levelwise schedule is the plain FP32 path only
+    if (p->schedule == FSG_SCHED_LEVELWISE && p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32)
+        return FSG_ERR_UNSUPPORTED;
     return FSG_OK;
 }
 
@@ -375,8 +377,16 @@ int fsg_profile_read(fsg_tree* t, float* ms, int64_t* launches) {
     return FSG_OK;
 }
 
-static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cudaStream_t s) {
+static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s) {
     Workspace& ws = t->ws;
+    if (schedule == FSG_SCHED_LEVELWISE) {
+        cudaError_t e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
+        if (e == cudaSuccess) {
+            PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
+            e = launch_levelwise(t, kp, d_deg, 1, s, &t->launches);
+        }
+        return status_of(e);
+    }
     cudaError_t e = cudaMemsetAsync(ws.bin_count, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.bin_cursor, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
@@ -409,6 +419,12 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, double* d_deg, cuda
     return status_of(e);
 }
 
+// Evaluations of the bin pass (every query against every point), counted on
+// the host; the levelwise schedule counts its own on the device.
+static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
+    return p->schedule == FSG_SCHED_LEVELWISE ? 0 : t->n * t->n;
+}
+
 // Statistics known on the host: samples run, bin-pass evaluations.
 __global__ static void stats_finish_kernel(fsg_stats* st, int64_t n_samples, int64_t bin_evals,
                                            const int32_t* status, fsg_stats* out) {
@@ -428,6 +444,12 @@ int fsg_degrees(fsg_tree* t, const fsg_params* p, double* d_deg, void* stream) {
     const KernelParams kp = make_kernel_params(p, 1, 0);
     begin_call(t);
     cudaError_t e;
+    if (p->schedule == FSG_SCHED_LEVELWISE) {
+        e = cudaMemsetAsync(t->ws.stats, 0, sizeof(fsg_stats), s);
+        PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
+        if (e == cudaSuccess) e = launch_levelwise(t, kp, d_deg, 0, s, &t->launches);
+        return status_of(e);
+    }
     {
         PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
         e = run_kde_bins(t, kp, s);
@@ -450,13 +472,13 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, L, seed);
     begin_call(t);
-    if ((rc = run_sampling(t, kp, nullptr, s)) != FSG_OK) return rc;
+    if ((rc = run_sampling(t, kp, p->schedule, nullptr, s)) != FSG_OK) return rc;
     cudaError_t e;
     {
         PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
         e = launch_outputs(t, kp, d_samples, d_flags, nullptr, s);
         if (e == cudaSuccess) {
-            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, t->n * t->n, t->status, nullptr);
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status, nullptr);
             e = cudaGetLastError();
         }
         t->launches += 2;
@@ -477,7 +499,7 @@ int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, 
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, L, seed);
     begin_call(t);
-    if ((rc = run_sampling(t, kp, d_deg, s)) != FSG_OK) return rc;
+    if ((rc = run_sampling(t, kp, p->schedule, d_deg, s)) != FSG_OK) return rc;
     cudaError_t e;
     {
         PhaseScope ph(t, FSG_PHASE_EDGES, s);
@@ -488,7 +510,7 @@ int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, 
         PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
         e = launch_outputs(t, kp, d_samples, d_flags, d_stats, s);
         if (e == cudaSuccess) {
-            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, t->n * t->n, t->status, d_stats);
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status, d_stats);
             e = cudaGetLastError();
         }
         t->launches += 2;

@@ -134,6 +134,8 @@ bool kde_bins_tc_supported(const fsg_tree* t);
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+cudaError_t launch_levelwise(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
+                             cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------------------
 // Device helpers
