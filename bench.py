@@ -42,11 +42,12 @@ FP32_LANES_PER_SM = 128
 MUFU_EX2_PER_SM = 16
 
 
-def alu_peak_evals(d: int, mhz: float = SM_MAX_MHZ) -> float:
+def alu_peak_evals(d: int, mhz: float = SM_MAX_MHZ, ops: int = 0) -> float:
     """ALU bound of the bin pass, in kernel evaluations/s: per evaluation the
     FP32 pipe executes d subtractions, d multiply-adds, one scale and one
-    accumulate (2d+2 lane operations) and the MUFU one ex2."""
-    fp32 = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / (2 * d + 2)
+    accumulate per row the value is added to (2d+2 lane operations, 2d+3 when
+    each value serves two rows) and the MUFU one ex2."""
+    fp32 = SM_COUNT * FP32_LANES_PER_SM * mhz * 1e6 / (ops or 2 * d + 2)
     mufu = SM_COUNT * MUFU_EX2_PER_SM * mhz * 1e6
     return min(fp32, mufu)
 
@@ -255,11 +256,18 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": "measured cuBLAS BF16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
     else:
-        achieved = n * n / (kde_avg * 1e-3) / 1e9
-        peak = alu_peak_evals(d) / 1e9
-        roof = {"bound": "alu", "kernel": f"kde_bins_sym_kernel<{d}>", "achieved": achieved, "peak": peak,
-                "unit": "Gkernel-evals/s", "frac": achieved / peak,
-                "peak_basis": f"{SM_COUNT} SMs x min({FP32_LANES_PER_SM} FP32 lanes/(2d+2), "
+        # executed evaluations of the bin pass; the symmetric kernel adds each
+        # value to two rows (2d+3 FP32 lane operations), the plain one to one (2d+2)
+        bin_evals = fsg.fsg_bin_pass_evals(tree, p)
+        sym = bin_evals < n * n
+        ops = 2 * d + (3 if sym else 2)
+        achieved = bin_evals / (kde_avg * 1e-3) / 1e9
+        peak = alu_peak_evals(d, ops=ops) / 1e9
+        roof = {"bound": "alu", "kernel": f"kde_bins_{'sym_' if sym else ''}kernel<{d}>", "achieved": achieved,
+                "peak": peak, "unit": "Gkernel-evals/s (executed)", "frac": achieved / peak,
+                "units_per_launch": bin_evals, "algorithmic_evals_per_launch": n * n,
+                "algorithmic_gevals_per_s": n * n / (kde_avg * 1e-3) / 1e9,
+                "peak_basis": f"{SM_COUNT} SMs x min({FP32_LANES_PER_SM} FP32 lanes/{ops} lane-ops per evaluation, "
                               f"{MUFU_EX2_PER_SM} ex2) x {SM_MAX_MHZ:.0f} MHz"}
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "kde_bins_traffic.json")

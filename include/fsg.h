@@ -133,6 +133,18 @@ void fsg_free_tree(fsg_tree* tree);
 int fsg_tree_info(const fsg_tree* tree, int64_t* n, int32_t* d, int32_t* depth);
 
 /*
+ * Kernel evaluations k(x_q, x_p) that the bin pass of the fused schedule
+ * executes on this tree with these parameters (a diagnostic for roofline
+ * accounting; Eq. 1 needs n^2 of them).  n^2 for the plain, generic-d and
+ * tensor-core passes; (n^2 + sum_k S_k^2) / 2 for the symmetric FP32 pass,
+ * S_k the point counts of its blocks of bins.  0 for the levelwise schedule,
+ * which counts its own evaluations on the device (fsg_stats.n_evals).
+ *   evals : host int64, written on success.
+ * Errors: INVALID_ARG.
+ */
+int fsg_bin_pass_evals(const fsg_tree* tree, const fsg_params* params, int64_t* evals);
+
+/*
  * Replaces the tree's points by new values of the same shape (n, d) in the
  * same tree order, without allocating (Sec. 4.1's tree is rebuilt in place).
  *   d_points : device float32 [n][d], read only during this call.

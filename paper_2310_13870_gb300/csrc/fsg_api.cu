@@ -70,13 +70,22 @@ void begin_call(fsg_tree* t) {
     for (int k = 0; k < FSG_NUM_PHASES; ++k) t->ev_used[k] = false;
 }
 
-// Bin pass: the symmetric kernel (each pair once) when bins hold <= 128 points.
+// Bin pass: the symmetric kernel (each pair once) when bins hold 61..128 points.
+bool use_tc(const fsg_tree* t, int precision) {
+    return precision == FSG_PREC_EXACT_INT || (precision == FSG_PREC_AUTO && kde_bins_tc_supported(t));
+}
+
 cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    const bool tc = kp.precision == FSG_PREC_EXACT_INT || (kp.precision == FSG_PREC_AUTO && kde_bins_tc_supported(t));
-    if (tc) return launch_kde_bins_tc(t, kp, s);
+    if (use_tc(t, kp.precision)) return launch_kde_bins_tc(t, kp, s);
     if (t->d > kMaxFmaDim) return launch_kde_bins_generic(t, kp, s);
     if (kde_bins_sym_supported(t)) return launch_kde_bins_sym(t, kp, s);
     return launch_kde_bins(t, kp, s);
+}
+
+// Kernel evaluations the bin pass executes (n^2, or about n^2/2 when symmetric).
+int64_t bin_pass_evals(const fsg_tree* t, int precision) {
+    if (!use_tc(t, precision) && t->d <= kMaxFmaDim && kde_bins_sym_supported(t)) return kde_bins_sym_evals(t);
+    return t->n * t->n;
 }
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
@@ -335,6 +344,14 @@ int fsg_tree_info(const fsg_tree* t, int64_t* n, int32_t* d, int32_t* depth) {
     return FSG_OK;
 }
 
+int fsg_bin_pass_evals(const fsg_tree* t, const fsg_params* p, int64_t* evals) {
+    if (!t || !evals) return FSG_ERR_INVALID_ARG;
+    const int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    *evals = p->schedule == FSG_SCHED_LEVELWISE ? 0 : bin_pass_evals(t, p->precision);
+    return FSG_OK;
+}
+
 int fsg_tree_update(fsg_tree* t, const float* d_points, void* stream) {
     if (!t || !d_points) return FSG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -408,8 +425,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_LEAF, s);
         if (t->d > kMaxFmaDim) {
-            const bool tc = kp.precision == FSG_PREC_EXACT_INT ||
-                            (kp.precision == FSG_PREC_AUTO && kde_bins_tc_supported(t));
+                    const bool tc = use_tc(t, kp.precision);
             e = tc && (1 << t->dm) <= 256 ? launch_leaf_values_tc(t, kp, s) : launch_leaf_values_generic(t, kp, s);
             t->launches += 1;
         }
@@ -422,7 +438,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
 // Evaluations of the bin pass (every query against every point), counted on
 // the host; the levelwise schedule counts its own on the device.
 static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
-    return p->schedule == FSG_SCHED_LEVELWISE ? 0 : t->n * t->n;
+    return p->schedule == FSG_SCHED_LEVELWISE ? 0 : bin_pass_evals(t, p->precision);
 }
 
 // Statistics known on the host: samples run, bin-pass evaluations.

@@ -120,6 +120,7 @@ cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStrea
 bool kde_bins_supported(const fsg_tree* t);
 cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 bool kde_bins_sym_supported(const fsg_tree* t);
+int64_t kde_bins_sym_evals(const fsg_tree* t);
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
                                cudaStream_t s);
 cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);

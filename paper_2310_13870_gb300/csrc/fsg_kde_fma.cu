@@ -15,6 +15,7 @@
 // staged into shared memory by cp.async.bulk on a 3-stage mbarrier ring.
 // Bin totals are staged in shared memory and written out as [query][bin] rows.
 #include <climits>
+#include <vector>
 
 #include "fsg_internal.cuh"
 
@@ -239,26 +240,47 @@ cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStrea
 
 // ---------------------------------------------------------------------------
 // Symmetric bin pass.  k(x_q, x_p) = k(x_p, x_q), so each unordered pair is
-// evaluated once: CTA (k1, k2), k2 >= k1, takes the 8 bins of block k1 as
-// queries (warp w <-> bin 8 k1 + w, lane <-> 4 consecutive queries of that
-// bin, as two FP32x2 pairs) and the points of block k2.  The value is added
-// to the query's row (register accumulators per bin, as in the plain pass)
-// and, for k2 > k1, to the point's row at the query's bin: the warp's 4 x 32
-// values per point are summed by a 16-point reduce-scatter across lanes, so
-// each lane ends up holding the bin sum of one point.  Diagonal blocks
-// (k2 == k1) are evaluated in both orders and not mirrored.  Every (row, bin)
-// entry has exactly one writer; rows are staged in shared memory and written
-// as 32-byte pieces.  Requires bins of at most 128 points.
+// evaluated once.  Bins are grouped into blocks of G consecutive bins; CTA
+// (k1, k2), k2 >= k1, takes the queries of block k1 and the points of block k2.
+//
+// Query side: the block's queries are laid out over the CTA's 256 lanes, each
+// bin on its own run of ceil(m/4) lanes (4 consecutive queries per lane, as
+// two FP32x2 pairs), so no lane mixes two bins and few lane slots are empty
+// whatever the bin size m.  A warp's 32 lanes then meet at most three bins
+// (every bin spans >= 16 lanes): "first" bin on the low lanes, "middle" bin,
+// "last" bin on the high lanes.
+//
+// Point side: one shared-memory stage per point bin (cp.async.bulk on an
+// mbarrier ring), so a bin's row sums are complete when its stage is done.
+//
+// Each value goes to the query's row (register accumulators, written when the
+// point bin ends) and, for k2 > k1, to the point's row at the query's bin:
+// per batch of 16 points the warp reduce-scatters the lane sums of its
+// first/last bins (half-warp sums: first bin on lanes 0-15, last bin on lanes
+// 16-31, or their total when there is no last bin) and of its middle bin,
+// and adds them to a shared-memory row per point.  A bin spans at most two
+// warps, so each (point, bin) entry receives at most two additions onto zero,
+// whose result does not depend on their order.  Diagonal blocks (k2 == k1)
+// are evaluated in both orders and not mirrored.
+// Requires bins of 61..128 points (at most 16 per block).
 // ---------------------------------------------------------------------------
 namespace fsg {
 namespace {
 
-constexpr int kSymWarps = 8;        // bins per block
+constexpr int kSymWarps = 8;
 constexpr int kSymThreads = kSymWarps * 32;
-constexpr int kSymTile = 128;       // points per shared-memory stage
+constexpr int kSymMaxBin = 128;     // points per bin (one shared-memory stage)
+constexpr int kSymMinBin = 61;      // a bin covers >= 16 lanes
+constexpr int kSymNodes = 16;       // bins per block at most
 constexpr int kSymStages = 3;
-constexpr int kSymBatch = 16;       // points per mirror reduce-scatter
+// points per mirror reduce-scatter (fewer for large d, to stay within 128 registers)
+template <int D>
+struct SymBatch {
+    static constexpr int B = D <= 9 ? 16 : 8;
+};
 
+// Kernel values of one point against the lane's four queries; adds them to
+// the row accumulators and returns their sum.
 template <int D, bool MASK>
 __device__ __forceinline__ float sym_point(const float* __restrict__ tp, int p, int gpos, const uint64_t (&q)[2][D],
                                            const int32_t (&qmask)[4], uint64_t nc2, uint64_t (&acc)[2]) {
@@ -303,11 +325,12 @@ __device__ __forceinline__ float sym_point(const float* __restrict__ tp, int p, 
     return t.x + t.y;
 }
 
-// Sum over the 32 lanes of v[j] (j < 16) for 16 points; lane l returns the
-// total of point (l & 15).
-__device__ __forceinline__ float reduce_scatter16(float (&v)[kSymBatch], int lane) {
+// Reduce-scatter of v[j] (j < B) over lanes: lane l returns the sum over its
+// half-warp (lanes 0-15 or 16-31) of point l % B.
+template <int B>
+__device__ __forceinline__ float reduce_scatter_half(float (&v)[B], int lane) {
 #pragma unroll
-    for (int half = 8; half >= 1; half >>= 1) {
+    for (int half = B / 2; half >= 1; half >>= 1) {
         const bool up = (lane & half) != 0;
 #pragma unroll
         for (int j = 0; j < half; ++j) {
@@ -316,67 +339,95 @@ __device__ __forceinline__ float reduce_scatter16(float (&v)[kSymBatch], int lan
             v[j] = keep + __shfl_xor_sync(0xffffffffu, send, half);
         }
     }
-    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+    float r = v[0];
+    if (B < 16) r += __shfl_xor_sync(0xffffffffu, r, 8);  // B == 8: lanes l and l ^ 8 hold halves
+    return r;
 }
 
-// The point loop of one symmetric tile; MIRROR = off-diagonal block.
-// Returns false if a bounded wait ran out.
-template <int D, bool MIRROR>
-__device__ __forceinline__ bool sym_tiles(float* pts, uint64_t* bars, const float* __restrict__ Xdup, int pa, int pe,
-                                          int ntiles, const int32_t* pbnd, int npb, const uint64_t (&q)[2][D],
-                                          const int32_t (&qmask)[4], uint64_t nc2, float* outs, float* mir, int w,
-                                          int lane, int tid, bool wvalid, int32_t* status) {
-    constexpr int DP = (D + 3) & ~3;
-    constexpr int STAGE_FLOATS = kSymTile * DP * 2;
-    uint64_t binacc[2] = {0ull, 0ull};
-    int bin = 0;
-    int next_b = pbnd[1];
+// Per-warp description of the query bins its lanes meet.
+struct SymWarp {
+    int nseg;   // bins met (0..3)
+    int rf;     // block-local index of the first one
+    bool mid;   // this lane's queries are in the middle bin
+};
 
-    for (int tile = 0; tile < ntiles; ++tile) {
-        const int s = tile % kSymStages;
-        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(tile / kSymStages) & 1u, status);
+// One batch of points (FULL: a whole batch, no bounds tests).
+template <int D, bool MIRROR, bool FULL>
+__device__ __forceinline__ void sym_batch(const float* __restrict__ tp, int pb, int nbat, int gp0,
+                                          const uint64_t (&q)[2][D], const int32_t (&qmask)[4], uint64_t nc2,
+                                          uint64_t (&acc)[2], const SymWarp& sw, float* mrow, int lane) {
+    constexpr int B = SymBatch<D>::B;
+    float colE[B], colM[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+        float tot = 0.f;
+        if (FULL || j < nbat) tot = sym_point<D, !MIRROR>(tp, pb + j, gp0 + j, q, qmask, nc2, acc);
+        colE[j] = sw.mid ? 0.f : tot;
+        colM[j] = sw.mid ? tot : 0.f;
+    }
+    if (MIRROR && sw.nseg > 0) {  // warp-uniform
+        const int pl = lane & (B - 1);
+        float eh = reduce_scatter_half<B>(colE, lane);
+        if (sw.nseg < 3) eh += __shfl_xor_sync(0xffffffffu, eh, 16);
+        if (FULL || pl < nbat) {
+            if (lane < B) atomicAdd(&mrow[(pb + pl) * kSymNodes + sw.rf], eh);
+            else if (sw.nseg == 3 && lane >= 16 && lane < 16 + B)
+                atomicAdd(&mrow[(pb + pl) * kSymNodes + sw.rf + 2], eh);
+        }
+        if (sw.nseg > 1) {
+            float mh = reduce_scatter_half<B>(colM, lane);
+            mh += __shfl_xor_sync(0xffffffffu, mh, 16);
+            if ((FULL || pl < nbat) && lane < B) atomicAdd(&mrow[(pb + pl) * kSymNodes + sw.rf + 1], mh);
+        }
+    }
+}
+
+// The point-bin loop of one CTA.  Returns false if a bounded wait ran out.
+template <int D, bool MIRROR>
+__device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars, const float* __restrict__ Xdup,
+                                         const int32_t* pbn, int np, const uint64_t (&q)[2][D],
+                                         const int32_t (&qmask)[4], const int32_t (&qpos)[4], uint64_t nc2,
+                                         const SymWarp& sw, int lane, int tid, int32_t* status,
+                                         float* __restrict__ binsum, int nb, int pn0, int qn0, int nq) {
+    constexpr int DP = (D + 3) & ~3;
+    constexpr int STAGE_FLOATS = kSymMaxBin * DP * 2;
+    for (int b = 0; b < np; ++b) {
+        const int s = b % kSymStages;
+        const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)(b / kSymStages) & 1u, status);
         if (__syncthreads_or(!ok)) {
-            for (int t2 = tile + 1; t2 < min(ntiles, tile + kSymStages); ++t2)
-                mbar_wait_bounded(&bars[t2 % kSymStages], (uint32_t)(t2 / kSymStages) & 1u, status);
+            for (int b2 = b + 1; b2 < min(np, b + kSymStages); ++b2)
+                mbar_wait_bounded(&bars[b2 % kSymStages], (uint32_t)(b2 / kSymStages) & 1u, status);
             return false;
         }
         const float* tp = pts + s * STAGE_FLOATS;
-        const int t0 = pa + tile * kSymTile;
-        const int cnt = min(kSymTile, pe - t0);
-        for (int pb = 0; pb < cnt; pb += kSymBatch) {
-            const int nbat = min(kSymBatch, cnt - pb);
-            float colv[kSymBatch];
+        float* mrow = mir + (b & 1) * kSymMaxBin * kSymNodes;
+        const int t0 = pbn[b], cnt = pbn[b + 1] - t0;
+        uint64_t acc[2] = {0ull, 0ull};
+        constexpr int B = SymBatch<D>::B;
+        int pb = 0;
+        for (; pb + B <= cnt; pb += B)
+            sym_batch<D, MIRROR, true>(tp, pb, B, t0 + pb, q, qmask, nc2, acc, sw, mrow, lane);
+        if (pb < cnt) sym_batch<D, MIRROR, false>(tp, pb, cnt - pb, t0 + pb, q, qmask, nc2, acc, sw, mrow, lane);
+        {   // this point bin's row sums of the lane's queries
+            const float2 v0 = f2_unpack(acc[0]), v1 = f2_unpack(acc[1]);
+            const float vv[4] = {v0.x, v0.y, v1.x, v1.y};
 #pragma unroll
-            for (int j = 0; j < kSymBatch; ++j) {
-                colv[j] = 0.f;
-                if (j < nbat) {
-                    const int gp = t0 + pb + j;
-                    colv[j] = sym_point<D, !MIRROR>(tp, pb + j, gp, q, qmask, nc2, binacc);
-                    if (gp + 1 == next_b) {  // end of a point bin: store this lane's 4 row sums
-                        const float2 v0 = f2_unpack(binacc[0]), v1 = f2_unpack(binacc[1]);
-                        const int qb = (w * 32 + lane) * 4;
-                        outs[(qb + 0) * kSymWarps + bin] = v0.x;
-                        outs[(qb + 1) * kSymWarps + bin] = v0.y;
-                        outs[(qb + 2) * kSymWarps + bin] = v1.x;
-                        outs[(qb + 3) * kSymWarps + bin] = v1.y;
-                        binacc[0] = binacc[1] = 0ull;
-                        ++bin;
-                        next_b = bin < npb ? pbnd[bin + 1] : -1;
-                    }
-                }
-            }
-            if (MIRROR) {
-                const float tot = reduce_scatter16(colv, lane);
-                const int pl = lane & 15;
-                if (lane < 16 && pl < nbat && wvalid) mir[(t0 + pb - pa + pl) * kSymWarps + w] = tot;
-            }
+            for (int h = 0; h < 4; ++h)
+                if (qpos[h] >= 0) binsum[(size_t)qpos[h] * nb + pn0 + b] = vv[h];
         }
         __syncthreads();
-        if (tid == 0 && tile + kSymStages < ntiles) {
-            const int p0 = pa + (tile + kSymStages) * kSymTile;
-            const uint32_t bytes = (uint32_t)min(kSymTile, pe - p0) * DP * 2 * 4;
+        if (tid == 0 && b + kSymStages < np) {
+            const int p0 = pbn[b + kSymStages];
+            const uint32_t bytes = (uint32_t)(pbn[b + kSymStages + 1] - p0) * DP * 2 * 4;
             mbar_arrive_expect_tx(&bars[s], bytes);
             bulk_g2s(pts + s * STAGE_FLOATS, Xdup + (size_t)p0 * DP * 2, bytes, &bars[s]);
+        }
+        if (MIRROR) {  // mirror rows of this bin's points: query bins qn0 .. qn0+nq-1
+            for (int e = tid; e < cnt * nq; e += kSymThreads) {
+                const int r = e / nq, c = e - r * nq;
+                binsum[(size_t)(t0 + r) * nb + qn0 + c] = mrow[r * kSymNodes + c];
+                mrow[r * kSymNodes + c] = 0.f;
+            }
         }
     }
     return true;
@@ -384,56 +435,65 @@ __device__ __forceinline__ bool sym_tiles(float* pts, uint64_t* bars, const floa
 
 template <int D>
 __global__ void __launch_bounds__(kSymThreads, 2)
-kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, int n,
-                    const int32_t* __restrict__ bnd, int nb, float neg_c, int self_exclude,
-                    float* __restrict__ binsum, int32_t* __restrict__ status) {
+kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, const int32_t* __restrict__ bnd,
+                    int nb, int G, float neg_c, int self_exclude, float* __restrict__ binsum,
+                    int32_t* __restrict__ status) {
     constexpr int DP = (D + 3) & ~3;
-    constexpr int STAGE_FLOATS = kSymTile * DP * 2;
-    constexpr int QMAX = kSymWarps * 128;  // query slots per block
+    constexpr int STAGE_FLOATS = kSymMaxBin * DP * 2;
     const int k2 = blockIdx.x, k1 = blockIdx.y;
     if (k2 < k1) return;
     const bool mirror = k2 > k1;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* pts = reinterpret_cast<float*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(pts + kSymStages * STAGE_FLOATS);
-    int32_t* bnd_s = reinterpret_cast<int32_t*>(bars + kSymStages);   // 2 x (kSymWarps + 1)
-    float* outs = reinterpret_cast<float*>(bnd_s + 2 * (kSymWarps + 1) + 2);  // [QMAX][8]
-    float* mir = outs + QMAX * kSymWarps;                                     // [8 * 128][8]
+    float* pts = reinterpret_cast<float*>(smem_raw);                       // [stages][128][DP][2]
+    float* mir = pts + kSymStages * STAGE_FLOATS;                          // [2][128][kSymNodes]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(mir + 2 * kSymMaxBin * kSymNodes);
+    int32_t* qb = reinterpret_cast<int32_t*>(bars + kSymStages);           // query bin bounds [G+1]
+    int32_t* pbn = qb + kSymNodes + 1;                                     // point bin bounds [G+1]
+    int32_t* lb = pbn + kSymNodes + 1;                                     // first lane of each query bin
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int qb0 = k1 * kSymWarps, pb0 = k2 * kSymWarps;
-    const int nqb = min(kSymWarps, nb - qb0), npb = min(kSymWarps, nb - pb0);
-    if (tid <= nqb) bnd_s[tid] = bnd[qb0 + tid];
-    if (tid <= npb) bnd_s[kSymWarps + 1 + tid] = bnd[pb0 + tid];
+    const int qn0 = k1 * G, pn0 = k2 * G;
+    const int nq = min(G, nb - qn0), np = min(G, nb - pn0);
+    if (tid <= nq) qb[tid] = bnd[qn0 + tid];
+    if (tid <= np) pbn[tid] = bnd[pn0 + tid];
+    for (int i = tid; i < 2 * kSymMaxBin * kSymNodes; i += kSymThreads) mir[i] = 0.f;
     if (tid == 0) {
         for (int s = 0; s < kSymStages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    const int32_t* pbnd = bnd_s + kSymWarps + 1;
-    const int pa = pbnd[0], pe = pbnd[npb];
-    const int ntiles = (pe - pa + kSymTile - 1) / kSymTile;
     if (tid == 0) {
-        for (int s = 0; s < kSymStages && s < ntiles; ++s) {
-            const int p0 = pa + s * kSymTile;
-            const uint32_t bytes = (uint32_t)min(kSymTile, pe - p0) * DP * 2 * 4;
+        lb[0] = 0;
+        for (int r = 0; r < nq; ++r) lb[r + 1] = lb[r] + (qb[r + 1] - qb[r] + 3) / 4;
+        for (int s = 0; s < kSymStages && s < np; ++s) {
+            const uint32_t bytes = (uint32_t)(pbn[s + 1] - pbn[s]) * DP * 2 * 4;
             mbar_arrive_expect_tx(&bars[s], bytes);
-            bulk_g2s(pts + s * STAGE_FLOATS, Xdup + (size_t)p0 * DP * 2, bytes, &bars[s]);
+            bulk_g2s(pts + s * STAGE_FLOATS, Xdup + (size_t)pbn[s] * DP * 2, bytes, &bars[s]);
         }
     }
-    // This warp's bin and this lane's four queries (two FP32x2 pairs).
-    const bool wvalid = w < nqb;
-    const int qlo = wvalid ? bnd_s[w] : 0, qhi = wvalid ? bnd_s[w + 1] : 0;
-    uint64_t q[2][D];
+    __syncthreads();
+    // This lane's query bin and four queries; the bins this warp meets.
+    const int nl = lb[nq];
+    auto bin_of_lane = [&](int x) {
+        int r = 0;
+        while (r + 1 < nq && x >= lb[r + 1]) ++r;
+        return r;
+    };
+    const int ru = tid < nl ? bin_of_lane(tid) : -1;
+    SymWarp sw;
+    sw.rf = w * 32 < nl ? bin_of_lane(w * 32) : 0;
+    sw.nseg = w * 32 < nl ? bin_of_lane(min(w * 32 + 31, nl - 1)) - sw.rf + 1 : 0;
+    sw.mid = ru >= 0 && ru == sw.rf + 1;
     int32_t qpos[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-        const int g = qlo + 4 * lane + h;
-        qpos[h] = g < qhi ? g : -1;
+        const int g = ru >= 0 ? qb[ru] + 4 * (tid - lb[ru]) + h : 0;
+        qpos[h] = (ru >= 0 && g < qb[ru + 1]) ? g : -1;
     }
     // Empty query slots sit at coordinate 1e19: every difference squared
     // overflows to +inf, so their kernel values (and mirror share) are 0.
+    uint64_t q[2][D];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
 #pragma unroll
@@ -448,47 +508,36 @@ kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt
     int32_t qmask[4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) qmask[h] = (!mirror && self_exclude) ? qpos[h] : -1;
-    const bool done = mirror
-        ? sym_tiles<D, true>(pts, bars, Xdup, pa, pe, ntiles, pbnd, npb, q, qmask, nc2, outs, mir, w, lane, tid,
-                             wvalid, status)
-        : sym_tiles<D, false>(pts, bars, Xdup, pa, pe, ntiles, pbnd, npb, q, qmask, nc2, outs, mir, w, lane, tid,
-                              wvalid, status);
-    if (!done) return;
-    __syncthreads();
-    // Query rows: bins pb0 .. pb0+npb-1 of every query of this block.
-    const int qa = bnd_s[0], qe = bnd_s[nqb];
-    for (int e = tid; e < (qe - qa) * npb; e += kSymThreads) {
-        const int r = e / npb, b = e - r * npb;
-        const int g = qa + r;
-        int wq = 0;
-        while (wq + 1 < nqb && g >= bnd_s[wq + 1]) ++wq;
-        const int slot = wq * 128 + (g - bnd_s[wq]);
-        binsum[(size_t)g * nb + pb0 + b] = outs[slot * kSymWarps + b];
-    }
-    // Point rows (mirror): bins qb0 .. qb0+nqb-1 of every point of block k2.
-    if (mirror) {
-        for (int e = tid; e < (pe - pa) * nqb; e += kSymThreads) {
-            const int r = e / nqb, b = e - r * nqb;
-            binsum[(size_t)(pa + r) * nb + qb0 + b] = mir[r * kSymWarps + b];
-        }
-    }
+    if (mirror)
+        sym_bins<D, true>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
+                          pn0, qn0, nq);
+    else
+        sym_bins<D, false>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
+                           pn0, qn0, nq);
+}
+
+// Bins per block: as many as fit the CTA's 256 lanes.
+int sym_block_bins(const fsg_tree* t) {
+    const int g = kSymThreads / ((t->mmax + 3) / 4);
+    return g < kSymNodes ? g : kSymNodes;
 }
 
 template <int D>
 cudaError_t launch_sym_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     constexpr int DP = (D + 3) & ~3;
-    const int nblk = (t->nb + kSymWarps - 1) / kSymWarps;
-    const size_t smem = (size_t)kSymStages * kSymTile * DP * 2 * 4 + kSymStages * 8 +
-                        (2 * (kSymWarps + 1) + 2) * 4 + (size_t)kSymWarps * 128 * kSymWarps * 4 * 2;
+    const int G = sym_block_bins(t);
+    const int nblk = (t->nb + G - 1) / G;
+    const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymNodes * 4 +
+                        kSymStages * 8 + 3 * (kSymNodes + 1) * 4;
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(kde_bins_sym_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid(nblk, nblk);
-    kde_bins_sym_kernel<D><<<grid, kSymThreads, smem, s>>>(t->Xdup, t->Xt, (int)t->n, t->bnd, t->nb, kp.neg_c,
+    kde_bins_sym_kernel<D><<<grid, kSymThreads, smem, s>>>(t->Xdup, t->Xt, t->bnd, t->nb, G, kp.neg_c,
                                                           kp.self_exclude, t->ws.binsum, t->status);
     return cudaGetLastError();
 }
@@ -496,7 +545,30 @@ cudaError_t launch_sym_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t
 }  // namespace
 
 bool kde_bins_sym_supported(const fsg_tree* t) {
-    return kde_bins_supported(t) && t->mmax <= 128;
+    return kde_bins_supported(t) && t->mmax <= kSymMaxBin && t->n / t->nb >= kSymMinBin;
+}
+
+// Kernel evaluations the symmetric pass executes: every ordered pair inside a
+// diagonal block, every unordered pair across blocks.
+int64_t kde_bins_sym_evals(const fsg_tree* t) {
+    const int G = sym_block_bins(t);
+    // node sizes follow from the halving rule: floor or ceil of n / nb
+    std::vector<int64_t> size(t->nb);
+    for (int b = 0; b < t->nb; ++b) {
+        int64_t lo = 0, hi = t->n;
+        for (int l = t->s0 - 1; l >= 0; --l) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if ((b >> l) & 1) lo = mid; else hi = mid;
+        }
+        size[b] = hi - lo;
+    }
+    int64_t sq = 0;
+    for (int b0 = 0; b0 < t->nb; b0 += G) {
+        int64_t sb = 0;
+        for (int b = b0; b < b0 + G && b < t->nb; ++b) sb += size[b];
+        sq += sb * sb;
+    }
+    return (t->n * t->n + sq) / 2;
 }
 
 cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {

@@ -36,7 +36,7 @@ FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE = 0, 1
 # Names every build of the library must export (checked by the CPU tests
 # against include/fsg.h).
 EXPORTED = [
-    "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info",
+    "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info", "fsg_bin_pass_evals",
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
     "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
@@ -121,6 +121,7 @@ def load(path: str = LIB_PATH):
     lib.fsg_free_tree.argtypes = [P]
     lib.fsg_free_tree.restype = None
     lib.fsg_tree_info.argtypes = [P, P, P, P]
+    lib.fsg_bin_pass_evals.argtypes = [P, P, P]
     lib.fsg_degrees.argtypes = [P, P, P, P]
     lib.fsg_sample_edges.argtypes = [P, P, I32, U64, P, P, P]
     lib.fsg_build_graph.argtypes = [P, P, I32, U64, I32, P, P, P, I64, P, P, P, P, P, P]
@@ -225,6 +226,13 @@ def fsg_tree_update(tree: Tree, points, stream=None):
         raise ValueError("points must be a CUDA float32 tensor of the tree's shape")
     points = points.contiguous()
     _check(load().fsg_tree_update(tree.handle, _dptr(points), _stream_ptr(stream)), "fsg_tree_update")
+
+
+def fsg_bin_pass_evals(tree: Tree, p: fsg_params) -> int:
+    """Kernel evaluations the fused schedule's bin pass executes (see fsg.h)."""
+    v = ctypes.c_int64()
+    _check(load().fsg_bin_pass_evals(tree.handle, ctypes.byref(p), ctypes.byref(v)), "fsg_bin_pass_evals")
+    return int(v.value)
 
 
 def fsg_profile(tree: Tree, enable: bool = True):

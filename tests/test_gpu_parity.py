@@ -301,3 +301,39 @@ def test_host_entry_point_matches_device_path(fsg):
     # a second call reuses the cached tree and gives the same result
     src2, dst2, w2 = fsg.fsg_build_graph_host(X, fsg.params(0.1), 16, 4)
     np.testing.assert_array_equal(src2, src)
+
+
+# ----------------------------------------------------------------------------
+# Symmetric bin pass: bin sizes from 61 to 128 points (1..3 bins per warp,
+# partial last block), d with 16- and 8-point mirror batches; against the
+# oracle and against the plain pass (leaf_max 1024 gives bins > 128)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [100, 976, 1000, 3905, 4097, 8192, 12289])
+@pytest.mark.parametrize("d", [3, 16])
+def test_symmetric_pass_bin_sizes(fsg, n, d):
+    X = inputs.gaussian_mixture(n=n, d=d, k=4, box=2.0, seed=n + d)
+    sigma = 1.0 if d == 3 else 2.0
+    gam = ora.gamma(sigma)
+    L, seed = 8, 11
+    g = gpu_graph(fsg, X, sigma, L, seed)
+    gp = gpu_graph(fsg, X, sigma, L, seed, leaf_max=1024)
+    q = np.unique(np.linspace(0, n - 1, 97).astype(np.int64))
+    check_degrees(g["deg"][q], ora.degrees(X, gam, queries=q), n)
+    np.testing.assert_allclose(g["deg"], gp["deg"], rtol=2e-5)
+    smp, _, _ = ora.sample(X, gam, L, seed, queries=q)
+    check_samples(g["samples"][q], g["flags"][q], smp)
+    both = (g["flags"] == 0) & (gp["flags"] == 0)
+    np.testing.assert_array_equal(g["samples"][both], gp["samples"][both])
+
+
+def test_bin_pass_evals(fsg):
+    for n, d, sym in [(10_000, 10, True), (10_000, 17, False), (50, 3, False)]:
+        X = inputs.gaussian_mixture(n=n, d=d, seed=1)
+        tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
+        ev = fsg.fsg_bin_pass_evals(tree, fsg.params(1.5))
+        if sym:
+            assert n * n // 2 < ev < 0.6 * n * n
+        else:
+            assert ev == n * n
+        assert fsg.fsg_bin_pass_evals(tree, fsg.params(1.5, schedule=fsg.FSG_SCHED_LEVELWISE)) == 0
+        tree.close()
