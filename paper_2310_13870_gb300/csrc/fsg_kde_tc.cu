@@ -5,14 +5,17 @@
 //   ||x - y||^2 = ||x||^2 + ||y||^2 - 2 x.y   (integer units, exact norms),
 //   k = ex2(neg_c / 255^2 * ||x - y||^2).
 //
-// CTA = one block of 128 queries x one chunk of bins (their points), 6 warps:
+// CTA = one block of 128 queries x one chunk of bins (their points), 10 warps:
 //   warp 0 (one thread): TMA producer, 4-stage ring of {A: 128 query rows,
 //                        B: 256 point rows} x 64 coordinates (128-byte swizzle);
 //   warp 1 (one thread): MMA issuer, tcgen05.mma kind::f16 M=128 N=256 K=16,
 //                        FP32 accumulators in TMEM, two 256-column buffers;
 //                        warp 1 also allocates / frees the 512 TMEM columns;
-//   warps 2..5         : epilogue, one per TMEM lane quadrant: tcgen05.ld of a
-//                        row's 256 dot products, kernel values, per-bin sums.
+//   warps 2..9         : epilogue, two per TMEM lane quadrant (one per half of
+//                        the 256 columns): tcgen05.ld of 64 dot products per
+//                        wait, kernel values, per-bin partial sums kept per
+//                        column half (each row has one owner thread per half)
+//                        and added half 0 + half 1 at the end.
 // Every mbarrier wait is bounded; on a timeout the CTA records
 // FSG_ERR_TIMEOUT, stops, waits (bounded) for its MMAs and frees TMEM.
 #include <cuda.h>
@@ -30,7 +33,7 @@ constexpr int kTcM = 128;
 constexpr int kTcN = 256;
 constexpr int kTcK = 64;   // BF16 coordinates per 128-byte swizzled row
 constexpr int kTcStages = 4;
-constexpr int kTcThreads = 192;
+constexpr int kTcEpiWarps = 8;  // epilogue warps (2 or 4 per TMEM lane quadrant)
 constexpr uint32_t kABytes = kTcM * 128;
 constexpr uint32_t kBBytes = kTcN * 128;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
@@ -94,7 +97,75 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Two 32-column loads of this warp's TMEM lanes, one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[32 * h + 0]), "=r"(r[32 * h + 1]), "=r"(r[32 * h + 2]), "=r"(r[32 * h + 3]),
+              "=r"(r[32 * h + 4]), "=r"(r[32 * h + 5]), "=r"(r[32 * h + 6]), "=r"(r[32 * h + 7]),
+              "=r"(r[32 * h + 8]), "=r"(r[32 * h + 9]), "=r"(r[32 * h + 10]), "=r"(r[32 * h + 11]),
+              "=r"(r[32 * h + 12]), "=r"(r[32 * h + 13]), "=r"(r[32 * h + 14]), "=r"(r[32 * h + 15]),
+              "=r"(r[32 * h + 16]), "=r"(r[32 * h + 17]), "=r"(r[32 * h + 18]), "=r"(r[32 * h + 19]),
+              "=r"(r[32 * h + 20]), "=r"(r[32 * h + 21]), "=r"(r[32 * h + 22]), "=r"(r[32 * h + 23]),
+              "=r"(r[32 * h + 24]), "=r"(r[32 * h + 25]), "=r"(r[32 * h + 26]), "=r"(r[32 * h + 27]),
+              "=r"(r[32 * h + 28]), "=r"(r[32 * h + 29]), "=r"(r[32 * h + 30]), "=r"(r[32 * h + 31])
+            : "r"(taddr + 32u * h));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Balanced pairwise sum of 64 values (fixed order).
+__device__ __forceinline__ float tree_sum64(float (&x)[64]) {
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+#pragma unroll
+        for (int j = 0; j < w; ++j) x[j] += x[j + w];
+    }
+    return x[0];
+}
+
+// Kernel values of 64 columns of one row, added to the row's bin sums.  Bins
+// hold more than 64 points, so at most one bin ends inside the 64 columns
+// (at a column that is the same for every row of the warp).
+// CHECK: test for the ragged end (p >= pe) and the query's own position.
+template <bool CHECK>
+__device__ __forceinline__ void tc_row_chunk(float (&v)[64], const float* __restrict__ pn, int pc, float nq,
+                                             float neg_c, int q, int pe, int self_exclude, float& acc, int& bin,
+                                             int& next_b, const int32_t* __restrict__ bnd_s, int nbc,
+                                             float* __restrict__ orow) {
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        // integer units: exact while the sums stay below 2^24
+        const float arg = fmaf(-2.f, v[j], nq + pn[j]);
+        float k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+        if (CHECK && (pc + j >= pe || (self_exclude && pc + j == q))) k = 0.f;
+        v[j] = k;
+    }
+    const int jb = next_b - 1 - pc;  // the current bin ends after column jb
+    if (jb >= 0 && jb < 64) {
+        float hi[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            hi[j] = j > jb ? v[j] : 0.f;
+            v[j] = j > jb ? 0.f : v[j];
+        }
+        orow[bin] += acc + tree_sum64(v);
+        acc = tree_sum64(hi);
+        ++bin;
+        next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
+    } else {
+        acc += tree_sum64(v);
+    }
+}
+
+template <int EW>
+__global__ void __launch_bounds__(64 + 32 * EW, 1)
 kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
                    int bpc, float neg_c, int self_exclude, float* __restrict__ binsum, int32_t* __restrict__ status) {
@@ -109,14 +180,15 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     int32_t* flags = reinterpret_cast<int32_t*>(tmem_slot + 1);  // [0] abort, [1] stages consumed by MMA
     int32_t* bnd_s = flags + 2;                                   // bpc + 1
-    float* outs = reinterpret_cast<float*>(bnd_s + ((bpc + 1 + 3) & ~3));  // [128][bpc]
+    float* pnorm = reinterpret_cast<float*>(bnd_s + ((bpc + 1 + 3) & ~3));  // [epilogue warp][128]
+    float* outs = pnorm + EW * (kTcN / (EW / 4));                   // [EW/4 parts][128][bpc]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q0 = blockIdx.x * kTcM;
     const int b0 = blockIdx.y * bpc;
     const int nbc = min(nb, b0 + bpc) - b0;
     if (tid <= nbc) bnd_s[tid] = bnd[b0 + tid];
-    for (int e = tid; e < kTcM * bpc; e += kTcThreads) outs[e] = 0.f;
+    for (int e = tid; e < (EW / 4) * kTcM * bpc; e += (64 + 32 * EW)) outs[e] = 0.f;
     if (tid == 0) {
         for (int s = 0; s < kTcStages; ++s) {
             mbar_init(&full[s], 1);
@@ -124,7 +196,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 128);
+            mbar_init(&tempty[a], 32 * EW);
         }
         mbar_init(fin, 1);
         flags[0] = 0;
@@ -200,14 +272,17 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             umma_commit(&tfull[a]);
         }
     } else if (!inexact && warp >= 2) {
-        // ---- epilogue: TMEM lane quadrant (warp % 4), row = query
+        // ---- epilogue: TMEM lane quadrant (warp % 4), row = query; column part (warp - 2) / 4
+        constexpr int kCols = kTcN / (EW / 4);  // columns of each epilogue warp per tile
         const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int r = 32 * quad + lane;
         const int q = q0 + r;
         const float nq = q < n ? norms[q] : 0.f;
+        float* pn = pnorm + (warp - 2) * kCols;
+        float* orow = outs + (half * kTcM + r) * bpc;  // partial sums of this column part
         int bin = 0;
         int next_b = nbc > 0 ? bnd_s[1] : INT_MAX;
-        float acc = 0.f;
         for (int tile = 0; tile < ntile; ++tile) {
             const int a = tile & 1;
             if (*abort_flag || !mbar_wait_bounded(&tfull[a], (uint32_t)(tile >> 1) & 1u, status)) {
@@ -215,29 +290,33 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 break;
             }
             tc_fence_after();
-            const int t0 = pa + tile * kTcN;
-#pragma unroll 1
-            for (int c = 0; c < kTcN / 32; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * kTcN + 32 * c), v);
-                const int pc = t0 + 32 * c;
+            const int c0 = pa + tile * kTcN + half * kCols;  // first point of this warp's columns
+            __syncwarp();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int p = pc + j;
-                    if (p < pe) {
-                        const float arg = fmaf(-2.f, v[j], nq + norms[p]);
-                        float k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
-                        if (self_exclude && p == q) k = 0.f;
-                        acc += k;
-                        if (p + 1 == next_b) {
-                            outs[r * bpc + bin] = acc;
-                            acc = 0.f;
-                            ++bin;
-                            next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
-                        }
-                    }
-                }
+            for (int i = 0; i < kCols / 32; ++i) {
+                const int p = c0 + 32 * i + lane;
+                pn[32 * i + lane] = p < pe ? norms[p] : 0.f;
             }
+            __syncwarp();
+            while (next_b <= c0) {  // bins that ended in the other half
+                ++bin;
+                next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
+            }
+            const bool check = c0 + kCols > pe || (self_exclude && c0 < q0 + kTcM && q0 < c0 + kCols);
+            float acc = 0.f;
+            const uint32_t tcol = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * kTcN + half * kCols);
+#pragma unroll 1
+            for (int cc = 0; cc < kCols; cc += 64) {
+                float v[64];
+                tmem_ld64(tcol + (uint32_t)cc, v);
+                if (check)
+                    tc_row_chunk<true>(v, pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b, bnd_s,
+                                       nbc, orow);
+                else
+                    tc_row_chunk<false>(v, pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
+                                        bnd_s, nbc, orow);
+            }
+            if (bin < nbc) orow[bin] += acc;  // the bin that continues past this half
             tc_fence_before();
             mbar_arrive(&tempty[a]);
         }
@@ -245,9 +324,12 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     __syncthreads();
     if (!inexact && !*abort_flag) {
         const int nq = min(kTcM, n - q0);
-        for (int e = tid; e < nq * nbc; e += kTcThreads) {
+        for (int e = tid; e < nq * nbc; e += (64 + 32 * EW)) {
             const int ql = e / nbc, b = e - ql * nbc;
-            binsum[(size_t)(q0 + ql) * nb + b0 + b] = outs[ql * bpc + b];
+            float v = outs[ql * bpc + b];
+#pragma unroll
+            for (int h = 1; h < EW / 4; ++h) v += outs[(h * kTcM + ql) * bpc + b];
+            binsum[(size_t)(q0 + ql) * nb + b0 + b] = v;
         }
     }
     if (inexact && tid == 0) atomicExch(status, FSG_ERR_UNSUPPORTED);
@@ -338,19 +420,25 @@ int tc_prepare(fsg_tree* t, cudaStream_t s) {
 
 bool kde_bins_tc_supported(const fsg_tree* t) { return t->Xb != nullptr && t->d >= 64; }
 
+namespace {
+size_t tc_bins_smem(int ew, int bpc) {
+    return 1024 + (size_t)kTcStages * kStageBytes + 8 * (2 * kTcStages + 5) + 16 + (size_t)((bpc + 1 + 3) & ~3) * 4 +
+           (size_t)ew * (kTcN / (ew / 4)) * 4 + (size_t)(ew / 4) * kTcM * bpc * 4;
+}
+}  // namespace
+
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const int qblocks = (int)((t->n + kTcM - 1) / kTcM);
     int chunks = (4 * 152 + qblocks - 1) / qblocks;
     if (chunks < 1) chunks = 1;
     if (chunks > t->nb) chunks = t->nb;
     int bpc = (t->nb + chunks - 1) / chunks;
-    if (bpc > 32) bpc = 32;
+    if (bpc > 24) bpc = 24;  // two [128][bpc] sum arrays beside the 4-stage ring
     chunks = (t->nb + bpc - 1) / bpc;
-    const size_t smem = 1024 + (size_t)kTcStages * kStageBytes + 8 * (2 * kTcStages + 5) + 16 +
-                        (size_t)((bpc + 1 + 3) & ~3) * 4 + (size_t)kTcM * bpc * 4;
+    const size_t smem = tc_bins_smem(kTcEpiWarps, bpc);
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kde_bins_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(kde_bins_tc_kernel<kTcEpiWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(227 * 1024));
         if (e != cudaSuccess) return e;
         attr = true;
@@ -358,7 +446,7 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
     // integer units: ||255 x - 255 y||^2 = 255^2 ||x - y||^2
     const float nc = kp.neg_c / (255.f * 255.f);
     dim3 grid(qblocks, chunks);
-    kde_bins_tc_kernel<<<grid, kTcThreads, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(t->tmap_a),
+    kde_bins_tc_kernel<kTcEpiWarps><<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(t->tmap_a),
                                                       *reinterpret_cast<const CUtensorMap*>(t->tmap_b), t->norms,
                                                       (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc, nc,
                                                       kp.self_exclude, t->ws.binsum, t->status);
