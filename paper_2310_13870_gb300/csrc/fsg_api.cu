@@ -84,8 +84,9 @@ cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t
 
 // Kernel evaluations the bin pass executes (n^2, or about n^2/2 when symmetric).
 int64_t bin_pass_evals(const fsg_tree* t, int precision) {
-    if (!use_tc(t, precision) && t->d <= kMaxFmaDim && kde_bins_sym_supported(t)) return kde_bins_sym_evals(t);
-    return t->n * t->n;
+    if (use_tc(t, precision)) return t->n * t->n;
+    if (t->d <= kMaxFmaDim) return kde_bins_sym_supported(t) ? kde_bins_sym_evals(t) : t->n * t->n;
+    return kde_bins_generic_sym_supported(t) ? kde_bins_generic_sym_evals(t) : t->n * t->n;
 }
 
 int check_path(const fsg_tree* t, const fsg_params* p) {

@@ -130,6 +130,8 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
                            fsg_stats* d_stats, cudaStream_t s);
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+bool kde_bins_generic_sym_supported(const fsg_tree* t);
+int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);

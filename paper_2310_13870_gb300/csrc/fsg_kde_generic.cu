@@ -9,7 +9,9 @@
 //   leaf_values_generic_kernel: for the items (queries) of one bin, the kernel
 //                               value at every leaf slot of the bin's tree,
 //                               written to a global [item][slot] buffer that the
-//                               leaf finish reads.
+//                               leaf finish reads;
+//   kde_bins_generic_sym_kernel: the bin pass evaluating each unordered pair
+//                               once (bins of <= 128 points), see below.
 #include <climits>
 
 #include "fsg_internal.cuh"
@@ -199,9 +201,232 @@ leaf_values_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Symmetric bin pass for d > 16.  The positions are cut into tiles of 128;
+// CTA (i, j >= i) (a linear index over the triangle) evaluates the 128 x 128
+// block of tile i (queries) against tile j (points) once, with FP32x2 pairs of
+// queries against duplicated point coordinates.  Its row sums go to (query,
+// point bin) and, for j > i, its column sums to (point, query bin).  The
+// partial sums are reduced in shared memory in a fixed order, then added with
+// one atomic addition per (row, bin) and CTA into bin sums zeroed beforehand.
+// A bin of <= 128 points meets at most two tiles, so every bin sum receives
+// at most two additions onto zero and does not depend on their order.
+// ---------------------------------------------------------------------------
+constexpr int kST = 128;             // tile side (queries and points)
+constexpr int kSK = 32;              // coordinates per chunk
+constexpr int kSQS = kST + 4;        // transposed query row stride (floats)
+constexpr int kSPS = kST + 2;        // transposed point row stride (float pairs)
+constexpr size_t kSymGenSmem = (size_t)kSK * kSQS * 4 + (size_t)kSK * kSPS * 8;
+
+// Tile pair (i, j >= i) of the linear index L over the upper triangle of T tiles.
+__device__ __forceinline__ void tri_index(long long L, int T, int& i, int& j) {
+    const double b = 2.0 * T + 1.0;
+    long long ii = (long long)((b - sqrt(b * b - 8.0 * (double)L)) * 0.5);
+    auto start = [&](long long r) { return r * T - r * (r - 1) / 2; };
+    if (ii < 0) ii = 0;
+    if (ii > T - 1) ii = T - 1;
+    while (ii > 0 && start(ii) > L) --ii;
+    while (ii + 1 < T && start(ii + 1) <= L) ++ii;
+    i = (int)ii;
+    j = (int)(ii + (L - start(ii)));
+}
+
+// First bin whose range contains position x (bnd ascending, bnd[nb] = n).
+__device__ __forceinline__ int bin_of(const int32_t* __restrict__ bnd, int nb, int x) {
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bnd[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kGT, 2)
+kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t* __restrict__ bnd, int nb,
+                            int T, float neg_c, int self_exclude, float* __restrict__ binsum) {
+    extern __shared__ __align__(16) float gsm[];
+    float* Qs = gsm;                                   // [kSK][kSQS]  query coordinate k of row r
+    float* Ps = gsm + kSK * kSQS;                      // [kSK][kSPS][2] point coordinate, twice
+    __shared__ int qb_s[4], pb_s[4];                   // bin bounds met by the two tiles
+    __shared__ int qbin0, pbin0, nqbin, npbin;
+    int ti, tj;
+    tri_index((long long)blockIdx.x, T, ti, tj);
+    const bool mirror = tj > ti;
+    const int tid = threadIdx.x, tq = tid & 15, tp = tid >> 4;
+    const int Q0 = ti * kST, P0 = tj * kST;
+    if (tid == 0) {
+        const int qe = min(Q0 + kST, n) - 1, pe = min(P0 + kST, n) - 1;
+        qbin0 = bin_of(bnd, nb, Q0);
+        pbin0 = bin_of(bnd, nb, P0);
+        nqbin = bin_of(bnd, nb, qe) - qbin0 + 1;
+        npbin = bin_of(bnd, nb, pe) - pbin0 + 1;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        qb_s[tid] = bnd[min(qbin0 + tid, nb)];
+        pb_s[tid] = bnd[min(pbin0 + tid, nb)];
+    }
+    // accumulators: 4 query pairs x 8 points (points 4 tp .. +3 and 64 + 4 tp .. +3)
+    uint64_t acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0ull;
+    for (int k0 = 0; k0 < dp; k0 += kSK) {
+        __syncthreads();
+        // chunk [k0, k0 + 32) of the 128 query rows and 128 point rows, transposed
+        for (int e = tid; e < kST * (kSK / 4); e += kGT) {
+            const int r = e >> 3, v = e & 7;
+            const int k = k0 + 4 * v;
+            float4 x = make_float4(1e19f, 1e19f, 1e19f, 1e19f);
+            if (Q0 + r < n) x = k < dp ? *reinterpret_cast<const float4*>(Xt + (size_t)(Q0 + r) * dp + k)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            else if (k >= dp) x = make_float4(0.f, 0.f, 0.f, 0.f);
+            Qs[(4 * v + 0) * kSQS + r] = x.x;
+            Qs[(4 * v + 1) * kSQS + r] = x.y;
+            Qs[(4 * v + 2) * kSQS + r] = x.z;
+            Qs[(4 * v + 3) * kSQS + r] = x.w;
+            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (P0 + r < n && k < dp) y = *reinterpret_cast<const float4*>(Xt + (size_t)(P0 + r) * dp + k);
+            float2* pd = reinterpret_cast<float2*>(Ps);
+            pd[(4 * v + 0) * kSPS + r] = make_float2(y.x, y.x);
+            pd[(4 * v + 1) * kSPS + r] = make_float2(y.y, y.y);
+            pd[(4 * v + 2) * kSPS + r] = make_float2(y.z, y.z);
+            pd[(4 * v + 3) * kSPS + r] = make_float2(y.w, y.w);
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int k = 0; k < kSK; ++k) {
+            const ulonglong2 qa = *reinterpret_cast<const ulonglong2*>(Qs + k * kSQS + 8 * tq);
+            const ulonglong2 qb = *reinterpret_cast<const ulonglong2*>(Qs + k * kSQS + 8 * tq + 4);
+            const uint64_t qv[4] = {qa.x, qa.y, qb.x, qb.y};
+            const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(Ps + 2 * (k * kSPS));
+            const ulonglong2 p0 = pr[2 * tp], p1 = pr[2 * tp + 1], p2 = pr[32 + 2 * tp], p3 = pr[32 + 2 * tp + 1];
+            const uint64_t pv[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y};
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const uint64_t dd = f2_sub(qv[a], pv[b]);
+                    acc[a][b] = f2_fma(dd, dd, acc[a][b]);
+                }
+            }
+        }
+    }
+    // kernel values of the thread's 8 queries x 8 points
+    float kv[8][8];
+    const uint64_t nc2 = f2_pack(neg_c, neg_c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float2 sv = f2_unpack(f2_mul(acc[a][b], nc2));
+            const int p = P0 + (b < 4 ? 4 * tp + b : 64 + 4 * tp + b - 4);
+            const int q0 = Q0 + 8 * tq + 2 * a;
+            float k0 = ex2_approx(sv.x), k1 = ex2_approx(sv.y);
+            if (p >= n) k0 = k1 = 0.f;
+            if (self_exclude && !mirror) {
+                if (p == q0) k0 = 0.f;
+                if (p == q0 + 1) k1 = 0.f;
+            }
+            kv[2 * a][b] = k0;
+            kv[2 * a + 1][b] = k1;
+        }
+    }
+    __syncthreads();  // the coordinate tiles become the partial-sum buffers
+    float* rowp = gsm;                   // [16 tp][128 q][3 point bins]
+    float* colp = gsm + 16 * kST * 3;    // [16 tq][128 p][3 query bins]
+    {
+        // row partials: the thread's points split into <= 2 bins per group of 4
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float r3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int p = P0 + 64 * g + 4 * tp + jj;
+                    const int lb = (p >= pb_s[1]) + (p >= pb_s[2]);
+                    const float k = kv[i][4 * g + jj];
+                    r3[0] += lb == 0 ? k : 0.f;
+                    r3[1] += lb == 1 ? k : 0.f;
+                    r3[2] += lb == 2 ? k : 0.f;
+                }
+            }
+            float* dst = rowp + (tp * kST + 8 * tq + i) * 3;
+            dst[0] = r3[0];
+            dst[1] = r3[1];
+            dst[2] = r3[2];
+        }
+        if (mirror) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                float c3[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int q = Q0 + 8 * tq + i;
+                    const int lb = (q >= qb_s[1]) + (q >= qb_s[2]);
+                    const float k = kv[i][b];
+                    c3[0] += lb == 0 ? k : 0.f;
+                    c3[1] += lb == 1 ? k : 0.f;
+                    c3[2] += lb == 2 ? k : 0.f;
+                }
+                const int pl = b < 4 ? 4 * tp + b : 64 + 4 * tp + b - 4;
+                float* dst = colp + (tq * kST + pl) * 3;
+                dst[0] = c3[0];
+                dst[1] = c3[1];
+                dst[2] = c3[2];
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kST * 3; e += kGT) {
+        const int r = e / 3, b = e - 3 * r;
+        if (b < npbin && Q0 + r < n) {
+            float s = 0.f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s += rowp[(u * kST + r) * 3 + b];
+            atomicAdd(&binsum[(size_t)(Q0 + r) * nb + pbin0 + b], s);
+        }
+        if (mirror && b < nqbin && P0 + r < n) {
+            float s = 0.f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s += colp[(u * kST + r) * 3 + b];
+            atomicAdd(&binsum[(size_t)(P0 + r) * nb + qbin0 + b], s);
+        }
+    }
+}
+
 }  // namespace
 
+bool kde_bins_generic_sym_supported(const fsg_tree* t) { return t->d > kMaxFmaDim && t->mmax <= kST; }
+
+// Evaluations executed by the symmetric generic pass: the triangle of tiles.
+int64_t kde_bins_generic_sym_evals(const fsg_tree* t) {
+    const int64_t T = (t->n + kST - 1) / kST;
+    return T * (T + 1) / 2 * kST * kST;
+}
+
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (kde_bins_generic_sym_supported(t)) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(kde_bins_generic_sym_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymGenSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        cudaError_t e = cudaMemsetAsync(t->ws.binsum, 0, sizeof(float) * (size_t)t->n * t->nb, s);
+        if (e != cudaSuccess) return e;
+        const int64_t T = (t->n + kST - 1) / kST;
+        const int64_t ctas = T * (T + 1) / 2;
+        if (ctas > INT_MAX) return cudaErrorInvalidValue;
+        kde_bins_generic_sym_kernel<<<(unsigned)ctas, kGT, kSymGenSmem, s>>>(t->Xt, (int)t->n, t->dp, t->bnd, t->nb,
+                                                                           (int)T, kp.neg_c, kp.self_exclude,
+                                                                           t->ws.binsum);
+        return cudaGetLastError();
+    }
     const int qblocks = (int)((t->n + kGQ - 1) / kGQ);
     int chunks = (2048 + qblocks - 1) / qblocks;
     if (chunks < 1) chunks = 1;

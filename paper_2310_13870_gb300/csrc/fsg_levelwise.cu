@@ -2,7 +2,8 @@
 // literally on the GPU, one launch per level of the halving tree.  At level
 // lev every distinct node reached by a query's samples gets both halves'
 // KDEs (Eq. 1) computed afresh with FP32 direct differences, one warp per
-// query, lanes striding over the node's points, butterfly sums; then each
+// query (lanes striding over the node's points for d <= 16, over each point's
+// coordinates for larger d), butterfly sums; then each
 // sample at that node takes its decision.  There is no bin pass and no reuse
 // of sums across levels: this is the comparison point for the fused
 // schedule, and gives the same samples up to flagged decisions.
@@ -18,6 +19,7 @@ constexpr unsigned kFullLw = 0xffffffffu;
 template <int DP>
 struct Query {
     float4 v[DP / 4];
+    __device__ __forceinline__ const float* row() const { return nullptr; }
     __device__ __forceinline__ void load(const float* __restrict__ xq, int) {
 #pragma unroll
         for (int c = 0; c < DP / 4; ++c) v[c] = reinterpret_cast<const float4*>(xq)[c];
@@ -39,6 +41,7 @@ template <>
 struct Query<0> {
     const float* x;
     __device__ __forceinline__ void load(const float* __restrict__ xq, int) { x = xq; }
+    __device__ __forceinline__ const float* row() const { return x; }
     __device__ __forceinline__ float dist2(const float* __restrict__ xp, int dp) const {
         float s = 0.f;
         for (int c = 0; c < dp; c += 4) {
@@ -54,21 +57,40 @@ struct Query<0> {
 };
 
 // Sums of k(x_q, x_p) over [nlo, mid) and [mid, nhi), reduced over the warp.
+// d <= 16: lanes stride over the node's points; larger d: the warp takes one
+// point at a time with lanes striding over its coordinates (coalesced rows).
 template <int DP>
 __device__ __forceinline__ void node_sums(const Query<DP>& xq, const float* __restrict__ Xt, int dp, int q,
                                           int nlo, int mid, int nhi, const KernelParams& kp, int lane, float& gl,
                                           float& gr) {
     gl = 0.f;
     gr = 0.f;
-    for (int p = nlo + lane; p < nhi; p += 32) {
-        float k = ex2_approx(xq.dist2(Xt + (size_t)p * dp, dp) * kp.neg_c);
-        if (kp.self_exclude && p == q) k = 0.f;
-        if (p < mid) gl += k; else gr += k;
-    }
+    if constexpr (DP == 0) {
+        const float* xqr = xq.row();
+        for (int p = nlo; p < nhi; ++p) {
+            const float* xp = Xt + (size_t)p * dp;
+            float s = 0.f;
+            for (int t = lane; t < dp; t += 32) {
+                const float dd = xqr[t] - xp[t];
+                s = fmaf(dd, dd, s);
+            }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gl += __shfl_xor_sync(kFullLw, gl, o);
-        gr += __shfl_xor_sync(kFullLw, gr, o);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFullLw, s, o);
+            float k = ex2_approx(s * kp.neg_c);
+            if (kp.self_exclude && p == q) k = 0.f;
+            if (p < mid) gl += k; else gr += k;
+        }
+    } else {
+        for (int p = nlo + lane; p < nhi; p += 32) {
+            float k = ex2_approx(xq.dist2(Xt + (size_t)p * dp, dp) * kp.neg_c);
+            if (kp.self_exclude && p == q) k = 0.f;
+            if (p < mid) gl += k; else gr += k;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gl += __shfl_xor_sync(kFullLw, gl, o);
+            gr += __shfl_xor_sync(kFullLw, gr, o);
+        }
     }
 }
 
