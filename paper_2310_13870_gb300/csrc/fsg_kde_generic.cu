@@ -133,75 +133,6 @@ kde_bins_generic_kernel(const float* __restrict__ Xt, int n, int d, int dp, cons
     }
 }
 
-// Leaf values: CTA (b, y) handles item chunks y, y + gridDim.y, ... of bin
-// b's segment; slots of the bin's perfect tree whose node is empty get 0.
-__global__ void __launch_bounds__(kGT, 2)
-leaf_values_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__ bnd,
-                           const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q, float neg_c,
-                           int self_exclude, int leafmax, float* __restrict__ Vg) {
-    __shared__ __align__(16) float Qs[kGK * kGQ];
-    __shared__ __align__(16) float Ps[kGK * kGP];
-    __shared__ int qrow[kGQ], prow[kGP];
-    const int tid = threadIdx.x, tq = tid & 15, tp = tid >> 4;
-    const int b = blockIdx.x;
-    const int seg = bin_off[b * kBinSlots];
-    const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
-    const int nchunks = (cnt + kGQ - 1) / kGQ;
-    if ((int)blockIdx.y >= nchunks) return;
-    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;
-    const int dm = ceil_log2_dev(m), leaf0 = 1 << dm;
-    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
-        const int it0 = chunk * kGQ;
-        const int qcnt = min(kGQ, cnt - it0);
-        for (int s0 = 0; s0 < leaf0; s0 += kGP) {
-            __syncthreads();
-            if (tid < kGQ) qrow[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
-            if (tid < kGP) {
-                const int sl = s0 + tid;
-                int pos = -1;
-                if (sl < leaf0) {
-                    int a = 0, c = m;
-                    for (int t = dm - 1; t >= 0; --t) {
-                        const int mid = a + (c - a) / 2;
-                        if ((sl >> t) & 1) a = mid; else c = mid;
-                    }
-                    if (c - a == 1) pos = p_lo + a;
-                }
-                prow[tid] = pos;
-            }
-            float acc[8][4];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-            for (int k0 = 0; k0 < dp; k0 += kGK) {
-                __syncthreads();
-                load_chunk(Qs, kGQ, qrow, Xt, dp, k0);
-                load_chunk(Ps, kGP, prow, Xt, dp, k0);
-                __syncthreads();
-                accumulate_chunk(Qs, Ps, tq, tp, acc);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int qq = 8 * tq + i;
-                if (qq >= qcnt) continue;
-                const int qp = qrow[qq];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int sl = s0 + 4 * tp + j;
-                    if (sl < leaf0) {
-                        const int pp = prow[4 * tp + j];
-                        float k = pp >= 0 ? ex2_approx(acc[i][j] * neg_c) : 0.f;
-                        if (self_exclude && pp == qp) k = 0.f;
-                        Vg[(size_t)(seg + it0 + qq) * leafmax + sl] = k;
-                    }
-                }
-            }
-        }
-    }
-}
-
-
 // ---------------------------------------------------------------------------
 // Symmetric bin pass for d > 16.  The positions are cut into tiles of 128;
 // CTA (i, j >= i) (a linear index over the triangle) evaluates the 128 x 128
@@ -219,6 +150,73 @@ constexpr int kSQS = kST + 4;        // transposed query row stride (floats)
 constexpr int kSPS = kST + 2;        // transposed point row stride (float pairs)
 constexpr size_t kSymGenSmem = (size_t)kSK * kSQS * 4 + (size_t)kSK * kSPS * 8;
 
+// Packed 128 x 128 tiles.  Thread (tq, tp) of 256 holds the rows 4 tq .. 4 tq + 3
+// and 64 + 4 tq .. 64 + 4 tq + 3 (four FP32x2 pairs) and the columns 4 tp ..
+// 4 tp + 3 and 64 + 4 tp .. 64 + 4 tp + 3 (NPG = 1: the first group only).
+__device__ __forceinline__ int tile_row(int tq, int i) { return i < 4 ? 4 * tq + i : 64 + 4 * tq + i - 4; }
+
+// Chunk [k0, k0 + 32) of 128 rows, transposed: rows into Qs[k][r] (absent rows
+// get `fill` on real coordinates), columns into Ps[k][r] twice (absent: 0).
+// Warp w stores coordinate group v = w of 32 consecutive rows per step, so the
+// transposed stores of a warp hit 32 different banks.
+template <typename RowQ, typename RowP>
+__device__ __forceinline__ void load_tiles(float* __restrict__ Qs, float* __restrict__ Ps, RowQ rowq, RowP rowp,
+                                           const float* __restrict__ Xt, int dp, int k0, float fill) {
+    const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+    const int k = k0 + 4 * v;
+    float2* pd = reinterpret_cast<float2*>(Ps);
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+        const int r = 32 * it + lane;
+        const int qpos = rowq(r), ppos = rowp(r);
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < dp) {
+            x = qpos >= 0 ? *reinterpret_cast<const float4*>(Xt + (size_t)qpos * dp + k)
+                          : make_float4(fill, fill, fill, fill);
+        }
+        Qs[(4 * v + 0) * kSQS + r] = x.x;
+        Qs[(4 * v + 1) * kSQS + r] = x.y;
+        Qs[(4 * v + 2) * kSQS + r] = x.z;
+        Qs[(4 * v + 3) * kSQS + r] = x.w;
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ppos >= 0 && k < dp) y = *reinterpret_cast<const float4*>(Xt + (size_t)ppos * dp + k);
+        pd[(4 * v + 0) * kSPS + r] = make_float2(y.x, y.x);
+        pd[(4 * v + 1) * kSPS + r] = make_float2(y.y, y.y);
+        pd[(4 * v + 2) * kSPS + r] = make_float2(y.z, y.z);
+        pd[(4 * v + 3) * kSPS + r] = make_float2(y.w, y.w);
+    }
+}
+
+// acc[a][b] += (row pair a - column b)^2 over the 32 coordinates of the chunk.
+template <int NPG>
+__device__ __forceinline__ void accumulate_pairs(const float* __restrict__ Qs, const float* __restrict__ Ps, int tq,
+                                                 int tp, uint64_t (&acc)[4][4 * NPG]) {
+#pragma unroll 2
+    for (int k = 0; k < kSK; ++k) {
+        const ulonglong2 qa = *reinterpret_cast<const ulonglong2*>(Qs + k * kSQS + 4 * tq);
+        const ulonglong2 qb = *reinterpret_cast<const ulonglong2*>(Qs + k * kSQS + 64 + 4 * tq);
+        const uint64_t qv[4] = {qa.x, qa.y, qb.x, qb.y};
+        const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(Ps + 2 * (k * kSPS));
+        uint64_t pv[4 * NPG];
+#pragma unroll
+        for (int g = 0; g < NPG; ++g) {
+            const ulonglong2 p0 = pr[32 * g + 2 * tp], p1 = pr[32 * g + 2 * tp + 1];
+            pv[4 * g + 0] = p0.x;
+            pv[4 * g + 1] = p0.y;
+            pv[4 * g + 2] = p1.x;
+            pv[4 * g + 3] = p1.y;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int b = 0; b < 4 * NPG; ++b) {
+                const uint64_t dd = f2_sub(qv[a], pv[b]);
+                acc[a][b] = f2_fma(dd, dd, acc[a][b]);
+            }
+        }
+    }
+}
+
 // Tile pair (i, j >= i) of the linear index L over the upper triangle of T tiles.
 __device__ __forceinline__ void tri_index(long long L, int T, int& i, int& j) {
     const double b = 2.0 * T + 1.0;
@@ -232,19 +230,32 @@ __device__ __forceinline__ void tri_index(long long L, int T, int& i, int& j) {
     j = (int)(ii + (L - start(ii)));
 }
 
-// First bin whose range contains position x (bnd ascending, bnd[nb] = n).
-__device__ __forceinline__ int bin_of(const int32_t* __restrict__ bnd, int nb, int x) {
-    int lo = 0, hi = nb - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (bnd[mid] <= x) lo = mid; else hi = mid - 1;
+// Bin of position x: s0 halving steps from the root (left half = floor(size/2)).
+__device__ __forceinline__ int bin_of(int n, int s0, int x) {
+    int b = 0, lo = 0, hi = n;
+    for (int t = 0; t < s0; ++t) {
+        const int mid = lo + (hi - lo) / 2;
+        b <<= 1;
+        if (x >= mid) {
+            b |= 1;
+            lo = mid;
+        } else {
+            hi = mid;
+        }
     }
-    return lo;
+    return b;
+}
+
+// Adds v to the slot lb (0..2) of a 3-slot accumulator without indexing.
+__device__ __forceinline__ void add3(float (&r)[3], int lb, float v) {
+    r[0] += lb == 0 ? v : 0.f;
+    r[1] += lb == 1 ? v : 0.f;
+    r[2] += lb == 2 ? v : 0.f;
 }
 
 __global__ void __launch_bounds__(kGT, 2)
 kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t* __restrict__ bnd, int nb,
-                            int T, float neg_c, int self_exclude, float* __restrict__ binsum) {
+                            int s0, int T, float neg_c, int self_exclude, float* __restrict__ binsum) {
     extern __shared__ __align__(16) float gsm[];
     float* Qs = gsm;                                   // [kSK][kSQS]  query coordinate k of row r
     float* Ps = gsm + kSK * kSQS;                      // [kSK][kSPS][2] point coordinate, twice
@@ -255,77 +266,47 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const i
     const bool mirror = tj > ti;
     const int tid = threadIdx.x, tq = tid & 15, tp = tid >> 4;
     const int Q0 = ti * kST, P0 = tj * kST;
-    if (tid == 0) {
-        const int qe = min(Q0 + kST, n) - 1, pe = min(P0 + kST, n) - 1;
-        qbin0 = bin_of(bnd, nb, Q0);
-        pbin0 = bin_of(bnd, nb, P0);
-        nqbin = bin_of(bnd, nb, qe) - qbin0 + 1;
-        npbin = bin_of(bnd, nb, pe) - pbin0 + 1;
+    if (tid < 4) {  // the bins met by the two tiles (no memory access)
+        const int x = tid == 0 ? Q0 : tid == 1 ? P0 : tid == 2 ? min(Q0 + kST, n) - 1 : min(P0 + kST, n) - 1;
+        const int b = bin_of(n, s0, x);
+        if (tid == 0) qbin0 = b;
+        if (tid == 1) pbin0 = b;
+        __syncwarp(0xfu);
+        if (tid == 2) nqbin = b - qbin0 + 1;
+        if (tid == 3) npbin = b - pbin0 + 1;
     }
     __syncthreads();
     if (tid < 4) {
         qb_s[tid] = bnd[min(qbin0 + tid, nb)];
         pb_s[tid] = bnd[min(pbin0 + tid, nb)];
     }
-    // accumulators: 4 query pairs x 8 points (points 4 tp .. +3 and 64 + 4 tp .. +3)
     uint64_t acc[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0ull;
+    // Absent query rows sit at 1e19: their squared distances overflow, k = 0.
+    auto rowq = [&](int r) { return Q0 + r < n ? Q0 + r : -1; };
+    auto rowp = [&](int r) { return P0 + r < n ? P0 + r : -1; };
     for (int k0 = 0; k0 < dp; k0 += kSK) {
         __syncthreads();
-        // chunk [k0, k0 + 32) of the 128 query rows and 128 point rows, transposed
-        for (int e = tid; e < kST * (kSK / 4); e += kGT) {
-            const int r = e >> 3, v = e & 7;
-            const int k = k0 + 4 * v;
-            float4 x = make_float4(1e19f, 1e19f, 1e19f, 1e19f);
-            if (Q0 + r < n) x = k < dp ? *reinterpret_cast<const float4*>(Xt + (size_t)(Q0 + r) * dp + k)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-            else if (k >= dp) x = make_float4(0.f, 0.f, 0.f, 0.f);
-            Qs[(4 * v + 0) * kSQS + r] = x.x;
-            Qs[(4 * v + 1) * kSQS + r] = x.y;
-            Qs[(4 * v + 2) * kSQS + r] = x.z;
-            Qs[(4 * v + 3) * kSQS + r] = x.w;
-            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (P0 + r < n && k < dp) y = *reinterpret_cast<const float4*>(Xt + (size_t)(P0 + r) * dp + k);
-            float2* pd = reinterpret_cast<float2*>(Ps);
-            pd[(4 * v + 0) * kSPS + r] = make_float2(y.x, y.x);
-            pd[(4 * v + 1) * kSPS + r] = make_float2(y.y, y.y);
-            pd[(4 * v + 2) * kSPS + r] = make_float2(y.z, y.z);
-            pd[(4 * v + 3) * kSPS + r] = make_float2(y.w, y.w);
-        }
+        load_tiles(Qs, Ps, rowq, rowp, Xt, dp, k0, 1e19f);
         __syncthreads();
-#pragma unroll 2
-        for (int k = 0; k < kSK; ++k) {
-            const ulonglong2 qa = *reinterpret_cast<const ulonglong2*>(Qs + k * kSQS + 8 * tq);
-            const ulonglong2 qb = *reinterpret_cast<const ulonglong2*>(Qs + k * kSQS + 8 * tq + 4);
-            const uint64_t qv[4] = {qa.x, qa.y, qb.x, qb.y};
-            const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(Ps + 2 * (k * kSPS));
-            const ulonglong2 p0 = pr[2 * tp], p1 = pr[2 * tp + 1], p2 = pr[32 + 2 * tp], p3 = pr[32 + 2 * tp + 1];
-            const uint64_t pv[8] = {p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, p3.x, p3.y};
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const uint64_t dd = f2_sub(qv[a], pv[b]);
-                    acc[a][b] = f2_fma(dd, dd, acc[a][b]);
-                }
-            }
-        }
+        accumulate_pairs<2>(Qs, Ps, tq, tp, acc);
     }
     // kernel values of the thread's 8 queries x 8 points
     float kv[8][8];
     const uint64_t nc2 = f2_pack(neg_c, neg_c);
+    const bool last = P0 + kST > n;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             const float2 sv = f2_unpack(f2_mul(acc[a][b], nc2));
-            const int p = P0 + (b < 4 ? 4 * tp + b : 64 + 4 * tp + b - 4);
-            const int q0 = Q0 + 8 * tq + 2 * a;
+            const int p = P0 + tile_row(tp, b);
+            const int q0 = Q0 + tile_row(tq, 2 * a);
             float k0 = ex2_approx(sv.x), k1 = ex2_approx(sv.y);
-            if (p >= n) k0 = k1 = 0.f;
+            if (last && p >= n) k0 = k1 = 0.f;
             if (self_exclude && !mirror) {
                 if (p == q0) k0 = 0.f;
                 if (p == q0 + 1) k1 = 0.f;
@@ -335,45 +316,62 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const i
         }
     }
     __syncthreads();  // the coordinate tiles become the partial-sum buffers
-    float* rowp = gsm;                   // [16 tp][128 q][3 point bins]
-    float* colp = gsm + 16 * kST * 3;    // [16 tq][128 p][3 query bins]
+    float* rowpart = gsm;                   // [16 tp][128 q][3 point bins]
+    float* colpart = gsm + 16 * kST * 3;    // [16 tq][128 p][3 query bins]
     {
-        // row partials: the thread's points split into <= 2 bins per group of 4
+        // row partials: a group of 4 consecutive points usually lies in one bin
+        int lbp[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int p = P0 + tile_row(tp, b);
+            lbp[b] = (p >= pb_s[1]) + (p >= pb_s[2]);
+        }
+        const bool g0 = lbp[0] == lbp[3], g1 = lbp[4] == lbp[7];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             float r3[3] = {0.f, 0.f, 0.f};
+            if (g0) {
+                add3(r3, lbp[0], (kv[i][0] + kv[i][1]) + (kv[i][2] + kv[i][3]));
+            } else {
 #pragma unroll
-            for (int g = 0; g < 2; ++g) {
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int p = P0 + 64 * g + 4 * tp + jj;
-                    const int lb = (p >= pb_s[1]) + (p >= pb_s[2]);
-                    const float k = kv[i][4 * g + jj];
-                    r3[0] += lb == 0 ? k : 0.f;
-                    r3[1] += lb == 1 ? k : 0.f;
-                    r3[2] += lb == 2 ? k : 0.f;
-                }
+                for (int b = 0; b < 4; ++b) add3(r3, lbp[b], kv[i][b]);
             }
-            float* dst = rowp + (tp * kST + 8 * tq + i) * 3;
+            if (g1) {
+                add3(r3, lbp[4], (kv[i][4] + kv[i][5]) + (kv[i][6] + kv[i][7]));
+            } else {
+#pragma unroll
+                for (int b = 4; b < 8; ++b) add3(r3, lbp[b], kv[i][b]);
+            }
+            float* dst = rowpart + (tp * kST + tile_row(tq, i)) * 3;
             dst[0] = r3[0];
             dst[1] = r3[1];
             dst[2] = r3[2];
         }
         if (mirror) {
+            // column partials: a group of 4 consecutive queries usually lies in one bin
+            int lbq[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int q = Q0 + tile_row(tq, i);
+                lbq[i] = (q >= qb_s[1]) + (q >= qb_s[2]);
+            }
+            const bool q0u = lbq[0] == lbq[3], q1u = lbq[4] == lbq[7];
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 float c3[3] = {0.f, 0.f, 0.f};
+                if (q0u) {
+                    add3(c3, lbq[0], (kv[0][b] + kv[1][b]) + (kv[2][b] + kv[3][b]));
+                } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int q = Q0 + 8 * tq + i;
-                    const int lb = (q >= qb_s[1]) + (q >= qb_s[2]);
-                    const float k = kv[i][b];
-                    c3[0] += lb == 0 ? k : 0.f;
-                    c3[1] += lb == 1 ? k : 0.f;
-                    c3[2] += lb == 2 ? k : 0.f;
+                    for (int i = 0; i < 4; ++i) add3(c3, lbq[i], kv[i][b]);
                 }
-                const int pl = b < 4 ? 4 * tp + b : 64 + 4 * tp + b - 4;
-                float* dst = colp + (tq * kST + pl) * 3;
+                if (q1u) {
+                    add3(c3, lbq[4], (kv[4][b] + kv[5][b]) + (kv[6][b] + kv[7][b]));
+                } else {
+#pragma unroll
+                    for (int i = 4; i < 8; ++i) add3(c3, lbq[i], kv[i][b]);
+                }
+                float* dst = colpart + (tq * kST + tile_row(tp, b)) * 3;
                 dst[0] = c3[0];
                 dst[1] = c3[1];
                 dst[2] = c3[2];
@@ -386,14 +384,105 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const i
         if (b < npbin && Q0 + r < n) {
             float s = 0.f;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) s += rowp[(u * kST + r) * 3 + b];
+            for (int u = 0; u < 16; ++u) s += rowpart[(u * kST + r) * 3 + b];
             atomicAdd(&binsum[(size_t)(Q0 + r) * nb + pbin0 + b], s);
         }
         if (mirror && b < nqbin && P0 + r < n) {
             float s = 0.f;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) s += colp[(u * kST + r) * 3 + b];
+            for (int u = 0; u < 16; ++u) s += colpart[(u * kST + r) * 3 + b];
             atomicAdd(&binsum[(size_t)(P0 + r) * nb + qbin0 + b], s);
+        }
+    }
+}
+
+// Leaf values (d > 16): CTA (b, y) takes item chunks y, y + gridDim.y, ... of
+// bin b's segment: 128 items (rows) against the leaf slots of the bin's
+// perfect tree (columns, 64 NPG per tile; slots whose node is empty get 0),
+// packed as in the symmetric pass; rows of leafv[item][slot] written as float4.
+template <int NPG>
+__global__ void __launch_bounds__(kGT, 2)
+leaf_values_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__ bnd,
+                           const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q, float neg_c,
+                           int self_exclude, int leafmax, float* __restrict__ Vg) {
+    extern __shared__ __align__(16) float gsm[];
+    float* Qs = gsm;
+    float* Ps = gsm + kSK * kSQS;
+    __shared__ int qrow[kST], prow[kST];
+    const int tid = threadIdx.x, tq = tid & 15, tp = tid >> 4;
+    const int b = blockIdx.x;
+    const int seg = bin_off[b * kBinSlots];
+    const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
+    const int nchunks = (cnt + kST - 1) / kST;
+    if ((int)blockIdx.y >= nchunks) return;
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;
+    const int dm = ceil_log2_dev(m), leaf0 = 1 << dm;
+    const uint64_t nc2 = f2_pack(neg_c, neg_c);
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        const int it0 = chunk * kST;
+        const int qcnt = min(kST, cnt - it0);
+        for (int s0 = 0; s0 < leaf0; s0 += 64 * NPG) {
+            __syncthreads();
+            if (tid < kST) {
+                qrow[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
+                const int sl = s0 + tid;
+                int pos = -1;
+                if (tid < 64 * NPG && sl < leaf0) {
+                    int a = 0, c = m;
+                    for (int t = dm - 1; t >= 0; --t) {
+                        const int mid = a + (c - a) / 2;
+                        if ((sl >> t) & 1) a = mid; else c = mid;
+                    }
+                    if (c - a == 1) pos = p_lo + a;
+                }
+                prow[tid] = pos;
+            }
+            uint64_t acc[4][4 * NPG];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4 * NPG; ++c) acc[a][c] = 0ull;
+            for (int k0 = 0; k0 < dp; k0 += kSK) {
+                __syncthreads();
+                load_tiles(Qs, Ps, [&](int r) { return qrow[r]; }, [&](int r) { return prow[r]; }, Xt, dp, k0, 0.f);
+                __syncthreads();
+                accumulate_pairs<NPG>(Qs, Ps, tq, tp, acc);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                float o[2][4 * NPG];
+#pragma unroll
+                for (int c = 0; c < 4 * NPG; ++c) {
+                    const float2 sv = f2_unpack(f2_mul(acc[a][c], nc2));
+                    const int pp = prow[tile_row(tp, c)];
+                    float k0 = pp >= 0 ? ex2_approx(sv.x) : 0.f, k1 = pp >= 0 ? ex2_approx(sv.y) : 0.f;
+                    if (self_exclude) {
+                        if (pp == qrow[tile_row(tq, 2 * a)]) k0 = 0.f;
+                        if (pp == qrow[tile_row(tq, 2 * a) + 1]) k1 = 0.f;
+                    }
+                    o[0][c] = k0;
+                    o[1][c] = k1;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int rr = tile_row(tq, 2 * a) + h;
+                    if (rr >= qcnt) continue;
+                    float* dst = Vg + (size_t)(seg + it0 + rr) * leafmax + s0;
+#pragma unroll
+                    for (int g = 0; g < NPG; ++g) {
+                        const int sl = 64 * g + 4 * tp;
+                        if (leaf0 >= 4) {
+                            if (s0 + sl < leaf0)
+                                *reinterpret_cast<float4*>(dst + sl) =
+                                    make_float4(o[h][4 * g], o[h][4 * g + 1], o[h][4 * g + 2], o[h][4 * g + 3]);
+                        } else {  // rows of 1 or 2 slots
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if (s0 + sl + c < leaf0) dst[sl + c] = o[h][4 * g + c];
+                        }
+                    }
+                }
+            }
         }
     }
 }
@@ -423,7 +512,7 @@ cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, c
         const int64_t ctas = T * (T + 1) / 2;
         if (ctas > INT_MAX) return cudaErrorInvalidValue;
         kde_bins_generic_sym_kernel<<<(unsigned)ctas, kGT, kSymGenSmem, s>>>(t->Xt, (int)t->n, t->dp, t->bnd, t->nb,
-                                                                           (int)T, kp.neg_c, kp.self_exclude,
+                                                                           t->s0, (int)T, kp.neg_c, kp.self_exclude,
                                                                            t->ws.binsum);
         return cudaGetLastError();
     }
@@ -442,14 +531,28 @@ cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, c
 
 cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
-    const int64_t chunks_per_bin = (items_est / t->nb + kGQ - 1) / kGQ + 1;
+    const int64_t chunks_per_bin = (items_est / t->nb + kST - 1) / kST + 1;
     int64_t S = (152 * 2 * 8 + t->nb - 1) / t->nb;
     if (S > chunks_per_bin) S = chunks_per_bin;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
-    leaf_values_generic_kernel<<<grid, kGT, 0, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off, t->ws.items_q, kp.neg_c,
-                                                    kp.self_exclude, 1 << t->dm, t->ws.leafv);
+    const bool wide = (1 << t->dm) > 64;
+    static bool attr[2] = {false, false};
+    if (!attr[wide]) {
+        cudaError_t e = cudaFuncSetAttribute(wide ? leaf_values_generic_kernel<2> : leaf_values_generic_kernel<1>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymGenSmem);
+        if (e != cudaSuccess) return e;
+        attr[wide] = true;
+    }
+    if (wide)
+        leaf_values_generic_kernel<2><<<grid, kGT, kSymGenSmem, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off,
+                                                                     t->ws.items_q, kp.neg_c, kp.self_exclude,
+                                                                     1 << t->dm, t->ws.leafv);
+    else
+        leaf_values_generic_kernel<1><<<grid, kGT, kSymGenSmem, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off,
+                                                                     t->ws.items_q, kp.neg_c, kp.self_exclude,
+                                                                     1 << t->dm, t->ws.leafv);
     return cudaGetLastError();
 }
 

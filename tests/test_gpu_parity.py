@@ -338,3 +338,13 @@ def test_bin_pass_evals(fsg):
             assert ev == n * n
         assert fsg.fsg_bin_pass_evals(tree, fsg.params(1.5, schedule=fsg.FSG_SCHED_LEVELWISE)) == 0
         tree.close()
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 64, 129])
+def test_generic_d_small_n(fsg, n):
+    X = inputs.gaussian_mixture(n=n, d=24, k=2, box=1.0, seed=n)
+    gam = ora.gamma(3.0)
+    g = gpu_graph(fsg, X, 3.0, 6, 4)
+    o = ora.build_graph(X, gam, 6, 4)
+    check_degrees(g["deg"], o["deg"], n)
+    check_samples(g["samples"], g["flags"], o["samples"])
