@@ -125,6 +125,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The slowest rank's value (timings are reported as the max over ranks);
+    x itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput of `world` independent replicas that each process
+    `units_per_rank` units in a step of `ms` milliseconds (the slowest rank's)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def cpu_oracle_throughput(X, n_queries: int, L: int, sigma: float, seed: int):
     """The oracle (as it stands) on a bounded sample: the descent of every
     sample of n_queries points plus their degrees, on all host cores.
@@ -234,11 +252,8 @@ def run_ours(args):
     ms = statistics.mean(step_ms)
     st = fsg.stats_dict(bufs)
     m = int(bufs.m.item())
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * L / (ms * 1e-3)
+    ms = max_over_ranks(ms, device="cuda")
+    value = replica_throughput(n * L, world, ms)
     evals_per_step = st["n_evals"]
     gevals = world * evals_per_step / (ms * 1e-3) / 1e9
 
@@ -320,11 +335,8 @@ def run_ours(args):
             if r >= 2:
                 times.append(dt)
         e2e_s = statistics.mean(times)
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * n * L / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
+        e2e_s = max_over_ranks(e2e_s, device="cuda")
+        e2e = {"value": replica_throughput(n * L, world, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
                "d2h_bytes_per_step": int(8 + mm * 12), "ms_per_step": e2e_s * 1e3}
 
     cpu = None
@@ -392,7 +404,29 @@ def run_seg_batch(args):
     n_tot = sum(int(X.shape[0]) for X in imgs)
     edges = sum(int(b.m.item()) for b in batch.bufs)
     evals = sum(int(b.stats[4].item()) for b in batch.bufs)
+    flagged = sum(int(b.stats[1].item()) for b in batch.bufs)
     t = statistics.mean(ms)
+    plain = None
+    if args.plain_steps > 0:  # the same images through the plain FP32 levelwise schedule, one timed run
+        batch.close()
+        with torch.cuda.stream(stream):
+            psets = [(X, fsg.params(sigma, schedule=fsg.FSG_SCHED_LEVELWISE), L, seed) for X, _, L, seed in sets]
+            pbatch = fsg.Batch(psets, streams=4, capture=False, stream=stream)
+        pbatch.run(stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pbatch.run(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        pt = e0.elapsed_time(e1)
+        pevals = sum(int(b.stats[4].item()) for b in pbatch.bufs)
+        plain = {"schedule": "levelwise (Algorithm 1 per level, FP32 direct differences, no bin pass)",
+                 "value": n_tot * L / (pt * 1e-3), "unit": UNIT, "ms_per_step": pt, "steps": 1,
+                 "evals_per_step": pevals, "flagged_samples": sum(int(b.stats[1].item()) for b in pbatch.bufs),
+                 "speedup_of_fused": pt / t}
+        pbatch.close()
+        batch = None
     line = {"metric": METRIC, "value": n_tot * L / (t * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -400,9 +434,11 @@ def run_seg_batch(args):
                                    f"sigma=0.05, L=48, SET edges", "points": n_tot,
                        "l2": "flushed (512 MB write) between steps", "parallelism": "4 streams, CUDA graph"},
             "gkernel_evals_per_s": evals / (t * 1e-3) / 1e9, "edges_per_step": edges, "clocks": clk,
+            "flagged_samples": flagged, "plain_fp32_gpu": plain,
             "p50_ms": statistics.median(ms), "p99_ms": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))]}
     print(json.dumps(line), flush=True)
-    batch.close()
+    if batch is not None:
+        batch.close()
     return 0
 
 
@@ -482,6 +518,30 @@ def run_serving(args):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     server.close()
+    plain = None
+    if args.plain_requests > 0:
+        # closed loop: the first K timed requests submitted at once, fused vs plain schedule
+        def burst(schedule):
+            srv = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8)
+            pp = fsg.params(sigma, schedule=schedule)
+            sub = timed_reqs[: args.plain_requests]
+            t0b = time.perf_counter()
+            ids = [srv.submit(pools[r.d][: r.n], pp, L, r.seed) for r in sub]
+            done = 0
+            while done < len(ids):
+                for rec, _ in srv.poll(wait_ms=5):
+                    if rec["status"] != fsg.FSG_OK:
+                        raise RuntimeError(f"request failed: {rec}")
+                    done += 1
+            wall_b = time.perf_counter() - t0b
+            srv.close()
+            return sum(r.n for r in sub) * L / wall_b, wall_b
+        vf, wf = burst(fsg.FSG_SCHED_FUSED)
+        vp, wp = burst(fsg.FSG_SCHED_LEVELWISE)
+        plain = {"schedule": "levelwise (Algorithm 1 per level, FP32 direct differences, no bin pass)",
+                 "requests": args.plain_requests, "mode": "closed loop, all submitted at once",
+                 "fused_value": vf, "fused_wall_s": wf, "value": vp, "wall_s": wp, "unit": UNIT,
+                 "speedup_of_fused": vf / vp}
     lat_sorted = sorted(lat)
     pct = lambda a, q: a[min(len(a) - 1, int(q * len(a)))]
     line = {"metric": METRIC, "value": sampled_done / wall, "unit": UNIT, "n_gpus": 1, "steps": len(timed_reqs),
@@ -492,7 +552,7 @@ def run_serving(args):
                        "hbm_budget_gb": 120, "slots": 8, "parallelism": "continuous admission, 8 streams"},
             "p50_ms": pct(lat_sorted, 0.5), "p99_ms": pct(lat_sorted, 0.99), "max_ms": lat_sorted[-1],
             "p50_queue_ms": pct(sorted(qms), 0.5), "edges": edges_done, "wall_s": wall,
-            "offered_s": timed_reqs[-1].arrival_s - base, "clocks": clk}
+            "offered_s": timed_reqs[-1].arrival_s - base, "clocks": clk, "plain_fp32_gpu": plain}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -515,6 +575,7 @@ def main():
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--images", type=int, default=64)
+    ap.add_argument("--plain-requests", type=int, default=40, help="serving: closed-loop burst for the plain path")
     args = ap.parse_args()
     if args.n:
         set_size(args.n)
