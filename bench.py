@@ -211,6 +211,10 @@ def run_ours(args):
         bufs.deg = torch.empty(n, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    tuning = None
+    if not args.no_tune:  # launch shapes picked by the library's autotuner (untimed)
+        tuning = fsg.fsg_autotune(tree, p, L, seed, reps=3, stream=stream)
+
     def step():
         fsg.fsg_tree_update(tree, pts, stream=stream)
         fsg.fsg_build_graph(tree, p, L, seed, bufs=bufs, stream=stream)
@@ -354,7 +358,7 @@ def run_ours(args):
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
-                "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain,
+                "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches1 - launches0)}
         print(json.dumps(line), flush=True)
@@ -568,6 +572,7 @@ def main():
     ap.add_argument("--ref-queries", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch-shape heuristics")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP32 levelwise path")
     ap.add_argument("--n", type=int, default=0, help="smaller point count (profiler captures only)")
     ap.add_argument("--d", type=int, default=0, help="other dimension of the mixture workload (kernel studies)")

@@ -145,6 +145,39 @@ int fsg_tree_info(const fsg_tree* tree, int64_t* n, int32_t* d, int32_t* depth);
 int fsg_bin_pass_evals(const fsg_tree* tree, const fsg_params* params, int64_t* evals);
 
 /*
+ * Launch shapes of the fused schedule's kernels; 0 selects the built-in
+ * heuristic.  They change how work is split among CTAs, not what is
+ * computed: results stay within the stated tolerances, and samples can differ
+ * only where a decision is flagged (the grouping of FP32 partial sums of the
+ * bin passes depends on sym_bins / tc_bins; leaf_splits changes nothing).
+ */
+typedef struct {
+    int32_t sym_bins;     /* bins per block of the symmetric d <= 16 bin pass   */
+    int32_t tc_bins;      /* bins per chunk of the tensor-core bin pass (<= 24) */
+    int32_t leaf_splits;  /* CTAs per bin of the leaf finish                   */
+    int32_t reserved[5];
+} fsg_tuning;
+
+/*
+ * Autotuner: times the candidate launch shapes of the bin pass that this tree
+ * and these parameters select (symmetric FP32: 4..16 bins per block;
+ * tensor-core: 8..24 bins per chunk) and of the leaf finish (the heuristic
+ * split count x 1/4 .. 4), each the best of `reps` runs on `stream`, keeps the
+ * fastest on the tree and writes it to *out (if not NULL).  The choice is
+ * cached per (d, n, L, bin layout, path) for the process: a second call for
+ * the same shape reuses it without timing.  Synchronizes `stream`; not for
+ * use during CUDA-graph capture.  The paper has no counterpart (launch shapes
+ * of this implementation).
+ * Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED.
+ */
+int fsg_autotune(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_t seed, int32_t reps, fsg_tuning* out,
+                 void* stream);
+
+/* Sets (tuning != NULL) and/or reads (out != NULL) the tree's launch shapes.
+ * Negative fields are refused with INVALID_ARG. */
+int fsg_tree_tuning(fsg_tree* tree, const fsg_tuning* tuning, fsg_tuning* out);
+
+/*
  * Replaces the tree's points by new values of the same shape (n, d) in the
  * same tree order, without allocating (Sec. 4.1's tree is rebuilt in place).
  *   d_points : device float32 [n][d], read only during this call.

@@ -1,6 +1,11 @@
 // C ABI entry points (include/fsg.h): argument checks, the tree object and
 // its workspace, and the fixed launch sequence of each call.
 #include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -342,6 +347,143 @@ int fsg_tree_info(const fsg_tree* t, int64_t* n, int32_t* d, int32_t* depth) {
     if (n) *n = t->n;
     if (d) *d = t->d;
     if (depth) *depth = t->depth;
+    return FSG_OK;
+}
+
+static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s);
+
+namespace {
+struct TuneKey {
+    int64_t n;
+    int32_t d, L, s0, mmax, path;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(n, d, L, s0, mmax, path) < std::tie(o.n, o.d, o.L, o.s0, o.mmax, o.path);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LaunchTuning> g_tune_cache;
+
+void to_public(const LaunchTuning& lt, fsg_tuning* out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof(*out));
+    out->sym_bins = lt.sym_bins;
+    out->tc_bins = lt.tc_bins;
+    out->leaf_splits = lt.leaf_splits;
+}
+}  // namespace
+
+int fsg_tree_tuning(fsg_tree* t, const fsg_tuning* tuning, fsg_tuning* out) {
+    if (!t) return FSG_ERR_INVALID_ARG;
+    if (tuning) {
+        if (tuning->sym_bins < 0 || tuning->tc_bins < 0 || tuning->leaf_splits < 0 || tuning->leaf_splits > 65535)
+            return FSG_ERR_INVALID_ARG;
+        t->tune.sym_bins = tuning->sym_bins;
+        t->tune.tc_bins = tuning->tc_bins;
+        t->tune.leaf_splits = tuning->leaf_splits;
+    }
+    to_public(t->tune, out);
+    return FSG_OK;
+}
+
+int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t reps, fsg_tuning* out,
+                 void* stream) {
+    if (!t || L < 1 || L > kMaxL || reps < 1 || reps > 100) return FSG_ERR_INVALID_ARG;
+    int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    if ((rc = check_path(t, p)) != FSG_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    if (p->schedule != FSG_SCHED_FUSED) {  // the levelwise schedule has no shapes to choose
+        to_public(t->tune, out);
+        return FSG_OK;
+    }
+    const bool tc = use_tc(t, p->precision);
+    const int path = tc ? 2 : (t->d <= kMaxFmaDim && kde_bins_sym_supported(t)) ? 1 : 0;
+    const TuneKey key{t->n, t->d, L, t->s0, t->mmax, path};
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            t->tune = it->second;
+            to_public(t->tune, out);
+            return FSG_OK;
+        }
+    }
+    const KernelParams kp = make_kernel_params(p, L, seed);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const bool was_profiling = t->profiling;
+    t->profiling = false;
+    // best of `reps` runs of fn(), in ms (a huge value on a CUDA error)
+    auto time_it = [&](auto fn) -> float {
+        float best = 1e30f;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = fn();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) best = ms;
+        }
+        return best;
+    };
+    LaunchTuning best = t->tune;
+    if (e == cudaSuccess && path != 0) {
+        std::vector<int> cand;
+        if (path == 1) {
+            const int gmax = 256 / ((t->mmax + 3) / 4);
+            for (int g : {4, 6, 8, 10, 12, 14, 16})
+                if (g <= gmax) cand.push_back(g);
+        } else {
+            for (int g : {8, 12, 16, 20, 24}) cand.push_back(g);
+        }
+        float tbest = 1e30f;
+        for (int g : cand) {
+            if (path == 1) t->tune.sym_bins = g; else t->tune.tc_bins = g;
+            const float ms = time_it([&] { return run_kde_bins(t, kp, s); });
+            if (ms < tbest) {
+                tbest = ms;
+                if (path == 1) best.sym_bins = g; else best.tc_bins = g;
+            }
+        }
+        t->tune = best;
+    }
+    if (e == cudaSuccess) {  // leaf finish: one full sampling pass sets up its inputs
+        begin_call(t);
+        rc = run_sampling(t, kp, FSG_SCHED_FUSED, nullptr, s);
+        if (rc != FSG_OK) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) {
+        const int64_t items_est = t->n * (int64_t)(L < t->nb ? L : t->nb);
+        const int qc = leaf_queries_per_tile(t);
+        int64_t S0 = (152 * 4 * 8 + t->nb - 1) / t->nb;
+        const int64_t cpb = (items_est / t->nb + qc - 1) / qc + 1;
+        if (S0 > cpb) S0 = cpb;
+        if (S0 < 1) S0 = 1;
+        float tbest = 1e30f;
+        for (int64_t S : {S0 / 4, S0 / 2, S0, 2 * S0, 4 * S0}) {
+            if (S < 1 || S > 65535) continue;
+            t->tune.leaf_splits = (int32_t)S;
+            const float ms = time_it([&] { return launch_leaf_finish(t, kp, s); });
+            if (ms < tbest) {
+                tbest = ms;
+                best.leaf_splits = (int32_t)S;
+            }
+        }
+        t->tune = best;
+    }
+    t->profiling = was_profiling;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != FSG_OK) return rc;
+    if (e != cudaSuccess) return status_of(e);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    to_public(best, out);
     return FSG_OK;
 }
 

@@ -456,6 +456,7 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
     const int64_t chunks_per_bin = (items_est / t->nb + qc - 1) / qc + 1;
     int64_t S = (152 * 4 * 8 + t->nb - 1) / t->nb;
     if (S > chunks_per_bin) S = chunks_per_bin;
+    if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);

@@ -54,6 +54,13 @@ struct Workspace {
     int64_t cap_n = 0, cap_L = 0;
 };
 
+// Launch shapes (0: the built-in heuristic), chosen by fsg_autotune.
+struct LaunchTuning {
+    int32_t sym_bins = 0;     // bins per block of the symmetric d <= 16 bin pass
+    int32_t tc_bins = 0;      // bins per chunk of the tensor-core bin pass
+    int32_t leaf_splits = 0;  // CTAs per bin of the leaf finish
+};
+
 }  // namespace fsg
 
 struct fsg_tree {
@@ -83,6 +90,7 @@ struct fsg_tree {
     alignas(64) unsigned char tmap_a[128] = {};
     alignas(64) unsigned char tmap_b[128] = {};
     fsg::Workspace ws;
+    fsg::LaunchTuning tune;
     // per-phase timing (fsg_profile) and kernel-launch count
     bool profiling = false;
     cudaEvent_t ev_start[FSG_NUM_PHASES] = {};
@@ -125,6 +133,7 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
                                cudaStream_t s);
 cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+int leaf_queries_per_tile(const fsg_tree* t);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
                          int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,

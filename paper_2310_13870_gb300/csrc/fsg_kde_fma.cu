@@ -516,10 +516,12 @@ kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt
                            pn0, qn0, nq);
 }
 
-// Bins per block: as many as fit the CTA's 256 lanes.
+// Bins per block: as many as fit the CTA's 256 lanes (fewer if tuned so).
 int sym_block_bins(const fsg_tree* t) {
-    const int g = kSymThreads / ((t->mmax + 3) / 4);
-    return g < kSymNodes ? g : kSymNodes;
+    int g = kSymThreads / ((t->mmax + 3) / 4);
+    if (g > kSymNodes) g = kSymNodes;
+    if (t->tune.sym_bins > 0 && t->tune.sym_bins < g) g = t->tune.sym_bins;
+    return g;
 }
 
 template <int D>

@@ -434,6 +434,7 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
     if (chunks > t->nb) chunks = t->nb;
     int bpc = (t->nb + chunks - 1) / chunks;
     if (bpc > 24) bpc = 24;  // two [128][bpc] sum arrays beside the 4-stage ring
+    if (t->tune.tc_bins > 0 && t->tune.tc_bins < bpc) bpc = t->tune.tc_bins;
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = tc_bins_smem(kTcEpiWarps, bpc);
     static bool attr = false;

@@ -37,6 +37,7 @@ FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE = 0, 1
 # against include/fsg.h).
 EXPORTED = [
     "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info", "fsg_bin_pass_evals",
+    "fsg_autotune", "fsg_tree_tuning",
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
     "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
@@ -122,6 +123,8 @@ def load(path: str = LIB_PATH):
     lib.fsg_free_tree.restype = None
     lib.fsg_tree_info.argtypes = [P, P, P, P]
     lib.fsg_bin_pass_evals.argtypes = [P, P, P]
+    lib.fsg_autotune.argtypes = [P, P, I32, U64, I32, P, P]
+    lib.fsg_tree_tuning.argtypes = [P, P, P]
     lib.fsg_degrees.argtypes = [P, P, P, P]
     lib.fsg_sample_edges.argtypes = [P, P, I32, U64, P, P, P]
     lib.fsg_build_graph.argtypes = [P, P, I32, U64, I32, P, P, P, I64, P, P, P, P, P, P]
@@ -233,6 +236,37 @@ def fsg_bin_pass_evals(tree: Tree, p: fsg_params) -> int:
     v = ctypes.c_int64()
     _check(load().fsg_bin_pass_evals(tree.handle, ctypes.byref(p), ctypes.byref(v)), "fsg_bin_pass_evals")
     return int(v.value)
+
+
+class fsg_tuning(ctypes.Structure):
+    _fields_ = [("sym_bins", ctypes.c_int32), ("tc_bins", ctypes.c_int32), ("leaf_splits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+def _tuning_dict(t: fsg_tuning) -> dict:
+    return {"sym_bins": t.sym_bins, "tc_bins": t.tc_bins, "leaf_splits": t.leaf_splits}
+
+
+def fsg_autotune(tree: Tree, p: fsg_params, L: int, seed: int = 0, reps: int = 3, stream=None) -> dict:
+    """Times the launch shapes of the bin pass and leaf finish, keeps the fastest (see fsg.h)."""
+    out = fsg_tuning()
+    _check(load().fsg_autotune(tree.handle, ctypes.byref(p), int(L), int(seed), int(reps), ctypes.byref(out),
+                               _stream_ptr(stream)), "fsg_autotune")
+    return _tuning_dict(out)
+
+
+def fsg_tree_tuning(tree: Tree, tuning: dict | None = None) -> dict:
+    """Sets (if given) and returns the tree's launch shapes (0 = heuristic)."""
+    t = None
+    if tuning is not None:
+        t = fsg_tuning()
+        t.sym_bins = int(tuning.get("sym_bins", 0))
+        t.tc_bins = int(tuning.get("tc_bins", 0))
+        t.leaf_splits = int(tuning.get("leaf_splits", 0))
+    out = fsg_tuning()
+    _check(load().fsg_tree_tuning(tree.handle, ctypes.byref(t) if t is not None else None, ctypes.byref(out)),
+           "fsg_tree_tuning")
+    return _tuning_dict(out)
 
 
 def fsg_profile(tree: Tree, enable: bool = True):

@@ -59,6 +59,11 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     p = fsg.params(0.1)
     assert lib.fsg_degrees(None, ctypes.byref(p), fake, None) == fsg.FSG_ERR_INVALID_ARG
     assert lib.fsg_sample_edges(None, ctypes.byref(p), 8, 0, fake, None, None) == fsg.FSG_ERR_INVALID_ARG
+    tun = fsg.fsg_tuning()
+    assert lib.fsg_autotune(None, ctypes.byref(p), 8, 0, 3, ctypes.byref(tun), None) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_tree_tuning(None, None, ctypes.byref(tun)) == fsg.FSG_ERR_INVALID_ARG
+    ev = ctypes.c_int64()
+    assert lib.fsg_bin_pass_evals(None, ctypes.byref(p), ctypes.byref(ev)) == fsg.FSG_ERR_INVALID_ARG
     m = ctypes.c_int64()
     buf = (ctypes.c_float * 8)()
     for bad in (fsg.params(0.0), fsg.params(float("nan")), fsg.params(-1.0), fsg.params(0.1, self_mode=3),
