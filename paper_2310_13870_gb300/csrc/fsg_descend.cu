@@ -304,7 +304,11 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 V[(size_t)qq * vs + leaf0 + sl] = leafv[(base + it0 + qq) * (size_t)leafmax + sl];
             }
         }
-        // Kernel values: lane = query, warp w = slot pairs w, w + 8, ...
+        // Kernel values: lane = query.  Bins of 128 leaf slots: warp w takes the
+        // contiguous slots 16 w .. 16 w + 15 and sums that subtree in registers
+        // (no barrier between its levels).  Other sizes: warp w takes slot
+        // pairs w, w + 8, ... and the levels are summed in shared memory.
+        const bool sub16 = !FROM_GLOBAL && leaf0 == 128;
         if (!FROM_GLOBAL && lane < qc_max) {
             const bool qv = lane < qcnt;
             const int my_pos = qv ? qpos[lane] : -2;
@@ -315,63 +319,97 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 qd[t] = f2_pack(x, x);
             }
             float* row = V + (size_t)lane * vs;
-            // Quads of 4 consecutive slots (two slot pairs): leaves, their two
-            // parents and their grandparent are formed here, in registers.
-            const int nquad = (leaf0 + 3) / 4;
-            for (int j = w; j < nquad; j += kThreadsC / 32) {
-                float kq[4];
+            // kernel values of slot pair pp (two slots), masked at the query itself
+            auto pair_values = [&](int pp, float& k0, float& k1) {
+                const float4* Pp = P + (size_t)pp * DH;
+                uint64_t s2 = 0ull, s3 = 0ull;
 #pragma unroll
-                for (int hp = 0; hp < 2; ++hp) {
-                    const int pp = 2 * j + hp;
-                    const float4* Pp = P + (size_t)pp * DH;
-                    uint64_t s2 = 0ull, s3 = 0ull;
-#pragma unroll
-                    for (int u = 0; u < DH; ++u) {
-                        const float4 c4 = Pp[u];
-                        const uint64_t ca = f2_pack(c4.x, c4.y), cb = f2_pack(c4.z, c4.w);
-                        uint64_t dd = f2_sub(qd[2 * u], ca);
-                        s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
-                        if (2 * u + 1 < D) {
-                            dd = f2_sub(qd[2 * u + 1], cb);
-                            s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
-                        }
+                for (int u = 0; u < DH; ++u) {
+                    const float4 c4 = Pp[u];
+                    const uint64_t ca = f2_pack(c4.x, c4.y), cb = f2_pack(c4.z, c4.w);
+                    uint64_t dd = f2_sub(qd[2 * u], ca);
+                    s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
+                    if (2 * u + 1 < D) {
+                        dd = f2_sub(qd[2 * u + 1], cb);
+                        s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
                     }
-                    if (D > 1) s2 = f2_add(s2, s3);
-                    const float2 sv = f2_unpack(f2_mul(s2, nc2));
-                    float k0 = ex2_approx(sv.x), k1 = ex2_approx(sv.y);
-                    if (kp.self_exclude) {
-                        if (spos[2 * pp] == my_pos) k0 = 0.f;
-                        if (spos[2 * pp + 1] == my_pos) k1 = 0.f;
-                    }
-                    kq[2 * hp] = k0;
-                    kq[2 * hp + 1] = k1;
                 }
-                const int s4 = 4 * j;
-                if (leaf0 >= 4) {
-                    row[leaf0 + s4] = kq[0];
-                    row[leaf0 + s4 + 1] = kq[1];
-                    row[leaf0 + s4 + 2] = kq[2];
-                    row[leaf0 + s4 + 3] = kq[3];
-                    const float p0 = kq[0] + kq[1], p1 = kq[2] + kq[3];
-                    row[(leaf0 + s4) / 2] = p0;
-                    row[(leaf0 + s4) / 2 + 1] = p1;
-                    row[(leaf0 + s4) / 4] = p0 + p1;
-                } else {
-                    for (int x = 0; x < leaf0; ++x) row[leaf0 + x] = kq[x];
-                    if (leaf0 == 2) row[1] = kq[0] + kq[1];
+                if (D > 1) s2 = f2_add(s2, s3);
+                const float2 sv = f2_unpack(f2_mul(s2, nc2));
+                k0 = ex2_approx(sv.x);
+                k1 = ex2_approx(sv.y);
+                if (kp.self_exclude) {
+                    if (spos[2 * pp] == my_pos) k0 = 0.f;
+                    if (spos[2 * pp + 1] == my_pos) k1 = 0.f;
+                }
+            };
+            if (sub16) {
+                float lv[16];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) pair_values(8 * w + j, lv[2 * j], lv[2 * j + 1]);
+                // heap positions: leaves 128 + 16 w + i, then halves up to the subtree root 8 + w
+#pragma unroll
+                for (int i = 0; i < 16; ++i) row[128 + 16 * w + i] = lv[i];
+#pragma unroll
+                for (int width = 8; width >= 1; width >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < width; ++i) {
+                        lv[i] = lv[2 * i] + lv[2 * i + 1];
+                        row[8 * width + width * w + i] = lv[i];
+                    }
+                }
+            } else {
+                // Quads of 4 consecutive slots (two slot pairs): leaves, their two
+                // parents and their grandparent are formed here, in registers.
+                const int nquad = (leaf0 + 3) / 4;
+                for (int j = w; j < nquad; j += kThreadsC / 32) {
+                    float kq[4];
+                    pair_values(2 * j, kq[0], kq[1]);
+                    pair_values(2 * j + 1, kq[2], kq[3]);
+                    const int s4 = 4 * j;
+                    if (leaf0 >= 4) {
+                        row[leaf0 + s4] = kq[0];
+                        row[leaf0 + s4 + 1] = kq[1];
+                        row[leaf0 + s4 + 2] = kq[2];
+                        row[leaf0 + s4 + 3] = kq[3];
+                        const float p0 = kq[0] + kq[1], p1 = kq[2] + kq[3];
+                        row[(leaf0 + s4) / 2] = p0;
+                        row[(leaf0 + s4) / 2 + 1] = p1;
+                        row[(leaf0 + s4) / 4] = p0 + p1;
+                    } else {
+                        for (int x = 0; x < leaf0; ++x) row[leaf0 + x] = kq[x];
+                        if (leaf0 == 2) row[1] = kq[0] + kq[1];
+                    }
                 }
             }
         }
         __syncthreads();
-        for (int lev = FROM_GLOBAL ? dm - 1 : dm - 3; lev >= 0; --lev) {
-            const int cn = qcnt << lev;
-            for (int e = tid; e < cn; e += kThreadsC) {
-                const int qq = e >> lev;
-                const int h = (1 << lev) + (e & ((1 << lev) - 1));
-                float* r = V + (size_t)qq * vs;
-                r[h] = r[2 * h] + r[2 * h + 1];
+        if (sub16) {  // the top three levels over the eight subtree roots, one thread per query
+            if (tid < qcnt) {
+                float* r = V + (size_t)tid * vs;
+                float l2[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    l2[i] = r[8 + 2 * i] + r[9 + 2 * i];
+                    r[4 + i] = l2[i];
+                }
+                const float a2 = l2[0] + l2[1], b2 = l2[2] + l2[3];
+                r[2] = a2;
+                r[3] = b2;
+                r[1] = a2 + b2;
             }
             __syncthreads();
+        } else {
+            for (int lev = FROM_GLOBAL ? dm - 1 : dm - 3; lev >= 0; --lev) {
+                const int cn = qcnt << lev;
+                for (int e = tid; e < cn; e += kThreadsC) {
+                    const int qq = e >> lev;
+                    const int h = (1 << lev) + (e & ((1 << lev) - 1));
+                    float* r = V + (size_t)qq * vs;
+                    r[h] = r[2 * h] + r[2 * h + 1];
+                }
+                __syncthreads();
+            }
         }
         // List of (query, sample) pairs of this chunk: warp 0, lane = query.
         if (tid < 32) {
