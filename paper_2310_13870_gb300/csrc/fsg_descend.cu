@@ -304,6 +304,22 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 V[(size_t)qq * vs + leaf0 + sl] = leafv[(base + it0 + qq) * (size_t)leafmax + sl];
             }
         }
+        // List of (query, sample) pairs of this chunk (warp 0, lane = query),
+        // built before warp 0's share of the kernel values.
+        if (tid < 32) {
+            const uint64_t mk0 = tid < qcnt ? qmask[tid] : 0ull;
+            const int c0 = __popcll(mk0);
+            int sv = c0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, sv, o);
+                if (tid >= o) sv += y;
+            }
+            int off = sv - c0;
+            if (tid < qcnt) loff[tid] = off;
+            if (tid == 31) loff[qcnt] = sv;
+            for (uint64_t mk = mk0; mk; mk &= mk - 1ull) list[off++] = (tid << 6) | (__ffsll((long long)mk) - 1);
+        }
         // Kernel values: lane = query.  Bins of 128 leaf slots: warp w takes the
         // contiguous slots 16 w .. 16 w + 15 and sums that subtree in registers
         // (no barrier between its levels).  Other sizes: warp w takes slot
@@ -398,7 +414,6 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 r[3] = b2;
                 r[1] = a2 + b2;
             }
-            __syncthreads();
         } else {
             for (int lev = FROM_GLOBAL ? dm - 1 : dm - 3; lev >= 0; --lev) {
                 const int cn = qcnt << lev;
@@ -408,25 +423,10 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                     float* r = V + (size_t)qq * vs;
                     r[h] = r[2 * h] + r[2 * h + 1];
                 }
-                __syncthreads();
+                if (lev > 0) __syncthreads();
             }
         }
-        // List of (query, sample) pairs of this chunk: warp 0, lane = query.
-        if (tid < 32) {
-            const uint64_t mk0 = tid < qcnt ? qmask[tid] : 0ull;
-            const int c0 = __popcll(mk0);
-            int sv = c0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, sv, o);
-                if (tid >= o) sv += y;
-            }
-            int off = sv - c0;
-            if (tid < qcnt) loff[tid] = off;
-            if (tid == 31) loff[qcnt] = sv;
-            for (uint64_t mk = mk0; mk; mk &= mk - 1ull) list[off++] = (tid << 6) | (__ffsll((long long)mk) - 1);
-        }
-        __syncthreads();
+        // (the Philox blocks below are drawn in the same phase as the last tree level)
         // Philox blocks of every sample's remaining levels, one per thread.
         const int nsamp = loff[qcnt];
         const int blk0 = s0 >> 2;
@@ -438,8 +438,8 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 const int qq = list[sidx] >> 6, l = list[sidx] & 63;
                 W[e] = draw_block(kp.seed, (uint32_t)qidx[qq], (uint32_t)l, (uint32_t)(4 * (blk0 + jb)));
             }
-            __syncthreads();
         }
+        __syncthreads();  // tree and Philox blocks complete
         for (int e = tid; e < nsamp; e += kThreadsC) {
             const int qq = list[e] >> 6, l = list[e] & 63;
             const float* row = V + (size_t)qq * vs;
