@@ -170,7 +170,7 @@ scatter_items_kernel(const int32_t* __restrict__ qitem_bin, const uint64_t* __re
 
 constexpr int kThreadsC = 256;
 
-constexpr int kLeafWords = 512;   // Philox blocks precomputed per chunk (more: computed inline)
+constexpr int kLeafWords = 256;   // Philox blocks precomputed per chunk (more: computed inline)
 
 // Shared-memory layout of the leaf finish (same arithmetic on host and device).
 struct LeafSmem {
@@ -205,7 +205,7 @@ struct LeafSmem {
 // FROM_GLOBAL: the leaf values were computed by another kernel (any d) and
 // are read from leafv[item][slot] instead of being evaluated here.
 template <int D, bool FROM_GLOBAL>
-__global__ void __launch_bounds__(kThreadsC)
+__global__ void __launch_bounds__(kThreadsC, 4)
 leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
                    int n, int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
                    const uint64_t* __restrict__ items_mask, const float* __restrict__ leafv, KernelParams kp,
