@@ -87,6 +87,24 @@ cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t
     return launch_kde_bins(t, kp, s);
 }
 
+// The remaining levels of every sample inside its bin.  Tensor-core path: one
+// fused kernel (leaf values and descent); d > 16 otherwise: leaf values, then
+// the leaf finish; d <= 16: the leaf finish evaluates its own values.
+cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (t->d > kMaxFmaDim && use_tc(t, kp.precision) && (1 << t->dm) <= 256) {
+        t->launches += 1;
+        return launch_leaf_values_tc(t, kp, s);
+    }
+    cudaError_t e = cudaSuccess;
+    if (t->d > kMaxFmaDim) {
+        e = launch_leaf_values_generic(t, kp, s);
+        t->launches += 1;
+    }
+    if (e == cudaSuccess) e = launch_leaf_finish(t, kp, s);
+    t->launches += 1;
+    return e;
+}
+
 // Kernel evaluations the bin pass executes (n^2, or about n^2/2 when symmetric).
 int64_t bin_pass_evals(const fsg_tree* t, int precision) {
     if (use_tc(t, precision)) return t->n * t->n;
@@ -457,8 +475,9 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
     }
     if (e == cudaSuccess) {
         const int64_t items_est = t->n * (int64_t)(L < t->nb ? L : t->nb);
-        const int qc = leaf_queries_per_tile(t);
-        int64_t S0 = (152 * 4 * 8 + t->nb - 1) / t->nb;
+        const bool fused_tc = t->d > kMaxFmaDim && tc && (1 << t->dm) <= 256;  // the heuristics of each launcher
+        const int qc = fused_tc ? 128 : leaf_queries_per_tile(t);
+        int64_t S0 = ((fused_tc ? 152 * 2 * 8 : 152 * 4 * 8) + t->nb - 1) / t->nb;
         const int64_t cpb = (items_est / t->nb + qc - 1) / qc + 1;
         if (S0 > cpb) S0 = cpb;
         if (S0 < 1) S0 = 1;
@@ -466,7 +485,7 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
         for (int64_t S : {S0 / 4, S0 / 2, S0, 2 * S0, 4 * S0}) {
             if (S < 1 || S > 65535) continue;
             t->tune.leaf_splits = (int32_t)S;
-            const float ms = time_it([&] { return launch_leaf_finish(t, kp, s); });
+            const float ms = time_it([&] { return run_leaf_phase(t, kp, s); });
             if (ms < tbest) {
                 tbest = ms;
                 best.leaf_splits = (int32_t)S;
@@ -567,13 +586,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
     }
     if (e == cudaSuccess) {
         PhaseScope ph(t, FSG_PHASE_LEAF, s);
-        if (t->d > kMaxFmaDim) {
-                    const bool tc = use_tc(t, kp.precision);
-            e = tc && (1 << t->dm) <= 256 ? launch_leaf_values_tc(t, kp, s) : launch_leaf_values_generic(t, kp, s);
-            t->launches += 1;
-        }
-        if (e == cudaSuccess) e = launch_leaf_finish(t, kp, s);
-        t->launches += 1;
+        e = run_leaf_phase(t, kp, s);
     }
     return status_of(e);
 }

@@ -457,14 +457,19 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
 }  // namespace fsg
 
 // ---------------------------------------------------------------------------
-// Tensor-core leaf values: for the items (queries) of one bin, the kernel
+// Tensor-core leaf finish: for the items (queries) of one bin, the kernel
 // value at every leaf slot of the bin's tree, k = ex2(neg_c (||x||^2 +
-// ||y||^2 - 2 x.y)) in the same integer units as the bin pass.  CTA (b, y)
-// handles chunks of 128 items of bin b: the item rows and the bin's slot rows
-// (zero rows for empty slots) are gathered with cp.async directly into the
-// 128-byte-swizzled K-major layout (3-stage ring), one thread issues
-// tcgen05.mma M=128 x N=slots x K=16, and the four warps read their TMEM lane
-// quadrants and write leafv[item][slot].
+// ||y||^2 - 2 x.y)) in the same integer units as the bin pass, then the
+// remaining levels of the item's samples.  CTA (b, y) handles chunks of 128
+// items of bin b: the item rows and the bin's slot rows (zero rows for empty
+// slots) are gathered with cp.async directly into the 128-byte-swizzled
+// K-major layout (3-stage ring), one thread issues tcgen05.mma M=128 x
+// N=slots x K=16, and each of the four warps reads its TMEM lane quadrant:
+// thread = item, its row of leaf values kept in shared memory.  The thread
+// then descends each of the item's samples through the bin's perfect tree,
+// the two child sums of a node being the sums of its two halves of slots
+// (fixed order), with the same Philox draws and decision rule as every
+// other level, and writes the sampled position, kernel value and flags.
 // ---------------------------------------------------------------------------
 namespace fsg {
 namespace {
@@ -477,12 +482,30 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
                  : "memory");
 }
 
+// Sum of v[lo .. lo + len) in a fixed pairwise order (len a power of two).
+__device__ __forceinline__ float range_sum(const float* __restrict__ v, int lo, int len) {
+    float s = 0.f;
+    for (int b = 0; b < len; b += 8) {
+        const float* x = v + lo + b;
+        if (len >= 8) {
+            s += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+        } else {
+            for (int i = 0; i < len; ++i) s += x[i];
+        }
+    }
+    return s;
+}
+
 template <int NS>  // slots (N of the MMA): 64, 128 or 256
 __global__ void __launch_bounds__(kLvThreads, 1)
 leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict__ norms, int dpad,
                       const int32_t* __restrict__ bnd, const int32_t* __restrict__ bin_off,
-                      const int32_t* __restrict__ items_q, float neg_c, int self_exclude, int leafmax,
-                      float* __restrict__ leafv, int32_t* __restrict__ status) {
+                      const int32_t* __restrict__ items_q, const uint64_t* __restrict__ items_mask,
+                      const int32_t* __restrict__ perm, KernelParams kp, float neg_c, int s0,
+                      int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp, uint8_t* __restrict__ lflags,
+                      unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items,
+                      int32_t* __restrict__ status) {
+    const int self_exclude = kp.self_exclude;
     constexpr uint32_t kA = 128 * 128, kB = NS * 128, kStage = kA + kB;
     constexpr uint32_t kIdescLv = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NS >> 3) << 17) |
                                   ((uint32_t)(128 >> 4) << 24);
@@ -502,6 +525,16 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
     int32_t* rowpos = reinterpret_cast<int32_t*>(tmem_slot + 4);  // [128] item query positions
     int32_t* slotpos = rowpos + 128;                              // [NS] slot point positions
     float* slotnorm = reinterpret_cast<float*>(slotpos + NS);     // [NS]
+    // [128][NS + 1] leaf values per item: the gather stages are idle during the
+    // epilogue (all copies landed, all MMAs of the chunk complete), so the rows
+    // live in their space
+    float* vrows = reinterpret_cast<float*>(base);
+    static_assert((size_t)128 * (NS + 1) * 4 <= (size_t)kLvStages * kStage, "leaf rows must fit the stages");
+    constexpr int BS = NS / 16;                                   // slots per block of the block tree
+    // [128][33]: per item, the sums of 16 blocks of slots and their tree (heap
+    // order); inside the idle stages when they have room, else after slotnorm
+    constexpr bool kTreeInStages = (size_t)128 * (NS + 1 + 33) * 4 <= (size_t)kLvStages * kStage;
+    float* btree = kTreeInStages ? vrows + (size_t)128 * (NS + 1) : slotnorm + NS;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;
@@ -611,32 +644,78 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
         const int r = tid;
         const int qp = rowpos[r];
         const float nq = qp >= 0 ? norms[qp] : 0.f;
+        float* vr = vrows + (size_t)r * (NS + 1);
 #pragma unroll 1
         for (int c0 = 0; c0 < NS; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-            if (r < qcnt && c0 < leaf0) {
-                float* dst = leafv + (size_t)(seg + it0 + r) * leafmax + c0;
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    float o[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int sl = c0 + j + u;
-                        const int pp = slotpos[sl];
-                        float k = 0.f;
-                        if (pp >= 0 && !(self_exclude && pp == qp)) {
-                            const float arg = fmaf(-2.f, v[j + u], nq + slotnorm[sl]);
-                            k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
-                        }
-                        o[u] = k;
-                    }
-                    if (c0 + j < leaf0) *reinterpret_cast<float4*>(dst + j) = make_float4(o[0], o[1], o[2], o[3]);
+            for (int j = 0; j < 32; ++j) {
+                const int sl = c0 + j;
+                const int pp = slotpos[sl];
+                float k = 0.f;
+                if (pp >= 0 && !(self_exclude && pp == qp)) {
+                    const float arg = fmaf(-2.f, v[j], nq + slotnorm[sl]);
+                    k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
                 }
+                vr[sl] = k;
+            }
+        }
+        // the remaining levels of this item's samples (thread = item): first the
+        // item's tree over 16 blocks of NS / 16 slots (node = left + right)
+        float* bt = btree + (size_t)r * 33;  // odd stride: the lanes' rows hit distinct banks
+#pragma unroll
+        for (int k = 0; k < 16; ++k) bt[16 + k] = range_sum(vr, k * BS, BS);
+#pragma unroll
+        for (int h = 15; h >= 1; --h) bt[h] = bt[2 * h] + bt[2 * h + 1];
+        if (r < qcnt) {
+            const uint64_t mask = items_mask[seg + it0 + r];
+            const uint32_t qi = (uint32_t)perm[qp];
+            for (uint64_t mk = mask; mk; mk &= mk - 1ull) {
+                const int l = __ffsll((long long)mk) - 1;
+                int a = 0, c = m, lo = 0, span = leaf0;
+                uint8_t f = 0;
+                uint4 blk = make_uint4(0, 0, 0, 0);
+                int blk_id = -1;
+                for (int t = 0; t < dm; ++t) {
+                    const int half = span >> 1;
+                    int right = 1;  // a single point sits in the right half
+                    if (c - a >= 2) {
+                        float gl, gr;
+                        if (half >= BS) {  // both halves are nodes of the block tree
+                            const int hb = (16 + lo / BS) / (half / BS);
+                            gl = bt[hb];
+                            gr = bt[hb + 1];
+                        } else {
+                            gl = range_sum(vr, lo, half);
+                            gr = range_sum(vr, lo + half, half);
+                        }
+                        const uint32_t lev = (uint32_t)(s0 + t);
+                        if ((int)(lev >> 2) != blk_id) {
+                            blk_id = (int)(lev >> 2);
+                            blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
+                        }
+                        right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
+                        const int mid = a + (c - a) / 2;
+                        if (right) a = mid; else c = mid;
+                    }
+                    if (right) lo += half;
+                    span = half;
+                }
+                const size_t o = (size_t)qp * kp.L + l;
+                leaf_pos[o] = p_lo + a;
+                ksmp[o] = vr[lo];
+                lflags[o] = f;
             }
         }
         tc_fence_before();
         __syncthreads();  // TMEM and rowpos are reused by the next chunk
+    }
+    if (tid == 0 && ok && (int)blockIdx.y < nchunks) {
+        unsigned long long its = 0;
+        for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) its += (unsigned long long)min(128, cnt - chunk * 128);
+        atomicAdd(n_items, its);
+        atomicAdd(n_evals, its * (unsigned long long)m);
     }
     // teardown: own copies landed, own MMAs complete, then free TMEM
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -656,7 +735,9 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
 template <int NS>
 cudaError_t launch_lv_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     constexpr uint32_t kStage = 128 * 128 + NS * 128;
-    const size_t smem = 1024 + (size_t)kLvStages * kStage + 8 * (kLvStages + 2) + 16 + 4 * 128 + 8 * NS;
+    constexpr bool kTreeInStages = (size_t)128 * (NS + 1 + 33) * 4 <= (size_t)kLvStages * kStage;
+    const size_t smem = 1024 + (size_t)kLvStages * kStage + 8 * (kLvStages + 2) + 16 + 4 * 128 + 8 * NS +
+                        (kTreeInStages ? 0 : (size_t)128 * 33 * 4);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(leaf_values_tc_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -668,12 +749,16 @@ cudaError_t launch_lv_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t
     const int64_t chunks_per_bin = (items_est / t->nb + 127) / 128 + 1;
     int64_t S = (152 * 2 * 8 + t->nb - 1) / t->nb;
     if (S > chunks_per_bin) S = chunks_per_bin;
+    if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
+    const auto& ws = t->ws;
     leaf_values_tc_kernel<NS><<<grid, kLvThreads, smem, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms, t->dpad, t->bnd, t->ws.bin_off, t->ws.items_q,
-        kp.neg_c / (255.f * 255.f), kp.self_exclude, 1 << t->dm, t->ws.leafv, t->status);
+        reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms, t->dpad, t->bnd, ws.bin_off, ws.items_q,
+        ws.items_mask, t->perm, kp, kp.neg_c / (255.f * 255.f), t->s0, ws.leaf_pos, ws.ksmp, ws.lflags,
+        reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+        reinterpret_cast<unsigned long long*>(&ws.stats->n_items), t->status);
     return cudaGetLastError();
 }
 
