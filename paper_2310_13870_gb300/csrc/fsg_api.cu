@@ -227,6 +227,7 @@ size_t tree_bytes_estimate(int64_t n, int32_t d, int32_t L) {
     const int dp = (d + 3) & ~3;
     size_t tot = sizeof(float) * (size_t)n_pad * dp * (d <= kMaxFmaDim ? 3 : 1) + sizeof(int32_t) * 2 * (size_t)n +
                  sizeof(int32_t) * (size_t)(nb + 1) + 64;
+    if (d > kMaxFmaDim && mmax <= 128) tot += generic_tile_bytes(n, d);
     size_t sz[kWsParts];
     workspace_sizes(n, d, dm, nb, L, sz);
     for (int k = 0; k < kWsParts; ++k) tot += align_up(sz[k], 256);
@@ -331,6 +332,11 @@ int fsg::build_tree_internal(const float* d_points, int64_t n, int32_t d, const 
         rc = status_of(e);
         if (rc == FSG_OK && st[0] != 0) rc = FSG_ERR_INVALID_ARG;
     }
+    if (rc == FSG_OK && d > kMaxFmaDim && !t->exact_int && t->mmax <= 128) {
+        // transposed tiles of the symmetric FP32 pass (allocated here, never during a capture)
+        e = tree_malloc(t, (void**)&t->Xtt, generic_tile_bytes(n, d), s);
+        rc = status_of(e);
+    }
     if (rc != FSG_OK) {
         cudaGetLastError();
         fsg_free_tree(t);
@@ -355,6 +361,7 @@ void fsg_free_tree(fsg_tree* t) {
     tree_free(t, t->bnd);
     tree_free(t, t->status);
     tree_free(t, t->ws.base);
+    tree_free(t, t->Xtt);
     if (t->Xb) cudaFree(t->Xb);
     if (t->norms) cudaFree(t->norms);
     delete t;

@@ -87,6 +87,10 @@ struct fsg_tree {
     void* Xb = nullptr;
     float* norms = nullptr;
     int32_t dpad = 0;
+    // FP32 path for d > 16: the points as transposed 128-position tiles (query
+    // layout [k][132] and duplicated point layout [k][130][2] per tile, k
+    // padded to a multiple of 32), refreshed by every generic bin pass
+    float* Xtt = nullptr;
     alignas(64) unsigned char tmap_a[128] = {};
     alignas(64) unsigned char tmap_b[128] = {};
     fsg::Workspace ws;
@@ -140,6 +144,7 @@ cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d
                            fsg_stats* d_stats, cudaStream_t s);
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 bool kde_bins_generic_sym_supported(const fsg_tree* t);
+size_t generic_tile_bytes(int64_t n, int32_t d);
 int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);

@@ -148,7 +148,7 @@ constexpr int kST = 128;             // tile side (queries and points)
 constexpr int kSK = 32;              // coordinates per chunk
 constexpr int kSQS = kST + 4;        // transposed query row stride (floats)
 constexpr int kSPS = kST + 2;        // transposed point row stride (float pairs)
-constexpr size_t kSymGenSmem = (size_t)kSK * kSQS * 4 + (size_t)kSK * kSPS * 8;
+constexpr size_t kSymGenSmem = (size_t)kSK * kSQS * 4 + (size_t)kSK * kSPS * 8;  // one stage
 
 // Packed 128 x 128 tiles.  Thread (tq, tp) of 256 holds the rows 4 tq .. 4 tq + 3
 // and 64 + 4 tq .. 64 + 4 tq + 3 (four FP32x2 pairs) and the columns 4 tp ..
@@ -217,10 +217,11 @@ __device__ __forceinline__ void accumulate_pairs(const float* __restrict__ Qs, c
     }
 }
 
-// Tile pair (i, j >= i) of the linear index L over the upper triangle of T tiles.
+// Tile pair (i, j >= i) of the linear index L over the upper triangle of T
+// tiles: an FP32 estimate of the row, corrected exactly in integers.
 __device__ __forceinline__ void tri_index(long long L, int T, int& i, int& j) {
-    const double b = 2.0 * T + 1.0;
-    long long ii = (long long)((b - sqrt(b * b - 8.0 * (double)L)) * 0.5);
+    const float b = 2.f * (float)T + 1.f;
+    long long ii = (long long)((b - sqrtf(fmaxf(b * b - 8.f * (float)L, 0.f))) * 0.5f);
     auto start = [&](long long r) { return r * T - r * (r - 1) / 2; };
     if (ii < 0) ii = 0;
     if (ii > T - 1) ii = T - 1;
@@ -253,12 +254,44 @@ __device__ __forceinline__ void add3(float (&r)[3], int lb, float v) {
     r[2] += lb == 2 ? v : 0.f;
 }
 
+// Transposed tiles: tile i holds, for k < dpc (d padded to a multiple of 32),
+// the query layout Q[k][132] (absent rows at 1e19 on real coordinates) and
+// then the duplicated point layout P[k][130][2] (absent rows 0).  Built per
+// (tile, 32-coordinate chunk) through a shared-memory transpose.
+__global__ void __launch_bounds__(kGT)
+generic_tiles_kernel(const float* __restrict__ Xt, int n, int d, int dp, int dpc, float* __restrict__ Xtt) {
+    __shared__ float sm[kST][kSK + 1];
+    const int i = blockIdx.x, c = blockIdx.y;
+    const int k0 = c * kSK;
+    for (int e = threadIdx.x; e < kST * kSK; e += kGT) {
+        const int r = e / kSK, k = e - r * kSK;
+        const int pos = i * kST + r;
+        sm[r][k] = (pos < n && k0 + k < d) ? Xt[(size_t)pos * dp + k0 + k] : 0.f;
+    }
+    __syncthreads();
+    float* tileQ = Xtt + (size_t)i * dpc * (kSQS + 2 * kSPS);
+    float* tileP = tileQ + (size_t)dpc * kSQS;
+    for (int e = threadIdx.x; e < kSK * kSQS; e += kGT) {
+        const int k = e / kSQS, r = e - k * kSQS;
+        const int pos = i * kST + r;
+        float v = 0.f;
+        if (r < kST) v = pos < n ? sm[r][k] : (k0 + k < d ? 1e19f : 0.f);
+        tileQ[(size_t)(k0 + k) * kSQS + r] = v;
+    }
+    for (int e = threadIdx.x; e < kSK * kSPS; e += kGT) {
+        const int k = e / kSPS, r = e - k * kSPS;
+        const float v = r < kST ? sm[r][k] : 0.f;
+        reinterpret_cast<float2*>(tileP)[(size_t)(k0 + k) * kSPS + r] = make_float2(v, v);
+    }
+}
+
 __global__ void __launch_bounds__(kGT, 2)
-kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t* __restrict__ bnd, int nb,
-                            int s0, int T, float neg_c, int self_exclude, float* __restrict__ binsum) {
+kde_bins_generic_sym_kernel(const float* __restrict__ Xtt, int n, int dpc, const int32_t* __restrict__ bnd, int nb,
+                            int s0, int T, float neg_c, int self_exclude, float* __restrict__ binsum,
+                            int32_t* __restrict__ status) {
     extern __shared__ __align__(16) float gsm[];
-    float* Qs = gsm;                                   // [kSK][kSQS]  query coordinate k of row r
-    float* Ps = gsm + kSK * kSQS;                      // [kSK][kSPS][2] point coordinate, twice
+    constexpr int kStageFloats = kSK * kSQS + kSK * kSPS * 2;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(gsm + 2 * kStageFloats);
     __shared__ int qb_s[4], pb_s[4];                   // bin bounds met by the two tiles
     __shared__ int qbin0, pbin0, nqbin, npbin;
     int ti, tj;
@@ -266,6 +299,24 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const i
     const bool mirror = tj > ti;
     const int tid = threadIdx.x, tq = tid & 15, tp = tid >> 4;
     const int Q0 = ti * kST, P0 = tj * kST;
+    const int nchunks = dpc / kSK;
+    const size_t tile_floats = (size_t)dpc * (kSQS + 2 * kSPS);
+    const float* tQ = Xtt + (size_t)ti * tile_floats;
+    const float* tP = Xtt + (size_t)tj * tile_floats + (size_t)dpc * kSQS;
+    constexpr uint32_t kQBytes = kSK * kSQS * 4, kPBytes = kSK * kSPS * 8;
+    auto issue = [&](int c, int st) {
+        float* dst = gsm + st * kStageFloats;
+        mbar_arrive_expect_tx(&bars[st], kQBytes + kPBytes);
+        bulk_g2s(dst, tQ + (size_t)c * kSK * kSQS, kQBytes, &bars[st]);
+        bulk_g2s(dst + kSK * kSQS, tP + (size_t)c * kSK * kSPS * 2, kPBytes, &bars[st]);
+    };
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        issue(0, 0);
+        if (nchunks > 1) issue(1, 1);
+    }
     if (tid < 4) {  // the bins met by the two tiles (no memory access)
         const int x = tid == 0 ? Q0 : tid == 1 ? P0 : tid == 2 ? min(Q0 + kST, n) - 1 : min(P0 + kST, n) - 1;
         const int b = bin_of(n, s0, x);
@@ -285,14 +336,21 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const i
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = 0ull;
-    // Absent query rows sit at 1e19: their squared distances overflow, k = 0.
-    auto rowq = [&](int r) { return Q0 + r < n ? Q0 + r : -1; };
-    auto rowp = [&](int r) { return P0 + r < n ? P0 + r : -1; };
-    for (int k0 = 0; k0 < dp; k0 += kSK) {
-        __syncthreads();
-        load_tiles(Qs, Ps, rowq, rowp, Xt, dp, k0, 1e19f);
-        __syncthreads();
-        accumulate_pairs<2>(Qs, Ps, tq, tp, acc);
+    for (int c = 0; c < nchunks; ++c) {
+        const int st = c & 1;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)(c >> 1) & 1u, status);
+        if (__syncthreads_or(!ok)) {  // a copy did not land in time: drain (bounded) and stop
+            if (tid == 0) {
+                mbar_wait_bounded(&bars[st], (uint32_t)(c >> 1) & 1u, status);
+                if (c + 1 < nchunks) mbar_wait_bounded(&bars[st ^ 1], (uint32_t)((c + 1) >> 1) & 1u, status);
+            }
+            __syncthreads();
+            return;
+        }
+        const float* Qs = gsm + st * kStageFloats;
+        accumulate_pairs<2>(Qs, Qs + kSK * kSQS, tq, tp, acc);
+        __syncthreads();  // stage st is free again
+        if (tid == 0 && c + 2 < nchunks) issue(c + 2, st);
     }
     // kernel values of the thread's 8 queries x 8 points
     float kv[8][8];
@@ -315,7 +373,7 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xt, int n, int dp, const i
             kv[2 * a + 1][b] = k1;
         }
     }
-    __syncthreads();  // the coordinate tiles become the partial-sum buffers
+    // the stages are free: they become the partial-sum buffers
     float* rowpart = gsm;                   // [16 tp][128 q][3 point bins]
     float* colpart = gsm + 16 * kST * 3;    // [16 tq][128 p][3 query bins]
     {
@@ -489,7 +547,16 @@ leaf_values_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* 
 
 }  // namespace
 
-bool kde_bins_generic_sym_supported(const fsg_tree* t) { return t->d > kMaxFmaDim && t->mmax <= kST; }
+bool kde_bins_generic_sym_supported(const fsg_tree* t) {
+    return t->d > kMaxFmaDim && t->mmax <= kST && t->Xtt != nullptr;
+}
+
+// Bytes of the transposed tiles of a tree of n points of dimension d.
+size_t generic_tile_bytes(int64_t n, int32_t d) {
+    const int64_t T = (n + kST - 1) / kST;
+    const int64_t dpc = ((d + 3) / 4 * 4 + kSK - 1) / kSK * kSK;
+    return sizeof(float) * (size_t)T * (size_t)dpc * (kSQS + 2 * kSPS);
+}
 
 // Evaluations executed by the symmetric generic pass: the triangle of tiles.
 int64_t kde_bins_generic_sym_evals(const fsg_tree* t) {
@@ -499,21 +566,26 @@ int64_t kde_bins_generic_sym_evals(const fsg_tree* t) {
 
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     if (kde_bins_generic_sym_supported(t)) {
+        const size_t smem = 2 * kSymGenSmem + 2 * sizeof(uint64_t);  // two stages and their mbarriers
         static bool attr = false;
         if (!attr) {
             cudaError_t e = cudaFuncSetAttribute(kde_bins_generic_sym_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymGenSmem);
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        cudaError_t e = cudaMemsetAsync(t->ws.binsum, 0, sizeof(float) * (size_t)t->n * t->nb, s);
-        if (e != cudaSuccess) return e;
         const int64_t T = (t->n + kST - 1) / kST;
+        const int dpc = (t->dp + kSK - 1) / kSK * kSK;
+        dim3 pg((unsigned)T, (unsigned)(dpc / kSK));
+        generic_tiles_kernel<<<pg, kGT, 0, s>>>(t->Xt, (int)t->n, t->d, t->dp, dpc, t->Xtt);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->ws.binsum, 0, sizeof(float) * (size_t)t->n * t->nb, s);
+        if (e != cudaSuccess) return e;
         const int64_t ctas = T * (T + 1) / 2;
         if (ctas > INT_MAX) return cudaErrorInvalidValue;
-        kde_bins_generic_sym_kernel<<<(unsigned)ctas, kGT, kSymGenSmem, s>>>(t->Xt, (int)t->n, t->dp, t->bnd, t->nb,
-                                                                           t->s0, (int)T, kp.neg_c, kp.self_exclude,
-                                                                           t->ws.binsum);
+        kde_bins_generic_sym_kernel<<<(unsigned)ctas, kGT, smem, s>>>(t->Xtt, (int)t->n, dpc, t->bnd, t->nb, t->s0,
+                                                                    (int)T, kp.neg_c, kp.self_exclude, t->ws.binsum,
+                                                                    t->status);
         return cudaGetLastError();
     }
     const int qblocks = (int)((t->n + kGQ - 1) / kGQ);
