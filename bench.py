@@ -568,7 +568,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (default 2048; 512 at d=784)")
+    ap.add_argument("--cpu-queries", type=int, default=0, help="oracle sample size (default 16384; 512 at d=784)")
     ap.add_argument("--ref-queries", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -595,8 +595,8 @@ def main():
         return run_seg_batch(args)
     if args.workload == "serving":
         return run_serving(args)
-    if not args.cpu_queries:
-        args.cpu_queries = 512 if args.workload == "digits" else 2048
+    if not args.cpu_queries:  # about 10 s of oracle work on 16 host cores
+        args.cpu_queries = 512 if args.workload == "digits" else 16384
     if args.workload == "digits":
         WORKLOAD.clear()
         WORKLOAD.update(DIGITS)

@@ -31,6 +31,13 @@ def _sets(fsg):
     out.append((torch.from_numpy(inputs.two_moons(n=1500, seed=3)).cuda(), fsg.params(0.1), 32, 1))
     out.append((torch.from_numpy(inputs.gaussian_mixture(n=2500, d=10, k=4, box=4.0, seed=5)).cuda(),
                 fsg.params(1.5, self_mode=1), 64, 2))
+    # the d > 16 FP32 path, the tensor-core path (8-bit data) and the levelwise schedule in the same batch
+    out.append((torch.from_numpy(inputs.gaussian_mixture(n=1700, d=40, k=4, box=3.0, seed=6)).cuda(),
+                fsg.params(2.5), 16, 3))
+    dig = inputs.digit_like(n=1300, d=784, seed=7)
+    out.append((torch.from_numpy(dig).cuda(), fsg.params(inputs.median_pair_distance(dig, m=1024) / 2), 16, 4))
+    out.append((torch.from_numpy(inputs.two_moons(n=900, seed=8)).cuda(),
+                fsg.params(0.1, schedule=fsg.FSG_SCHED_LEVELWISE), 16, 5))
     return out
 
 

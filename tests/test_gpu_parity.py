@@ -348,3 +348,28 @@ def test_generic_d_small_n(fsg, n):
     o = ora.build_graph(X, gam, 6, 4)
     check_degrees(g["deg"], o["deg"], n)
     check_samples(g["samples"], g["flags"], o["samples"])
+
+
+# ----------------------------------------------------------------------------
+# Self term and edge semantics on the d > 16 FP32 path and the tensor-core path
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("path", ["generic", "tc"])
+def test_include_self_and_multi_edges_large_d(fsg, path):
+    if path == "generic":
+        X = inputs.gaussian_mixture(n=900, d=24, k=3, box=1.5, seed=21)
+        sigma = 2.5
+    else:
+        X = inputs.digit_like(n=900, d=784, seed=21)
+        sigma = inputs.median_pair_distance(X, m=900) / 2
+    gam = ora.gamma(sigma)
+    g = gpu_graph(fsg, X, sigma, 10, 6, edge_mode=1, self_mode=1)
+    o = ora.build_graph(X, gam, 10, 6, self_mode=ora.SELF_INCLUDE, edge_mode=ora.EDGES_MULTI)
+    check_degrees(g["deg"], o["deg"], 900)
+    check_samples(g["samples"], g["flags"], o["samples"])
+    n_self = int((g["samples"] == np.arange(900)[:, None]).sum())
+    assert g["stats"]["n_self"] == n_self
+    assert g["m"] == 900 * 10 - n_self
+    e = ora.build_graph(X, gam, 10, 6)  # SET semantics, EXCLUDE, on the same path
+    ge = gpu_graph(fsg, X, sigma, 10, 6)
+    check_samples(ge["samples"], ge["flags"], e["samples"])
+    assert (ge["src"] != ge["dst"]).all()
