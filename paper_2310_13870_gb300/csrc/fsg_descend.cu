@@ -506,6 +506,240 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
     return cudaGetLastError();
 }
 
+// Leaf finish for bins of 128 leaf slots (d <= 16): chunks of 128 items.
+// Warp w evaluates the contiguous slots 16 w .. 16 w + 15 for every item of
+// the chunk (four rounds of 32, lane = item) and keeps only the node sums of
+// at least 4 slots (63 per item, heap order); one thread per item forms the
+// top three levels; then one thread per item descends its samples, reading
+// the kept nodes and, at a 4-slot node, re-evaluating its four leaves with
+// the same arithmetic (so the pair and leaf values equal those that formed
+// the node).  Three barriers per 128 items.
+constexpr int kC128 = 128;   // items per chunk
+constexpr int kV128 = 65;    // heap row stride (odd: the lanes' rows hit distinct banks)
+
+template <int D>
+__global__ void __launch_bounds__(kThreadsC, 4)
+leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
+               int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
+               const uint64_t* __restrict__ items_mask, KernelParams kp, int32_t* __restrict__ leaf_pos,
+               float* __restrict__ ksmp, uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
+               unsigned long long* __restrict__ n_items) {
+    constexpr int DP = (D + 3) & ~3;
+    constexpr int DH = (D + 1) / 2;
+    extern __shared__ __align__(16) unsigned char smem128[];
+    float4* P = reinterpret_cast<float4*>(smem128);                        // [64][DH] slot pairs, interleaved
+    uint64_t* qmask = reinterpret_cast<uint64_t*>(P + 64 * DH);            // [128]
+    int32_t* spos = reinterpret_cast<int32_t*>(qmask + kC128);             // [128]
+    int32_t* qpos = spos + 128;                                             // [128]
+    int32_t* qidx = qpos + kC128;                                           // [128]
+    float* qco = reinterpret_cast<float*>(qidx + kC128);                    // [128][DP]
+    float* V = qco + kC128 * DP;                                            // [128][65] node sums >= 4 slots
+    const int b = blockIdx.x;
+    const int base = bin_off[b * kBinSlots];
+    const int cnt = bin_off[(b + 1) * kBinSlots] - base;
+    const int nchunks = (cnt + kC128 - 1) / kC128;
+    if ((int)blockIdx.y >= nchunks) return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;  // 65 <= m <= 128: dm = 7
+    for (int sl = tid; sl < 128; sl += kThreadsC) {
+        int a = 0, c = m;
+        for (int t = 6; t >= 0; --t) {
+            const int mid = a + (c - a) / 2;
+            if ((sl >> t) & 1) a = mid; else c = mid;
+        }
+        const int pos = c - a == 1 ? p_lo + a : -1;
+        spos[sl] = pos;
+        float* Pw = reinterpret_cast<float*>(P + (size_t)(sl >> 1) * DH);
+#pragma unroll
+        for (int u = 0; u < DH; ++u) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = 2 * u + h;
+                Pw[4 * u + 2 * h + (sl & 1)] = (t < D) ? (pos >= 0 ? Xt[(size_t)pos * DP + t] : 1e19f) : 0.f;
+            }
+        }
+    }
+    const uint64_t nc2 = f2_pack(kp.neg_c, kp.neg_c);
+    // kernel values of slot pair pp for the query at qd (two slots), masked at the query itself
+    auto pair_values = [&](const uint64_t (&qd)[D], int my_pos, int pp, float& k0, float& k1) {
+        const float4* Pp = P + (size_t)pp * DH;
+        uint64_t s2 = 0ull, s3 = 0ull;
+#pragma unroll
+        for (int u = 0; u < DH; ++u) {
+            const float4 c4 = Pp[u];
+            const uint64_t ca = f2_pack(c4.x, c4.y), cb = f2_pack(c4.z, c4.w);
+            uint64_t dd = f2_sub(qd[2 * u], ca);
+            s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
+            if (2 * u + 1 < D) {
+                dd = f2_sub(qd[2 * u + 1], cb);
+                s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
+            }
+        }
+        if (D > 1) s2 = f2_add(s2, s3);
+        const float2 sv = f2_unpack(f2_mul(s2, nc2));
+        k0 = ex2_approx(sv.x);
+        k1 = ex2_approx(sv.y);
+        if (kp.self_exclude) {
+            if (spos[2 * pp] == my_pos) k0 = 0.f;
+            if (spos[2 * pp + 1] == my_pos) k1 = 0.f;
+        }
+    };
+    const int L = kp.L;
+    const size_t ibase = (size_t)base;
+    unsigned long long ev_acc = 0, it_acc = 0;
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        const int it0 = chunk * kC128;
+        const int qcnt = min(kC128, cnt - it0);
+        if (tid < kC128) {  // this chunk's items
+            if (tid < qcnt) {
+                const int q = items_q[ibase + it0 + tid];
+                qpos[tid] = q;
+                qidx[tid] = perm[q];
+                qmask[tid] = items_mask[ibase + it0 + tid];
+#pragma unroll
+                for (int t = 0; t < D; ++t) qco[tid * DP + t] = Xt[(size_t)q * DP + t];
+            } else {
+                qpos[tid] = -2;
+                qmask[tid] = 0ull;
+#pragma unroll
+                for (int t = 0; t < D; ++t) qco[tid * DP + t] = 1e19f;
+            }
+        }
+        __syncthreads();
+        // node sums of >= 4 slots: warp w owns slots 16 w .. 16 w + 15
+        for (int g = 0; g < kC128 / 32; ++g) {
+            const int it = 32 * g + lane;
+            if (32 * g >= qcnt) break;  // warp-uniform
+            uint64_t qd[D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const float x = qco[it * DP + t];
+                qd[t] = f2_pack(x, x);
+            }
+            const int my_pos = qpos[it];
+            float lv[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) pair_values(qd, my_pos, 8 * w + j, lv[2 * j], lv[2 * j + 1]);
+            float* row = V + (size_t)it * kV128;
+            float q4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                q4[i] = (lv[4 * i] + lv[4 * i + 1]) + (lv[4 * i + 2] + lv[4 * i + 3]);
+                row[32 + 4 * w + i] = q4[i];
+            }
+            const float e0 = q4[0] + q4[1], e1 = q4[2] + q4[3];
+            row[16 + 2 * w] = e0;
+            row[16 + 2 * w + 1] = e1;
+            row[8 + w] = e0 + e1;
+        }
+        __syncthreads();
+        if (tid < qcnt) {  // the top three levels over the eight subtree roots
+            float* r = V + (size_t)tid * kV128;
+            float l2[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                l2[i] = r[8 + 2 * i] + r[9 + 2 * i];
+                r[4 + i] = l2[i];
+            }
+            const float a2 = l2[0] + l2[1], b2 = l2[2] + l2[3];
+            r[2] = a2;
+            r[3] = b2;
+            r[1] = a2 + b2;
+        }
+        __syncthreads();
+        // descents: thread = item, over the item's samples
+        if (tid < qcnt) {
+            const float* row = V + (size_t)tid * kV128;
+            const int my_pos = qpos[tid];
+            const uint32_t qi = (uint32_t)qidx[tid];
+            uint64_t qd[D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) {
+                const float x = qco[tid * DP + t];
+                qd[t] = f2_pack(x, x);
+            }
+            for (uint64_t mk = qmask[tid]; mk; mk &= mk - 1ull) {
+                const int l = __ffsll((long long)mk) - 1;
+                int a = 0, c = m, h = 1;
+                uint8_t f = 0;
+                uint4 blk = make_uint4(0, 0, 0, 0);
+                int blk_id = -1;
+                float lf[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int t = 0; t < 7; ++t) {
+                    float gl, gr;
+                    if (t < 5) {
+                        gl = row[2 * h];
+                        gr = row[2 * h + 1];
+                    } else {
+                        if (t == 5) {  // h is a 4-slot node: its leaves again, as they were formed
+                            const int pp = 2 * (h - 32);
+                            pair_values(qd, my_pos, pp, lf[0], lf[1]);
+                            pair_values(qd, my_pos, pp + 1, lf[2], lf[3]);
+                            gl = lf[0] + lf[1];
+                            gr = lf[2] + lf[3];
+                        } else {
+                            const int o = (h & 1) * 2;
+                            gl = lf[o];
+                            gr = lf[o + 1];
+                        }
+                    }
+                    int right = 1;  // a single point sits in the right half
+                    if (c - a >= 2) {
+                        const uint32_t lev = (uint32_t)(s0 + t);
+                        if ((int)(lev >> 2) != blk_id) {
+                            blk_id = (int)(lev >> 2);
+                            blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
+                        }
+                        right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
+                        const int mid = a + (c - a) / 2;
+                        if (right) a = mid; else c = mid;
+                    }
+                    h = 2 * h + right;
+                }
+                const size_t o = (size_t)my_pos * L + l;
+                leaf_pos[o] = p_lo + a;
+                ksmp[o] = lf[h & 3];
+                lflags[o] = f;
+            }
+        }
+        ev_acc += (unsigned long long)qcnt * (unsigned long long)m;
+        it_acc += (unsigned long long)qcnt;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        atomicAdd(n_evals, ev_acc);
+        atomicAdd(n_items, it_acc);
+    }
+}
+
+template <int D>
+cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
+    const int64_t chunks_per_bin = (items_est / t->nb + kC128 - 1) / kC128 + 1;
+    int64_t S = (152 * 4 * 4 + t->nb - 1) / t->nb;
+    if (S > chunks_per_bin) S = chunks_per_bin;
+    if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
+    if (S < 1) S = 1;
+    if (S > 65535) S = 65535;
+    dim3 grid(t->nb, (unsigned)S);
+    const auto& ws = t->ws;
+    constexpr int DP = (D + 3) & ~3, DH = (D + 1) / 2;
+    constexpr size_t smem = (size_t)64 * DH * 16 + kC128 * 8 + 128 * 4 + 2 * kC128 * 4 + (size_t)kC128 * DP * 4 +
+                            (size_t)kC128 * kV128 * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(leaf128_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    leaf128_kernel<D><<<grid, kThreadsC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
+                                                 kp, ws.leaf_pos, ws.ksmp, ws.lflags,
+                                                 reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+                                                 reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int leaf_queries_per_tile(const fsg_tree* t) {
@@ -550,6 +784,26 @@ cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_
 }
 
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (t->dm == 7 && t->d <= kMaxFmaDim && t->n / t->nb >= 65) {  // every bin has 128 leaf slots
+        switch (t->d) {
+            case 1: return launch_leaf128_d<1>(t, kp, s);
+            case 2: return launch_leaf128_d<2>(t, kp, s);
+            case 3: return launch_leaf128_d<3>(t, kp, s);
+            case 4: return launch_leaf128_d<4>(t, kp, s);
+            case 5: return launch_leaf128_d<5>(t, kp, s);
+            case 6: return launch_leaf128_d<6>(t, kp, s);
+            case 7: return launch_leaf128_d<7>(t, kp, s);
+            case 8: return launch_leaf128_d<8>(t, kp, s);
+            case 9: return launch_leaf128_d<9>(t, kp, s);
+            case 10: return launch_leaf128_d<10>(t, kp, s);
+            case 11: return launch_leaf128_d<11>(t, kp, s);
+            case 12: return launch_leaf128_d<12>(t, kp, s);
+            case 13: return launch_leaf128_d<13>(t, kp, s);
+            case 14: return launch_leaf128_d<14>(t, kp, s);
+            case 15: return launch_leaf128_d<15>(t, kp, s);
+            default: return launch_leaf128_d<16>(t, kp, s);
+        }
+    }
     const int qt = leaf_queries_per_tile(t);
     switch (t->d) {
         case 1: return launch_leaf_d<1>(t, kp, qt, s);
