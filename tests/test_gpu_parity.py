@@ -373,3 +373,21 @@ def test_include_self_and_multi_edges_large_d(fsg, path):
     ge = gpu_graph(fsg, X, sigma, 10, 6)
     check_samples(ge["samples"], ge["flags"], e["samples"])
     assert (ge["src"] != ge["dst"]).all()
+
+
+# ----------------------------------------------------------------------------
+# The paper's largest two-moons size: n = 1,000,000 (bins of ~488 points, the
+# non-symmetric bin pass and the general leaf finish), sampled against the oracle
+# ----------------------------------------------------------------------------
+def test_two_moons_one_million(fsg):
+    n = 1_000_000
+    X = inputs.two_moons(n=n, seed=11)
+    g = gpu_graph(fsg, X, 0.02, 8, 3)
+    assert g["stats"]["status"] == 0 and g["stats"]["n_samples"] == n * 8
+    assert g["stats"]["n_evals"] >= n * n  # int64 counts past 2^31
+    q = np.random.default_rng(1).choice(n, size=6, replace=False)
+    gam = ora.gamma(0.02)
+    check_degrees(g["deg"][q], ora.degrees(X, gam, queries=q), n)
+    smp, _, _ = ora.sample(X, gam, 8, 3, queries=q)
+    check_samples(g["samples"][q], g["flags"][q], smp)
+    assert g["stats"]["n_flagged"] <= 0.01 * n * 8
