@@ -469,7 +469,8 @@ def run_serving(args):
                                                                                        torch.float32))
             for _ in range(24)]
     free_ring = list(range(len(ring)))
-    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8)
+    admission = {"arrival": fsg.FSG_ADMIT_ARRIVAL, "ratio": fsg.FSG_ADMIT_RESPONSE_RATIO}[args.admission]
+    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8, admission=admission)
     p = fsg.params(sigma)
     owner = {}
     lat, qms, edges_done = [], [], 0
@@ -526,7 +527,7 @@ def run_serving(args):
     if args.plain_requests > 0:
         # closed loop: the first K timed requests submitted at once, fused vs plain schedule
         def burst(schedule):
-            srv = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8)
+            srv = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8, admission=admission)
             pp = fsg.params(sigma, schedule=schedule)
             sub = timed_reqs[: args.plain_requests]
             t0b = time.perf_counter()
@@ -553,7 +554,9 @@ def run_serving(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving: {len(timed_reqs)} requests, Poisson {args.rate}/s, n log-uniform "
                                    f"[1e3, 2e5], d in {{2,10,64}}, mixture data, sigma=1.5, L=32, SET edges",
-                       "hbm_budget_gb": 120, "slots": 8, "parallelism": "continuous admission, 8 streams"},
+                       "hbm_budget_gb": 120, "slots": 8, "parallelism": "continuous admission, 8 streams",
+                       "admission": {"arrival": "arrival order",
+                                     "ratio": "highest response ratio next"}[args.admission]},
             "p50_ms": pct(lat_sorted, 0.5), "p99_ms": pct(lat_sorted, 0.99), "max_ms": lat_sorted[-1],
             "p50_queue_ms": pct(sorted(qms), 0.5), "edges": edges_done, "wall_s": wall,
             "offered_s": timed_reqs[-1].arrival_s - base, "clocks": clk, "plain_fp32_gpu": plain}
@@ -581,6 +584,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--plain-requests", type=int, default=40, help="serving: closed-loop burst for the plain path")
+    ap.add_argument("--admission", choices=["arrival", "ratio"], default="arrival", help="serving: admission order")
     args = ap.parse_args()
     if args.n:
         set_size(args.n)

@@ -319,9 +319,9 @@ void fsg_batch_destroy(fsg_batch* batch);
 /*
  * Serving: a request loop inside the library.  Graph-build requests (host
  * points, host outputs) of different n and d are queued; a worker thread
- * admits them in arrival order whenever a slot (a stream) is free and the
- * request's device memory estimate fits the HBM budget next to the requests
- * in flight.  Admitted requests run concurrently on their slots' streams, so
+ * admits them (in arrival order, or by response ratio: see admission below)
+ * whenever a slot (a stream) is free and the request's device memory
+ * estimate fits the HBM budget next to the requests in flight.  Admitted requests run concurrently on their slots' streams, so
  * their kernels overlap on the GPU; device memory comes from the server's own
  * stream-ordered pool, so admitting and retiring requests never synchronizes
  * the device.  A request's result (edge list in its host buffers, latency) is
@@ -333,8 +333,19 @@ typedef struct {
     int32_t max_slots;               /* requests in flight at once, 1..64            */
     int32_t queue_cap;               /* pending requests before BUSY (0 = 65536)     */
     int32_t inject_alloc_fail_every; /* testing: every k-th admission fails with OOM */
-    int32_t reserved[5];
+    int32_t admission;               /* FSG_ADMIT_ARRIVAL (0) | FSG_ADMIT_RESPONSE_RATIO */
+    int32_t reserved[4];
 } fsg_server_opts;
+
+/* Admission order.  ARRIVAL: strict arrival order.  RESPONSE_RATIO: highest
+ * response ratio next (Brinch Hansen, 1971): the queued request with the
+ * largest (waiting time + estimated run time) / estimated run time goes
+ * first, so short requests overtake long ones while a long request's ratio
+ * grows with its wait and it is never starved.  The run-time estimate is
+ * proportional to the n^2 (d + 6) pair work of the request plus a fixed
+ * launch cost.  In both orders the chosen request waits at the head until the
+ * budget has room for it; results do not depend on the order. */
+enum { FSG_ADMIT_ARRIVAL = 0, FSG_ADMIT_RESPONSE_RATIO = 1 };
 
 typedef struct {
     const float* h_points;  /* host float32 [n][d]; valid until the result is polled */

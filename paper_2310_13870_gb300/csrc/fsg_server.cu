@@ -26,6 +26,7 @@ struct Pending {
     fsg_request req;
     Clock::time_point t_submit;
     size_t bytes;
+    double est_ms;  // run-time estimate for the response-ratio order
 };
 
 struct Slot {
@@ -49,6 +50,15 @@ struct Slot {
 size_t request_bytes(const fsg_request& r) {
     return fsg::tree_bytes_estimate(r.n, r.d, r.L) + sizeof(float) * (size_t)r.n * r.d +
            (sizeof(int32_t) * 2 + sizeof(float)) * (size_t)r.n * r.L + 4096;
+}
+
+// Run-time estimate of one request alone: the bin pass and leaf work scale
+// with n^2 (d + 6) pair operations (about 4.5e-11 ms each on one GB300 for the
+// fused schedule), plus a fixed cost for the launches and copies.  Only the
+// ratio between requests and against waiting time matters.
+double request_est_ms(const fsg_request& r) {
+    const double n = (double)r.n;
+    return 0.25 + 4.5e-11 * n * n * (double)(r.d + 6);
 }
 
 }  // namespace
@@ -189,7 +199,7 @@ struct fsg_server {
                     release(s);
                 }
             }
-            // Admission: strict arrival order, slot and budget permitting.
+            // Admission: the next request in the chosen order, slot and budget permitting.
             for (;;) {
                 Slot* free_slot = nullptr;
                 for (Slot& s : slots)
@@ -198,9 +208,19 @@ struct fsg_server {
                 {
                     std::unique_lock<std::mutex> lock(mu);
                     if (!free_slot || pending.empty()) break;
-                    if (bytes_in_use + (int64_t)pending.front().bytes > opts.hbm_budget_bytes) break;
-                    p = pending.front();
-                    pending.pop_front();
+                    size_t pick = 0;
+                    if (opts.admission == FSG_ADMIT_RESPONSE_RATIO) {
+                        const Clock::time_point now = Clock::now();
+                        double best = -1.0;
+                        for (size_t k = 0; k < pending.size(); ++k) {
+                            const Pending& q = pending[k];
+                            const double ratio = (ms_since(q.t_submit, now) + q.est_ms) / q.est_ms;
+                            if (ratio > best) { best = ratio; pick = k; }  // ties keep arrival order
+                        }
+                    }
+                    if (bytes_in_use + (int64_t)pending[pick].bytes > opts.hbm_budget_bytes) break;
+                    p = pending[pick];
+                    pending.erase(pending.begin() + (ptrdiff_t)pick);
                     bytes_in_use += (int64_t)p.bytes;
                 }
                 progress = true;
@@ -235,7 +255,8 @@ extern "C" {
 
 int fsg_server_create(const fsg_server_opts* opts, fsg_server** out) {
     if (!out || !opts || opts->hbm_budget_bytes <= 0 || opts->max_slots < 1 || opts->max_slots > 64 ||
-        opts->queue_cap < 0 || opts->inject_alloc_fail_every < 0)
+        opts->queue_cap < 0 || opts->inject_alloc_fail_every < 0 ||
+        (opts->admission != FSG_ADMIT_ARRIVAL && opts->admission != FSG_ADMIT_RESPONSE_RATIO))
         return FSG_ERR_INVALID_ARG;
     *out = nullptr;
     fsg_server* sv = new (std::nothrow) fsg_server();
@@ -283,6 +304,7 @@ int fsg_server_submit(fsg_server* sv, const fsg_request* r, uint64_t* id_out) {
     pd.req = *r;
     pd.t_submit = Clock::now();
     pd.bytes = request_bytes(*r);
+    pd.est_ms = request_est_ms(*r);
     if ((int64_t)pd.bytes > sv->opts.hbm_budget_bytes) return FSG_ERR_BUSY;  // could never be admitted
     {
         std::lock_guard<std::mutex> lock(sv->mu);

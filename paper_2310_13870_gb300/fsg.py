@@ -32,6 +32,7 @@ FSG_SELF_EXCLUDE, FSG_SELF_INCLUDE = 0, 1
 FSG_PREC_AUTO, FSG_PREC_FP32, FSG_PREC_SPLIT_BF16, FSG_PREC_EXACT_INT = 0, 1, 2, 3
 FSG_EDGES_SET, FSG_EDGES_MULTI = 0, 1
 FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE = 0, 1
+FSG_ADMIT_ARRIVAL, FSG_ADMIT_RESPONSE_RATIO = 0, 1
 
 # Names every build of the library must export (checked by the CPU tests
 # against include/fsg.h).
@@ -75,7 +76,8 @@ class fsg_batch_item(ctypes.Structure):
 
 class fsg_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("queue_cap", ctypes.c_int32),
-                ("inject_alloc_fail_every", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("inject_alloc_fail_every", ctypes.c_int32), ("admission", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class fsg_request(ctypes.Structure):
@@ -427,8 +429,9 @@ class Server:
     here (pinned) and is returned by poll() with the result record."""
 
     def __init__(self, hbm_budget_bytes: int, max_slots: int = 8, queue_cap: int = 0,
-                 inject_alloc_fail_every: int = 0):
+                 inject_alloc_fail_every: int = 0, admission: int = 0):
         o = fsg_server_opts()
+        o.admission = admission
         o.hbm_budget_bytes = int(hbm_budget_bytes)
         o.max_slots = max_slots
         o.queue_cap = queue_cap

@@ -76,6 +76,14 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     # L outside 1..64
     rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(p), 65, 0, 0, buf, buf, buf, 1000, ctypes.byref(m), None)
     assert rc == fsg.FSG_ERR_INVALID_ARG
+    # server options: budget, slots and admission order are checked before any device call
+    sv = ctypes.c_void_p()
+    for field, value in (("hbm_budget_bytes", 0), ("max_slots", 0), ("max_slots", 65), ("queue_cap", -1),
+                         ("admission", 2), ("admission", -1)):
+        o = fsg.fsg_server_opts()
+        o.hbm_budget_bytes, o.max_slots = 1 << 30, 4
+        setattr(o, field, value)
+        assert lib.fsg_server_create(ctypes.byref(o), ctypes.byref(sv)) == fsg.FSG_ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header():

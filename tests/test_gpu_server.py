@@ -54,11 +54,11 @@ def _drain(server, expect, timeout_s=120):
     return got
 
 
-@pytest.mark.parametrize("budget_mb,slots", [(8192, 8), (64, 2)])
-def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots):
+@pytest.mark.parametrize("budget_mb,slots,admission", [(8192, 8, 0), (64, 2, 0), (8192, 8, 1), (64, 1, 1)])
+def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots, admission):
     reqs = _requests()
     want = [_alone(fsg, *r) for r in reqs]
-    server = fsg.Server(hbm_budget_bytes=budget_mb << 20, max_slots=slots)
+    server = fsg.Server(hbm_budget_bytes=budget_mb << 20, max_slots=slots, admission=admission)
     ids = [server.submit(X, fsg.params(s), L, seed) for X, s, L, seed in reqs]
     got = _drain(server, len(ids))
     for rid, (src, dst, w) in zip(ids, want):
@@ -70,6 +70,47 @@ def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots):
         np.testing.assert_array_equal(gw, w)
     assert server.info() == {"pending": 0, "in_flight": 0, "bytes_in_use": 0}
     server.close()
+
+
+def test_response_ratio_lets_short_requests_overtake(fsg):
+    # one slot: a long request (200k points) is admitted first, then three long
+    # and three short requests queue behind it; by response ratio the short
+    # ones run before the queued long ones, in arrival order after them.  Points
+    # and outputs are pinned beforehand so that every submission is quick
+    # next to the first request's run time.
+    def pinned(a):
+        return torch.from_numpy(a).pin_memory().numpy()
+
+    first = pinned(inputs.gaussian_mixture(n=200_000, d=64, k=4, box=4.0, seed=6))
+    big = pinned(inputs.gaussian_mixture(n=60_000, d=64, k=4, box=4.0, seed=7))
+    small = pinned(inputs.gaussian_mixture(n=500, d=2, k=4, box=4.0, seed=8))
+    L = 8
+    outs = [tuple(pinned(np.empty(200_000 * L, dt)) for dt in (np.int32, np.int32, np.float32)) for _ in range(7)]
+    order = {}
+    for admission in (fsg.FSG_ADMIT_ARRIVAL, fsg.FSG_ADMIT_RESPONSE_RATIO):
+        server = fsg.Server(hbm_budget_bytes=1 << 34, max_slots=1, admission=admission)
+        kinds, t_sub = {}, {}
+
+        def submit(X, sigma, seed, kind):
+            t = time.perf_counter()
+            rid = server.submit(X, fsg.params(sigma), L, seed, out=outs[len(kinds)])
+            kinds[rid], t_sub[rid] = kind, t
+
+        submit(first, 1.5, 0, "long")
+        t0 = time.time()
+        while server.info()["pending"] and time.time() - t0 < 10:
+            time.sleep(0.0002)
+        for k in range(3):
+            submit(big, 1.5, 1 + k, "long")
+        for k in range(3):
+            submit(small, 0.3, 10 + k, "short")
+        got = _drain(server, 7, timeout_s=300)
+        assert all(rec["status"] == fsg.FSG_OK for rec, _ in got.values())
+        admitted = sorted(got, key=lambda rid: t_sub[rid] + got[rid][0]["queue_ms"] * 1e-3)
+        order[admission] = [kinds[rid] for rid in admitted]
+        server.close()
+    assert order[fsg.FSG_ADMIT_ARRIVAL] == ["long"] * 4 + ["short"] * 3
+    assert order[fsg.FSG_ADMIT_RESPONSE_RATIO] == ["long"] + ["short"] * 3 + ["long"] * 3
 
 
 def test_injected_allocation_failure_and_cancellation(fsg):
