@@ -483,11 +483,13 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
     if (e == cudaSuccess) {
         const int64_t items_est = t->n * (int64_t)(L < t->nb ? L : t->nb);
         const bool fused_tc = t->d > kMaxFmaDim && tc && (1 << t->dm) <= 256;  // the heuristics of each launcher
-        const int qc = fused_tc ? 128 : leaf_queries_per_tile(t);
-        int64_t S0 = ((fused_tc ? 152 * 2 * 8 : 152 * 4 * 8) + t->nb - 1) / t->nb;
-        const int64_t cpb = (items_est / t->nb + qc - 1) / qc + 1;
-        if (S0 > cpb) S0 = cpb;
-        if (S0 < 1) S0 = 1;
+        int64_t S0 = leaf_default_splits(t, L);
+        if (fused_tc) {
+            S0 = (152 * 2 * 8 + t->nb - 1) / t->nb;
+            const int64_t cpb = (items_est / t->nb + 127) / 128 + 1;
+            if (S0 > cpb) S0 = cpb;
+            if (S0 < 1) S0 = 1;
+        }
         float tbest = 1e30f;
         for (int64_t S : {S0 / 4, S0 / 2, S0, 2 * S0, 4 * S0}) {
             if (S < 1 || S > 65535) continue;

@@ -31,13 +31,33 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
     extern __shared__ __align__(16) unsigned char smem_b[];
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t* sbin = reinterpret_cast<int32_t*>(smem_b) + (size_t)w * 64;             // [64] per warp
-    float* tree = reinterpret_cast<float*>(reinterpret_cast<int32_t*>(smem_b) + (size_t)warps * 64) +
-                  (size_t)w * 2 * nb;                                                 // [2 nb] per warp
+    float* tree = reinterpret_cast<float*>(smem_b) + (size_t)w * 2 * nb;  // [2 nb] per warp
     const int L = kp.L;
-    for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
-        const float* row = binsum + (size_t)q * nb;
-        for (int b = lane; b < nb; b += 32) tree[nb + b] = row[b];
+    // Rows of 128..1024 bins move as float4 (one row = nb/128 per lane), the
+    // next query's row in flight while the current one is processed; other
+    // bin counts load one float per lane and iteration.
+    const bool vec = (nb & 127) == 0 && nb <= 1024;
+    const int nv = nb >> 7;
+    const int qstride = gridDim.x * warps;
+    float4 v[8];
+    auto load_row = [&](int qq) {
+        const float4* r4 = reinterpret_cast<const float4*>(binsum + (size_t)qq * nb);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < nv) v[k] = __ldcs(r4 + k * 32 + lane);
+    };
+    if (vec && blockIdx.x * warps + w < n) load_row(blockIdx.x * warps + w);
+    for (int q = blockIdx.x * warps + w; q < n; q += qstride) {
+        if (vec) {
+            float4* t4 = reinterpret_cast<float4*>(tree + nb);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (k < nv) t4[k * 32 + lane] = v[k];
+            if (q + qstride < n) load_row(q + qstride);
+        } else {
+            const float* row = binsum + (size_t)q * nb;
+            for (int b = lane; b < nb; b += 32) tree[nb + b] = row[b];
+        }
         __syncwarp();
         for (int lev = s0 - 1; lev >= 0; --lev) {
             for (int h = (1 << lev) + lane; h < (2 << lev); h += 32) tree[h] = tree[2 * h] + tree[2 * h + 1];
@@ -67,21 +87,25 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                         binv[r] = h - nb;
                         flags[(size_t)q * L + l] = f;
                     }
-                    sbin[l] = binv[r];
                 }
                 __syncwarp();
-                // Group the samples by bin: sample l's mask holds every sample at its bin.
-                uint64_t M[2] = {0ull, 0ull};
-                for (int e = 0; e < 64; e += 4) {
-                    const int4 v = *reinterpret_cast<const int4*>(sbin + e);
+                // Group the samples by bin: sample l's mask holds every sample
+                // at its bin, gathered in a per-bin table that reuses the tree
+                // storage (nb 64-bit words; the tree is no longer read).
+                uint64_t* group = reinterpret_cast<uint64_t*>(tree);
 #pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        M[r] |= (uint64_t)(v.x == binv[r]) << e;
-                        M[r] |= (uint64_t)(v.y == binv[r]) << (e + 1);
-                        M[r] |= (uint64_t)(v.z == binv[r]) << (e + 2);
-                        M[r] |= (uint64_t)(v.w == binv[r]) << (e + 3);
-                    }
-                }
+                for (int r = 0; r < 2; ++r)
+                    if (binv[r] >= 0) group[binv[r]] = 0ull;
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (binv[r] >= 0) atomicOr(reinterpret_cast<unsigned long long*>(group + binv[r]),
+                                               1ull << (lane + 32 * r));
+                __syncwarp();
+                uint64_t M[2] = {0ull, 0ull};
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (binv[r] >= 0) M[r] = group[binv[r]];
                 __syncwarp();
                 // The lowest sample of each bin writes the (bin, mask) item of
                 // this query; items are packed per query and counted per bin.
@@ -489,11 +513,7 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    // Splits per bin: about 8 waves of CTAs over the expected items.
-    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
-    const int64_t chunks_per_bin = (items_est / t->nb + qc - 1) / qc + 1;
-    int64_t S = (152 * 4 * 8 + t->nb - 1) / t->nb;
-    if (S > chunks_per_bin) S = chunks_per_bin;
+    int64_t S = leaf_default_splits(t, kp.L);
     if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
@@ -506,199 +526,265 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
     return cudaGetLastError();
 }
 
-// Leaf finish for bins of 128 leaf slots (d <= 16): chunks of 128 items.
-// Warp w evaluates the contiguous slots 16 w .. 16 w + 15 for every item of
-// the chunk (four rounds of 32, lane = item) and keeps only the node sums of
-// at least 4 slots (63 per item, heap order); one thread per item forms the
-// top three levels; then one thread per item descends its samples, reading
-// the kept nodes and, at a 4-slot node, re-evaluating its four leaves with
-// the same arithmetic (so the pair and leaf values equal those that formed
-// the node).  Three barriers per 128 items.
-constexpr int kC128 = 128;   // items per chunk
-constexpr int kV128 = 65;    // heap row stride (odd: the lanes' rows hit distinct banks)
+// Leaf finish for bins of 65..128 points (seven halvings below the bin,
+// d <= 16): chunks of 128 items, one item per thread.
+//  * Node sums: warp w owns the bin's quarter w (the depth-2 node w below the
+//    bin) and evaluates only its real points, for two items per lane packed
+//    into the two FP32x2 lanes (both use the same point coordinates), in
+//    groups of the 2..4 points of a depth-5 node.  It keeps the sums of
+//    depths 2..4 (nodes 4..31 in heap order).
+//  * Descent: each thread forms its item's nodes 2 and 3 and descends the
+//    item's samples through depths 0..3 on the kept sums.  Below the depth-4
+//    node reached (4..8 points) it evaluates that node's points again with the
+//    same arithmetic (scalar FP32, the same rounding as one packed lane) and
+//    takes the remaining decisions on partial sums of those values.
+// Two barriers per chunk of 128 items.
+constexpr int kLC = 128;  // items per chunk = threads per CTA
+constexpr int kLV = 31;   // kept node sums per item (node h at h - 1), odd row stride
+
+// Kernel values of the point at Pr for two queries (packed lanes), the point
+// dropped for a query whose own local index it is.
+template <int D, bool SELF>
+__device__ __forceinline__ uint64_t leaf_kv2(const uint64_t (&qd)[D], const float4* __restrict__ Pr, uint64_t nc2,
+                                             int r, int sa, int sb) {
+    constexpr int DH = (D + 1) / 2;
+    uint64_t s2 = 0ull, s3 = 0ull;
+#pragma unroll
+    for (int u = 0; u < DH; ++u) {
+        const float4 c4 = Pr[u];
+        uint64_t dd = f2_sub(qd[2 * u], f2_pack(c4.x, c4.y));
+        s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
+        if (2 * u + 1 < D) {
+            dd = f2_sub(qd[2 * u + 1], f2_pack(c4.z, c4.w));
+            s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
+        }
+    }
+    if (D > 1) s2 = f2_add(s2, s3);
+    const float2 sv = f2_unpack(f2_mul(s2, nc2));
+    float ka = ex2_approx(sv.x), kb = ex2_approx(sv.y);
+    if (SELF) {
+        if (r == sa) ka = 0.f;
+        if (r == sb) kb = 0.f;
+    }
+    return f2_pack(ka, kb);
+}
+
+// One lane of leaf_kv2, operation for operation.
+template <int D>
+__device__ __forceinline__ float leaf_kv1(const float (&x)[D], const float4* __restrict__ Pr, float neg_c) {
+    constexpr int DH = (D + 1) / 2;
+    float s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int u = 0; u < DH; ++u) {
+        const float4 c4 = Pr[u];
+        float dd = __fsub_rn(x[2 * u], c4.x);
+        s2 = u == 0 ? __fmul_rn(dd, dd) : __fmaf_rn(dd, dd, s2);
+        if (2 * u + 1 < D) {
+            dd = __fsub_rn(x[2 * u + 1], c4.z);
+            s3 = u == 0 ? __fmul_rn(dd, dd) : __fmaf_rn(dd, dd, s3);
+        }
+    }
+    if (D > 1) s2 = __fadd_rn(s2, s3);
+    return ex2_approx(__fmul_rn(s2, neg_c));
+}
+
+// Sums of the eight depth-5 nodes of quarter w for the lane's two items.
+template <int D, bool SELF>
+__device__ __forceinline__ void leaf_quarter(const uint64_t (&qd)[D], const float4* __restrict__ P2,
+                                             const int32_t* __restrict__ r5, int w, uint64_t nc2, int sa, int sb,
+                                             uint64_t (&n5)[8]) {
+    constexpr int DH = (D + 1) / 2;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int r0 = r5[8 * w + j], c = r5[8 * w + j + 1] - r0;  // 2..4 points
+        uint64_t v = f2_add(leaf_kv2<D, SELF>(qd, P2 + (size_t)r0 * DH, nc2, r0, sa, sb),
+                            leaf_kv2<D, SELF>(qd, P2 + (size_t)(r0 + 1) * DH, nc2, r0 + 1, sa, sb));
+        if (c > 2) {
+            uint64_t v2 = leaf_kv2<D, SELF>(qd, P2 + (size_t)(r0 + 2) * DH, nc2, r0 + 2, sa, sb);
+            if (c > 3) v2 = f2_add(v2, leaf_kv2<D, SELF>(qd, P2 + (size_t)(r0 + 3) * DH, nc2, r0 + 3, sa, sb));
+            v = f2_add(v, v2);
+        }
+        n5[j] = v;
+    }
+}
 
 template <int D>
-__global__ void __launch_bounds__(kThreadsC, 4)
+struct Leaf128Layout {
+    static constexpr int DP = (D + 3) & ~3;
+    static constexpr int DH = (D + 1) / 2;
+    static constexpr int QS = D | 1;  // odd row stride of the item coordinates
+    static constexpr size_t P2 = 0;                                    // float4 [128][DH]: (c, c, c', c')
+    static constexpr size_t R5 = P2 + (size_t)128 * DH * 16;           // int [33] depth-5 node starts
+    static constexpr size_t QMASK = R5 + 48 * 4;                       // uint64 [128]
+    static constexpr size_t QPOS = QMASK + (size_t)kLC * 8;            // int [128]
+    static constexpr size_t QIDX = QPOS + (size_t)kLC * 4;             // int [128]
+    static constexpr size_t QCO = QIDX + (size_t)kLC * 4;              // float [128][QS]
+    static constexpr size_t V = QCO + (((size_t)kLC * QS * 4 + 15) & ~size_t(15));  // float [128][31]
+    static constexpr size_t total = V + (size_t)kLC * kLV * 4;
+};
+
+template <int D>
+__global__ void __launch_bounds__(kLC)
 leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
                int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
                const uint64_t* __restrict__ items_mask, KernelParams kp, int32_t* __restrict__ leaf_pos,
                float* __restrict__ ksmp, uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
                unsigned long long* __restrict__ n_items) {
-    constexpr int DP = (D + 3) & ~3;
-    constexpr int DH = (D + 1) / 2;
+    using LY = Leaf128Layout<D>;
+    constexpr int DP = LY::DP, DH = LY::DH, QS = LY::QS;
     extern __shared__ __align__(16) unsigned char smem128[];
-    float4* P = reinterpret_cast<float4*>(smem128);                        // [64][DH] slot pairs, interleaved
-    uint64_t* qmask = reinterpret_cast<uint64_t*>(P + 64 * DH);            // [128]
-    int32_t* spos = reinterpret_cast<int32_t*>(qmask + kC128);             // [128]
-    int32_t* qpos = spos + 128;                                             // [128]
-    int32_t* qidx = qpos + kC128;                                           // [128]
-    float* qco = reinterpret_cast<float*>(qidx + kC128);                    // [128][DP]
-    float* V = qco + kC128 * DP;                                            // [128][65] node sums >= 4 slots
+    float4* P2 = reinterpret_cast<float4*>(smem128 + LY::P2);
+    int32_t* r5 = reinterpret_cast<int32_t*>(smem128 + LY::R5);
+    uint64_t* qmask = reinterpret_cast<uint64_t*>(smem128 + LY::QMASK);
+    int32_t* qpos = reinterpret_cast<int32_t*>(smem128 + LY::QPOS);
+    int32_t* qidx = reinterpret_cast<int32_t*>(smem128 + LY::QIDX);
+    float* qco = reinterpret_cast<float*>(smem128 + LY::QCO);
+    float* V = reinterpret_cast<float*>(smem128 + LY::V);
     const int b = blockIdx.x;
     const int base = bin_off[b * kBinSlots];
     const int cnt = bin_off[(b + 1) * kBinSlots] - base;
-    const int nchunks = (cnt + kC128 - 1) / kC128;
+    const int nchunks = (cnt + kLC - 1) / kLC;
     if ((int)blockIdx.y >= nchunks) return;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;  // 65 <= m <= 128: dm = 7
-    for (int sl = tid; sl < 128; sl += kThreadsC) {
-        int a = 0, c = m;
-        for (int t = 6; t >= 0; --t) {
-            const int mid = a + (c - a) / 2;
-            if ((sl >> t) & 1) a = mid; else c = mid;
-        }
-        const int pos = c - a == 1 ? p_lo + a : -1;
-        spos[sl] = pos;
-        float* Pw = reinterpret_cast<float*>(P + (size_t)(sl >> 1) * DH);
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;  // 65 <= m <= 128
+    if (tid < m) {
 #pragma unroll
         for (int u = 0; u < DH; ++u) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t = 2 * u + h;
-                Pw[4 * u + 2 * h + (sl & 1)] = (t < D) ? (pos >= 0 ? Xt[(size_t)pos * DP + t] : 1e19f) : 0.f;
-            }
+            const float c0 = Xt[(size_t)(p_lo + tid) * DP + 2 * u];
+            const float c1 = (2 * u + 1 < D) ? Xt[(size_t)(p_lo + tid) * DP + 2 * u + 1] : 0.f;
+            P2[(size_t)tid * DH + u] = make_float4(c0, c0, c1, c1);
         }
     }
-    const uint64_t nc2 = f2_pack(kp.neg_c, kp.neg_c);
-    // kernel values of slot pair pp for the query at qd (two slots), masked at the query itself
-    auto pair_values = [&](const uint64_t (&qd)[D], int my_pos, int pp, float& k0, float& k1) {
-        const float4* Pp = P + (size_t)pp * DH;
-        uint64_t s2 = 0ull, s3 = 0ull;
-#pragma unroll
-        for (int u = 0; u < DH; ++u) {
-            const float4 c4 = Pp[u];
-            const uint64_t ca = f2_pack(c4.x, c4.y), cb = f2_pack(c4.z, c4.w);
-            uint64_t dd = f2_sub(qd[2 * u], ca);
-            s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
-            if (2 * u + 1 < D) {
-                dd = f2_sub(qd[2 * u + 1], cb);
-                s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
+    if (tid <= 32) {  // start of depth-5 node tid of the bin (tid = 32: the end)
+        int a = 0, c = m;
+        if (tid < 32) {
+            for (int t = 4; t >= 0; --t) {
+                const int mid = a + (c - a) / 2;
+                if ((tid >> t) & 1) a = mid; else c = mid;
             }
+        } else {
+            a = m;
         }
-        if (D > 1) s2 = f2_add(s2, s3);
-        const float2 sv = f2_unpack(f2_mul(s2, nc2));
-        k0 = ex2_approx(sv.x);
-        k1 = ex2_approx(sv.y);
-        if (kp.self_exclude) {
-            if (spos[2 * pp] == my_pos) k0 = 0.f;
-            if (spos[2 * pp + 1] == my_pos) k1 = 0.f;
-        }
-    };
+        r5[tid] = a;
+    }
+    const uint64_t nc2 = f2_pack(kp.neg_c, kp.neg_c);
     const int L = kp.L;
     const size_t ibase = (size_t)base;
     unsigned long long ev_acc = 0, it_acc = 0;
     for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
-        const int it0 = chunk * kC128;
-        const int qcnt = min(kC128, cnt - it0);
-        if (tid < kC128) {  // this chunk's items
-            if (tid < qcnt) {
-                const int q = items_q[ibase + it0 + tid];
-                qpos[tid] = q;
-                qidx[tid] = perm[q];
-                qmask[tid] = items_mask[ibase + it0 + tid];
+        const int it0 = chunk * kLC;
+        const int qcnt = min(kLC, cnt - it0);
+        if (tid < qcnt) {
+            const int q = items_q[ibase + it0 + tid];
+            qpos[tid] = q;
+            qidx[tid] = perm[q];
+            qmask[tid] = items_mask[ibase + it0 + tid];
 #pragma unroll
-                for (int t = 0; t < D; ++t) qco[tid * DP + t] = Xt[(size_t)q * DP + t];
-            } else {
-                qpos[tid] = -2;
-                qmask[tid] = 0ull;
+            for (int t = 0; t < D; ++t) qco[tid * QS + t] = Xt[(size_t)q * DP + t];
+        } else {
+            qpos[tid] = -1;
+            qmask[tid] = 0ull;
 #pragma unroll
-                for (int t = 0; t < D; ++t) qco[tid * DP + t] = 1e19f;
-            }
+            for (int t = 0; t < D; ++t) qco[tid * QS + t] = 1e19f;  // far away: every value is 0
         }
         __syncthreads();
-        // node sums of >= 4 slots: warp w owns slots 16 w .. 16 w + 15
-        for (int g = 0; g < kC128 / 32; ++g) {
-            const int it = 32 * g + lane;
-            if (32 * g >= qcnt) break;  // warp-uniform
+        // node sums of depths 2..4 over quarter w, two items per lane
+        for (int pass = 0; pass < kLC / 64; ++pass) {
+            if (64 * pass >= qcnt) break;  // warp-uniform
+            const int ia = 64 * pass + lane, ib = ia + 32;
             uint64_t qd[D];
 #pragma unroll
-            for (int t = 0; t < D; ++t) {
-                const float x = qco[it * DP + t];
-                qd[t] = f2_pack(x, x);
-            }
-            const int my_pos = qpos[it];
-            float lv[16];
+            for (int t = 0; t < D; ++t) qd[t] = f2_pack(qco[ia * QS + t], qco[ib * QS + t]);
+            const int sa = qpos[ia] - p_lo, sb = qpos[ib] - p_lo;  // local index of the query itself
+            const int lo = r5[8 * w], hi = r5[8 * w + 8];
+            const bool self_here = kp.self_exclude &&
+                                   __any_sync(0xffffffffu, (sa >= lo && sa < hi) || (sb >= lo && sb < hi));
+            uint64_t n5[8];
+            if (self_here) leaf_quarter<D, true>(qd, P2, r5, w, nc2, sa, sb, n5);
+            else leaf_quarter<D, false>(qd, P2, r5, w, nc2, sa, sb, n5);
+            uint64_t n4[4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) pair_values(qd, my_pos, 8 * w + j, lv[2 * j], lv[2 * j + 1]);
-            float* row = V + (size_t)it * kV128;
-            float q4[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                q4[i] = (lv[4 * i] + lv[4 * i + 1]) + (lv[4 * i + 2] + lv[4 * i + 3]);
-                row[32 + 4 * w + i] = q4[i];
-            }
-            const float e0 = q4[0] + q4[1], e1 = q4[2] + q4[3];
-            row[16 + 2 * w] = e0;
-            row[16 + 2 * w + 1] = e1;
-            row[8 + w] = e0 + e1;
-        }
-        __syncthreads();
-        if (tid < qcnt) {  // the top three levels over the eight subtree roots
-            float* r = V + (size_t)tid * kV128;
-            float l2[4];
+            for (int i = 0; i < 4; ++i) n4[i] = f2_add(n5[2 * i], n5[2 * i + 1]);
+            const uint64_t n3a = f2_add(n4[0], n4[1]), n3b = f2_add(n4[2], n4[3]);
+            const uint64_t n2 = f2_add(n3a, n3b);
+            float* Va = V + (size_t)ia * kLV;
+            float* Vb = V + (size_t)ib * kLV;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                l2[i] = r[8 + 2 * i] + r[9 + 2 * i];
-                r[4 + i] = l2[i];
+                const float2 v = f2_unpack(n4[i]);
+                Va[15 + 4 * w + i] = v.x;
+                Vb[15 + 4 * w + i] = v.y;
             }
-            const float a2 = l2[0] + l2[1], b2 = l2[2] + l2[3];
-            r[2] = a2;
-            r[3] = b2;
-            r[1] = a2 + b2;
+            const float2 v3a = f2_unpack(n3a), v3b = f2_unpack(n3b), v2 = f2_unpack(n2);
+            Va[7 + 2 * w] = v3a.x;
+            Vb[7 + 2 * w] = v3a.y;
+            Va[8 + 2 * w] = v3b.x;
+            Vb[8 + 2 * w] = v3b.y;
+            Va[3 + w] = v2.x;
+            Vb[3 + w] = v2.y;
         }
         __syncthreads();
         // descents: thread = item, over the item's samples
         if (tid < qcnt) {
-            const float* row = V + (size_t)tid * kV128;
+            float* row = V + (size_t)tid * kLV;
+            row[1] = row[3] + row[4];  // node 2
+            row[2] = row[5] + row[6];  // node 3
             const int my_pos = qpos[tid];
+            const int s_self = kp.self_exclude ? my_pos - p_lo : -1;
             const uint32_t qi = (uint32_t)qidx[tid];
-            uint64_t qd[D];
+            float x[D];
 #pragma unroll
-            for (int t = 0; t < D; ++t) {
-                const float x = qco[tid * DP + t];
-                qd[t] = f2_pack(x, x);
-            }
+            for (int t = 0; t < D; ++t) x[t] = qco[tid * QS + t];
             for (uint64_t mk = qmask[tid]; mk; mk &= mk - 1ull) {
                 const int l = __ffsll((long long)mk) - 1;
                 int a = 0, c = m, h = 1;
                 uint8_t f = 0;
                 uint4 blk = make_uint4(0, 0, 0, 0);
                 int blk_id = -1;
-                float lf[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int t = 0; t < 7; ++t) {
-                    float gl, gr;
-                    if (t < 5) {
-                        gl = row[2 * h];
-                        gr = row[2 * h + 1];
-                    } else {
-                        if (t == 5) {  // h is a 4-slot node: its leaves again, as they were formed
-                            const int pp = 2 * (h - 32);
-                            pair_values(qd, my_pos, pp, lf[0], lf[1]);
-                            pair_values(qd, my_pos, pp + 1, lf[2], lf[3]);
-                            gl = lf[0] + lf[1];
-                            gr = lf[2] + lf[3];
-                        } else {
-                            const int o = (h & 1) * 2;
-                            gl = lf[o];
-                            gr = lf[o + 1];
-                        }
+                for (int t = 0; t < 4; ++t) {  // nodes of >= 8 points
+                    const uint32_t lev = (uint32_t)(s0 + t);
+                    if ((int)(lev >> 2) != blk_id) {
+                        blk_id = (int)(lev >> 2);
+                        blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
                     }
-                    int right = 1;  // a single point sits in the right half
-                    if (c - a >= 2) {
-                        const uint32_t lev = (uint32_t)(s0 + t);
-                        if ((int)(lev >> 2) != blk_id) {
-                            blk_id = (int)(lev >> 2);
-                            blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
-                        }
-                        right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
-                        const int mid = a + (c - a) / 2;
-                        if (right) a = mid; else c = mid;
-                    }
+                    const int right = descend_decide(row[2 * h - 1], row[2 * h], block_word(blk, lev), kp.flag_eps, f);
+                    const int mid = a + (c - a) / 2;
+                    if (right) a = mid; else c = mid;
                     h = 2 * h + right;
                 }
+                // the depth-4 node [a, c) of 4..8 points, evaluated again
+                const int a0 = a, cnt4 = c - a;
+                float lf[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    lf[k] = 0.f;
+                    if (k < cnt4 && a0 + k != s_self) lf[k] = leaf_kv1<D>(x, P2 + (size_t)(a0 + k) * DH, kp.neg_c);
+                }
+                for (int t = 4; t < 7; ++t) {
+                    if (c - a < 2) break;
+                    const int mid = a + (c - a) / 2;
+                    float gl = 0.f, gr = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int r = a0 + k;
+                        if (r >= a && r < mid) gl += lf[k];
+                        if (r >= mid && r < c) gr += lf[k];
+                    }
+                    const uint32_t lev = (uint32_t)(s0 + t);
+                    if ((int)(lev >> 2) != blk_id) {
+                        blk_id = (int)(lev >> 2);
+                        blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
+                    }
+                    const int right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
+                    if (right) a = mid; else c = mid;
+                }
+                float kval = 0.f;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (a0 + k == a) kval = lf[k];
                 const size_t o = (size_t)my_pos * L + l;
                 leaf_pos[o] = p_lo + a;
-                ksmp[o] = lf[h & 3];
+                ksmp[o] = kval;
                 lflags[o] = f;
             }
         }
@@ -712,20 +798,19 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
     }
 }
 
+bool use_leaf128(const fsg_tree* t) {
+    return t->dm == 7 && t->d <= kMaxFmaDim && t->n / t->nb >= 65;  // every bin holds 65..128 points
+}
+
 template <int D>
 cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
-    const int64_t chunks_per_bin = (items_est / t->nb + kC128 - 1) / kC128 + 1;
-    int64_t S = (152 * 4 * 4 + t->nb - 1) / t->nb;
-    if (S > chunks_per_bin) S = chunks_per_bin;
+    int64_t S = leaf_default_splits(t, kp.L);
     if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
-    constexpr int DP = (D + 3) & ~3, DH = (D + 1) / 2;
-    constexpr size_t smem = (size_t)64 * DH * 16 + kC128 * 8 + 128 * 4 + 2 * kC128 * 4 + (size_t)kC128 * DP * 4 +
-                            (size_t)kC128 * kV128 * 4;
+    constexpr size_t smem = Leaf128Layout<D>::total;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(leaf128_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -733,14 +818,26 @@ cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStre
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    leaf128_kernel<D><<<grid, kThreadsC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
-                                                 kp, ws.leaf_pos, ws.ksmp, ws.lflags,
-                                                 reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
-                                                 reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
+    leaf128_kernel<D><<<grid, kLC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
+                                              kp, ws.leaf_pos, ws.ksmp, ws.lflags,
+                                              reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+                                              reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
     return cudaGetLastError();
 }
 
 }  // namespace
+
+// CTAs per bin of the d <= 16 leaf kernels: a few waves over the expected
+// items (one per (query, bin) reached, at most min(L, nb) per query).
+int64_t leaf_default_splits(const fsg_tree* t, int L) {
+    const int64_t items_est = t->n * (int64_t)(L < t->nb ? L : t->nb);
+    const bool c128 = use_leaf128(t);
+    const int qc = c128 ? 128 : leaf_queries_per_tile(t);
+    const int64_t chunks_per_bin = (items_est / t->nb + qc - 1) / qc + 1;
+    int64_t S = ((c128 ? 152 * 6 * 4 : 152 * 4 * 8) + t->nb - 1) / t->nb;
+    if (S > chunks_per_bin) S = chunks_per_bin;
+    return S < 1 ? 1 : S;
+}
 
 int leaf_queries_per_tile(const fsg_tree* t) {
     int qc = 8192 / (2 << t->dm);  // <= 32 KB of per-query trees, one query per lane
@@ -752,8 +849,8 @@ int leaf_queries_per_tile(const fsg_tree* t) {
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
                                cudaStream_t s) {
     int warps = 8;
-    while (warps > 1 && (size_t)warps * (256 + 8 * t->nb) > 96 * 1024) warps >>= 1;
-    const size_t smem = (size_t)warps * (256 + 8 * t->nb);  // per warp: 64 sample bins + 2 nb tree nodes
+    while (warps > 1 && (size_t)warps * 8 * t->nb > 96 * 1024) warps >>= 1;
+    const size_t smem = (size_t)warps * 8 * t->nb;  // per warp: 2 nb tree nodes (later nb bin masks)
     static size_t attr = 0;
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(descend_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -784,7 +881,7 @@ cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_
 }
 
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    if (t->dm == 7 && t->d <= kMaxFmaDim && t->n / t->nb >= 65) {  // every bin has 128 leaf slots
+    if (use_leaf128(t)) {
         switch (t->d) {
             case 1: return launch_leaf128_d<1>(t, kp, s);
             case 2: return launch_leaf128_d<2>(t, kp, s);

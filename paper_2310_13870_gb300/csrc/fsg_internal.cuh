@@ -138,6 +138,7 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
 cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 int leaf_queries_per_tile(const fsg_tree* t);
+int64_t leaf_default_splits(const fsg_tree* t, int L);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
                          int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
