@@ -83,7 +83,8 @@ struct fsg_tree {
     int32_t* status = nullptr;  // device status word
     int exact_int = 0;       // points are multiples of 1/255 in [0,1]
     // tensor-core path (d >= 64, exact 8-bit data): BF16 copy of 255 x,
-    // squared norms in integer units, TMA descriptors (A: 128 rows, B: 256 rows)
+    // squared norms in integer units, TMA descriptors (A: 128 rows, B: 256 rows,
+    // P: 16 rows)
     void* Xb = nullptr;
     float* norms = nullptr;
     int32_t dpad = 0;
@@ -93,6 +94,7 @@ struct fsg_tree {
     float* Xtt = nullptr;
     alignas(64) unsigned char tmap_a[128] = {};
     alignas(64) unsigned char tmap_b[128] = {};
+    alignas(64) unsigned char tmap_p[128] = {};  // 16-row boxes: point rows of the tensor-core leaf kernel
     fsg::Workspace ws;
     fsg::LaunchTuning tune;
     // per-phase timing (fsg_profile) and kernel-launch count
@@ -233,6 +235,13 @@ __device__ __forceinline__ float2 f2_unpack(uint64_t v) {
 // --- mbarrier + 1-D bulk copy (TMA engine) --------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+// The first 1024-byte boundary at or after p (dynamic shared memory), by
+// pointer arithmetic on p itself, so accesses through the result stay
+// shared-memory instructions (a round trip through an integer would make
+// them generic loads and stores).
+__device__ __forceinline__ unsigned char* smem_align1024(unsigned char* p) {
+    return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

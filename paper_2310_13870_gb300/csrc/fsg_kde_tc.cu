@@ -170,8 +170,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                    const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
                    int bpc, float neg_c, int self_exclude, float* __restrict__ binsum, int32_t* __restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* base = smem_align1024(smem_raw);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
     uint64_t* empty = full + kTcStages;
     uint64_t* tfull = empty + kTcStages;
@@ -407,7 +406,12 @@ int tc_prepare(fsg_tree* t, cudaStream_t s) {
         CUresult r2 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_b), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xb, gdim,
                           gstride, boxB, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return FSG_ERR_UNSUPPORTED;
+        const cuuint32_t boxP[2] = {(cuuint32_t)kTcK, 16u};  // point rows of the leaf kernel
+        CUresult r3 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_p), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xb, gdim,
+                          gstride, boxP, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS)
+            return FSG_ERR_UNSUPPORTED;
         t->dpad = dpad;
     }
     dim3 block(32, 8);
@@ -458,136 +462,154 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
 
 // ---------------------------------------------------------------------------
 // Tensor-core leaf finish: for the items (queries) of one bin, the kernel
-// value at every leaf slot of the bin's tree, k = ex2(neg_c (||x||^2 +
+// value of every (item, point) pair of the bin, k = ex2(neg_c (||x||^2 +
 // ||y||^2 - 2 x.y)) in the same integer units as the bin pass, then the
 // remaining levels of the item's samples.  CTA (b, y) handles chunks of 128
-// items of bin b: the item rows and the bin's slot rows (zero rows for empty
-// slots) are gathered with cp.async directly into the 128-byte-swizzled
-// K-major layout (3-stage ring), one thread issues tcgen05.mma M=128 x
-// N=slots x K=16, and each of the four warps reads its TMEM lane quadrant:
-// thread = item, its row of leaf values kept in shared memory.  The thread
-// then descends each of the item's samples through the bin's perfect tree,
-// the two child sums of a node being the sums of its two halves of slots
-// (fixed order), with the same Philox draws and decision rule as every
-// other level, and writes the sampled position, kernel value and flags.
+// items of bin b (3-stage ring over K chunks of 64 coordinates, 128-byte
+// swizzled K-major):
+//   A = the 128 item rows, gathered with cp.async (16 bytes per copy);
+//   B = the bin's m points, contiguous in tree order, by TMA in boxes of 16
+//       rows (N = m rounded up to 16 columns; columns past m are ignored);
+// one thread issues tcgen05.mma M=128 x N x K=16, and each of the four warps
+// reads its TMEM lane quadrant: thread = item, its row of values kept in
+// shared memory (the idle stages).  The thread then descends each of the
+// item's samples through the bin's halving tree: the 16 nodes of depth 4 are
+// summed once per item (and their tree above), deeper nodes are sums over
+// their points' values, with the same Philox draws and decision rule as
+// every other level; it writes the sampled position, kernel value and flags.
+// With bins of up to 160 points two CTAs share an SM, so one CTA's epilogue
+// and descents overlap the other's copies and MMAs.
 // ---------------------------------------------------------------------------
 namespace fsg {
 namespace {
 
 constexpr int kLvStages = 3;
 constexpr int kLvThreads = 128;
+constexpr int kLvBox = 16;  // point rows per TMA box
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
                  : "memory");
 }
 
-// Sum of v[lo .. lo + len) in a fixed pairwise order (len a power of two).
-__device__ __forceinline__ float range_sum(const float* __restrict__ v, int lo, int len) {
-    float s = 0.f;
-    for (int b = 0; b < len; b += 8) {
-        const float* x = v + lo + b;
-        if (len >= 8) {
-            s += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
-        } else {
-            for (int i = 0; i < len; ++i) s += x[i];
-        }
+// Shared-memory layout of the leaf kernel for point operands of up to nmax
+// rows (nmax a multiple of 16); the same arithmetic on host and device.
+struct LvLayout {
+    uint32_t kB, stage, bars, rowpos, pnorm, bnd4, btree, total;
+    bool tree_in_stages;
+    __host__ __device__ explicit LvLayout(int nmax) {
+        kB = (uint32_t)nmax * 128u;
+        stage = 128u * 128u + kB;
+        bars = kLvStages * stage;                        // done[3], full[3], accf, fin
+        rowpos = bars + 8 * (2 * kLvStages + 2) + 16;    // + TMEM slot
+        pnorm = rowpos + 128 * 4;
+        bnd4 = pnorm + (uint32_t)nmax * 4;
+        const uint32_t after = bnd4 + 17 * 4 + 12;
+        tree_in_stages = (size_t)128 * (nmax + 1 + 33) * 4 <= (size_t)kLvStages * stage;
+        btree = tree_in_stages ? 128u * (uint32_t)(nmax + 1) * 4u : ((after + 15u) & ~15u);
+        total = tree_in_stages ? after : btree + 128 * 33 * 4;
     }
-    return s;
-}
+};
 
-template <int NS>  // slots (N of the MMA): 64, 128 or 256
-__global__ void __launch_bounds__(kLvThreads, 1)
-leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict__ norms, int dpad,
-                      const int32_t* __restrict__ bnd, const int32_t* __restrict__ bin_off,
-                      const int32_t* __restrict__ items_q, const uint64_t* __restrict__ items_mask,
-                      const int32_t* __restrict__ perm, KernelParams kp, float neg_c, int s0,
-                      int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp, uint8_t* __restrict__ lflags,
-                      unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items,
-                      int32_t* __restrict__ status) {
+__global__ void __launch_bounds__(kLvThreads, 2)
+leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat16* __restrict__ Xb,
+                      const float* __restrict__ norms, int dpad, int nmax, const int32_t* __restrict__ bnd,
+                      const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
+                      const uint64_t* __restrict__ items_mask, const int32_t* __restrict__ perm, KernelParams kp,
+                      float neg_c, int s0, int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp,
+                      uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
+                      unsigned long long* __restrict__ n_items, int32_t* __restrict__ status) {
     const int self_exclude = kp.self_exclude;
-    constexpr uint32_t kA = 128 * 128, kB = NS * 128, kStage = kA + kB;
-    constexpr uint32_t kIdescLv = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NS >> 3) << 17) |
-                                  ((uint32_t)(128 >> 4) << 24);
     const int b = blockIdx.x;
     const int seg = bin_off[b * kBinSlots];
     const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
     const int nchunks = (cnt + 127) / 128;
     if ((int)blockIdx.y >= nchunks) return;
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;
+    const int N = (m + 15) & ~15;  // MMA columns (<= nmax)
+    const int dm = ceil_log2_dev(m);
+    uint32_t tcols = 32;
+    while ((int)tcols < N) tcols <<= 1;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const LvLayout ly(nmax);
+    const uint32_t kA = 128u * 128u;
 
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* done = reinterpret_cast<uint64_t*>(base + kLvStages * kStage);  // MMAs reading a stage are done
-    uint64_t* accf = done + kLvStages;                                          // accumulator complete
-    uint64_t* fin = accf + 1;                                                   // teardown
+    unsigned char* base = smem_align1024(smem_raw);
+    uint64_t* done = reinterpret_cast<uint64_t*>(base + ly.bars);  // MMAs reading a stage are done
+    uint64_t* full = done + kLvStages;                              // a stage's point rows landed
+    uint64_t* accf = full + kLvStages;                              // accumulator complete
+    uint64_t* fin = accf + 1;                                       // teardown
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
-    int32_t* rowpos = reinterpret_cast<int32_t*>(tmem_slot + 4);  // [128] item query positions
-    int32_t* slotpos = rowpos + 128;                              // [NS] slot point positions
-    float* slotnorm = reinterpret_cast<float*>(slotpos + NS);     // [NS]
-    // [128][NS + 1] leaf values per item: the gather stages are idle during the
-    // epilogue (all copies landed, all MMAs of the chunk complete), so the rows
-    // live in their space
+    int32_t* rowpos = reinterpret_cast<int32_t*>(base + ly.rowpos);  // [128] item query positions
+    float* pnorm = reinterpret_cast<float*>(base + ly.pnorm);        // [nmax] point norms
+    int32_t* bnd4 = reinterpret_cast<int32_t*>(base + ly.bnd4);      // [17] depth-4 node starts
+    // [128][nmax + 1] values per item: the stages are idle during the epilogue
+    // (all copies landed, all MMAs of the chunk complete), so the rows live there
     float* vrows = reinterpret_cast<float*>(base);
-    static_assert((size_t)128 * (NS + 1) * 4 <= (size_t)kLvStages * kStage, "leaf rows must fit the stages");
-    constexpr int BS = NS / 16;                                   // slots per block of the block tree
-    // [128][33]: per item, the sums of 16 blocks of slots and their tree (heap
-    // order); inside the idle stages when they have room, else after slotnorm
-    constexpr bool kTreeInStages = (size_t)128 * (NS + 1 + 33) * 4 <= (size_t)kLvStages * kStage;
-    float* btree = kTreeInStages ? vrows + (size_t)128 * (NS + 1) : slotnorm + NS;
+    const int vstride = nmax + 1;
+    float* btree = reinterpret_cast<float*>(base + ly.btree);  // [128][33] depth-4 node sums and their tree
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;
-    const int dm = ceil_log2_dev(m), leaf0 = 1 << dm;
     const int kchunks = dpad / 64;
     if (tid == 0) {
-        for (int s = 0; s < kLvStages; ++s) mbar_init(&done[s], 1);
+        for (int s = 0; s < kLvStages; ++s) {
+            mbar_init(&done[s], 1);
+            mbar_init(&full[s], 1);
+        }
         mbar_init(accf, 1);
         mbar_init(fin, 1);
         fence_mbar_init();
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)NS)
+                     "r"(tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // slot table of this bin (the same for every chunk)
-    for (int sl = tid; sl < NS; sl += kLvThreads) {
-        int pos = -1;
-        if (sl < leaf0) {
-            int a = 0, c = m;
-            for (int t = dm - 1; t >= 0; --t) {
+    for (int j = tid; j < N; j += kLvThreads) pnorm[j] = j < m ? norms[p_lo + j] : 0.f;
+    if (tid <= 16) {  // start of depth-4 node tid of the bin (tid = 16: the end)
+        int a = 0, c = m;
+        if (tid < 16) {
+            for (int t = 3; t >= 0; --t) {
                 const int mid = a + (c - a) / 2;
-                if ((sl >> t) & 1) a = mid; else c = mid;
+                if ((tid >> t) & 1) a = mid; else c = mid;
             }
-            if (c - a == 1) pos = p_lo + a;
+        } else {
+            a = m;
         }
-        slotpos[sl] = pos;
-        slotnorm[sl] = pos >= 0 ? norms[pos] : 0.f;
+        bnd4[tid] = a;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    int g = 0;          // stage uses issued so far (stage g % kLvStages, its use number g / kLvStages)
-    int tiles = 0;      // accumulator tiles completed
+    int g = 0;      // stage uses issued so far (stage g % kLvStages, its use number g / kLvStages)
+    int tiles = 0;  // accumulator tiles completed
     bool mma_issued = false;
     bool ok = true;
-    // Gathers K chunk kc (64 coordinates) of the 128 item rows and NS slot rows
-    // into stage s, in the 128-byte-swizzled K-major layout; empty rows are 0.
+    int nfill = 0, ncons = 0;  // thread 0: stage uses whose TMA was issued / whose arrival was seen
+    // This thread's 16-byte pieces of the item rows: rows tid / 8 + 16 i
+    // (i < 8), piece tid % 8 of each 128-byte row, at the 128-byte-swizzled
+    // position (the row's phase within its 8-row group is the same for all i).
+    const uint32_t gdst = (uint32_t)(tid >> 3) * 128u + (uint32_t)(((tid & 7) ^ ((tid >> 3) & 7)) << 4);
+    const __nv_bfloat16* gsrc[8];
+    uint32_t gbytes = 0;  // bit i: row i holds an item
+    // K chunk kc (64 coordinates) into stage s: the 128 item rows by cp.async
+    // (empty rows are 0), the point rows by TMA (one thread)
     auto fill = [&](int kc, int s) {
-        unsigned char* st = base + s * kStage;
-        for (int e = tid; e < (128 + NS) * 8; e += kLvThreads) {
-            const int r = e >> 3, c = e & 7;
-            const bool is_a = r < 128;
-            const int rr = is_a ? r : r - 128;
-            const int pos = is_a ? rowpos[rr] : slotpos[rr];
-            unsigned char* dst = st + (is_a ? 0u : kA) + (uint32_t)rr * 128u + (uint32_t)((c ^ (rr & 7)) << 4);
-            const __nv_bfloat16* src = Xb + (size_t)(pos >= 0 ? pos : 0) * dpad + kc * 64 + c * 8;
-            cp_async16(dst, src, pos >= 0 ? 16 : 0);
-        }
+        unsigned char* st = base + s * ly.stage;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            cp_async16(st + gdst + i * 2048, gsrc[i] + kc * 64, ((gbytes >> i) & 1u) ? 16 : 0);
         asm volatile("cp.async.commit_group;" ::: "memory");
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&full[s], (uint32_t)N * 128u);
+            for (int j = 0; j < N; j += kLvBox)
+                tma_load_2d(st + kA + (uint32_t)j * 128u, &tmP, kc * 64, p_lo + j, &full[s]);
+            ++nfill;
+        }
     };
     // waits until the MMAs of stage use g2 - kLvStages are done
     auto stage_free = [&](int g2) -> bool {
@@ -600,16 +622,23 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
         const int qcnt = min(128, cnt - it0);
         rowpos[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
         __syncthreads();
+        gbytes = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int pos = rowpos[(tid >> 3) + 16 * i];
+            gsrc[i] = Xb + (size_t)(pos >= 0 ? pos : 0) * dpad + (tid & 7) * 8;
+            gbytes |= (pos >= 0 ? 1u : 0u) << i;
+        }
         const int pre = min(kLvStages - 1, kchunks);
         for (int kc = 0; kc < pre; ++kc) {
-            ok = ok && stage_free(g + kc);
-            fill(kc, (g + kc) % kLvStages);
+            if (ok) ok = stage_free(g + kc);
+            if (ok) fill(kc, (g + kc) % kLvStages);
         }
         for (int kc = 0; kc < kchunks; ++kc) {
-            const int s = (g + kc) % kLvStages;
+            const int gs = g + kc, s = gs % kLvStages;
             if (kc + pre < kchunks) {
-                ok = ok && stage_free(g + kc + pre);
-                fill(kc + pre, (g + kc + pre) % kLvStages);
+                if (ok) ok = stage_free(g + kc + pre);
+                if (ok) fill(kc + pre, (g + kc + pre) % kLvStages);
                 asm volatile("cp.async.wait_group %0;" ::"n"(kLvStages - 1) : "memory");
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -617,24 +646,28 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (__syncthreads_or(!ok)) { ok = false; break; }
             if (tid == 0) {
-                tc_fence_after();
-                const uint32_t sa = smem_u32(base + s * kStage);
-                const uint64_t da = sdesc(sa), db = sdesc(sa + kA);
+                ok = mbar_wait_bounded(&full[s], (uint32_t)(gs / kLvStages) & 1u, status);
+                if (ok) {
+                    ++ncons;
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(base + s * ly.stage);
+                    const uint64_t da = sdesc(sa), db = sdesc(sa + kA);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(da + (uint64_t)(2 * k)), "l"(db + (uint64_t)(2 * k)), "r"(kIdescLv),
-                        "r"((kc | k) != 0 ? 1u : 0u)
-                        : "memory");
+                    for (int k = 0; k < 4; ++k) {
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                            "l"(da + (uint64_t)(2 * k)), "l"(db + (uint64_t)(2 * k)), "r"(idesc),
+                            "r"((kc | k) != 0 ? 1u : 0u)
+                            : "memory");
+                    }
+                    mma_issued = true;
+                    umma_commit(&done[s]);
+                    if (kc == kchunks - 1) umma_commit(accf);
                 }
-                mma_issued = true;
-                umma_commit(&done[s]);
-                if (kc == kchunks - 1) umma_commit(accf);
             }
         }
-        if (!ok) break;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
         g += kchunks;
         // epilogue: thread = item row = TMEM lane (warp w reads lanes 32 w .. 32 w + 31)
         ok = mbar_wait_bounded(accf, (uint32_t)tiles & 1u, status);
@@ -644,28 +677,36 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
         const int r = tid;
         const int qp = rowpos[r];
         const float nq = qp >= 0 ? norms[qp] : 0.f;
-        float* vr = vrows + (size_t)r * (NS + 1);
+        float* vr = vrows + (size_t)r * vstride;
+        // columns past m (up to N, zero or another bin's rows) land in the
+        // row's padding (stride nmax + 1 >= N) and are never read
 #pragma unroll 1
-        for (int c0 = 0; c0 < NS; c0 += 32) {
+        for (int c0 = 0; c0 < N; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            if (c0 + 32 <= N) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int sl = c0 + j;
-                const int pp = slotpos[sl];
-                float k = 0.f;
-                if (pp >= 0 && !(self_exclude && pp == qp)) {
-                    const float arg = fmaf(-2.f, v[j], nq + slotnorm[sl]);
-                    k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                for (int j = 0; j < 32; ++j) {
+                    const float arg = fmaf(-2.f, v[j], nq + pnorm[c0 + j]);
+                    vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
                 }
-                vr[sl] = k;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {  // N - c0 = 16
+                    const float arg = fmaf(-2.f, v[j], nq + pnorm[c0 + j]);
+                    vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                }
             }
         }
-        // the remaining levels of this item's samples (thread = item): first the
-        // item's tree over 16 blocks of NS / 16 slots (node = left + right)
+        if (self_exclude && qp >= p_lo && qp < p_lo + m) vr[qp - p_lo] = 0.f;  // the query itself
+        // the remaining levels of this item's samples (thread = item): the
+        // sums of the 16 depth-4 nodes and their tree (node = left + right)
         float* bt = btree + (size_t)r * 33;  // odd stride: the lanes' rows hit distinct banks
-#pragma unroll
-        for (int k = 0; k < 16; ++k) bt[16 + k] = range_sum(vr, k * BS, BS);
+        for (int k = 0; k < 16; ++k) {
+            float acc = 0.f;
+            for (int j = bnd4[k]; j < bnd4[k + 1]; ++j) acc += vr[j];
+            bt[16 + k] = acc;
+        }
 #pragma unroll
         for (int h = 15; h >= 1; --h) bt[h] = bt[2 * h] + bt[2 * h + 1];
         if (r < qcnt) {
@@ -673,22 +714,23 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
             const uint32_t qi = (uint32_t)perm[qp];
             for (uint64_t mk = mask; mk; mk &= mk - 1ull) {
                 const int l = __ffsll((long long)mk) - 1;
-                int a = 0, c = m, lo = 0, span = leaf0;
+                int a = 0, c = m, h = 1;
                 uint8_t f = 0;
                 uint4 blk = make_uint4(0, 0, 0, 0);
                 int blk_id = -1;
                 for (int t = 0; t < dm; ++t) {
-                    const int half = span >> 1;
                     int right = 1;  // a single point sits in the right half
                     if (c - a >= 2) {
+                        const int mid = a + (c - a) / 2;
                         float gl, gr;
-                        if (half >= BS) {  // both halves are nodes of the block tree
-                            const int hb = (16 + lo / BS) / (half / BS);
-                            gl = bt[hb];
-                            gr = bt[hb + 1];
+                        if (t < 4) {  // both halves are nodes of the depth-4 tree
+                            gl = bt[2 * h];
+                            gr = bt[2 * h + 1];
                         } else {
-                            gl = range_sum(vr, lo, half);
-                            gr = range_sum(vr, lo + half, half);
+                            gl = 0.f;
+                            gr = 0.f;
+                            for (int j = a; j < mid; ++j) gl += vr[j];
+                            for (int j = mid; j < c; ++j) gr += vr[j];
                         }
                         const uint32_t lev = (uint32_t)(s0 + t);
                         if ((int)(lev >> 2) != blk_id) {
@@ -696,20 +738,18 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
                             blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
                         }
                         right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
-                        const int mid = a + (c - a) / 2;
                         if (right) a = mid; else c = mid;
                     }
-                    if (right) lo += half;
-                    span = half;
+                    h = 2 * h + right;
                 }
                 const size_t o = (size_t)qp * kp.L + l;
                 leaf_pos[o] = p_lo + a;
-                ksmp[o] = vr[lo];
+                ksmp[o] = vr[a];
                 lflags[o] = f;
             }
         }
         tc_fence_before();
-        __syncthreads();  // TMEM and rowpos are reused by the next chunk
+        __syncthreads();  // TMEM, the stages and rowpos are reused by the next chunk
     }
     if (tid == 0 && ok && (int)blockIdx.y < nchunks) {
         unsigned long long its = 0;
@@ -717,31 +757,35 @@ leaf_values_tc_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restr
         atomicAdd(n_items, its);
         atomicAdd(n_evals, its * (unsigned long long)m);
     }
-    // teardown: own copies landed, own MMAs complete, then free TMEM
+    // teardown: own copies landed (cp.async and TMA), own MMAs complete, then free TMEM
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (tid == 0 && mma_issued) {
-        umma_commit(fin);
-        mbar_wait_bounded(fin, 0u, status);
+    if (tid == 0) {
+        // point rows still in flight (an aborted chunk): let them land
+        for (int gs = ncons; gs < nfill; ++gs)
+            mbar_wait_bounded(&full[gs % kLvStages], (uint32_t)(gs / kLvStages) & 1u, status);
+        if (mma_issued) {
+            umma_commit(fin);
+            mbar_wait_bounded(fin, 0u, status);
+        }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NS)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
     }
 }
 
-template <int NS>
-cudaError_t launch_lv_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    constexpr uint32_t kStage = 128 * 128 + NS * 128;
-    constexpr bool kTreeInStages = (size_t)128 * (NS + 1 + 33) * 4 <= (size_t)kLvStages * kStage;
-    const size_t smem = 1024 + (size_t)kLvStages * kStage + 8 * (kLvStages + 2) + 16 + 4 * 128 + 8 * NS +
-                        (kTreeInStages ? 0 : (size_t)128 * 33 * 4);
+}  // namespace
+
+cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const int nmax = (t->mmax + 15) & ~15;  // point rows of the largest bin, rounded to the TMA box
+    if (nmax > 256) return cudaErrorInvalidValue;
+    const size_t smem = 1024 + LvLayout(nmax).total;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_values_tc_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(leaf_values_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -754,21 +798,12 @@ cudaError_t launch_lv_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
-    leaf_values_tc_kernel<NS><<<grid, kLvThreads, smem, s>>>(
-        reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms, t->dpad, t->bnd, ws.bin_off, ws.items_q,
-        ws.items_mask, t->perm, kp, kp.neg_c / (255.f * 255.f), t->s0, ws.leaf_pos, ws.ksmp, ws.lflags,
-        reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+    leaf_values_tc_kernel<<<grid, kLvThreads, smem, s>>>(
+        *reinterpret_cast<const CUtensorMap*>(t->tmap_p), reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms,
+        t->dpad, nmax, t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, kp.neg_c / (255.f * 255.f), t->s0,
+        ws.leaf_pos, ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&ws.stats->n_items), t->status);
     return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    const int leaf0 = 1 << t->dm;
-    if (leaf0 <= 64) return launch_lv_tc<64>(t, kp, s);
-    if (leaf0 <= 128) return launch_lv_tc<128>(t, kp, s);
-    return launch_lv_tc<256>(t, kp, s);
 }
 
 }  // namespace fsg
