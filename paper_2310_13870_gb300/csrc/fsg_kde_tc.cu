@@ -97,70 +97,85 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Two 32-column loads of this warp's TMEM lanes, one wait.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-    uint32_t r[64];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-            : "=r"(r[32 * h + 0]), "=r"(r[32 * h + 1]), "=r"(r[32 * h + 2]), "=r"(r[32 * h + 3]),
-              "=r"(r[32 * h + 4]), "=r"(r[32 * h + 5]), "=r"(r[32 * h + 6]), "=r"(r[32 * h + 7]),
-              "=r"(r[32 * h + 8]), "=r"(r[32 * h + 9]), "=r"(r[32 * h + 10]), "=r"(r[32 * h + 11]),
-              "=r"(r[32 * h + 12]), "=r"(r[32 * h + 13]), "=r"(r[32 * h + 14]), "=r"(r[32 * h + 15]),
-              "=r"(r[32 * h + 16]), "=r"(r[32 * h + 17]), "=r"(r[32 * h + 18]), "=r"(r[32 * h + 19]),
-              "=r"(r[32 * h + 20]), "=r"(r[32 * h + 21]), "=r"(r[32 * h + 22]), "=r"(r[32 * h + 23]),
-              "=r"(r[32 * h + 24]), "=r"(r[32 * h + 25]), "=r"(r[32 * h + 26]), "=r"(r[32 * h + 27]),
-              "=r"(r[32 * h + 28]), "=r"(r[32 * h + 29]), "=r"(r[32 * h + 30]), "=r"(r[32 * h + 31])
-            : "r"(taddr + 32u * h));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j]);
+// Issue a 32-column load of this warp's TMEM lanes (completed by tmem_wait).
+__device__ __forceinline__ void tmem_issue32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+// Wait for this thread's TMEM loads; the registers of the load being waited
+// for are operands, so no use of them can move above the wait.
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
-// Balanced pairwise sum of 64 values (fixed order).
-__device__ __forceinline__ float tree_sum64(float (&x)[64]) {
+// Balanced pairwise sum of 32 values (fixed order: x[j] += x[j + w] for
+// w = 16, 8, 4, 2, 1), the first four levels on FP32x2 pairs.
+__device__ __forceinline__ float tree_sum32(float (&x)[32]) {
+    uint64_t p[16];
 #pragma unroll
-    for (int w = 32; w >= 1; w >>= 1) {
+    for (int j = 0; j < 16; ++j) p[j] = f2_pack(x[2 * j], x[2 * j + 1]);
 #pragma unroll
-        for (int j = 0; j < w; ++j) x[j] += x[j + w];
+    for (int w = 8; w >= 1; w >>= 1) {
+#pragma unroll
+        for (int j = 0; j < w; ++j) p[j] = f2_add(p[j], p[j + w]);
     }
-    return x[0];
+    const float2 t = f2_unpack(p[0]);
+    return t.x + t.y;
 }
 
-// Kernel values of 64 columns of one row, added to the row's bin sums.  Bins
-// hold more than 64 points, so at most one bin ends inside the 64 columns
+// Kernel values of 32 columns of one row, added to the row's bin sums.  Bins
+// hold more than 32 points, so at most one bin ends inside the 32 columns
 // (at a column that is the same for every row of the warp).
 // CHECK: test for the ragged end (p >= pe) and the query's own position.
 template <bool CHECK>
-__device__ __forceinline__ void tc_row_chunk(float (&v)[64], const float* __restrict__ pn, int pc, float nq,
+__device__ __forceinline__ void tc_row_chunk(const uint32_t (&r)[32], const float* __restrict__ pn, int pc, float nq,
                                              float neg_c, int q, int pe, int self_exclude, float& acc, int& bin,
                                              int& next_b, const int32_t* __restrict__ bnd_s, int nbc,
                                              float* __restrict__ orow) {
+    float v[32];
+    const uint64_t nq2 = f2_pack(nq, nq), m2 = f2_pack(-2.f, -2.f), nc2 = f2_pack(neg_c, neg_c);
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
+    for (int j = 0; j < 32; j += 2) {
         // integer units: exact while the sums stay below 2^24
-        const float arg = fmaf(-2.f, v[j], nq + pn[j]);
-        float k = ex2_approx(fmaxf(arg, 0.f) * neg_c);
-        if (CHECK && (pc + j >= pe || (self_exclude && pc + j == q))) k = 0.f;
-        v[j] = k;
+        const uint64_t arg = f2_fma(m2, f2_pack(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                                    f2_add(nq2, f2_pack(pn[j], pn[j + 1])));
+        const float2 a = f2_unpack(arg);
+        const float2 e = f2_unpack(f2_mul(f2_pack(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)), nc2));
+        float k0 = ex2_approx(e.x), k1 = ex2_approx(e.y);
+        if (CHECK) {
+            if (pc + j >= pe || (self_exclude && pc + j == q)) k0 = 0.f;
+            if (pc + j + 1 >= pe || (self_exclude && pc + j + 1 == q)) k1 = 0.f;
+        }
+        v[j] = k0;
+        v[j + 1] = k1;
     }
     const int jb = next_b - 1 - pc;  // the current bin ends after column jb
-    if (jb >= 0 && jb < 64) {
-        float hi[64];
+    if (jb >= 0 && jb < 32) {
+        float hi[32];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
+        for (int j = 0; j < 32; ++j) {
             hi[j] = j > jb ? v[j] : 0.f;
             v[j] = j > jb ? 0.f : v[j];
         }
-        orow[bin] += acc + tree_sum64(v);
-        acc = tree_sum64(hi);
+        orow[bin] += acc + tree_sum32(v);
+        acc = tree_sum32(hi);
         ++bin;
         next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
     } else {
-        acc += tree_sum64(v);
+        acc += tree_sum32(v);
     }
 }
 
@@ -282,6 +297,17 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         float* orow = outs + (half * kTcM + r) * bpc;  // partial sums of this column part
         int bin = 0;
         int next_b = nbc > 0 ? bnd_s[1] : INT_MAX;
+        // point norms of this warp's columns, one tile ahead
+        float nn[kCols / 32];
+        auto load_norms = [&](int tile) {
+            const int c = pa + tile * kTcN + half * kCols;
+#pragma unroll
+            for (int i = 0; i < kCols / 32; ++i) {
+                const int p = c + 32 * i + lane;
+                nn[i] = p < pe ? norms[p] : 0.f;
+            }
+        };
+        load_norms(0);
         for (int tile = 0; tile < ntile; ++tile) {
             const int a = tile & 1;
             if (*abort_flag || !mbar_wait_bounded(&tfull[a], (uint32_t)(tile >> 1) & 1u, status)) {
@@ -292,11 +318,9 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             const int c0 = pa + tile * kTcN + half * kCols;  // first point of this warp's columns
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < kCols / 32; ++i) {
-                const int p = c0 + 32 * i + lane;
-                pn[32 * i + lane] = p < pe ? norms[p] : 0.f;
-            }
+            for (int i = 0; i < kCols / 32; ++i) pn[32 * i + lane] = nn[i];
             __syncwarp();
+            if (tile + 1 < ntile) load_norms(tile + 1);
             while (next_b <= c0) {  // bins that ended in the other half
                 ++bin;
                 next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
@@ -304,15 +328,19 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             const bool check = c0 + kCols > pe || (self_exclude && c0 < q0 + kTcM && q0 < c0 + kCols);
             float acc = 0.f;
             const uint32_t tcol = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * kTcN + half * kCols);
-#pragma unroll 1
-            for (int cc = 0; cc < kCols; cc += 64) {
-                float v[64];
-                tmem_ld64(tcol + (uint32_t)cc, v);
+            // 32 columns per step, the next step's TMEM load in flight
+            uint32_t rb[2][32];
+            tmem_issue32(tcol, rb[0]);
+#pragma unroll
+            for (int cc = 0; cc < kCols; cc += 32) {
+                const int cur = (cc >> 5) & 1;
+                tmem_wait32(rb[cur]);  // the only load in flight
+                if (cc + 32 < kCols) tmem_issue32(tcol + (uint32_t)(cc + 32), rb[cur ^ 1]);
                 if (check)
-                    tc_row_chunk<true>(v, pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b, bnd_s,
-                                       nbc, orow);
+                    tc_row_chunk<true>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
+                                       bnd_s, nbc, orow);
                 else
-                    tc_row_chunk<false>(v, pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
+                    tc_row_chunk<false>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
                                         bnd_s, nbc, orow);
             }
             if (bin < nbc) orow[bin] += acc;  // the bin that continues past this half
