@@ -512,7 +512,7 @@ namespace fsg {
 namespace {
 
 constexpr int kLvStages = 3;
-constexpr int kLvThreads = 128;
+constexpr int kLvThreads = 256;  // two threads per item row (TMEM lane): warps w and w + 4
 constexpr int kLvBox = 16;  // point rows per TMA box
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
@@ -523,14 +523,16 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
 // Shared-memory layout of the leaf kernel for point operands of up to nmax
 // rows (nmax a multiple of 16); the same arithmetic on host and device.
 struct LvLayout {
-    uint32_t kB, stage, bars, rowpos, pnorm, bnd4, btree, total;
+    uint32_t kB, stage, bars, rowpos, qmask, prefix, pnorm, bnd4, btree, total;
     bool tree_in_stages;
     __host__ __device__ explicit LvLayout(int nmax) {
         kB = (uint32_t)nmax * 128u;
         stage = 128u * 128u + kB;
         bars = kLvStages * stage;                        // done[3], full[3], accf, fin
         rowpos = bars + 8 * (2 * kLvStages + 2) + 16;    // + TMEM slot
-        pnorm = rowpos + 128 * 4;
+        qmask = rowpos + 128 * 4;                        // [128] sample masks of the chunk's items
+        prefix = qmask + 128 * 8;                        // [129] samples before each item (+ 3 words)
+        pnorm = prefix + 132 * 4;
         bnd4 = pnorm + (uint32_t)nmax * 4;
         const uint32_t after = bnd4 + 17 * 4 + 12;
         tree_in_stages = (size_t)128 * (nmax + 1 + 33) * 4 <= (size_t)kLvStages * stage;
@@ -571,6 +573,8 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     uint64_t* fin = accf + 1;                                       // teardown
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     int32_t* rowpos = reinterpret_cast<int32_t*>(base + ly.rowpos);  // [128] item query positions
+    uint64_t* qmask = reinterpret_cast<uint64_t*>(base + ly.qmask);  // [128] item sample masks
+    int32_t* prefix = reinterpret_cast<int32_t*>(base + ly.prefix);  // [129] samples before item r
     float* pnorm = reinterpret_cast<float*>(base + ly.pnorm);        // [nmax] point norms
     int32_t* bnd4 = reinterpret_cast<int32_t*>(base + ly.bnd4);      // [17] depth-4 node starts
     // [128][nmax + 1] values per item: the stages are idle during the epilogue
@@ -618,19 +622,19 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     bool mma_issued = false;
     bool ok = true;
     int nfill = 0, ncons = 0;  // thread 0: stage uses whose TMA was issued / whose arrival was seen
-    // This thread's 16-byte pieces of the item rows: rows tid / 8 + 16 i
-    // (i < 8), piece tid % 8 of each 128-byte row, at the 128-byte-swizzled
+    // This thread's 16-byte pieces of the item rows: rows tid / 8 + 32 i
+    // (i < 4), piece tid % 8 of each 128-byte row, at the 128-byte-swizzled
     // position (the row's phase within its 8-row group is the same for all i).
     const uint32_t gdst = (uint32_t)(tid >> 3) * 128u + (uint32_t)(((tid & 7) ^ ((tid >> 3) & 7)) << 4);
-    const __nv_bfloat16* gsrc[8];
+    const __nv_bfloat16* gsrc[4];
     uint32_t gbytes = 0;  // bit i: row i holds an item
     // K chunk kc (64 coordinates) into stage s: the 128 item rows by cp.async
     // (empty rows are 0), the point rows by TMA (one thread)
     auto fill = [&](int kc, int s) {
         unsigned char* st = base + s * ly.stage;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            cp_async16(st + gdst + i * 2048, gsrc[i] + kc * 64, ((gbytes >> i) & 1u) ? 16 : 0);
+        for (int i = 0; i < 4; ++i)
+            cp_async16(st + gdst + i * 4096, gsrc[i] + kc * 64, ((gbytes >> i) & 1u) ? 16 : 0);
         asm volatile("cp.async.commit_group;" ::: "memory");
         if (tid == 0) {
             mbar_arrive_expect_tx(&full[s], (uint32_t)N * 128u);
@@ -648,12 +652,15 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
         const int it0 = chunk * 128;
         const int qcnt = min(128, cnt - it0);
-        rowpos[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
+        if (tid < 128) {
+            rowpos[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
+            qmask[tid] = tid < qcnt ? items_mask[seg + it0 + tid] : 0ull;
+        }
         __syncthreads();
         gbytes = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int pos = rowpos[(tid >> 3) + 16 * i];
+        for (int i = 0; i < 4; ++i) {
+            const int pos = rowpos[(tid >> 3) + 32 * i];
             gsrc[i] = Xb + (size_t)(pos >= 0 ? pos : 0) * dpad + (tid & 7) * 8;
             gbytes |= (pos >= 0 ? 1u : 0u) << i;
         }
@@ -697,21 +704,24 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
         }
         if (__syncthreads_or(!ok)) { ok = false; break; }
         g += kchunks;
-        // epilogue: thread = item row = TMEM lane (warp w reads lanes 32 w .. 32 w + 31)
+        // epilogue: item row r = TMEM lane (warps w and w + 4 read lanes
+        // 32 (w % 4) .. + 31), half hh of the thread pair takes the 32-column
+        // steps hh, hh + 2, ...
         ok = mbar_wait_bounded(accf, (uint32_t)tiles & 1u, status);
         ++tiles;
         if (__syncthreads_or(!ok)) { ok = false; break; }
         tc_fence_after();
-        const int r = tid;
+        const int r = tid & 127, hh = tid >> 7;
         const int qp = rowpos[r];
         const float nq = qp >= 0 ? norms[qp] : 0.f;
         float* vr = vrows + (size_t)r * vstride;
+        const int sc = (self_exclude && qp >= p_lo && qp < p_lo + m) ? qp - p_lo : -1;  // the query itself
         // columns past m (up to N, zero or another bin's rows) land in the
         // row's padding (stride nmax + 1 >= N) and are never read
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += 32) {
+        for (int c0 = 32 * hh; c0 < N; c0 += 64) {
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
             if (c0 + 32 <= N) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -725,56 +735,88 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
                     vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
                 }
             }
+            if (sc >= c0 && sc < c0 + 32) vr[sc] = 0.f;
         }
-        if (self_exclude && qp >= p_lo && qp < p_lo + m) vr[qp - p_lo] = 0.f;  // the query itself
-        // the remaining levels of this item's samples (thread = item): the
-        // sums of the 16 depth-4 nodes and their tree (node = left + right)
+        // samples of the chunk's items: prefix[r] = samples of items < r
+        if (tid < 128) {
+            const int c = __popcll(qmask[tid]);
+            int x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((tid & 31) >= o) x += y;
+            }
+            prefix[tid + 1] = x;  // inclusive within the warp
+        }
+        __syncthreads();
+        // the 16 depth-4 node sums of row r: half hh sums nodes 8 hh .. 8 hh + 7
         float* bt = btree + (size_t)r * 33;  // odd stride: the lanes' rows hit distinct banks
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 8 * hh; k < 8 * hh + 8; ++k) {
             float acc = 0.f;
             for (int j = bnd4[k]; j < bnd4[k + 1]; ++j) acc += vr[j];
             bt[16 + k] = acc;
         }
-#pragma unroll
-        for (int h = 15; h >= 1; --h) bt[h] = bt[2 * h] + bt[2 * h + 1];
-        if (r < qcnt) {
-            const uint64_t mask = items_mask[seg + it0 + r];
-            const uint32_t qi = (uint32_t)perm[qp];
-            for (uint64_t mk = mask; mk; mk &= mk - 1ull) {
-                const int l = __ffsll((long long)mk) - 1;
-                int a = 0, c = m, h = 1;
-                uint8_t f = 0;
-                uint4 blk = make_uint4(0, 0, 0, 0);
-                int blk_id = -1;
-                for (int t = 0; t < dm; ++t) {
-                    int right = 1;  // a single point sits in the right half
-                    if (c - a >= 2) {
-                        const int mid = a + (c - a) / 2;
-                        float gl, gr;
-                        if (t < 4) {  // both halves are nodes of the depth-4 tree
-                            gl = bt[2 * h];
-                            gr = bt[2 * h + 1];
-                        } else {
-                            gl = 0.f;
-                            gr = 0.f;
-                            for (int j = a; j < mid; ++j) gl += vr[j];
-                            for (int j = mid; j < c; ++j) gr += vr[j];
-                        }
-                        const uint32_t lev = (uint32_t)(s0 + t);
-                        if ((int)(lev >> 2) != blk_id) {
-                            blk_id = (int)(lev >> 2);
-                            blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
-                        }
-                        right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
-                        if (right) a = mid; else c = mid;
-                    }
-                    h = 2 * h + right;
-                }
-                const size_t o = (size_t)qp * kp.L + l;
-                leaf_pos[o] = p_lo + a;
-                ksmp[o] = vr[a];
-                lflags[o] = f;
+        if (tid == 0) {  // warp totals into the prefix
+            prefix[0] = 0;
+            for (int w2 = 1; w2 < 4; ++w2) {
+                const int add = prefix[32 * w2];
+                for (int i = 32 * w2 + 1; i <= 32 * w2 + 32; ++i) prefix[i] += add;
             }
+        }
+        __syncthreads();
+        if (hh == 0) {
+#pragma unroll
+            for (int h = 15; h >= 1; --h) bt[h] = bt[2 * h] + bt[2 * h + 1];
+        }
+        __syncthreads();
+        // descents: the chunk's samples spread over all threads
+        const int total = prefix[128];
+        for (int gsm = tid; gsm < total; gsm += kLvThreads) {
+            int lo = 0, hi = 128;  // item: prefix[lo] <= gsm < prefix[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (prefix[mid] <= gsm) lo = mid; else hi = mid;
+            }
+            const int it = lo;
+            uint64_t mk = qmask[it];
+            for (int k = gsm - prefix[it]; k > 0; --k) mk &= mk - 1ull;
+            const int l = __ffsll((long long)mk) - 1;
+            const int ip = rowpos[it];
+            const uint32_t qi = (uint32_t)perm[ip];
+            const float* vi = vrows + (size_t)it * vstride;
+            const float* bi = btree + (size_t)it * 33;
+            int a = 0, c = m, h = 1;
+            uint8_t f = 0;
+            uint4 blk = make_uint4(0, 0, 0, 0);
+            int blk_id = -1;
+            for (int t = 0; t < dm; ++t) {
+                int right = 1;  // a single point sits in the right half
+                if (c - a >= 2) {
+                    const int mid = a + (c - a) / 2;
+                    float gl, gr;
+                    if (t < 4) {  // both halves are nodes of the depth-4 tree
+                        gl = bi[2 * h];
+                        gr = bi[2 * h + 1];
+                    } else {
+                        gl = 0.f;
+                        gr = 0.f;
+                        for (int j = a; j < mid; ++j) gl += vi[j];
+                        for (int j = mid; j < c; ++j) gr += vi[j];
+                    }
+                    const uint32_t lev = (uint32_t)(s0 + t);
+                    if ((int)(lev >> 2) != blk_id) {
+                        blk_id = (int)(lev >> 2);
+                        blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
+                    }
+                    right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
+                    if (right) a = mid; else c = mid;
+                }
+                h = 2 * h + right;
+            }
+            const size_t o = (size_t)ip * kp.L + l;
+            leaf_pos[o] = p_lo + a;
+            ksmp[o] = vi[a];
+            lflags[o] = f;
         }
         tc_fence_before();
         __syncthreads();  // TMEM, the stages and rowpos are reused by the next chunk
