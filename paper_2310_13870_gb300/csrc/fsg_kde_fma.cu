@@ -278,6 +278,12 @@ template <int D>
 struct SymBatch {
     static constexpr int B = D <= 9 ? 16 : 8;
 };
+// CTAs per SM the register budget is cut for: three (80 registers) where that
+// costs at most a few spilled words, two (128 registers) elsewhere.
+template <int D>
+struct SymOccupancy {
+    static constexpr int value = (D <= 8 || D == 10) ? 3 : 2;
+};
 
 // Kernel values of one point against the lane's four queries; adds them to
 // the row accumulators and returns their sum.
@@ -434,7 +440,7 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
 }
 
 template <int D>
-__global__ void __launch_bounds__(kSymThreads, 2)
+__global__ void __launch_bounds__(kSymThreads, SymOccupancy<D>::value)
 kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, const int32_t* __restrict__ bnd,
                     int nb, int G, float neg_c, int self_exclude, float* __restrict__ binsum,
                     int32_t* __restrict__ status) {
