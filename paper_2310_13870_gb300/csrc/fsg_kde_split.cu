@@ -1,0 +1,336 @@
+// Split-precision tensor-core bin pass (FSG_PREC_SPLIT_BF16) for FP32 data,
+// 17 <= d <= 64: the bin sums of Eq. 1 for every query, like the other bin
+// passes, with the dot products on the tensor cores.
+//
+// CTA = one tile of 128 queries (128 consecutive tree positions) x one chunk
+// of bins.  Both operands are centred at the query tile's centre c (the mean
+// of its points): a = x - c, b = y - c.  Under a spatial tree order
+// (fsg_spatial_order) a tile is a compact group, the centred norms are small
+// next to the data's spread, and ||x - y||^2 = ||a||^2 + ||b||^2 - 2 a.b loses
+// little to cancellation.  Each centred FP32 coordinate is split into three
+// BF16 parts, v = hi + mid + lo, each part the BF16 rounding of what the
+// previous ones leave (the residuals are exact in FP32; the three parts hold
+// 24 significand bits), and a.b is accumulated in FP32 in TMEM as six
+// products per coordinate,
+//   lo.hi + hi.lo + mid.mid + mid.hi + hi.mid + hi.hi
+// (small terms first; mid.lo, lo.mid and lo.lo lie below 2^-24 relative).
+// Every BF16 x BF16 product is exact in FP32.
+//
+// Warp roles (13 warps):
+//   warps 0-3 : producers: the query parts and norms (once), then per tile of
+//               128 points the centred, split point parts and their norms,
+//               two stages (shared-memory stores, a proxy fence, an mbarrier
+//               arrive per thread);
+//   warp 4    : TMEM allocation; one thread issues the 24 tcgen05.mma (K = 16)
+//               of a tile into one of two 128-column accumulators;
+//   warps 5-12: epilogue, two per TMEM lane quadrant (one per half of the 128
+//               columns): kernel values and bin sums, as in the 8-bit pass.
+// Every mbarrier wait is bounded; on a timeout the CTA records
+// FSG_ERR_TIMEOUT, stops, waits (bounded) for its own MMAs and frees TMEM.
+#include <cuda_bf16.h>
+
+#include "fsg_tc.cuh"
+
+namespace fsg {
+namespace {
+
+constexpr int kSpM = 128;             // queries per tile
+constexpr int kSpN = 128;             // points per tile
+constexpr int kSpDim = 64;            // coordinates (d <= 64, zero-padded)
+constexpr int kSpStages = 2;
+constexpr int kSpParts = 3;           // hi, mid, lo
+constexpr int kSpEpiWarps = 8;
+constexpr int kSpThreads = 32 * (5 + kSpEpiWarps);
+constexpr int kSpMaxBins = 24;        // bins per chunk
+constexpr uint32_t kPart = 128u * 128u;  // one part of 128 rows x 64 BF16 (128-byte swizzled rows)
+constexpr uint32_t kTmemCols = 256;   // two 128-column accumulators
+
+struct SpLayout {
+    static constexpr uint32_t A = 0;                                      // [3][128 rows]
+    static constexpr uint32_t B = A + kSpParts * kPart;                   // [2 stages][3][128 rows]
+    static constexpr uint32_t CN = B + kSpStages * kSpParts * kPart;      // [2][128] point norms
+    static constexpr uint32_t AN = CN + kSpStages * kSpN * 4;             // [128] query norms
+    static constexpr uint32_t CEN = AN + kSpM * 4;                        // [64] centre
+    static constexpr uint32_t BARS = CEN + kSpDim * 4;                    // full[2] empty[2] tfull[2] tempty[2] fin
+    static constexpr uint32_t SLOT = BARS + 9 * 8;                        // TMEM slot, abort flag
+    static constexpr uint32_t BND = SLOT + 16;                            // [kSpMaxBins + 1]
+    static constexpr uint32_t PN = (BND + 112 + 15) & ~15u;               // [8 warps][64] norms of a warp's columns
+    static constexpr uint32_t OUTS = PN + kSpEpiWarps * 64 * 4;           // [2 halves][128][bpc]
+    static constexpr uint32_t total(int bpc) { return OUTS + 2u * kSpM * (uint32_t)bpc * 4u; }
+};
+static_assert(SpLayout::BARS % 8 == 0 && SpLayout::PN % 16 == 0 && SpLayout::B % 1024 == 0, "layout");
+
+// Three BF16 parts of two values, packed (low half = a, high half = b): each
+// part the BF16 rounding of what the previous parts leave (exact residuals).
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& mid, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    const float ra = __fsub_rn(a, __uint_as_float(hi << 16)), rb = __fsub_rn(b, __uint_as_float(hi & 0xffff0000u));
+    const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+    mid = *reinterpret_cast<const uint32_t*>(&m);
+    const float sa = __fsub_rn(ra, __uint_as_float(mid << 16)), sb = __fsub_rn(rb, __uint_as_float(mid & 0xffff0000u));
+    const __nv_bfloat162 l = __floats2bfloat162_rn(sa, sb);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// One operand row's coordinates (tree position p, zeros for p < 0).
+__device__ __forceinline__ void load_row(const float* __restrict__ Xt, int dp, int p, float4 (&x)[kSpDim / 4]) {
+#pragma unroll
+    for (int u = 0; u < kSpDim / 4; ++u)
+        x[u] = (p >= 0 && 4 * u < dp) ? *reinterpret_cast<const float4*>(Xt + (size_t)p * dp + 4 * u)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// The row centred (coordinates past dd are 0), split and stored as three
+// 128-byte swizzled rows at parts + part * kPart; returns its squared norm.
+__device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], int dd, const float* __restrict__ cen,
+                                           unsigned char* parts, int row) {
+    float norm = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {  // 16-byte chunk k = coordinates 8k .. 8k + 7
+        const float v[8] = {x[2 * k].x, x[2 * k].y, x[2 * k].z, x[2 * k].w,
+                            x[2 * k + 1].x, x[2 * k + 1].y, x[2 * k + 1].z, x[2 * k + 1].w};
+        float a[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            a[i] = (8 * k + i < dd) ? __fsub_rn(v[i], cen[8 * k + i]) : 0.f;
+            norm = __fmaf_rn(a[i], a[i], norm);
+        }
+        uint4 hi, mid, lo;
+        split2(a[0], a[1], hi.x, mid.x, lo.x);
+        split2(a[2], a[3], hi.y, mid.y, lo.y);
+        split2(a[4], a[5], hi.z, mid.z, lo.z);
+        split2(a[6], a[7], hi.w, mid.w, lo.w);
+        const uint32_t off = (uint32_t)row * 128u + (uint32_t)((k ^ (row & 7)) << 4);
+        *reinterpret_cast<uint4*>(parts + off) = hi;
+        *reinterpret_cast<uint4*>(parts + kPart + off) = mid;
+        *reinterpret_cast<uint4*>(parts + 2 * kPart + off) = lo;
+    }
+    return norm;
+}
+
+__global__ void __launch_bounds__(kSpThreads, 1)
+kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const int32_t* __restrict__ bnd, int nb,
+                      int bpc, float neg_c, int self_exclude, float* __restrict__ binsum,
+                      int32_t* __restrict__ status) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_align1024(smem_raw);
+    unsigned char* sA = base + SpLayout::A;
+    unsigned char* sB = base + SpLayout::B;
+    float* cn = reinterpret_cast<float*>(base + SpLayout::CN);
+    float* an = reinterpret_cast<float*>(base + SpLayout::AN);
+    float* cen = reinterpret_cast<float*>(base + SpLayout::CEN);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + SpLayout::BARS);
+    uint64_t* empty = full + kSpStages;
+    uint64_t* tfull = empty + kSpStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* fin = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + SpLayout::SLOT);
+    volatile int32_t* abort_flag = reinterpret_cast<int32_t*>(base + SpLayout::SLOT + 4);
+    int32_t* bnd_s = reinterpret_cast<int32_t*>(base + SpLayout::BND);
+    float* pn_all = reinterpret_cast<float*>(base + SpLayout::PN);
+    float* outs = reinterpret_cast<float*>(base + SpLayout::OUTS);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q0 = blockIdx.x * kSpM;
+    const int b0 = blockIdx.y * bpc;
+    const int nbc = min(nb, b0 + bpc) - b0;
+    if (tid <= nbc) bnd_s[tid] = bnd[b0 + tid];
+    for (int e = tid; e < 2 * kSpM * bpc; e += kSpThreads) outs[e] = 0.f;
+    if (tid == 0) {
+        for (int s = 0; s < kSpStages; ++s) {
+            mbar_init(&full[s], 128);                // the producers' arrivals
+            mbar_init(&empty[s], 1 + kSpEpiWarps);   // MMA commit + the epilogue warps (point norms read)
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 32 * kSpEpiWarps);
+        }
+        mbar_init(fin, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // centre of the query tile (its points' mean; any centre is exact, a near one is accurate)
+    if (tid < kSpDim) {
+        const int nq = min(kSpM, n - q0);
+        float c = 0.f;
+        if (tid < d) {
+            for (int r = 0; r < nq; ++r) c += Xt[(size_t)(q0 + r) * dp + tid];
+            c /= (float)nq;
+        }
+        cen[tid] = c;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // the query tile's parts and norms (producers, once)
+    if (tid < kSpM) {
+        const int q = q0 + tid;
+        float4 x[kSpDim / 4];
+        load_row(Xt, dp, q < n ? q : -1, x);
+        an[tid] = split_row(x, q < n ? d : 0, cen, sA, tid);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int pa = bnd_s[0], pe = bnd_s[nbc];
+    const int ntile = (pe - pa + kSpN - 1) / kSpN;
+    int mma_issued = 0;
+
+    if (warp < 4) {
+        // ---- producers: point tile t into stage t % 2; the next tile's row is
+        // loaded while this thread waits for its stage to be free
+        float4 x[kSpDim / 4];
+        int p = pa + tid;
+        load_row(Xt, dp, p < pe ? p : -1, x);
+        for (int t = 0; t < ntile && !*abort_flag; ++t) {
+            const int s = t & 1;
+            if (!mbar_wait_bounded(&empty[s], ((uint32_t)(t >> 1) & 1u) ^ 1u, status)) {
+                *abort_flag = 1;
+                break;
+            }
+            cn[s * kSpN + tid] = split_row(x, p < pe ? d : 0, cen, sB + (uint32_t)s * kSpParts * kPart, tid);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[s]);
+            p += kSpN;
+            if (t + 1 < ntile) load_row(Xt, dp, p < pe ? p : -1, x);
+        }
+    } else if (warp == 4) {
+        if (lane == 0) {
+            // ---- MMA issuer: six products per coordinate, small terms first
+            const int pi[6] = {2, 0, 1, 1, 0, 0};  // A part (0 hi, 1 mid, 2 lo)
+            const int pj[6] = {0, 2, 1, 0, 1, 0};  // B part
+            const uint32_t idesc = idesc_bf16(kSpM, kSpN);
+            for (int t = 0; t < ntile && !*abort_flag; ++t) {
+                const int a = t & 1, s = t & 1;
+                if (!mbar_wait_bounded(&tempty[a], ((uint32_t)(t >> 1) & 1u) ^ 1u, status) ||
+                    !mbar_wait_bounded(&full[s], (uint32_t)(t >> 1) & 1u, status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(a * kSpN);
+#pragma unroll
+                for (int u = 0; u < 6; ++u) {
+                    const uint64_t da = sdesc(smem_u32(sA + pi[u] * kPart));
+                    const uint64_t db = sdesc(smem_u32(sB + (uint32_t)s * kSpParts * kPart + pj[u] * kPart));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)  // 32 bytes of K per MMA inside the swizzled row
+                        umma_bf16(dt, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (u | k) != 0 ? 1u : 0u);
+                }
+                mma_issued = 1;
+                umma_commit(&empty[s]);
+                umma_commit(&tfull[a]);
+            }
+        }
+    } else {
+        // ---- epilogue: TMEM lane quadrant (warp % 4), row = query; column half (warp - 5) / 4
+        constexpr int kCols = kSpN / 2;
+        const int ew = warp - 5;
+        const int quad = warp & 3;
+        const int half = ew >> 2;
+        const int r = 32 * quad + lane;
+        const int q = q0 + r;
+        const float nq = an[r];
+        float* pn = pn_all + ew * kCols;
+        float* orow = outs + (half * kSpM + r) * bpc;  // partial sums of this column half
+        int bin = 0;
+        int next_b = nbc > 0 ? bnd_s[1] : INT_MAX;
+        for (int t = 0; t < ntile; ++t) {
+            const int a = t & 1, s = t & 1;
+            if (*abort_flag || !mbar_wait_bounded(&tfull[a], (uint32_t)(t >> 1) & 1u, status) ||
+                !mbar_wait_bounded(&full[s], (uint32_t)(t >> 1) & 1u, status)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int c0 = pa + t * kSpN + half * kCols;  // first point of this warp's columns
+            __syncwarp();
+            pn[lane] = cn[s * kSpN + half * kCols + lane];
+            pn[lane + 32] = cn[s * kSpN + half * kCols + lane + 32];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // this stage's point norms are read
+            while (next_b <= c0) {  // bins that ended in the other half
+                ++bin;
+                next_b = bin < nbc ? bnd_s[bin + 1] : INT_MAX;
+            }
+            const bool check = c0 + kCols > pe || (self_exclude && c0 < q0 + kSpM && q0 < c0 + kCols);
+            float acc = 0.f;
+            const uint32_t tcol = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * kSpN + half * kCols);
+            uint32_t rb[2][32];
+            tmem_issue32(tcol, rb[0]);
+#pragma unroll
+            for (int cc = 0; cc < kCols; cc += 32) {
+                const int cur = (cc >> 5) & 1;
+                tmem_wait32(rb[cur]);  // the only load in flight
+                if (cc + 32 < kCols) tmem_issue32(tcol + (uint32_t)(cc + 32), rb[cur ^ 1]);
+                if (check)
+                    tc_row_chunk<true>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
+                                       bnd_s, nbc, orow);
+                else
+                    tc_row_chunk<false>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
+                                        bnd_s, nbc, orow);
+            }
+            if (bin < nbc) orow[bin] += acc;  // the bin that continues past this half
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
+        }
+    }
+    __syncthreads();
+    if (!*abort_flag) {
+        const int nq = min(kSpM, n - q0);
+        for (int e = tid; e < nq * nbc; e += kSpThreads) {
+            const int ql = e / nbc, b = e - ql * nbc;
+            binsum[(size_t)(q0 + ql) * nb + b0 + b] = outs[ql * bpc + b] + outs[(kSpM + ql) * bpc + b];
+        }
+    }
+    if (warp == 4) {
+        if (lane == 0 && mma_issued) {
+            // all MMAs of this CTA must be complete before TMEM is freed
+            umma_commit(fin);
+            mbar_wait_bounded(fin, 0u, status);
+        }
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+// d in 17..64; every bin of at least 32 points, so at most one bin ends in the
+// 32 columns of an epilogue step.
+bool kde_bins_split_supported(const fsg_tree* t) {
+    return t->d > kMaxFmaDim && t->d <= kSpDim && t->n / t->nb >= 32;
+}
+
+cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const int qblocks = (int)((t->n + kSpM - 1) / kSpM);
+    int chunks = (4 * 152 + qblocks - 1) / qblocks;
+    if (chunks < 1) chunks = 1;
+    if (chunks > t->nb) chunks = t->nb;
+    int bpc = (t->nb + chunks - 1) / chunks;
+    if (bpc > kSpMaxBins) bpc = kSpMaxBins;
+    chunks = (t->nb + bpc - 1) / bpc;
+    const size_t smem = 1024 + SpLayout::total(bpc);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(kde_bins_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid(qblocks, chunks);
+    kde_bins_split_kernel<<<grid, kSpThreads, smem, s>>>(t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc,
+                                                          kp.neg_c, kp.self_exclude, t->ws.binsum, t->status);
+    return cudaGetLastError();
+}
+
+}  // namespace fsg

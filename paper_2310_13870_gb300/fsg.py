@@ -38,6 +38,7 @@ FSG_ADMIT_ARRIVAL, FSG_ADMIT_RESPONSE_RATIO = 0, 1
 # against include/fsg.h).
 EXPORTED = [
     "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info", "fsg_bin_pass_evals",
+    "fsg_spatial_order",
     "fsg_autotune", "fsg_tree_tuning",
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
@@ -147,6 +148,7 @@ def load(path: str = LIB_PATH):
     lib.fsg_server_info.argtypes = [P, P, P, P]
     lib.fsg_server_destroy.argtypes = [P]
     lib.fsg_server_destroy.restype = None
+    lib.fsg_spatial_order.argtypes = [P, ctypes.c_int64, I32, I32, P]
     for name in EXPORTED:
         if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy", "fsg_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -222,6 +224,15 @@ def fsg_build_tree(points, perm=None, leaf_max: int = 0, stream=None) -> Tree:
     _check(lib.fsg_build_tree(_dptr(points), points.shape[0], points.shape[1], ctypes.byref(opts),
                               _stream_ptr(stream), ctypes.byref(h)), "fsg_build_tree")
     return Tree(h, points.shape[0], points.shape[1])
+
+
+def fsg_spatial_order(points: np.ndarray, leaf: int = 32) -> np.ndarray:
+    """Host spatial tree order (see fsg.h): int32 [n], position -> original index."""
+    X = np.ascontiguousarray(points, dtype=np.float32)
+    n, d = X.shape
+    perm = np.empty(n, np.int32)
+    _check(load().fsg_spatial_order(X.ctypes.data, n, d, leaf, perm.ctypes.data), "fsg_spatial_order")
+    return perm
 
 
 def fsg_tree_update(tree: Tree, points, stream=None):
