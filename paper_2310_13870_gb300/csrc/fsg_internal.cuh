@@ -298,7 +298,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait_sleep(bar, parity, 1u << 20)) return true;
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if ((it & 31u) == 0u && global_ns() - t0 > kWaitLimitNs) {
             atomicExch(status, kStatusTimeout);
             return false;
         }

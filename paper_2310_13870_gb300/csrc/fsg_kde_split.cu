@@ -81,11 +81,23 @@ __device__ __forceinline__ void load_row(const float* __restrict__ Xt, int dp, i
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// The row centred (coordinates past dd are 0), split and stored as three
-// 128-byte swizzled rows at parts + part * kPart; returns its squared norm.
-__device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], int dd, const float* __restrict__ cen,
+// The row centred, split and stored as three 128-byte swizzled rows at
+// parts + part * kPart; returns its squared norm.  A point's coordinates past
+// d are zero, as are the centre's, so they stay zero; `valid` = false (no
+// point) stores zero rows.
+__device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], bool valid, const float* __restrict__ cen,
                                            unsigned char* parts, int row) {
     float norm = 0.f;
+    if (!valid) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t off = (uint32_t)row * 128u + (uint32_t)((k ^ (row & 7)) << 4);
+            *reinterpret_cast<uint4*>(parts + off) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(parts + kPart + off) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(parts + 2 * kPart + off) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        return 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {  // 16-byte chunk k = coordinates 8k .. 8k + 7
         const float v[8] = {x[2 * k].x, x[2 * k].y, x[2 * k].z, x[2 * k].w,
@@ -93,7 +105,7 @@ __device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], int dd
         float a[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            a[i] = (8 * k + i < dd) ? __fsub_rn(v[i], cen[8 * k + i]) : 0.f;
+            a[i] = __fsub_rn(v[i], cen[8 * k + i]);
             norm = __fmaf_rn(a[i], a[i], norm);
         }
         uint4 hi, mid, lo;
@@ -175,7 +187,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
         const int q = q0 + tid;
         float4 x[kSpDim / 4];
         load_row(Xt, dp, q < n ? q : -1, x);
-        an[tid] = split_row(x, q < n ? d : 0, cen, sA, tid);
+        an[tid] = split_row(x, q < n, cen, sA, tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
@@ -196,7 +208,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
                 *abort_flag = 1;
                 break;
             }
-            cn[s * kSpN + tid] = split_row(x, p < pe ? d : 0, cen, sB + (uint32_t)s * kSpParts * kPart, tid);
+            cn[s * kSpN + tid] = split_row(x, p < pe, cen, sB + (uint32_t)s * kSpParts * kPart, tid);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full[s]);
             p += kSpN;
