@@ -90,13 +90,18 @@ cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t
     return launch_kde_bins(t, kp, s);
 }
 
-// The remaining levels of every sample inside its bin.  Tensor-core path: one
-// fused kernel (leaf values and descent); d > 16 otherwise: leaf values, then
-// the leaf finish; d <= 16: the leaf finish evaluates its own values.
+// The remaining levels of every sample inside its bin.  Tensor-core path and
+// d > 16 with bins of <= 128 points: one fused kernel (values and descent);
+// other d > 16 bins: leaf values, then the leaf finish; d <= 16: the leaf
+// finish evaluates its own values.
 cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     if (t->d > kMaxFmaDim && use_tc(t, kp.precision) && (1 << t->dm) <= 256) {
         t->launches += 1;
         return launch_leaf_values_tc(t, kp, s);
+    }
+    if (leaf_fused_generic_supported(t)) {  // d > 16, bins of <= 128 points: values stay on chip
+        t->launches += 1;
+        return launch_leaf_fused_generic(t, kp, s);
     }
     cudaError_t e = cudaSuccess;
     if (t->d > kMaxFmaDim) {

@@ -152,6 +152,8 @@ int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);
 bool kde_bins_split_supported(const fsg_tree* t);
+bool leaf_fused_generic_supported(const fsg_tree* t);
+cudaError_t launch_leaf_fused_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
@@ -307,6 +309,58 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 __device__ __forceinline__ int ceil_log2_dev(int m) {
     return m <= 1 ? 0 : 32 - __clz(m - 1);
+}
+
+// Start of node k (0..15) at depth 4 of a bin of m points, by the halving
+// rule (k = 16: the end).  Shared by the leaf kernels that keep a bin's row
+// of values.
+__device__ __forceinline__ int depth4_start(int k, int m) {
+    if (k >= 16) return m;
+    int a = 0, c = m;
+    for (int t = 3; t >= 0; --t) {
+        const int mid = a + (c - a) / 2;
+        if ((k >> t) & 1) a = mid; else c = mid;
+    }
+    return a;
+}
+
+// One sample's remaining decisions inside a bin of m points (dm = ceil(log2 m)
+// levels, the first at tree level s0), from the item's row of values vi
+// (vi[j] = k(query, point j of the bin)) and the tree bi of its depth-4 node
+// sums (bi[16 + k] = node k, bi[h] = bi[2h] + bi[2h+1]): the four top levels
+// read bi, deeper ones sum the values of the node's two halves.  Returns the
+// leaf's offset in the bin and sets the flags.
+__device__ __forceinline__ int descend_bin_row(const float* __restrict__ vi, const float* __restrict__ bi, int m,
+                                               int dm, int s0, uint64_t seed, uint32_t qi, uint32_t l, float eps,
+                                               uint8_t& f) {
+    int a = 0, c = m, h = 1;
+    uint4 blk = make_uint4(0, 0, 0, 0);
+    int blk_id = -1;
+    for (int t = 0; t < dm; ++t) {
+        int right = 1;  // a single point sits in the right half
+        if (c - a >= 2) {
+            const int mid = a + (c - a) / 2;
+            float gl, gr;
+            if (t < 4) {  // both halves are nodes of the depth-4 tree
+                gl = bi[2 * h];
+                gr = bi[2 * h + 1];
+            } else {
+                gl = 0.f;
+                gr = 0.f;
+                for (int j = a; j < mid; ++j) gl += vi[j];
+                for (int j = mid; j < c; ++j) gr += vi[j];
+            }
+            const uint32_t lev = (uint32_t)(s0 + t);
+            if ((int)(lev >> 2) != blk_id) {
+                blk_id = (int)(lev >> 2);
+                blk = draw_block(seed, qi, l, lev);
+            }
+            right = descend_decide(gl, gr, block_word(blk, lev), eps, f);
+            if (right) a = mid; else c = mid;
+        }
+        h = 2 * h + right;
+    }
+    return a;
 }
 
 #endif  // __CUDACC__

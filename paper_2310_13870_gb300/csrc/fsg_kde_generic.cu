@@ -601,6 +601,180 @@ cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, c
     return cudaGetLastError();
 }
 
+namespace {
+
+// Fused leaf phase for d > 16 and bins of at most 128 points: per chunk of
+// 128 items of a bin, the kernel values against the bin's m points (compact:
+// column j = point p_lo + j) in the packed 128 x 128 tile of the bin pass,
+// kept in shared memory (over the coordinate tiles, which are idle by then);
+// then the 16 depth-4 node sums of every item (two threads per item) and
+// their tree; then every sample of the chunk's items, spread over all threads,
+// descends through the bin (descend_bin_row).  No value goes to HBM.
+constexpr int kLfVS = kST + 1;  // value row stride (odd)
+constexpr size_t kLfU = (size_t)kST * kLfVS * 4 > kSymGenSmem ? (size_t)kST * kLfVS * 4 : kSymGenSmem;
+constexpr size_t kLfBT = kLfU;                          // [128][33] depth-4 node sums and their tree
+constexpr size_t kLfMask = kLfBT + (size_t)kST * 33 * 4;  // [128] sample masks
+constexpr size_t kLfPre = kLfMask + (size_t)kST * 8;      // [129] samples before item r
+constexpr size_t kLfB4 = kLfPre + 132 * 4;                // [17] depth-4 node starts
+constexpr size_t kLfSmem = kLfB4 + 20 * 4;
+
+__global__ void __launch_bounds__(kGT, 2)
+leaf_fused_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__ bnd, int s0,
+                          const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
+                          const uint64_t* __restrict__ items_mask, const int32_t* __restrict__ perm, KernelParams kp,
+                          int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp, uint8_t* __restrict__ lflags,
+                          unsigned long long* __restrict__ n_evals, unsigned long long* __restrict__ n_items) {
+    extern __shared__ __align__(16) float gsm[];
+    float* Qs = gsm;
+    float* Ps = gsm + kSK * kSQS;
+    float* V = gsm;  // after the coordinate loop
+    unsigned char* sb = reinterpret_cast<unsigned char*>(gsm);
+    float* bt_all = reinterpret_cast<float*>(sb + kLfBT);
+    uint64_t* qmask = reinterpret_cast<uint64_t*>(sb + kLfMask);
+    int32_t* prefix = reinterpret_cast<int32_t*>(sb + kLfPre);
+    int32_t* bnd4 = reinterpret_cast<int32_t*>(sb + kLfB4);
+    __shared__ int qrow[kST], prow[kST];
+    const int tid = threadIdx.x, tq = tid & 15, tp = tid >> 4;
+    const int b = blockIdx.x;
+    const int seg = bin_off[b * kBinSlots];
+    const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
+    const int nchunks = (cnt + kST - 1) / kST;
+    if ((int)blockIdx.y >= nchunks) return;
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;  // m <= 128
+    const int dm = ceil_log2_dev(m);
+    const uint64_t nc2 = f2_pack(kp.neg_c, kp.neg_c);
+    if (tid < kST) prow[tid] = tid < m ? p_lo + tid : -1;
+    if (tid <= 16) bnd4[tid] = depth4_start(tid, m);
+    unsigned long long ev_acc = 0, it_acc = 0;
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        const int it0 = chunk * kST;
+        const int qcnt = min(kST, cnt - it0);
+        __syncthreads();  // the previous chunk's descents are done with V, qmask and prefix
+        if (tid < kST) {
+            qrow[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
+            qmask[tid] = tid < qcnt ? items_mask[seg + it0 + tid] : 0ull;
+        }
+        uint64_t acc[4][8];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[a][c] = 0ull;
+        for (int k0 = 0; k0 < dp; k0 += kSK) {
+            __syncthreads();
+            load_tiles(Qs, Ps, [&](int r) { return qrow[r]; }, [&](int r) { return prow[r]; }, Xt, dp, k0, 0.f);
+            __syncthreads();
+            accumulate_pairs<2>(Qs, Ps, tq, tp, acc);
+        }
+        __syncthreads();  // every thread is done with Qs and Ps: V takes their place
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int col = tile_row(tp, c);
+                const int pp = prow[col];
+                const float2 sv = f2_unpack(f2_mul(acc[a][c], nc2));
+                const int r0 = tile_row(tq, 2 * a);
+                float k0v = pp >= 0 ? ex2_approx(sv.x) : 0.f, k1v = pp >= 0 ? ex2_approx(sv.y) : 0.f;
+                if (kp.self_exclude) {
+                    if (pp == qrow[r0]) k0v = 0.f;
+                    if (pp == qrow[r0 + 1]) k1v = 0.f;
+                }
+                V[r0 * kLfVS + col] = k0v;
+                V[(r0 + 1) * kLfVS + col] = k1v;
+            }
+        }
+        // samples of the chunk's items: prefix[r] = samples of items < r
+        if (tid < kST) {
+            int x = __popcll(qmask[tid]);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((tid & 31) >= o) x += y;
+            }
+            prefix[tid + 1] = x;  // inclusive within the warp
+        }
+        __syncthreads();
+        // depth-4 node sums: item r = tid % 128, nodes 8 hh .. 8 hh + 7
+        {
+            const int r = tid & (kST - 1), hh = tid >> 7;
+            const float* vr = V + r * kLfVS;
+            float* bt = bt_all + r * 33;
+            for (int k = 8 * hh; k < 8 * hh + 8; ++k) {
+                float sacc = 0.f;
+                for (int j = bnd4[k]; j < bnd4[k + 1]; ++j) sacc += vr[j];
+                bt[16 + k] = sacc;
+            }
+        }
+        if (tid == 0) {  // warp totals into the prefix
+            prefix[0] = 0;
+            for (int w2 = 1; w2 < 4; ++w2) {
+                const int add = prefix[32 * w2];
+                for (int i = 32 * w2 + 1; i <= 32 * w2 + 32; ++i) prefix[i] += add;
+            }
+        }
+        __syncthreads();
+        if (tid < kST) {
+            float* bt = bt_all + tid * 33;
+#pragma unroll
+            for (int h = 15; h >= 1; --h) bt[h] = bt[2 * h] + bt[2 * h + 1];
+        }
+        __syncthreads();
+        const int total = prefix[kST];
+        for (int gsm_i = tid; gsm_i < total; gsm_i += kGT) {
+            int lo = 0, hi = kST;  // item: prefix[lo] <= gsm_i < prefix[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (prefix[mid] <= gsm_i) lo = mid; else hi = mid;
+            }
+            uint64_t mk = qmask[lo];
+            for (int k = gsm_i - prefix[lo]; k > 0; --k) mk &= mk - 1ull;
+            const int l = __ffsll((long long)mk) - 1;
+            const int ip = qrow[lo];
+            const float* vi = V + lo * kLfVS;
+            uint8_t f = 0;
+            const int a = descend_bin_row(vi, bt_all + lo * 33, m, dm, s0, kp.seed, (uint32_t)perm[ip], (uint32_t)l,
+                                          kp.flag_eps, f);
+            const size_t o = (size_t)ip * kp.L + l;
+            leaf_pos[o] = p_lo + a;
+            ksmp[o] = vi[a];
+            lflags[o] = f;
+        }
+        ev_acc += (unsigned long long)qcnt * (unsigned long long)m;
+        it_acc += (unsigned long long)qcnt;
+    }
+    if (tid == 0) {
+        atomicAdd(n_evals, ev_acc);
+        atomicAdd(n_items, it_acc);
+    }
+}
+
+}  // namespace
+
+bool leaf_fused_generic_supported(const fsg_tree* t) { return t->d > kMaxFmaDim && t->mmax <= kST; }
+
+cudaError_t launch_leaf_fused_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
+    const int64_t chunks_per_bin = (items_est / t->nb + kST - 1) / kST + 1;
+    int64_t S = (152 * 2 * 8 + t->nb - 1) / t->nb;
+    if (S > chunks_per_bin) S = chunks_per_bin;
+    if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
+    if (S < 1) S = 1;
+    if (S > 65535) S = 65535;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(leaf_fused_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kLfSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const auto& ws = t->ws;
+    leaf_fused_generic_kernel<<<dim3(t->nb, (unsigned)S), kGT, kLfSmem, s>>>(
+        t->Xt, t->dp, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, ws.leaf_pos, ws.ksmp,
+        ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+        reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
     const int64_t chunks_per_bin = (items_est / t->nb + kST - 1) / kST + 1;

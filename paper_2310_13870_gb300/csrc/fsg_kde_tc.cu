@@ -462,18 +462,7 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     for (int j = tid; j < N; j += kLvThreads) pnorm[j] = j < m ? norms[p_lo + j] : 0.f;
-    if (tid <= 16) {  // start of depth-4 node tid of the bin (tid = 16: the end)
-        int a = 0, c = m;
-        if (tid < 16) {
-            for (int t = 3; t >= 0; --t) {
-                const int mid = a + (c - a) / 2;
-                if ((tid >> t) & 1) a = mid; else c = mid;
-            }
-        } else {
-            a = m;
-        }
-        bnd4[tid] = a;
-    }
+    if (tid <= 16) bnd4[tid] = depth4_start(tid, m);  // depth-4 node starts of the bin (tid = 16: the end)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -646,34 +635,8 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
             const uint32_t qi = (uint32_t)perm[ip];
             const float* vi = vrows + (size_t)it * vstride;
             const float* bi = btree + (size_t)it * 33;
-            int a = 0, c = m, h = 1;
             uint8_t f = 0;
-            uint4 blk = make_uint4(0, 0, 0, 0);
-            int blk_id = -1;
-            for (int t = 0; t < dm; ++t) {
-                int right = 1;  // a single point sits in the right half
-                if (c - a >= 2) {
-                    const int mid = a + (c - a) / 2;
-                    float gl, gr;
-                    if (t < 4) {  // both halves are nodes of the depth-4 tree
-                        gl = bi[2 * h];
-                        gr = bi[2 * h + 1];
-                    } else {
-                        gl = 0.f;
-                        gr = 0.f;
-                        for (int j = a; j < mid; ++j) gl += vi[j];
-                        for (int j = mid; j < c; ++j) gr += vi[j];
-                    }
-                    const uint32_t lev = (uint32_t)(s0 + t);
-                    if ((int)(lev >> 2) != blk_id) {
-                        blk_id = (int)(lev >> 2);
-                        blk = draw_block(kp.seed, qi, (uint32_t)l, lev);
-                    }
-                    right = descend_decide(gl, gr, block_word(blk, lev), kp.flag_eps, f);
-                    if (right) a = mid; else c = mid;
-                }
-                h = 2 * h + right;
-            }
+            const int a = descend_bin_row(vi, bi, m, dm, s0, kp.seed, qi, (uint32_t)l, kp.flag_eps, f);
             const size_t o = (size_t)ip * kp.L + l;
             leaf_pos[o] = p_lo + a;
             ksmp[o] = vi[a];
