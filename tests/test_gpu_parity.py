@@ -291,6 +291,51 @@ def test_gpu_sampler_chi_square(fsg):
     tree.close()
 
 
+@pytest.mark.parametrize("mode", ["split", "exact_int"])
+def test_gpu_sampler_chi_square_tensor_core_modes(fsg, mode):
+    # the sampled frequencies of the tensor-core bin passes against the exact
+    # k(x_i, x_j) / deg(x_i) (FP64): split precision on a spatial order (d = 20,
+    # bins of 100 points), exact 8-bit products (digit-like, d = 64)
+    from scipy.spatial.distance import cdist
+    from scipy.stats import chi2
+    n, L = 200, 64
+    if mode == "split":
+        X = inputs.gaussian_mixture(n=n, d=20, k=3, box=1.5, seed=4)
+        sigma, prec = 1.5, fsg.FSG_PREC_SPLIT_BF16
+        perm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
+    else:
+        X = inputs.digit_like(n=n, d=64, seed=5)
+        sigma, prec, perm = 1.2, fsg.FSG_PREC_EXACT_INT, None
+    gam = ora.gamma(sigma)
+    tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda(), perm=perm)
+    p = fsg.params(sigma, precision=prec)
+    queries = [0, 77, 150, 199]
+    counts = np.zeros((len(queries), n))
+    for seed in range(2000, 2600):
+        smp, _ = fsg.fsg_sample_edges(tree, p, L, seed)
+        s = smp[queries].cpu().numpy()
+        for r in range(len(queries)):
+            counts[r] += np.bincount(s[r], minlength=n)
+    assert fsg.fsg_sync(tree) == 0
+    K = np.exp(-gam * cdist(X.astype(np.float64), X.astype(np.float64), "sqeuclidean"))
+    np.fill_diagonal(K, 0.0)
+    for r, i in enumerate(queries):
+        probs = K[i] / K[i].sum()
+        exp = probs * counts[r].sum()
+        order = np.argsort(exp)
+        oc, ec, ao, ae = [], [], 0.0, 0.0
+        for t in order:
+            ao += counts[r][t]
+            ae += exp[t]
+            if ae >= 5:
+                oc.append(ao); ec.append(ae); ao = ae = 0.0
+        oc[-1] += ao; ec[-1] += ae
+        oc, ec = np.array(oc), np.array(ec)
+        pval = chi2.sf(((oc - ec) ** 2 / ec).sum(), len(ec) - 1)
+        assert pval > 0.01 / len(queries), (mode, i, pval)
+    tree.close()
+
+
 def test_host_entry_point_matches_device_path(fsg):
     X = inputs.two_moons(n=1000, seed=2)
     src, dst, w = fsg.fsg_build_graph_host(X, fsg.params(0.1), 16, 4)
