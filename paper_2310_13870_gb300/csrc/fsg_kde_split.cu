@@ -47,12 +47,12 @@ constexpr uint32_t kTmemCols = 256;   // two 128-column accumulators
 
 struct SpLayout {
     static constexpr uint32_t A = 0;                                      // [3][128 rows]
-    static constexpr uint32_t B = A + kSpParts * kPart;                   // [2 stages][3][128 rows]
-    static constexpr uint32_t CN = B + kSpStages * kSpParts * kPart;      // [2][128] point norms
+    static constexpr uint32_t B = A + kSpParts * kPart;                   // [stages][3][128 rows]
+    static constexpr uint32_t CN = B + kSpStages * kSpParts * kPart;      // [stages][128] point norms
     static constexpr uint32_t AN = CN + kSpStages * kSpN * 4;             // [128] query norms
     static constexpr uint32_t CEN = AN + kSpM * 4;                        // [64] centre
     static constexpr uint32_t BARS = CEN + kSpDim * 4;                    // full[2] empty[2] tfull[2] tempty[2] fin
-    static constexpr uint32_t SLOT = BARS + 9 * 8;                        // TMEM slot, abort flag
+    static constexpr uint32_t SLOT = BARS + (2 * kSpStages + 5) * 8;      // TMEM slot, abort flag
     static constexpr uint32_t BND = SLOT + 16;                            // [kSpMaxBins + 1]
     static constexpr uint32_t PN = (BND + 112 + 15) & ~15u;               // [8 warps][64] norms of a warp's columns
     static constexpr uint32_t OUTS = PN + kSpEpiWarps * 64 * 4;           // [2 halves][128][bpc]
@@ -203,8 +203,8 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
         int p = pa + tid;
         load_row(Xt, dp, p < pe ? p : -1, x);
         for (int t = 0; t < ntile && !*abort_flag; ++t) {
-            const int s = t & 1;
-            if (!mbar_wait_bounded(&empty[s], ((uint32_t)(t >> 1) & 1u) ^ 1u, status)) {
+            const int s = t % kSpStages;
+            if (!mbar_wait_bounded(&empty[s], ((uint32_t)(t / kSpStages) & 1u) ^ 1u, status)) {
                 *abort_flag = 1;
                 break;
             }
@@ -221,9 +221,9 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
             const int pj[6] = {0, 2, 1, 0, 1, 0};  // B part
             const uint32_t idesc = idesc_bf16(kSpM, kSpN);
             for (int t = 0; t < ntile && !*abort_flag; ++t) {
-                const int a = t & 1, s = t & 1;
+                const int a = t & 1, s = t % kSpStages;
                 if (!mbar_wait_bounded(&tempty[a], ((uint32_t)(t >> 1) & 1u) ^ 1u, status) ||
-                    !mbar_wait_bounded(&full[s], (uint32_t)(t >> 1) & 1u, status)) {
+                    !mbar_wait_bounded(&full[s], (uint32_t)(t / kSpStages) & 1u, status)) {
                     *abort_flag = 1;
                     break;
                 }
@@ -256,9 +256,9 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
         int bin = 0;
         int next_b = nbc > 0 ? bnd_s[1] : INT_MAX;
         for (int t = 0; t < ntile; ++t) {
-            const int a = t & 1, s = t & 1;
+            const int a = t & 1, s = t % kSpStages;
             if (*abort_flag || !mbar_wait_bounded(&tfull[a], (uint32_t)(t >> 1) & 1u, status) ||
-                !mbar_wait_bounded(&full[s], (uint32_t)(t >> 1) & 1u, status)) {
+                !mbar_wait_bounded(&full[s], (uint32_t)(t / kSpStages) & 1u, status)) {
                 *abort_flag = 1;
                 break;
             }

@@ -74,6 +74,19 @@ def test_split_matches_oracle(fsg, n, d, sigma, L, seed):
             assert math.isclose(w, wo[key], rel_tol=2 * SPLIT_DEG_RTOL), (key, w, wo[key])
 
 
+@pytest.mark.parametrize("n,d", [(40, 20), (129, 64), (300, 48)])
+def test_split_small_point_sets(fsg, n, d):
+    # one bin, a ragged second query tile, bins of 75 points
+    X = inputs.gaussian_mixture(n=n, d=d, k=2, box=2.0, seed=n)
+    perm = fsg.fsg_spatial_order(X)
+    gam = ora.gamma(1.5)
+    g = run(fsg, X, perm, 1.5, 16, 7, fsg.FSG_PREC_SPLIT_BF16)
+    want = ora.degrees(X, gam)
+    assert (np.abs(g["deg"] - want) <= SPLIT_DEG_RTOL * want + n * TINY).all()
+    osmp, _, _ = ora.sample(X, gam, 16, 7, perm=perm)
+    assert not ((g["samples"] != osmp) & (g["flags"] == 0)).any()
+
+
 def test_split_against_fp32_path(fsg):
     # same tree, same draws: degrees within the stated bound of the FP32 path's,
     # samples equal wherever neither path flagged
