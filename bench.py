@@ -479,6 +479,9 @@ def run_serving(args):
     admission = {"arrival": fsg.FSG_ADMIT_ARRIVAL, "ratio": fsg.FSG_ADMIT_RESPONSE_RATIO}[args.admission]
     server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8, admission=admission)
     p = fsg.params(sigma)
+    # --precision split: the d = 64 requests take the split-precision tensor-core
+    # bin pass (identity tree order; within the mode's stated bound)
+    p_large = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16) if args.precision == "split" else p
     owner = {}
     lat, qms, edges_done = [], [], 0
     sampled_done = 0
@@ -501,7 +504,7 @@ def run_serving(args):
             collect(wait_ms=1)
         slot = free_ring.pop()
         X = pools[r.d][: r.n]
-        rid = server.submit(X, p, L, r.seed, out=ring[slot])
+        rid = server.submit(X, p_large if r.d > 16 else p, L, r.seed, out=ring[slot])
         owner[rid] = (slot, r.n, timed)
 
     for r in reqs[: args.warmup]:  # warm-up: untimed
@@ -562,6 +565,7 @@ def run_serving(args):
             "config": {"workload": f"serving: {len(timed_reqs)} requests, Poisson {args.rate}/s, n log-uniform "
                                    f"[1e3, 2e5], d in {{2,10,64}}, mixture data, sigma=1.5, L=32, SET edges",
                        "hbm_budget_gb": 120, "slots": 8, "parallelism": "continuous admission, 8 streams",
+                       "precision": "d = 64 in split precision" if args.precision == "split" else "FP32 / auto",
                        "admission": {"arrival": "arrival order",
                                      "ratio": "highest response ratio next"}[args.admission]},
             "p50_ms": pct(lat_sorted, 0.5), "p99_ms": pct(lat_sorted, 0.99), "max_ms": lat_sorted[-1],

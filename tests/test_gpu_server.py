@@ -39,8 +39,14 @@ def _requests():
     return reqs
 
 
-def _alone(fsg, X, sigma, L, seed):
-    src, dst, w = fsg.fsg_build_graph_host(X, fsg.params(sigma), L, seed)
+def _params(fsg, X, sigma, split):
+    if split and X.shape[1] > 16:  # d = 64 requests in split precision
+        return fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16)
+    return fsg.params(sigma)
+
+
+def _alone(fsg, X, sigma, L, seed, split=False):
+    src, dst, w = fsg.fsg_build_graph_host(X, _params(fsg, X, sigma, split), L, seed)
     return src.copy(), dst.copy(), w.copy()
 
 
@@ -54,12 +60,13 @@ def _drain(server, expect, timeout_s=120):
     return got
 
 
-@pytest.mark.parametrize("budget_mb,slots,admission", [(8192, 8, 0), (64, 2, 0), (8192, 8, 1), (64, 1, 1)])
-def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots, admission):
+@pytest.mark.parametrize("budget_mb,slots,admission,split", [(8192, 8, 0, False), (64, 2, 0, False),
+                                                           (8192, 8, 1, False), (64, 1, 1, False), (8192, 8, 0, True)])
+def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots, admission, split):
     reqs = _requests()
-    want = [_alone(fsg, *r) for r in reqs]
+    want = [_alone(fsg, *r, split=split) for r in reqs]
     server = fsg.Server(hbm_budget_bytes=budget_mb << 20, max_slots=slots, admission=admission)
-    ids = [server.submit(X, fsg.params(s), L, seed) for X, s, L, seed in reqs]
+    ids = [server.submit(X, _params(fsg, X, s, split), L, seed) for X, s, L, seed in reqs]
     got = _drain(server, len(ids))
     for rid, (src, dst, w) in zip(ids, want):
         rec, (gs, gd, gw) = got[rid]
