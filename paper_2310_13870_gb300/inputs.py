@@ -40,11 +40,17 @@ def two_moons(n: int = 2000, noise: float = 0.05, seed: int = 0) -> np.ndarray:
     return X.astype(np.float32)
 
 
+def two_moons_labels(n: int = 2000) -> np.ndarray:
+    """The moon of each point of two_moons(n): 0 for the first n//2, else 1."""
+    return (np.arange(n) >= n // 2).astype(np.int64)
+
+
 def gaussian_mixture(n: int = 100_000, d: int = 10, k: int = 10, box: float = 10.0,
-                     seed: int = 0, shuffle: bool = True) -> np.ndarray:
+                     seed: int = 0, shuffle: bool = True, return_labels: bool = False):
     """k equal-weight N(c, I) blobs with centres uniform in [-box, box]^d.
     Points are shuffled (as generators of blob data usually do), so tree order
-    carries no cluster structure.  float32 [n][d]."""
+    carries no cluster structure.  float32 [n][d]; with return_labels also the
+    blob of each point (the same points either way)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     centres = rng.uniform(-box, box, size=(k, d))
     counts = np.full(k, n // k)
@@ -52,7 +58,10 @@ def gaussian_mixture(n: int = 100_000, d: int = 10, k: int = 10, box: float = 10
     labels = np.repeat(np.arange(k), counts)
     X = centres[labels] + rng.normal(0.0, 1.0, size=(n, d))
     if shuffle:
-        X = X[rng.permutation(n)]
+        order = rng.permutation(n)
+        X, labels = X[order], labels[order]
+    if return_labels:
+        return X.astype(np.float32), labels
     return X.astype(np.float32)
 
 
@@ -94,10 +103,11 @@ def median_pair_distance(X: np.ndarray, m: int = 4096, seed: int = 0) -> float:
     return float(dist[(dist.shape[0] - 1) // 2])
 
 
-def segmentation_image(h: int, w: int, seed: int = 0, noise: float = 0.03) -> np.ndarray:
+def segmentation_image(h: int, w: int, seed: int = 0, noise: float = 0.03, return_labels: bool = False):
     """(r,g,b,x,y) features of an h x w image made of 6-12 Voronoi regions of
     uniform random colour plus N(0, noise^2) per channel; x, y scaled to
-    [0,1].  float32 [h*w][5], row-major pixel order."""
+    [0,1].  float32 [h*w][5], row-major pixel order; with return_labels also
+    the region of each pixel (the same features either way)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     k = int(rng.integers(6, 13))
     sites = rng.uniform(0.0, 1.0, size=(k, 2))
@@ -109,7 +119,8 @@ def segmentation_image(h: int, w: int, seed: int = 0, noise: float = 0.03) -> np
     d2 = ((pts[:, None, :] - sites[None, :, :]) ** 2).sum(-1)
     region = d2.argmin(1)
     rgb = colours[region] + rng.normal(0.0, noise, size=(h * w, 3))
-    return np.concatenate([rgb, pts], axis=1).astype(np.float32)
+    X = np.concatenate([rgb, pts], axis=1).astype(np.float32)
+    return (X, region.astype(np.int64)) if return_labels else X
 
 
 def segmentation_batch(count: int = 64, h_min: int = 160, h_max: int = 321, w_max: int = 481,
