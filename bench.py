@@ -304,9 +304,8 @@ def run_ours(args):
             traffic = json.load(f).get("bytes_per_launch")
 
     # the plain FP32 exact GPU path (levelwise schedule) on the same input, same clocks regime
-    plain = None
-    if args.plain_steps > 0:
-        pl = fsg.params(sigma, schedule=fsg.FSG_SCHED_LEVELWISE)
+    def run_plain(schedule):
+        pl = fsg.params(sigma, schedule=schedule)
         fsg.fsg_build_graph(tree, pl, L, seed, bufs=bufs, stream=stream)  # warm-up
         stream.synchronize()
         pms = []
@@ -323,10 +322,16 @@ def run_ours(args):
         assert fsg.fsg_sync(tree, stream=stream) == 0
         pst = fsg.stats_dict(bufs)
         pt = statistics.mean(pms)
-        plain = {"schedule": "levelwise (Algorithm 1 per level, FP32 direct differences, no bin pass)",
-                 "value": n * L / (pt * 1e-3), "unit": UNIT, "ms_per_step": pt, "steps": args.plain_steps,
-                 "evals_per_step": pst["n_evals"], "gkernel_evals_per_s": pst["n_evals"] / (pt * 1e-3) / 1e9,
-                 "flagged_samples": pst["n_flagged"], "speedup_of_fused": (n * L / (ms * 1e-3)) / (n * L / (pt * 1e-3))}
+        return {"value": n * L / (pt * 1e-3), "unit": UNIT, "ms_per_step": pt, "steps": args.plain_steps,
+                "evals_per_step": pst["n_evals"], "gkernel_evals_per_s": pst["n_evals"] / (pt * 1e-3) / 1e9,
+                "flagged_samples": pst["n_flagged"], "speedup_of_fused": (n * L / (ms * 1e-3)) / (n * L / (pt * 1e-3))}
+
+    plain = carried = None
+    if args.plain_steps > 0 and not split:
+        plain = dict(schedule="levelwise (Algorithm 1 per level, FP32 direct differences, no bin pass)",
+                     **run_plain(fsg.FSG_SCHED_LEVELWISE))
+        carried = dict(schedule="carried denominator (left half per level, g_R = g_node - g_L)",
+                       **run_plain(fsg.FSG_SCHED_CARRIED))
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -365,7 +370,8 @@ def run_ours(args):
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
-                "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "tuning": tuning,
+                "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "carried_fp32_gpu": carried,
+                "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches1 - launches0)}
         print(json.dumps(line), flush=True)

@@ -75,6 +75,9 @@ extern "C" {
 /* Sampling schedule. */
 #define FSG_SCHED_FUSED 0       /* top levels from one bin pass, then leaf finish */
 #define FSG_SCHED_LEVELWISE 1   /* literal per-level KDE of both halves           */
+#define FSG_SCHED_CARRIED 2     /* per level the left half only, g_R = g - g_L    */
+                                /* carried from the parent (decisions flagged    */
+                                /* within the carried error bound)               */
 
 typedef struct fsg_tree fsg_tree; /* opaque */
 

@@ -35,7 +35,8 @@ int check_params(const fsg_params* p) {
     if (p->scale_conv != FSG_TWO_SIGMA_SQ && p->scale_conv != FSG_SIGMA_SQ) return FSG_ERR_INVALID_ARG;
     if (p->self_mode != FSG_SELF_EXCLUDE && p->self_mode != FSG_SELF_INCLUDE) return FSG_ERR_INVALID_ARG;
     if (p->precision < FSG_PREC_AUTO || p->precision > FSG_PREC_EXACT_INT) return FSG_ERR_INVALID_ARG;
-    if (p->schedule != FSG_SCHED_FUSED && p->schedule != FSG_SCHED_LEVELWISE) return FSG_ERR_INVALID_ARG;
+    if (p->schedule != FSG_SCHED_FUSED && p->schedule != FSG_SCHED_LEVELWISE && p->schedule != FSG_SCHED_CARRIED)
+        return FSG_ERR_INVALID_ARG;
     if (!(p->flag_eps >= 0.f) || !std::isfinite(p->flag_eps) || p->flag_eps > 0.25f) return FSG_ERR_INVALID_ARG;
     return FSG_OK;
 }
@@ -123,8 +124,8 @@ int64_t bin_pass_evals(const fsg_tree* t, int precision) {
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
     if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
-    // the levelwise schedule is the plain FP32 path only
-    if (p->schedule == FSG_SCHED_LEVELWISE && p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32)
+    // the levelwise schedules are plain FP32 paths only
+    if (p->schedule != FSG_SCHED_FUSED && p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32)
         return FSG_ERR_UNSUPPORTED;
     return FSG_OK;
 }
@@ -527,7 +528,7 @@ int fsg_bin_pass_evals(const fsg_tree* t, const fsg_params* p, int64_t* evals) {
     if (!t || !evals) return FSG_ERR_INVALID_ARG;
     const int rc = check_params(p);
     if (rc != FSG_OK) return rc;
-    *evals = p->schedule == FSG_SCHED_LEVELWISE ? 0 : bin_pass_evals(t, p->precision);
+    *evals = p->schedule != FSG_SCHED_FUSED ? 0 : bin_pass_evals(t, p->precision);
     return FSG_OK;
 }
 
@@ -575,11 +576,11 @@ int fsg_profile_read(fsg_tree* t, float* ms, int64_t* launches) {
 
 static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s) {
     Workspace& ws = t->ws;
-    if (schedule == FSG_SCHED_LEVELWISE) {
+    if (schedule != FSG_SCHED_FUSED) {
         cudaError_t e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
         if (e == cudaSuccess) {
             PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
-            e = launch_levelwise(t, kp, d_deg, 1, s, &t->launches);
+            e = launch_levelwise(t, kp, d_deg, 1, schedule == FSG_SCHED_CARRIED, s, &t->launches);
         }
         return status_of(e);
     }
@@ -611,7 +612,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
 // Evaluations of the bin pass (every query against every point), counted on
 // the host; the levelwise schedule counts its own on the device.
 static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
-    return p->schedule == FSG_SCHED_LEVELWISE ? 0 : bin_pass_evals(t, p->precision);
+    return p->schedule != FSG_SCHED_FUSED ? 0 : bin_pass_evals(t, p->precision);
 }
 
 // Statistics known on the host: samples run, bin-pass evaluations.
@@ -633,10 +634,10 @@ int fsg_degrees(fsg_tree* t, const fsg_params* p, double* d_deg, void* stream) {
     const KernelParams kp = make_kernel_params(p, 1, 0);
     begin_call(t);
     cudaError_t e;
-    if (p->schedule == FSG_SCHED_LEVELWISE) {
+    if (p->schedule != FSG_SCHED_FUSED) {  // both levelwise schedules: the root pass
         e = cudaMemsetAsync(t->ws.stats, 0, sizeof(fsg_stats), s);
         PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
-        if (e == cudaSuccess) e = launch_levelwise(t, kp, d_deg, 0, s, &t->launches);
+        if (e == cudaSuccess) e = launch_levelwise(t, kp, d_deg, 0, 0, s, &t->launches);
         return status_of(e);
     }
     {

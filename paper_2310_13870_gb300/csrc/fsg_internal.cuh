@@ -159,7 +159,7 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
 cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_levelwise(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
-                             cudaStream_t s, int64_t* launches);
+                             int carried, cudaStream_t s, int64_t* launches);
 
 // ---------------------------------------------------------------------------
 // Device helpers

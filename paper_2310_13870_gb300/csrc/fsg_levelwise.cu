@@ -7,6 +7,10 @@
 // sample at that node takes its decision.  There is no bin pass and no reuse
 // of sums across levels: this is the comparison point for the fused
 // schedule, and gives the same samples up to flagged decisions.
+// The carried-denominator variant (FSG_SCHED_CARRIED) sums only the left
+// child at levels >= 1 and carries each sample's node sum down, taking g_R as
+// g_node - g_L: half the evaluations per level, paid for in precision (the
+// carried error bound widens the flag tolerance as the descent goes right).
 #include "fsg_internal.cuh"
 
 namespace fsg {
@@ -63,6 +67,7 @@ template <int DP>
 __device__ __forceinline__ void node_sums(const Query<DP>& xq, const float* __restrict__ Xt, int dp, int q,
                                           int nlo, int mid, int nhi, const KernelParams& kp, int lane, float& gl,
                                           float& gr) {
+    // (the carried-denominator schedule passes nhi = mid: the left half only)
     gl = 0.f;
     gr = 0.f;
     if constexpr (DP == 0) {
@@ -94,6 +99,32 @@ __device__ __forceinline__ void node_sums(const Query<DP>& xq, const float* __re
     }
 }
 
+// Carried-denominator decision (the variant of Algorithm 1 that sums only the
+// left child and takes g_R = g_node - g_L from the parent's sum): go right iff
+// u g_node >= g_L.  eg bounds the absolute error of the carried g_node, eps the
+// relative error of a fresh FP32 sum; the decision is flagged when
+// |u g_node - g_L| < eg + 2 eps g_L + 2^-22 g_node, which covers both.  The
+// chosen child's sum and its error bound replace (g, eg): g_L (fresh), or
+// g - g_L, whose bound adds the parent's, g_L's and the subtraction's rounding.
+__device__ __forceinline__ int carried_decide(float gl, float& g, float& eg, uint32_t word, float eps, uint8_t& f) {
+    if (!(g > 0.f)) {
+        f |= 2;
+        return 1;
+    }
+    const float u = __uint2float_rz(word >> 8) * 0x1p-24f;
+    const float dlt = fmaf(u, g, -gl);
+    if (fabsf(dlt) < eg + 2.f * eps * gl + 0x1p-22f * g) f |= 1;
+    if (dlt < 0.f) {
+        g = gl;
+        eg = eps * gl;
+        return 0;
+    }
+    const float gr = g - gl;
+    eg = eg + eps * gl + 0x1p-24f * fabsf(gr);
+    g = gr;
+    return 1;
+}
+
 // Level 0: the root [0, n) of every query, i.e. its degree, and (with
 // samples) the first decision of each of its L samples.
 template <int DP>
@@ -101,7 +132,7 @@ __global__ void __launch_bounds__(128)
 levelwise_root_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t* __restrict__ perm,
                       KernelParams kp, int with_samples, int32_t* __restrict__ lo_s, int32_t* __restrict__ hi_s,
                       uint8_t* __restrict__ flags, double* __restrict__ d_deg, float* __restrict__ degf,
-                      unsigned long long* __restrict__ n_evals) {
+                      unsigned long long* __restrict__ n_evals, float* __restrict__ g_s, float* __restrict__ eg_s) {
     const int lane = threadIdx.x & 31;
     const int q = blockIdx.x * 4 + (threadIdx.x >> 5);
     if (q >= n) return;
@@ -120,13 +151,20 @@ levelwise_root_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t
     for (int l = lane; l < kp.L; l += 32) {
         uint8_t f = 0;
         int lo = 0, hi = n;
+        float g = gl + gr, eg = kp.flag_eps * g;  // carried state (the carried schedule)
         if (n >= 2) {
             const uint4 blk = draw_block(kp.seed, i, (uint32_t)l, 0u);
-            if (descend_decide(gl, gr, blk.x, kp.flag_eps, f)) lo = mid; else hi = mid;
+            const int right = g_s ? carried_decide(gl, g, eg, blk.x, kp.flag_eps, f)
+                                  : descend_decide(gl, gr, blk.x, kp.flag_eps, f);
+            if (right) lo = mid; else hi = mid;
         }
         lo_s[(size_t)q * kp.L + l] = lo;
         hi_s[(size_t)q * kp.L + l] = hi;
         flags[(size_t)q * kp.L + l] = f;
+        if (g_s) {
+            g_s[(size_t)q * kp.L + l] = g;
+            eg_s[(size_t)q * kp.L + l] = eg;
+        }
     }
 }
 
@@ -139,7 +177,7 @@ __global__ void __launch_bounds__(128)
 levelwise_step_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t* __restrict__ perm,
                       KernelParams kp, int lev, int32_t* __restrict__ lo_s, int32_t* __restrict__ hi_s,
                       uint8_t* __restrict__ flags, const float* __restrict__ degf,
-                      unsigned long long* __restrict__ n_evals) {
+                      unsigned long long* __restrict__ n_evals, float* __restrict__ g_s, float* __restrict__ eg_s) {
     __shared__ int32_t sk[4][kMaxL];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = blockIdx.x * 4 + w;
@@ -149,6 +187,7 @@ levelwise_step_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t
     int lo[2], hi[2];
     uint8_t f[2];
     bool act[2];
+    float g[2] = {0.f, 0.f}, eg[2] = {0.f, 0.f};  // carried node sums (the carried schedule)
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int l = lane + 32 * r;
@@ -160,6 +199,10 @@ levelwise_step_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t
             hi[r] = hi_s[(size_t)q * L + l];
             f[r] = flags[(size_t)q * L + l];
             act[r] = hi[r] - lo[r] >= 2;
+            if (g_s) {
+                g[r] = g_s[(size_t)q * L + l];
+                eg[r] = eg_s[(size_t)q * L + l];
+            }
         }
         sk[w][l] = act[r] ? lo[r] : -1;
     }
@@ -189,15 +232,17 @@ levelwise_step_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t
         const int nhi = __shfl_sync(kFullLw, src_r ? hi[1] : hi[0], src_lane);
         const int mid = nlo + (nhi - nlo) / 2;
         float gl, gr;
-        node_sums<DP>(xq, Xt, dp, q, nlo, mid, nhi, kp, lane, gl, gr);
-        evals += (unsigned long long)(nhi - nlo);
+        node_sums<DP>(xq, Xt, dp, q, nlo, mid, g_s ? mid : nhi, kp, lane, gl, gr);
+        evals += (unsigned long long)((g_s ? mid : nhi) - nlo);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             if (act[r] && lo[r] == nlo) {
                 const uint32_t l = (uint32_t)(lane + 32 * r);
                 const uint4 blk = draw_block(kp.seed, i, l, (uint32_t)lev);
-                if (descend_decide(gl, gr, block_word(blk, (uint32_t)lev), kp.flag_eps, f[r])) lo[r] = mid;
-                else hi[r] = mid;
+                const uint32_t word = block_word(blk, (uint32_t)lev);
+                const int right = g_s ? carried_decide(gl, g[r], eg[r], word, kp.flag_eps, f[r])
+                                      : descend_decide(gl, gr, word, kp.flag_eps, f[r]);
+                if (right) lo[r] = mid; else hi[r] = mid;
             }
         }
     }
@@ -208,6 +253,10 @@ levelwise_step_kernel(const float* __restrict__ Xt, int n, int dp, const int32_t
             lo_s[(size_t)q * L + l] = lo[r];
             hi_s[(size_t)q * L + l] = hi[r];
             flags[(size_t)q * L + l] = f[r];
+            if (g_s) {
+                g_s[(size_t)q * L + l] = g[r];
+                eg_s[(size_t)q * L + l] = eg[r];
+            }
         }
     }
     if (lane == 0) atomicAdd(n_evals, evals);
@@ -244,23 +293,27 @@ __global__ void levelwise_finish_kernel(const float* __restrict__ Xt, int n, int
 }
 
 template <int DP>
-cudaError_t launch_levels(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
+cudaError_t launch_levels(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples, int carried,
                           cudaStream_t s, int64_t* launches) {
     const auto& ws = t->ws;
     const int n = (int)t->n;
-    // the per-sample node ranges live in the item arrays, unused by this schedule
+    // the per-sample node ranges live in the item arrays, unused by this
+    // schedule; the carried sums and their error bounds in the leaf outputs,
+    // which the finish kernel writes only after the last level
     int32_t* lo_s = ws.qitem_bin;
     int32_t* hi_s = reinterpret_cast<int32_t*>(ws.qitem_mask);
+    float* g_s = carried ? ws.ksmp : nullptr;
+    float* eg_s = carried ? reinterpret_cast<float*>(ws.leaf_pos) : nullptr;
     unsigned long long* ev = reinterpret_cast<unsigned long long*>(&ws.stats->n_evals);
     const int grid = (n + 3) / 4;
     levelwise_root_kernel<DP><<<grid, 128, 0, s>>>(t->Xt, n, t->dp, t->perm, kp, with_samples, lo_s, hi_s,
-                                                   ws.flags, d_deg, ws.degf, ev);
+                                                   ws.flags, d_deg, ws.degf, ev, g_s, eg_s);
     cudaError_t e = cudaGetLastError();
     *launches += 1;
     if (!with_samples) return e;
     for (int lev = 1; lev < t->depth && e == cudaSuccess; ++lev) {
         levelwise_step_kernel<DP><<<grid, 128, 0, s>>>(t->Xt, n, t->dp, t->perm, kp, lev, lo_s, hi_s, ws.flags,
-                                                       ws.degf, ev);
+                                                       ws.degf, ev, g_s, eg_s);
         e = cudaGetLastError();
         *launches += 1;
     }
@@ -278,13 +331,13 @@ cudaError_t launch_levels(const fsg_tree* t, const KernelParams& kp, double* d_d
 // The whole descent (or, without samples, the degrees alone) by the levelwise
 // schedule.  Statistics: n_evals counts every kernel evaluation executed.
 cudaError_t launch_levelwise(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
-                             cudaStream_t s, int64_t* launches) {
+                             int carried, cudaStream_t s, int64_t* launches) {
     switch (t->dp) {
-        case 4: return launch_levels<4>(t, kp, d_deg, with_samples, s, launches);
-        case 8: return launch_levels<8>(t, kp, d_deg, with_samples, s, launches);
-        case 12: return launch_levels<12>(t, kp, d_deg, with_samples, s, launches);
-        case 16: return launch_levels<16>(t, kp, d_deg, with_samples, s, launches);
-        default: return launch_levels<0>(t, kp, d_deg, with_samples, s, launches);
+        case 4: return launch_levels<4>(t, kp, d_deg, with_samples, carried, s, launches);
+        case 8: return launch_levels<8>(t, kp, d_deg, with_samples, carried, s, launches);
+        case 12: return launch_levels<12>(t, kp, d_deg, with_samples, carried, s, launches);
+        case 16: return launch_levels<16>(t, kp, d_deg, with_samples, carried, s, launches);
+        default: return launch_levels<0>(t, kp, d_deg, with_samples, carried, s, launches);
     }
 }
 

@@ -31,7 +31,7 @@ FSG_TWO_SIGMA_SQ, FSG_SIGMA_SQ = 0, 1
 FSG_SELF_EXCLUDE, FSG_SELF_INCLUDE = 0, 1
 FSG_PREC_AUTO, FSG_PREC_FP32, FSG_PREC_SPLIT_BF16, FSG_PREC_EXACT_INT = 0, 1, 2, 3
 FSG_EDGES_SET, FSG_EDGES_MULTI = 0, 1
-FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE = 0, 1
+FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE, FSG_SCHED_CARRIED = 0, 1, 2
 FSG_ADMIT_ARRIVAL, FSG_ADMIT_RESPONSE_RATIO = 0, 1
 
 # Names every build of the library must export (checked by the CPU tests

@@ -132,3 +132,28 @@ def test_levelwise_refuses_tensor_core_precision(fsg):
         fsg.fsg_degrees(tree, fsg.params(1.0, precision=fsg.FSG_PREC_EXACT_INT, schedule=fsg.FSG_SCHED_LEVELWISE))
     assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
     tree.close()
+
+
+@pytest.mark.parametrize("n,d,sigma,L,seed", [
+    (2000, 2, 0.1, 32, 0),
+    (1500, 10, 1.5, 64, 1),
+    (777, 17, 1.5, 7, 2),
+])
+def test_carried_denominator_variant(fsg, n, d, sigma, L, seed):
+    # only the left half is summed below the root; g_R = g_node - g_L is
+    # carried, and its error bound widens the flag tolerance: the oracle's
+    # samples wherever no decision was flagged, with fewer evaluations
+    X = inputs.two_moons(n=n, seed=seed) if d == 2 else inputs.gaussian_mixture(n=n, d=d, k=5, box=3.0, seed=seed)
+    gam = ora.gamma(sigma)
+    cv = run(fsg, X, sigma, L, seed, fsg.FSG_SCHED_CARRIED)
+    lw = run(fsg, X, sigma, L, seed, fsg.FSG_SCHED_LEVELWISE)
+    o = ora.build_graph(X, gam, L, seed)
+    err = np.abs(cv["deg"] - o["deg"])
+    assert (err <= DEG_RTOL * o["deg"] + n * TINY).all()
+    assert not ((cv["samples"] != o["samples"]) & (cv["flags"] == 0)).any()
+    both = (cv["flags"] == 0) & (lw["flags"] == 0)
+    np.testing.assert_array_equal(cv["samples"][both], lw["samples"][both])
+    st = cv["stats"]
+    assert st["status"] == 0 and st["n_samples"] == n * L
+    assert st["n_flagged"] <= 0.05 * n * L
+    assert n * n <= st["n_evals"] < lw["stats"]["n_evals"]
