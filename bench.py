@@ -297,11 +297,15 @@ def run_ours(args):
                 "algorithmic_gevals_per_s": n * n / (kde_avg * 1e-3) / 1e9,
                 "peak_basis": f"{SM_COUNT} SMs x min({FP32_LANES_PER_SM} FP32 lanes/{ops} lane-ops per evaluation, "
                               f"{MUFU_EX2_PER_SM} ex2) x {SM_MAX_MHZ:.0f} MHz"}
+    # DRAM bytes per launch of the dominant kernel, from the committed ncu
+    # summary of this workload at full size (null for other workloads)
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "kde_bins_traffic.json")
-    if os.path.exists(tfile):
+    tfile = os.path.join(ROOT, "profiles", "kde_bins_sym_traffic_gmm_n100000_d10.md")
+    if os.path.exists(tfile) and not split and d == 10 and n == 100_000 and not WORKLOAD["workload"].startswith("digit"):
         with open(tfile) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+            for line in f:
+                if line.startswith("bytes_per_launch:"):
+                    traffic = int(line.split(":")[1])
 
     # the plain FP32 exact GPU path (levelwise schedule) on the same input, same clocks regime
     def run_plain(schedule):
