@@ -143,18 +143,29 @@ def replica_throughput(units_per_rank: int, world: int, ms: float) -> float:
     return world * units_per_rank / (ms * 1e-3)
 
 
-def cpu_oracle_throughput(X, n_queries: int, L: int, sigma: float, seed: int):
+def cpu_oracle_throughput(X, n_queries: int, L: int, sigma: float, seed: int, keep: dict = None):
     """The oracle (as it stands) on a bounded sample: the descent of every
     sample of n_queries points plus their degrees, on all host cores.
-    Returns (sampled edges/s, seconds, threads)."""
+    Returns (sampled edges/s, seconds, threads); `keep` receives the sampled
+    query indices and their FP64 degrees."""
     import oracle as ora
     gam = ora.gamma(sigma)
     q = np.arange(n_queries, dtype=np.int64) * (X.shape[0] // n_queries)
     t0 = time.perf_counter()
     ora.sample(X, gam, L, seed, queries=q)
-    ora.degrees(X, gam, queries=q)
+    deg = ora.degrees(X, gam, queries=q)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep["q"], keep["deg"] = q, deg
     return n_queries * L / dt, dt, ora.num_threads()
+
+
+def kde_error(deg_gpu, ref) -> dict:
+    """Relative error of GPU degrees against the oracle's FP64 degrees."""
+    q, want = ref["q"], ref["deg"]
+    rel = np.abs(np.asarray(deg_gpu)[q] - want) / want
+    return {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(q.size),
+            "kind": "degrees (Eq. 1 over all points) vs the FP64 oracle"}
 
 
 def run_reference(args):
@@ -260,6 +271,7 @@ def run_ours(args):
     ms = statistics.mean(step_ms)
     st = fsg.stats_dict(bufs)
     m = int(bufs.m.item())
+    deg_main = bufs.deg.cpu().numpy()  # the timed path's degrees (the comparison runs below reuse bufs)
     ms = max_over_ranks(ms, device="cuda")
     value = replica_throughput(n * L, world, ms)
     evals_per_step = st["n_evals"]
@@ -359,8 +371,33 @@ def run_ours(args):
                "d2h_bytes_per_step": int(8 + mm * 12), "ms_per_step": e2e_s * 1e3}
 
     cpu = None
+    err = split_cmp = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed)
+        ref = {}
+        v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed, keep=ref)
+        err = kde_error(deg_main, ref)
+        if not split and not on_tc and d <= 64 and args.plain_steps > 0:
+            # the split-precision path on the same tree and input, beside the FP32 path
+            ps = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16)
+            fsg.fsg_build_graph(tree, ps, L, seed, bufs=bufs, stream=stream)  # warm-up
+            sms = []
+            for _ in range(max(3, args.plain_steps)):
+                with torch.cuda.stream(stream):
+                    flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fsg.fsg_tree_update(tree, pts, stream=stream)
+                fsg.fsg_build_graph(tree, ps, L, seed, bufs=bufs, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                sms.append(e0.elapsed_time(e1))
+            assert fsg.fsg_sync(tree, stream=stream) == 0
+            sst = fsg.stats_dict(bufs)
+            st_ms = statistics.mean(sms)
+            split_cmp = {"precision": "split (three-part BF16 tcgen05 bin pass, identity tree order)",
+                         "value": n * L / (st_ms * 1e-3), "unit": UNIT, "ms_per_step": st_ms,
+                         "flagged_samples": sst["n_flagged"], "flag_eps": 2.0 ** -10,
+                         "kde_error": kde_error(bufs.deg.cpu().numpy(), ref)}
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_queries} of the {n} query points (all {L} samples each + their degrees), "
                          f"{dt:.1f} s, extrapolated per sampled edge"}
@@ -374,6 +411,7 @@ def run_ours(args):
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
+                "kde_error": err, "split_precision": split_cmp,
                 "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "carried_fp32_gpu": carried,
                 "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

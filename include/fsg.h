@@ -64,7 +64,7 @@ extern "C" {
 /* Arithmetic of the kernel evaluations. */
 #define FSG_PREC_AUTO 0         /* FP32 for d <= 16; tensor-core form for large d */
 #define FSG_PREC_FP32 1         /* FP32 direct differences + ex2 on every d       */
-#define FSG_PREC_SPLIT_BF16 2   /* 17 <= d <= 64: centred tiles, 3-part BF16     */
+#define FSG_PREC_SPLIT_BF16 2   /* d <= 64: centred tiles, 3-part BF16           */
                                 /* split, six tcgen05 products, FP32 accumulate; */
                                 /* use with fsg_spatial_order (bin pass only:    */
                                 /* the leaf phase stays FP32)                    */

@@ -1,6 +1,6 @@
 // Split-precision tensor-core bin pass (FSG_PREC_SPLIT_BF16) for FP32 data,
-// 17 <= d <= 64: the bin sums of Eq. 1 for every query, like the other bin
-// passes, with the dot products on the tensor cores.
+// d <= 64: the bin sums of Eq. 1 for every query, like the other bin passes,
+// with the dot products on the tensor cores.
 //
 // CTA = one tile of 128 queries (128 consecutive tree positions) x one chunk
 // of bins.  Both operands are centred at the query tile's centre c (the mean
@@ -317,11 +317,9 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
 
 }  // namespace
 
-// d in 17..64; every bin of at least 32 points, so at most one bin ends in the
-// 32 columns of an epilogue step.
-bool kde_bins_split_supported(const fsg_tree* t) {
-    return t->d > kMaxFmaDim && t->d <= kSpDim && t->n / t->nb >= 32;
-}
+// d <= 64 (coordinates zero-padded to 64); every bin of at least 32 points, so
+// at most one bin ends in the 32 columns of an epilogue step.
+bool kde_bins_split_supported(const fsg_tree* t) { return t->d <= kSpDim && t->n / t->nb >= 32; }
 
 cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const int qblocks = (int)((t->n + kSpM - 1) / kSpM);

@@ -49,6 +49,8 @@ def run(fsg, X, perm, sigma, L, seed, precision, edge_mode=0, self_mode=0):
 
 @pytest.mark.parametrize("n,d,sigma,L,seed", [
     (3000, 64, 1.5, 32, 0),    # the mixture workload's dimension
+    (5000, 10, 1.5, 64, 3),    # d <= 16: the FP32 leaf finish of that range behind it
+    (2000, 2, 0.1, 32, 4),     # two moons's dimension
     (2777, 33, 1.5, 24, 1),    # ragged n, padded coordinates
     (4100, 17, 1.0, 64, 2),    # the smallest split dimension, full sample mask
 ])
@@ -111,7 +113,7 @@ def test_split_include_self_and_multi(fsg):
 
 
 def test_split_refused_outside_its_range(fsg):
-    for d in (16, 65):
+    for d in (65,):
         X = inputs.gaussian_mixture(n=1000, d=d, seed=1)
         tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
         with pytest.raises(fsg.FsgError) as e:
