@@ -645,7 +645,7 @@ def main():
     ap.add_argument("--plain-requests", type=int, default=40, help="serving: closed-loop burst for the plain path")
     ap.add_argument("--admission", choices=["arrival", "ratio"], default="arrival", help="serving: admission order")
     ap.add_argument("--precision", choices=["auto", "split"], default="auto",
-                    help="mixture workload, 17 <= d <= 64: split-precision tensor-core bin pass on a spatial tree order")
+                    help="mixture workload, d <= 64: split-precision tensor-core bin pass on a spatial tree order")
     args = ap.parse_args()
     if args.n:
         set_size(args.n)
