@@ -145,8 +145,8 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
  * original index); nodes of at most `leaf` points keep original-index order.
  * The KDE, the degrees and the sampling distribution do not depend on the
  * order (Eq. 1); sample identities under given Philox draws do, as they do on
- * any permutation.  FSG_PREC_SPLIT_BF16 centres its tiles on it (more
- * accurate when tiles are compact).
+ * any permutation.  FSG_PREC_SPLIT_BF16 centres each query tile at its mean,
+ * which cancels less when the tile is a compact group.
  *   h_points : host float32 [n][d], finite.   h_perm : host int32 [n] out,
  *   position -> original index.   Deterministic.
  * Errors: INVALID_ARG (null pointer, n or d out of range, leaf < 1, a
