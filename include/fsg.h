@@ -117,6 +117,9 @@ typedef struct {
     int64_t n_items;       /* distinct (query, node) pairs in the leaf finish   */
     int64_t n_edges;       /* edges written                                     */
     int64_t status;        /* device status word (FSG_OK or FSG_ERR_TIMEOUT)    */
+    int64_t n_bin_evals;   /* of n_evals, those of the bin pass (the split pass */
+                           /* skips tile pairs whose values are all zero)       */
+    int64_t reserved;
 } fsg_stats;
 
 /* Library version string and a description of a status code. */
@@ -163,8 +166,11 @@ int fsg_tree_info(const fsg_tree* tree, int64_t* n, int32_t* d, int32_t* depth);
  * executes on this tree with these parameters (a diagnostic for roofline
  * accounting; Eq. 1 needs n^2 of them).  n^2 for the plain, generic-d and
  * tensor-core passes; (n^2 + sum_k S_k^2) / 2 for the symmetric FP32 pass,
- * S_k the point counts of its blocks of bins.  0 for the levelwise schedule,
- * which counts its own evaluations on the device (fsg_stats.n_evals).
+ * S_k the point counts of its blocks of bins; for the split pass n^2 is an
+ * upper bound (it skips tile pairs whose values are all zero in FP32 and
+ * counts what it executes in fsg_stats.n_bin_evals).  0 for the levelwise
+ * schedules, which count their own evaluations on the device
+ * (fsg_stats.n_evals).
  *   evals : host int64, written on success.
  * Errors: INVALID_ARG.
  */

@@ -179,6 +179,18 @@ void workspace_sizes(int64_t n, int d, int dm, int nb, int64_t Lc, size_t (&sz)[
 }
 }  // namespace
 
+// The split-precision pass's bin boxes (allocated on first use).
+int ensure_split(fsg_tree* t, const fsg_params* p, cudaStream_t s) {
+    if (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED || t->sboxes) return FSG_OK;
+    const size_t qblocks = (size_t)((t->n + 127) / 128);  // bin boxes, then the 128-position tiles' boxes
+    if (tree_malloc(t, (void**)&t->sboxes, sizeof(float) * ((size_t)t->nb + qblocks) * 128, s) != cudaSuccess) {
+        cudaGetLastError();
+        t->sboxes = nullptr;
+        return FSG_ERR_OOM;
+    }
+    return FSG_OK;
+}
+
 int ensure_workspace(fsg_tree* t, int L, cudaStream_t s) {
     Workspace& ws = t->ws;
     if (ws.base && ws.cap_n >= t->n && ws.cap_L >= L) return FSG_OK;
@@ -371,6 +383,7 @@ void fsg_free_tree(fsg_tree* t) {
     tree_free(t, t->status);
     tree_free(t, t->ws.base);
     tree_free(t, t->Xtt);
+    tree_free(t, t->sboxes);
     if (t->Xb) cudaFree(t->Xb);
     if (t->norms) cudaFree(t->norms);
     delete t;
@@ -427,6 +440,7 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
     if ((rc = check_path(t, p)) != FSG_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
     if (p->schedule != FSG_SCHED_FUSED) {  // the levelwise schedule has no shapes to choose
         to_public(t->tune, out);
         return FSG_OK;
@@ -612,14 +626,16 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
 // Evaluations of the bin pass (every query against every point), counted on
 // the host; the levelwise schedule counts its own on the device.
 static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
-    return p->schedule != FSG_SCHED_FUSED ? 0 : bin_pass_evals(t, p->precision);
+    if (p->schedule != FSG_SCHED_FUSED || p->precision == FSG_PREC_SPLIT_BF16) return 0;
+    return bin_pass_evals(t, p->precision);
 }
 
 // Statistics known on the host: samples run, bin-pass evaluations.
 __global__ static void stats_finish_kernel(fsg_stats* st, int64_t n_samples, int64_t bin_evals,
                                            const int32_t* status, fsg_stats* out) {
     st->n_samples = n_samples;
-    st->n_evals += bin_evals;
+    st->n_evals += bin_evals;       // the split pass counts its own on the device
+    st->n_bin_evals += bin_evals;
     st->status = status[0];
     if (out) *out = *st;
 }
@@ -631,6 +647,7 @@ int fsg_degrees(fsg_tree* t, const fsg_params* p, double* d_deg, void* stream) {
     if ((rc = check_path(t, p)) != FSG_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, 1, s)) != FSG_OK) return rc;
+    if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, 1, 0);
     begin_call(t);
     cudaError_t e;
@@ -660,6 +677,7 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
     if ((rc = check_path(t, p)) != FSG_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, L, seed);
     begin_call(t);
     if ((rc = run_sampling(t, kp, p->schedule, nullptr, s)) != FSG_OK) return rc;
@@ -687,6 +705,7 @@ int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, 
     if ((rc = check_path(t, p)) != FSG_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, L, seed);
     begin_call(t);
     if ((rc = run_sampling(t, kp, p->schedule, d_deg, s)) != FSG_OK) return rc;

@@ -92,6 +92,8 @@ struct fsg_tree {
     // layout [k][132] and duplicated point layout [k][130][2] per tile, k
     // padded to a multiple of 32), refreshed by every generic bin pass
     float* Xtt = nullptr;
+    // split-precision pass: per bin, the bounding box of its points ([nb][2][64])
+    float* sboxes = nullptr;
     alignas(64) unsigned char tmap_a[128] = {};
     alignas(64) unsigned char tmap_b[128] = {};
     alignas(64) unsigned char tmap_p[128] = {};  // 16-row boxes: point rows of the tensor-core leaf kernel

@@ -44,6 +44,7 @@ constexpr int kSpThreads = 32 * (5 + kSpEpiWarps);
 constexpr int kSpMaxBins = 24;        // bins per chunk
 constexpr uint32_t kPart = 128u * 128u;  // one part of 128 rows x 64 BF16 (128-byte swizzled rows)
 constexpr uint32_t kTmemCols = 256;   // two 128-column accumulators
+constexpr int kSpMaxTiles = 252;      // point tiles per CTA (kept list)
 
 struct SpLayout {
     static constexpr uint32_t A = 0;                                      // [3][128 rows]
@@ -54,7 +55,10 @@ struct SpLayout {
     static constexpr uint32_t BARS = CEN + kSpDim * 4;                    // full[2] empty[2] tfull[2] tempty[2] fin
     static constexpr uint32_t SLOT = BARS + (2 * kSpStages + 5) * 8;      // TMEM slot, abort flag
     static constexpr uint32_t BND = SLOT + 16;                            // [kSpMaxBins + 1]
-    static constexpr uint32_t PN = (BND + 112 + 15) & ~15u;               // [8 warps][64] norms of a warp's columns
+    static constexpr uint32_t QLO = (BND + 112 + 15) & ~15u;              // [64] query tile's box: low corner
+    static constexpr uint32_t QHI = QLO + kSpDim * 4;                     // [64] high corner
+    static constexpr uint32_t TL = QHI + kSpDim * 4;                      // [kSpMaxTiles] kept point tiles, count
+    static constexpr uint32_t PN = TL + (kSpMaxTiles + 4) * 4;            // [8 warps][64] norms of a warp's columns
     static constexpr uint32_t OUTS = PN + kSpEpiWarps * 64 * 4;           // [2 halves][128][bpc]
     static constexpr uint32_t total(int bpc) { return OUTS + 2u * kSpM * (uint32_t)bpc * 4u; }
 };
@@ -123,8 +127,10 @@ __device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], bool v
 
 __global__ void __launch_bounds__(kSpThreads, 1)
 kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const int32_t* __restrict__ bnd, int nb,
-                      int bpc, float neg_c, int self_exclude, float* __restrict__ binsum,
-                      int32_t* __restrict__ status) {
+                      int bpc, float neg_c, int self_exclude, const float* __restrict__ boxes,
+                      const float* __restrict__ qboxes,
+                      float* __restrict__ binsum, unsigned long long* __restrict__ n_evals,
+                      unsigned long long* __restrict__ n_bin_evals, int32_t* __restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     unsigned char* sA = base + SpLayout::A;
@@ -141,13 +147,77 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
     volatile int32_t* abort_flag = reinterpret_cast<int32_t*>(base + SpLayout::SLOT + 4);
     int32_t* bnd_s = reinterpret_cast<int32_t*>(base + SpLayout::BND);
     float* pn_all = reinterpret_cast<float*>(base + SpLayout::PN);
+    float* qlo = reinterpret_cast<float*>(base + SpLayout::QLO);
+    float* qhi = reinterpret_cast<float*>(base + SpLayout::QHI);
+    int32_t* tl = reinterpret_cast<int32_t*>(base + SpLayout::TL);  // kept tiles; tl[kSpMaxTiles] = their count
     float* outs = reinterpret_cast<float*>(base + SpLayout::OUTS);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q0 = blockIdx.x * kSpM;
     const int b0 = blockIdx.y * bpc;
     const int nbc = min(nb, b0 + bpc) - b0;
+    const int nqv = min(kSpM, n - q0);  // queries of this tile
     if (tid <= nbc) bnd_s[tid] = bnd[b0 + tid];
+    if (tid < kSpDim) {  // the query tile's bounding box
+        qlo[tid] = qboxes[(size_t)blockIdx.x * 128 + tid];
+        qhi[tid] = qboxes[(size_t)blockIdx.x * 128 + 64 + tid];
+    }
+    __syncthreads();
+    const int pa = bnd_s[0], pe = bnd_s[nbc];
+    const int ntall = (pe - pa + kSpN - 1) / kSpN;
+    // Point tiles whose every kernel value is exactly zero in FP32 are skipped:
+    // when the gap between the query tile's box and the union of the boxes of
+    // the tile's bins puts neg_c * d^2 below -128, every ex2 is below 2^-126
+    // and flushes to +0 (two units of margin over the rounding of d^2), so the
+    // bin sums are the same bit for bit.  The chunk's bin boxes are staged in
+    // the (not yet used) output buffer; warp w tests tiles w, w + 13, ... with
+    // its lanes over the coordinates; warp 0 lists the kept tiles in order.
+    float* bx = outs;  // [nbc][128]: low corner, high corner
+    for (int e = tid; e < nbc * 128; e += kSpThreads) bx[e] = boxes[(size_t)b0 * 128 + e];
+    __syncthreads();
+    for (int t = warp; t < ntall; t += kSpThreads / 32) {
+        const int ps = pa + t * kSpN, pq = min(pe, ps + kSpN);
+        int bf = 0;  // the tile's bins are bf .. bl (consecutive)
+        while (bf + 1 < nbc && bnd_s[bf + 1] <= ps) ++bf;
+        int bl = bf;
+        while (bl + 1 < nbc && bnd_s[bl + 1] < pq) ++bl;
+        float d2 = 0.f;
+        for (int c = lane; c < d; c += 32) {
+            float lo = bx[bf * 128 + c], hi = bx[bf * 128 + 64 + c];
+            for (int b = bf + 1; b <= bl; ++b) {
+                lo = fminf(lo, bx[b * 128 + c]);
+                hi = fmaxf(hi, bx[b * 128 + 64 + c]);
+            }
+            const float gap = fmaxf(0.f, fmaxf(lo - qhi[c], qlo[c] - hi));
+            d2 = fmaf(gap, gap, d2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        if (lane == 0 && t < kSpMaxTiles) tl[t] = !(neg_c * d2 < -128.f);  // keep flag, compacted below
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int kept = 0;
+        for (int t0 = 0; t0 < ntall; t0 += 32) {
+            const int t = t0 + lane;
+            const bool keep = t < ntall && tl[t] != 0;
+            const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();  // every lane has read its flag before any is overwritten
+            if (keep) tl[kept + __popc(bal & ((1u << lane) - 1u))] = t;
+            kept += __popc(bal);
+            __syncwarp();
+        }
+        if (lane == 0) tl[kSpMaxTiles] = kept;
+    }
+    __syncthreads();
+    const int ntile = tl[kSpMaxTiles];  // tiles processed (the list's order is the tiles' order)
+    if (ntile == 0) {  // every value of this CTA is zero: its bin sums are 0, nothing else to do
+        for (int e = tid; e < nqv * nbc; e += kSpThreads) {
+            const int ql = e / nbc, b = e - ql * nbc;
+            binsum[(size_t)(q0 + ql) * nb + b0 + b] = 0.f;
+        }
+        return;
+    }
     for (int e = tid; e < 2 * kSpM * bpc; e += kSpThreads) outs[e] = 0.f;
     if (tid == 0) {
         for (int s = 0; s < kSpStages; ++s) {
@@ -170,11 +240,10 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
     }
     // centre of the query tile (its points' mean; any centre is exact, a near one is accurate)
     if (tid < kSpDim) {
-        const int nq = min(kSpM, n - q0);
         float c = 0.f;
         if (tid < d) {
-            for (int r = 0; r < nq; ++r) c += Xt[(size_t)(q0 + r) * dp + tid];
-            c /= (float)nq;
+            for (int r = 0; r < nqv; ++r) c += Xt[(size_t)(q0 + r) * dp + tid];
+            c /= (float)nqv;
         }
         cen[tid] = c;
     }
@@ -191,16 +260,13 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-
-    const int pa = bnd_s[0], pe = bnd_s[nbc];
-    const int ntile = (pe - pa + kSpN - 1) / kSpN;
     int mma_issued = 0;
 
     if (warp < 4) {
         // ---- producers: point tile t into stage t % 2; the next tile's row is
         // loaded while this thread waits for its stage to be free
         float4 x[kSpDim / 4];
-        int p = pa + tid;
+        int p = ntile > 0 ? pa + tl[0] * kSpN + tid : pe;
         load_row(Xt, dp, p < pe ? p : -1, x);
         for (int t = 0; t < ntile && !*abort_flag; ++t) {
             const int s = t % kSpStages;
@@ -211,8 +277,10 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
             cn[s * kSpN + tid] = split_row(x, p < pe, cen, sB + (uint32_t)s * kSpParts * kPart, tid);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full[s]);
-            p += kSpN;
-            if (t + 1 < ntile) load_row(Xt, dp, p < pe ? p : -1, x);
+            if (t + 1 < ntile) {
+                p = pa + tl[t + 1] * kSpN + tid;
+                load_row(Xt, dp, p < pe ? p : -1, x);
+            }
         }
     } else if (warp == 4) {
         if (lane == 0) {
@@ -263,7 +331,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
                 break;
             }
             tc_fence_after();
-            const int c0 = pa + t * kSpN + half * kCols;  // first point of this warp's columns
+            const int c0 = pa + tl[t] * kSpN + half * kCols;  // first point of this warp's columns
             __syncwarp();
             pn[lane] = cn[s * kSpN + half * kCols + lane];
             pn[lane + 32] = cn[s * kSpN + half * kCols + lane + 32];
@@ -298,6 +366,12 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
     __syncthreads();
     if (!*abort_flag) {
         const int nq = min(kSpM, n - q0);
+        if (tid == 0) {  // evaluations executed: the kept tiles' points against the tile's queries
+            unsigned long long pts = 0;
+            for (int j = 0; j < ntile; ++j) pts += (unsigned long long)(min(pe, pa + (tl[j] + 1) * kSpN) - (pa + tl[j] * kSpN));
+            atomicAdd(n_evals, pts * (unsigned long long)nq);
+            atomicAdd(n_bin_evals, pts * (unsigned long long)nq);
+        }
         for (int e = tid; e < nq * nbc; e += kSpThreads) {
             const int ql = e / nbc, b = e - ql * nbc;
             binsum[(size_t)(q0 + ql) * nb + b0 + b] = outs[ql * bpc + b] + outs[(kSpM + ql) * bpc + b];
@@ -315,6 +389,42 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
     }
 }
 
+// Per bin, the bounding box of its points (coordinates past d are 0): block
+// b, thread = coordinate.
+__global__ void bin_boxes_kernel(const float* __restrict__ Xt, int dp, int d, const int32_t* __restrict__ bnd,
+                                 float* __restrict__ boxes) {
+    const int b = blockIdx.x, c = threadIdx.x;
+    float lo = 0.f, hi = 0.f;
+    if (c < d) {
+        const int p0 = bnd[b], p1 = bnd[b + 1];
+        lo = hi = Xt[(size_t)p0 * dp + c];
+        for (int p = p0 + 1; p < p1; ++p) {
+            const float x = Xt[(size_t)p * dp + c];
+            lo = fminf(lo, x);
+            hi = fmaxf(hi, x);
+        }
+    }
+    boxes[(size_t)b * 128 + c] = lo;
+    boxes[(size_t)b * 128 + 64 + c] = hi;
+}
+
+// Per tile of 128 consecutive tree positions, the bounding box of its points.
+__global__ void tile_boxes_kernel(const float* __restrict__ Xt, int dp, int d, int n, float* __restrict__ boxes) {
+    const int tb = blockIdx.x, c = threadIdx.x;
+    float lo = 0.f, hi = 0.f;
+    if (c < d) {
+        const int p0 = tb * kSpM, p1 = min(n, p0 + kSpM);
+        lo = hi = Xt[(size_t)p0 * dp + c];
+        for (int p = p0 + 1; p < p1; ++p) {
+            const float x = Xt[(size_t)p * dp + c];
+            lo = fminf(lo, x);
+            hi = fmaxf(hi, x);
+        }
+    }
+    boxes[(size_t)tb * 128 + c] = lo;
+    boxes[(size_t)tb * 128 + 64 + c] = hi;
+}
+
 }  // namespace
 
 // d <= 64 (coordinates zero-padded to 64); every bin of at least 32 points, so
@@ -328,6 +438,8 @@ cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cud
     if (chunks > t->nb) chunks = t->nb;
     int bpc = (t->nb + chunks - 1) / chunks;
     if (bpc > kSpMaxBins) bpc = kSpMaxBins;
+    while (bpc > 1 && ((int64_t)bpc * t->mmax + kSpN - 1) / kSpN > kSpMaxTiles) --bpc;  // the kept-tile list
+    if (((int64_t)bpc * t->mmax + kSpN - 1) / kSpN > kSpMaxTiles) return cudaErrorInvalidValue;
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = 1024 + SpLayout::total(bpc);
     static bool attr = false;
@@ -337,9 +449,15 @@ cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cud
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    if (!t->sboxes) return cudaErrorInvalidValue;
+    float* qboxes = t->sboxes + (size_t)t->nb * 128;  // after the bin boxes: [qblocks][2][64]
+    bin_boxes_kernel<<<t->nb, kSpDim, 0, s>>>(t->Xt, t->dp, t->d, t->bnd, t->sboxes);
+    tile_boxes_kernel<<<qblocks, kSpDim, 0, s>>>(t->Xt, t->dp, t->d, (int)t->n, qboxes);
     dim3 grid(qblocks, chunks);
-    kde_bins_split_kernel<<<grid, kSpThreads, smem, s>>>(t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc,
-                                                          kp.neg_c, kp.self_exclude, t->ws.binsum, t->status);
+    kde_bins_split_kernel<<<grid, kSpThreads, smem, s>>>(
+        t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc, kp.neg_c, kp.self_exclude, t->sboxes, qboxes, t->ws.binsum,
+        reinterpret_cast<unsigned long long*>(&t->ws.stats->n_evals),
+        reinterpret_cast<unsigned long long*>(&t->ws.stats->n_bin_evals), t->status);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,8 @@ class fsg_result(ctypes.Structure):
                 ("queue_ms", ctypes.c_double)]
 
 
-STATS_FIELDS = ["n_samples", "n_flagged", "n_self", "n_empty", "n_evals", "n_items", "n_edges", "status"]
+STATS_FIELDS = ["n_samples", "n_flagged", "n_self", "n_empty", "n_evals", "n_items", "n_edges", "status",
+                "n_bin_evals", "reserved"]
 
 
 class fsg_stats(ctypes.Structure):

@@ -93,4 +93,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(fsg.fsg_result) == 48
     assert ctypes.sizeof(fsg.fsg_params) == 48
     assert ctypes.sizeof(fsg.fsg_tree_opts) == 32
-    assert ctypes.sizeof(fsg.fsg_stats) == 64
+    assert ctypes.sizeof(fsg.fsg_stats) == 80

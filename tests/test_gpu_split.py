@@ -126,3 +126,21 @@ def test_split_refused_outside_its_range(fsg):
         fsg.fsg_degrees(tree, fsg.params(1.5, precision=fsg.FSG_PREC_SPLIT_BF16, schedule=fsg.FSG_SCHED_LEVELWISE))
     assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
     tree.close()
+
+
+def test_split_skips_zero_tiles_exactly(fsg):
+    # four clusters far apart (box 60, sigma 1.5): on the spatial order most
+    # tile pairs have every value below 2^-126 and are skipped, which must not
+    # change any sum: every degree within the stated bound of the oracle, the
+    # oracle's samples wherever no decision was flagged
+    X = inputs.gaussian_mixture(n=4096, d=32, k=4, box=60.0, seed=11)
+    perm = fsg.fsg_spatial_order(X)
+    gam = ora.gamma(1.5)
+    g = run(fsg, X, perm, 1.5, 16, 3, fsg.FSG_PREC_SPLIT_BF16)
+    st = g["stats"]
+    assert st["status"] == 0 and 0 < st["n_bin_evals"] < 0.6 * 4096 * 4096
+    want = ora.degrees(X, gam)
+    assert (np.abs(g["deg"] - want) <= SPLIT_DEG_RTOL * want + 4096 * TINY).all()
+    q = np.arange(0, 4096, 5)
+    osmp, _, _ = ora.sample(X, gam, 16, 3, queries=q, perm=perm)
+    assert not ((g["samples"][q] != osmp) & (g["flags"][q] == 0)).any()
