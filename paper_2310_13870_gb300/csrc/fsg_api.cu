@@ -179,11 +179,11 @@ void workspace_sizes(int64_t n, int d, int dm, int nb, int64_t Lc, size_t (&sz)[
 }
 }  // namespace
 
-// The split-precision pass's bin boxes (allocated on first use).
+// The split-precision pass's workspace: bin and tile boxes, the query tiles'
+// split images (allocated on first use).
 int ensure_split(fsg_tree* t, const fsg_params* p, cudaStream_t s) {
     if (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED || t->sboxes) return FSG_OK;
-    const size_t qblocks = (size_t)((t->n + 127) / 128);  // bin boxes, then the 128-position tiles' boxes
-    if (tree_malloc(t, (void**)&t->sboxes, sizeof(float) * ((size_t)t->nb + qblocks) * 128, s) != cudaSuccess) {
+    if (tree_malloc(t, (void**)&t->sboxes, split_workspace_bytes(t->n, t->nb), s) != cudaSuccess) {
         cudaGetLastError();
         t->sboxes = nullptr;
         return FSG_ERR_OOM;

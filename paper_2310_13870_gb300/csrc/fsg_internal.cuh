@@ -154,6 +154,8 @@ int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);
 bool kde_bins_split_supported(const fsg_tree* t);
+// Bytes of the split-precision pass's per-tree workspace (boxes, query-tile images).
+size_t split_workspace_bytes(int64_t n, int64_t nb);
 bool leaf_fused_generic_supported(const fsg_tree* t);
 cudaError_t launch_leaf_fused_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);

@@ -16,12 +16,16 @@
 // (small terms first; mid.lo, lo.mid and lo.lo lie below 2^-24 relative).
 // Every BF16 x BF16 product is exact in FP32.
 //
+// The query side does not depend on the bin chunk: split_prep_kernel writes
+// each query tile's parts, centred norms and centre once per launch, and
+// every CTA of that tile bulk-copies the image (49,920 bytes).
+//
 // Warp roles (13 warps):
-//   warps 0-3 : producers: the query parts and norms (once), then per tile of
-//               128 points the centred, split point parts and their norms,
-//               two stages (shared-memory stores, a proxy fence, an mbarrier
-//               arrive per thread);
-//   warp 4    : TMEM allocation; one thread issues the 24 tcgen05.mma (K = 16)
+//   warps 0-3 : producers: per tile of 128 points the centred, split point
+//               parts and their norms, two stages (shared-memory stores, a
+//               proxy fence, an mbarrier arrive per thread);
+//   warp 4    : TMEM allocation; one thread issues the 6 x ceil(d / 16)
+//               tcgen05.mma (K = 16; 24 at d > 48)
 //               of a tile into one of two 128-column accumulators;
 //   warps 5-12: epilogue, two per TMEM lane quadrant (one per half of the 128
 //               columns): kernel values and bin sums, as in the 8-bit pass.
@@ -45,6 +49,10 @@ constexpr int kSpMaxBins = 24;        // bins per chunk
 constexpr uint32_t kPart = 128u * 128u;  // one part of 128 rows x 64 BF16 (128-byte swizzled rows)
 constexpr uint32_t kTmemCols = 256;   // two 128-column accumulators
 constexpr int kSpMaxTiles = 252;      // point tiles per CTA (kept list)
+// A query tile's image, written once per launch by split_prep_kernel and
+// bulk-copied by every CTA of that tile: its three swizzled parts, then the
+// centred norms of its 128 rows, then its centre.
+constexpr uint32_t kQImg = kSpParts * kPart + kSpM * 4 + kSpDim * 4;
 
 struct SpLayout {
     static constexpr uint32_t A = 0;                                      // [3][128 rows]
@@ -52,8 +60,8 @@ struct SpLayout {
     static constexpr uint32_t CN = B + kSpStages * kSpParts * kPart;      // [stages][128] point norms
     static constexpr uint32_t AN = CN + kSpStages * kSpN * 4;             // [128] query norms
     static constexpr uint32_t CEN = AN + kSpM * 4;                        // [64] centre
-    static constexpr uint32_t BARS = CEN + kSpDim * 4;                    // full[2] empty[2] tfull[2] tempty[2] fin
-    static constexpr uint32_t SLOT = BARS + (2 * kSpStages + 5) * 8;      // TMEM slot, abort flag
+    static constexpr uint32_t BARS = CEN + kSpDim * 4;                    // full[2] empty[2] tfull[2] tempty[2] fin qbar
+    static constexpr uint32_t SLOT = BARS + (2 * kSpStages + 6) * 8;      // TMEM slot, abort flag
     static constexpr uint32_t BND = SLOT + 16;                            // [kSpMaxBins + 1]
     static constexpr uint32_t QLO = (BND + 112 + 15) & ~15u;              // [64] query tile's box: low corner
     static constexpr uint32_t QHI = QLO + kSpDim * 4;                     // [64] high corner
@@ -63,6 +71,9 @@ struct SpLayout {
     static constexpr uint32_t total(int bpc) { return OUTS + 2u * kSpM * (uint32_t)bpc * 4u; }
 };
 static_assert(SpLayout::BARS % 8 == 0 && SpLayout::PN % 16 == 0 && SpLayout::B % 1024 == 0, "layout");
+static_assert(SpLayout::AN == SpLayout::CN + kSpStages * kSpN * 4 && SpLayout::CEN == SpLayout::AN + kSpM * 4 &&
+                  SpLayout::AN % 16 == 0 && kQImg % 16 == 0,
+              "the query image's norms and centre land in AN and CEN by 16-byte bulk copies");
 
 // Three BF16 parts of two values, packed (low half = a, high half = b): each
 // part the BF16 rounding of what the previous parts leave (exact residuals).
@@ -88,13 +99,15 @@ __device__ __forceinline__ void load_row(const float* __restrict__ Xt, int dp, i
 // The row centred, split and stored as three 128-byte swizzled rows at
 // parts + part * kPart; returns its squared norm.  A point's coordinates past
 // d are zero, as are the centre's, so they stay zero; `valid` = false (no
-// point) stores zero rows.
+// point) stores zero rows.  Only the first nch 16-byte chunks (coordinates
+// 0 .. 8 nch - 1) are written: the caller keeps the others zero.
 __device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], bool valid, const float* __restrict__ cen,
-                                           unsigned char* parts, int row) {
+                                           unsigned char* parts, int row, int nch = 8) {
     float norm = 0.f;
     if (!valid) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
+            if (k >= nch) break;
             const uint32_t off = (uint32_t)row * 128u + (uint32_t)((k ^ (row & 7)) << 4);
             *reinterpret_cast<uint4*>(parts + off) = make_uint4(0u, 0u, 0u, 0u);
             *reinterpret_cast<uint4*>(parts + kPart + off) = make_uint4(0u, 0u, 0u, 0u);
@@ -104,6 +117,7 @@ __device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], bool v
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {  // 16-byte chunk k = coordinates 8k .. 8k + 7
+        if (k >= nch) break;
         const float v[8] = {x[2 * k].x, x[2 * k].y, x[2 * k].z, x[2 * k].w,
                             x[2 * k + 1].x, x[2 * k + 1].y, x[2 * k + 1].z, x[2 * k + 1].w};
         float a[8];
@@ -128,7 +142,7 @@ __device__ __forceinline__ float split_row(const float4 (&x)[kSpDim / 4], bool v
 __global__ void __launch_bounds__(kSpThreads, 1)
 kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const int32_t* __restrict__ bnd, int nb,
                       int bpc, float neg_c, int self_exclude, const float* __restrict__ boxes,
-                      const float* __restrict__ qboxes,
+                      const float* __restrict__ qboxes, const unsigned char* __restrict__ qimg,
                       float* __restrict__ binsum, unsigned long long* __restrict__ n_evals,
                       unsigned long long* __restrict__ n_bin_evals, int32_t* __restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
@@ -143,6 +157,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
     uint64_t* tfull = empty + kSpStages;
     uint64_t* tempty = tfull + 2;
     uint64_t* fin = tempty + 2;
+    uint64_t* qbar = fin + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + SpLayout::SLOT);
     volatile int32_t* abort_flag = reinterpret_cast<int32_t*>(base + SpLayout::SLOT + 4);
     int32_t* bnd_s = reinterpret_cast<int32_t*>(base + SpLayout::BND);
@@ -219,6 +234,15 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
         return;
     }
     for (int e = tid; e < 2 * kSpM * bpc; e += kSpThreads) outs[e] = 0.f;
+    // Coordinates past d are zero in every part: the producers write the first
+    // nch 16-byte chunks of a row, the rest of the point stages is cleared
+    // once here, and the MMAs run only the kk K-steps of 16 that hold data.
+    const int nch = (d + 7) / 8, kk = (d + 15) / 16;
+    if (nch < 8) {
+        for (int e = tid; e < (int)(kSpStages * kSpParts * kPart / 16); e += kSpThreads)
+            reinterpret_cast<uint4*>(sB)[e] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
     if (tid == 0) {
         for (int s = 0; s < kSpStages; ++s) {
             mbar_init(&full[s], 128);                // the producers' arrivals
@@ -229,6 +253,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
             mbar_init(&tempty[a], 32 * kSpEpiWarps);
         }
         mbar_init(fin, 1);
+        mbar_init(qbar, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -238,27 +263,20 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // centre of the query tile (its points' mean; any centre is exact, a near one is accurate)
-    if (tid < kSpDim) {
-        float c = 0.f;
-        if (tid < d) {
-            for (int r = 0; r < nqv; ++r) c += Xt[(size_t)(q0 + r) * dp + tid];
-            c /= (float)nqv;
-        }
-        cen[tid] = c;
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // the query tile's parts and norms (producers, once)
-    if (tid < kSpM) {
-        const int q = q0 + tid;
-        float4 x[kSpDim / 4];
-        load_row(Xt, dp, q < n ? q : -1, x);
-        an[tid] = split_row(x, q < n, cen, sA, tid);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // the query tile's parts, norms and centre: one image, bulk-copied
+    if (tid == 0) {
+        const unsigned char* src = qimg + (size_t)blockIdx.x * kQImg;
+        mbar_arrive_expect_tx(qbar, kQImg);
+        bulk_g2s(sA, src, kSpParts * kPart, qbar);
+        bulk_g2s(an, src + kSpParts * kPart, kSpM * 4, qbar);
+        bulk_g2s(cen, src + kSpParts * kPart + kSpM * 4, kSpDim * 4, qbar);
     }
+    const bool qready = mbar_wait_bounded(qbar, 0u, status);
+    if (!qready) *abort_flag = 1;
     __syncthreads();
     int mma_issued = 0;
 
@@ -274,7 +292,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
                 *abort_flag = 1;
                 break;
             }
-            cn[s * kSpN + tid] = split_row(x, p < pe, cen, sB + (uint32_t)s * kSpParts * kPart, tid);
+            cn[s * kSpN + tid] = split_row(x, p < pe, cen, sB + (uint32_t)s * kSpParts * kPart, tid, nch);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full[s]);
             if (t + 1 < ntile) {
@@ -302,8 +320,10 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
                     const uint64_t da = sdesc(smem_u32(sA + pi[u] * kPart));
                     const uint64_t db = sdesc(smem_u32(sB + (uint32_t)s * kSpParts * kPart + pj[u] * kPart));
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)  // 32 bytes of K per MMA inside the swizzled row
+                    for (int k = 0; k < 4; ++k) {  // 32 bytes of K per MMA inside the swizzled row
+                        if (k >= kk) break;
                         umma_bf16(dt, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (u | k) != 0 ? 1u : 0u);
+                    }
                 }
                 mma_issued = 1;
                 umma_commit(&empty[s]);
@@ -377,6 +397,7 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
             binsum[(size_t)(q0 + ql) * nb + b0 + b] = outs[ql * bpc + b] + outs[(kSpM + ql) * bpc + b];
         }
     }
+    if (tid == 0 && !qready) mbar_wait_bounded(qbar, 0u, status);  // the query image copy still in flight
     if (warp == 4) {
         if (lane == 0 && mma_issued) {
             // all MMAs of this CTA must be complete before TMEM is freed
@@ -408,21 +429,44 @@ __global__ void bin_boxes_kernel(const float* __restrict__ Xt, int dp, int d, co
     boxes[(size_t)b * 128 + 64 + c] = hi;
 }
 
-// Per tile of 128 consecutive tree positions, the bounding box of its points.
-__global__ void tile_boxes_kernel(const float* __restrict__ Xt, int dp, int d, int n, float* __restrict__ boxes) {
-    const int tb = blockIdx.x, c = threadIdx.x;
-    float lo = 0.f, hi = 0.f;
-    if (c < d) {
-        const int p0 = tb * kSpM, p1 = min(n, p0 + kSpM);
-        lo = hi = Xt[(size_t)p0 * dp + c];
-        for (int p = p0 + 1; p < p1; ++p) {
-            const float x = Xt[(size_t)p * dp + c];
-            lo = fminf(lo, x);
-            hi = fmaxf(hi, x);
+// Per tile of 128 consecutive tree positions (block tb, 128 threads): the
+// bounding box of its points, and its image for the bin pass: centre c (the
+// mean of its points; any centre is exact, a near one is accurate), each row
+// centred and split into three swizzled BF16 parts, and the rows' centred
+// squared norms.  Rows past n are zero.
+__global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restrict__ Xt, int dp, int d, int n,
+                                                          float* __restrict__ boxes, unsigned char* __restrict__ qimg) {
+    constexpr int kStride = kSpDim + 4;  // row stride in floats: conflict-free 16-byte stores and column reads
+    __shared__ __align__(16) float xs[kSpM * kStride];
+    __shared__ float cen[kSpDim];
+    const int tb = blockIdx.x, r = threadIdx.x;
+    const int p0 = tb * kSpM, nv = min(kSpM, n - p0);
+    float4 x[kSpDim / 4];
+    load_row(Xt, dp, r < nv ? p0 + r : -1, x);
+#pragma unroll
+    for (int u = 0; u < kSpDim / 4; ++u) *reinterpret_cast<float4*>(xs + r * kStride + 4 * u) = x[u];
+    __syncthreads();
+    if (r < kSpDim) {
+        float lo = 0.f, hi = 0.f, c = 0.f;
+        if (r < d) {
+            lo = hi = xs[r];
+            for (int q = 0; q < nv; ++q) {
+                const float v = xs[q * kStride + r];
+                lo = fminf(lo, v);
+                hi = fmaxf(hi, v);
+                c += v;
+            }
+            c /= (float)nv;
         }
+        boxes[(size_t)tb * 128 + r] = lo;
+        boxes[(size_t)tb * 128 + 64 + r] = hi;
+        cen[r] = c;
     }
-    boxes[(size_t)tb * 128 + c] = lo;
-    boxes[(size_t)tb * 128 + 64 + c] = hi;
+    __syncthreads();
+    unsigned char* img = qimg + (size_t)tb * kQImg;
+    const float norm = split_row(x, r < nv, cen, img, r);
+    reinterpret_cast<float*>(img + kSpParts * kPart)[r] = norm;
+    if (r < kSpDim) reinterpret_cast<float*>(img + kSpParts * kPart + kSpM * 4)[r] = cen[r];
 }
 
 }  // namespace
@@ -430,6 +474,13 @@ __global__ void tile_boxes_kernel(const float* __restrict__ Xt, int dp, int d, i
 // d <= 64 (coordinates zero-padded to 64); every bin of at least 32 points, so
 // at most one bin ends in the 32 columns of an epilogue step.
 bool kde_bins_split_supported(const fsg_tree* t) { return t->d <= kSpDim && t->n / t->nb >= 32; }
+
+// Bin boxes, tile boxes, then the tiles' images (16-byte aligned: every
+// preceding array is a multiple of 512 bytes).
+size_t split_workspace_bytes(int64_t n, int64_t nb) {
+    const int64_t qblocks = (n + kSpM - 1) / kSpM;
+    return sizeof(float) * (size_t)(nb + qblocks) * 128 + (size_t)qblocks * kQImg;
+}
 
 cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const int qblocks = (int)((t->n + kSpM - 1) / kSpM);
@@ -451,11 +502,13 @@ cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cud
     }
     if (!t->sboxes) return cudaErrorInvalidValue;
     float* qboxes = t->sboxes + (size_t)t->nb * 128;  // after the bin boxes: [qblocks][2][64]
+    unsigned char* qimg = reinterpret_cast<unsigned char*>(qboxes + (size_t)qblocks * 128);  // then the tile images
     bin_boxes_kernel<<<t->nb, kSpDim, 0, s>>>(t->Xt, t->dp, t->d, t->bnd, t->sboxes);
-    tile_boxes_kernel<<<qblocks, kSpDim, 0, s>>>(t->Xt, t->dp, t->d, (int)t->n, qboxes);
+    split_prep_kernel<<<qblocks, kSpM, 0, s>>>(t->Xt, t->dp, t->d, (int)t->n, qboxes, qimg);
     dim3 grid(qblocks, chunks);
     kde_bins_split_kernel<<<grid, kSpThreads, smem, s>>>(
-        t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc, kp.neg_c, kp.self_exclude, t->sboxes, qboxes, t->ws.binsum,
+        t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc, kp.neg_c, kp.self_exclude, t->sboxes, qboxes, qimg,
+        t->ws.binsum,
         reinterpret_cast<unsigned long long*>(&t->ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&t->ws.stats->n_bin_evals), t->status);
     return cudaGetLastError();
