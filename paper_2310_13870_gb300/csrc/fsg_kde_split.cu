@@ -45,7 +45,7 @@ constexpr int kSpStages = 2;
 constexpr int kSpParts = 3;           // hi, mid, lo
 constexpr int kSpEpiWarps = 8;
 constexpr int kSpThreads = 32 * (5 + kSpEpiWarps);
-constexpr int kSpMaxBins = 24;        // bins per chunk
+constexpr int kSpMaxBins = 48;        // bins per chunk
 constexpr uint32_t kPart = 128u * 128u;  // one part of 128 rows x 64 BF16 (128-byte swizzled rows)
 constexpr uint32_t kTmemCols = 256;   // two 128-column accumulators
 constexpr int kSpMaxTiles = 252;      // point tiles per CTA (kept list)
@@ -63,7 +63,7 @@ struct SpLayout {
     static constexpr uint32_t BARS = CEN + kSpDim * 4;                    // full[2] empty[2] tfull[2] tempty[2] fin qbar
     static constexpr uint32_t SLOT = BARS + (2 * kSpStages + 6) * 8;      // TMEM slot, abort flag
     static constexpr uint32_t BND = SLOT + 16;                            // [kSpMaxBins + 1]
-    static constexpr uint32_t QLO = (BND + 112 + 15) & ~15u;              // [64] query tile's box: low corner
+    static constexpr uint32_t QLO = (BND + (kSpMaxBins + 1) * 4 + 15) & ~15u;  // [64] query tile's box: low corner
     static constexpr uint32_t QHI = QLO + kSpDim * 4;                     // [64] high corner
     static constexpr uint32_t TL = QHI + kSpDim * 4;                      // [kSpMaxTiles] kept point tiles, count
     static constexpr uint32_t PN = TL + (kSpMaxTiles + 4) * 4;            // [8 warps][64] norms of a warp's columns
@@ -71,6 +71,7 @@ struct SpLayout {
     static constexpr uint32_t total(int bpc) { return OUTS + 2u * kSpM * (uint32_t)bpc * 4u; }
 };
 static_assert(SpLayout::BARS % 8 == 0 && SpLayout::PN % 16 == 0 && SpLayout::B % 1024 == 0, "layout");
+static_assert(1024 + SpLayout::total(kSpMaxBins) <= 227 * 1024, "shared memory of a full chunk");
 static_assert(SpLayout::AN == SpLayout::CN + kSpStages * kSpN * 4 && SpLayout::CEN == SpLayout::AN + kSpM * 4 &&
                   SpLayout::AN % 16 == 0 && kQImg % 16 == 0,
               "the query image's norms and centre land in AN and CEN by 16-byte bulk copies");
