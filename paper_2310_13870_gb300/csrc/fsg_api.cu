@@ -100,6 +100,10 @@ cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) 
         t->launches += 1;
         return launch_leaf_values_tc(t, kp, s);
     }
+    if (kp.precision == FSG_PREC_SPLIT_BF16 && leaf_split_tc_supported(t)) {  // the split mode's arithmetic
+        t->launches += 2;
+        return launch_leaf_split_tc(t, kp, s);
+    }
     if (leaf_fused_generic_supported(t)) {  // d > 16, bins of <= 128 points: values stay on chip
         t->launches += 1;
         return launch_leaf_fused_generic(t, kp, s);
@@ -183,7 +187,8 @@ void workspace_sizes(int64_t n, int d, int dm, int nb, int64_t Lc, size_t (&sz)[
 // split images (allocated on first use).
 int ensure_split(fsg_tree* t, const fsg_params* p, cudaStream_t s) {
     if (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED || t->sboxes) return FSG_OK;
-    if (tree_malloc(t, (void**)&t->sboxes, split_workspace_bytes(t->n, t->nb), s) != cudaSuccess) {
+    if (tree_malloc(t, (void**)&t->sboxes, split_workspace_bytes(t->n, t->nb, leaf_split_tc_supported(t)), s) !=
+        cudaSuccess) {
         cudaGetLastError();
         t->sboxes = nullptr;
         return FSG_ERR_OOM;

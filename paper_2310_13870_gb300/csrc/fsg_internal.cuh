@@ -154,8 +154,13 @@ int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);
 bool kde_bins_split_supported(const fsg_tree* t);
-// Bytes of the split-precision pass's per-tree workspace (boxes, query-tile images).
-size_t split_workspace_bytes(int64_t n, int64_t nb);
+// Bytes of the split-precision pass's per-tree workspace (boxes, query-tile
+// images, and the bins' images when the split leaf phase runs).
+size_t split_workspace_bytes(int64_t n, int64_t nb, bool bin_images);
+// Split-precision leaf phase on the tensor cores: d in 17..64, bins of at
+// most 128 points (after the split bin pass, whose workspace it shares).
+bool leaf_split_tc_supported(const fsg_tree* t);
+cudaError_t launch_leaf_split_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 bool leaf_fused_generic_supported(const fsg_tree* t);
 cudaError_t launch_leaf_fused_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);

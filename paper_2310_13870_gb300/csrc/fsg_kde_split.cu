@@ -430,18 +430,17 @@ __global__ void bin_boxes_kernel(const float* __restrict__ Xt, int dp, int d, co
     boxes[(size_t)b * 128 + 64 + c] = hi;
 }
 
-// Per tile of 128 consecutive tree positions (block tb, 128 threads): the
-// bounding box of its points, and its image for the bin pass: centre c (the
-// mean of its points; any centre is exact, a near one is accurate), each row
-// centred and split into three swizzled BF16 parts, and the rows' centred
-// squared norms.  Rows past n are zero.
-__global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restrict__ Xt, int dp, int d, int n,
-                                                          float* __restrict__ boxes, unsigned char* __restrict__ qimg) {
+// The image of nv <= 128 consecutive tree positions p0 .. p0 + nv - 1 (128
+// threads, thread = row): centre c (the mean of the points; any centre is
+// exact, a near one is accurate), each row centred and split into three
+// swizzled BF16 parts, the rows' centred squared norms, c; rows past nv are
+// zero.  With box != nullptr also the points' bounding box (low, high corner).
+__device__ __forceinline__ void write_image(const float* __restrict__ Xt, int dp, int d, int p0, int nv,
+                                            unsigned char* __restrict__ img, float* __restrict__ box) {
     constexpr int kStride = kSpDim + 4;  // row stride in floats: conflict-free 16-byte stores and column reads
     __shared__ __align__(16) float xs[kSpM * kStride];
     __shared__ float cen[kSpDim];
-    const int tb = blockIdx.x, r = threadIdx.x;
-    const int p0 = tb * kSpM, nv = min(kSpM, n - p0);
+    const int r = threadIdx.x;
     float4 x[kSpDim / 4];
     load_row(Xt, dp, r < nv ? p0 + r : -1, x);
 #pragma unroll
@@ -459,15 +458,347 @@ __global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restric
             }
             c /= (float)nv;
         }
-        boxes[(size_t)tb * 128 + r] = lo;
-        boxes[(size_t)tb * 128 + 64 + r] = hi;
+        if (box) {
+            box[r] = lo;
+            box[64 + r] = hi;
+        }
         cen[r] = c;
     }
     __syncthreads();
-    unsigned char* img = qimg + (size_t)tb * kQImg;
     const float norm = split_row(x, r < nv, cen, img, r);
     reinterpret_cast<float*>(img + kSpParts * kPart)[r] = norm;
     if (r < kSpDim) reinterpret_cast<float*>(img + kSpParts * kPart + kSpM * 4)[r] = cen[r];
+}
+
+// Per tile of 128 consecutive tree positions (block tb): its bounding box and
+// its image, the query operand of the bin pass.
+__global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restrict__ Xt, int dp, int d, int n,
+                                                          float* __restrict__ boxes, unsigned char* __restrict__ qimg) {
+    const int tb = blockIdx.x, p0 = tb * kSpM;
+    write_image(Xt, dp, d, p0, min(kSpM, n - p0), qimg + (size_t)tb * kQImg, boxes + (size_t)tb * 128);
+}
+
+// Per bin of at most 128 points (block b): its image, the point operand of
+// the split-precision leaf phase.
+__global__ void __launch_bounds__(kSpM) bin_images_kernel(const float* __restrict__ Xt, int dp, int d,
+                                                          const int32_t* __restrict__ bnd,
+                                                          unsigned char* __restrict__ bimg) {
+    const int b = blockIdx.x, p0 = bnd[b];
+    write_image(Xt, dp, d, p0, bnd[b + 1] - p0, bimg + (size_t)b * kQImg, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision leaf phase (d in 17..64, bins of at most 128 points): per
+// chunk of 128 items of a bin, the kernel values of each item's query against
+// the bin's m points, k = ex2(neg_c ||a - b||^2) with a, b centred at the
+// bin's centre and a.b from the six BF16 products on the tensor cores (the
+// bin pass's arithmetic, so the mode's bound covers both phases); the values
+// stay in shared memory for the descents through the bin (the depth-4 node
+// sums, then descend_bin_row), as in the FP32 fused leaf kernel.
+//
+// Per CTA (one bin, chunks blockIdx.y, + gridDim.y, ...; 256 threads, two
+// CTAs per SM): the bin's norms and centre are bulk-copied once; per chunk
+// thread 0 bulk-copies the bin's three parts (B), all threads gather, centre
+// and split the items' query rows (A: thread pair per row, half the
+// coordinates each), thread 0 issues the 6 x ceil(d / 16) MMAs of N = m
+// rounded up to 16 into a 128-column accumulator, and thread = (row, column
+// half) turns its TMEM lane into values.  The value rows and the depth-4
+// trees take the place of A and B, which are idle by then; the next chunk's
+// copy starts after the descents.  Every wait is bounded; on a timeout the
+// CTA records FSG_ERR_TIMEOUT, waits (bounded) for its own copies and MMAs,
+// frees TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int kLsThreads = 256;
+constexpr int kLsVS = kSpN + 1;  // value row stride (odd)
+
+struct LsLayout {
+    static constexpr uint32_t A = 0;                                   // [3][128 rows] query parts
+    static constexpr uint32_t B = A + kSpParts * kPart;                // [3][128 rows] the bin's parts
+    static constexpr uint32_t V = 0;                                   // [128][kLsVS] values (over A and B)
+    static constexpr uint32_t BT = V + kSpM * kLsVS * 4;               // [128][33] depth-4 node sums and tree
+    static constexpr uint32_t BN = B + kSpParts * kPart;               // [128] the bin's centred norms
+    static constexpr uint32_t BCEN = BN + kSpN * 4;                    // [64] the bin's centre
+    static constexpr uint32_t AN = BCEN + kSpDim * 4;                  // [2][128] query norm halves
+    static constexpr uint32_t ROWPOS = AN + 2 * kSpM * 4;              // [128] item query positions
+    static constexpr uint32_t QMASK = ROWPOS + kSpM * 4;               // [128] item sample masks
+    static constexpr uint32_t PREFIX = QMASK + kSpM * 8;               // [129] samples before item r (+ 3)
+    static constexpr uint32_t BND4 = PREFIX + 132 * 4;                 // [17] depth-4 node starts (+ 3)
+    static constexpr uint32_t BARS = BND4 + 20 * 4;                    // nbar, bbar, accf, fin
+    static constexpr uint32_t SLOT = BARS + 4 * 8;                     // TMEM slot
+    static constexpr uint32_t total = SLOT + 16;
+};
+static_assert(LsLayout::BT + kSpM * 33 * 4 <= LsLayout::BN, "values and trees fit over the operands");
+static_assert(LsLayout::BCEN == LsLayout::BN + kSpN * 4 && LsLayout::BN % 16 == 0 && LsLayout::QMASK % 8 == 0 &&
+                  LsLayout::BARS % 8 == 0,
+              "layout");
+static_assert(2 * (1024 + LsLayout::total + 1024) <= 228 * 1024, "two CTAs per SM");
+
+// Coordinates 32 h .. 32 h + 31 of tree position p (zeros past dp, or for p < 0).
+__device__ __forceinline__ void load_half_row(const float* __restrict__ Xt, int dp, int p, int h, float4 (&x)[8]) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int c = 32 * h + 4 * u;
+        x[u] = (p >= 0 && c < dp) ? *reinterpret_cast<const float4*>(Xt + (size_t)p * dp + c)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Chunks 4 h .. 4 h + 3 of a row (those below nchw), centred at cen, split
+// and stored like split_row; returns their part of the squared norm.
+__device__ __forceinline__ float split_half_row(const float4 (&x)[8], bool valid, const float* __restrict__ cen,
+                                                unsigned char* parts, int row, int h, int nchw) {
+    float norm = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = 4 * h + i;
+        if (k >= nchw) break;
+        const uint32_t off = (uint32_t)row * 128u + (uint32_t)((k ^ (row & 7)) << 4);
+        if (!valid) {
+            *reinterpret_cast<uint4*>(parts + off) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(parts + kPart + off) = make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(parts + 2 * kPart + off) = make_uint4(0u, 0u, 0u, 0u);
+            continue;
+        }
+        const float v[8] = {x[2 * i].x, x[2 * i].y, x[2 * i].z, x[2 * i].w,
+                            x[2 * i + 1].x, x[2 * i + 1].y, x[2 * i + 1].z, x[2 * i + 1].w};
+        float a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            a[j] = __fsub_rn(v[j], cen[8 * k + j]);
+            norm = __fmaf_rn(a[j], a[j], norm);
+        }
+        uint4 hi, mid, lo;
+        split2(a[0], a[1], hi.x, mid.x, lo.x);
+        split2(a[2], a[3], hi.y, mid.y, lo.y);
+        split2(a[4], a[5], hi.z, mid.z, lo.z);
+        split2(a[6], a[7], hi.w, mid.w, lo.w);
+        *reinterpret_cast<uint4*>(parts + off) = hi;
+        *reinterpret_cast<uint4*>(parts + kPart + off) = mid;
+        *reinterpret_cast<uint4*>(parts + 2 * kPart + off) = lo;
+    }
+    return norm;
+}
+
+__global__ void __launch_bounds__(kLsThreads, 2)
+leaf_split_tc_kernel(const float* __restrict__ Xt, int dp, int d, const unsigned char* __restrict__ bimg,
+                     const int32_t* __restrict__ bnd, const int32_t* __restrict__ bin_off,
+                     const int32_t* __restrict__ items_q, const uint64_t* __restrict__ items_mask,
+                     const int32_t* __restrict__ perm, KernelParams kp, int s0, int32_t* __restrict__ leaf_pos,
+                     float* __restrict__ ksmp, uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
+                     unsigned long long* __restrict__ n_items, int32_t* __restrict__ status) {
+    const int b = blockIdx.x;
+    const int seg = bin_off[b * kBinSlots];
+    const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
+    const int nchunks = (cnt + kSpM - 1) / kSpM;
+    if ((int)blockIdx.y >= nchunks) return;
+    const int p_lo = bnd[b], m = bnd[b + 1] - p_lo;  // m <= 128
+    const int N = (m + 15) & ~15;                     // MMA columns
+    const int dm = ceil_log2_dev(m);
+    const uint32_t idesc = idesc_bf16(kSpM, N);
+    const int kk = (d + 15) / 16, nchw = 2 * kk;  // K-steps; 16-byte chunks the MMAs read
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_align1024(smem_raw);
+    unsigned char* sA = base + LsLayout::A;
+    unsigned char* sB = base + LsLayout::B;
+    float* vrows = reinterpret_cast<float*>(base + LsLayout::V);
+    float* btree = reinterpret_cast<float*>(base + LsLayout::BT);
+    float* bn = reinterpret_cast<float*>(base + LsLayout::BN);
+    float* bcen = reinterpret_cast<float*>(base + LsLayout::BCEN);
+    float* anp = reinterpret_cast<float*>(base + LsLayout::AN);
+    int32_t* rowpos = reinterpret_cast<int32_t*>(base + LsLayout::ROWPOS);
+    uint64_t* qmask = reinterpret_cast<uint64_t*>(base + LsLayout::QMASK);
+    int32_t* prefix = reinterpret_cast<int32_t*>(base + LsLayout::PREFIX);
+    int32_t* bnd4 = reinterpret_cast<int32_t*>(base + LsLayout::BND4);
+    uint64_t* nbar = reinterpret_cast<uint64_t*>(base + LsLayout::BARS);  // the bin's norms and centre landed
+    uint64_t* bbar = nbar + 1;                                            // the bin's parts landed (per chunk)
+    uint64_t* accf = nbar + 2;                                            // the chunk's MMAs complete
+    uint64_t* fin = nbar + 3;                                             // teardown
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + LsLayout::SLOT);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(nbar, 1);
+        mbar_init(bbar, 1);
+        mbar_init(accf, 1);
+        mbar_init(fin, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid <= 16) bnd4[tid] = depth4_start(tid, m);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const unsigned char* img = bimg + (size_t)b * kQImg;
+    if (tid == 0) {
+        mbar_arrive_expect_tx(nbar, kSpN * 4 + kSpDim * 4);
+        bulk_g2s(bn, img + kSpParts * kPart, kSpN * 4 + kSpDim * 4, nbar);
+    }
+    bool ok = mbar_wait_bounded(nbar, 0u, status);
+    bool mma_issued = false;
+    int nfill = 0, ncons = 0;  // thread 0: bin-part copies issued / seen complete
+    int tiles = 0;             // chunks whose accumulator completed
+    for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        const int it0 = chunk * kSpM;
+        const int qcnt = min(kSpM, cnt - it0);
+        if (tid == 0) {  // B: the previous chunk's values and trees over it are no longer read
+            mbar_arrive_expect_tx(bbar, kSpParts * kPart);
+            bulk_g2s(sB, img, kSpParts * kPart, bbar);
+            ++nfill;
+        }
+        if (tid < kSpM) {
+            rowpos[tid] = tid < qcnt ? items_q[seg + it0 + tid] : -1;
+            qmask[tid] = tid < qcnt ? items_mask[seg + it0 + tid] : 0ull;
+        }
+        __syncthreads();
+        {  // A: the items' query rows, centred at the bin's centre and split
+            const int r = tid & (kSpM - 1), h = tid >> 7;
+            const int pos = rowpos[r];
+            float4 x[8];
+            load_half_row(Xt, dp, pos, h, x);
+            anp[h * kSpM + r] = split_half_row(x, pos >= 0, bcen, sA, r, h, nchw);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            ok = mbar_wait_bounded(bbar, (uint32_t)tiles & 1u, status);
+            if (ok) {
+                ++ncons;
+                tc_fence_after();
+                const int pi[6] = {2, 0, 1, 1, 0, 0};  // A part (0 hi, 1 mid, 2 lo)
+                const int pj[6] = {0, 2, 1, 0, 1, 0};  // B part
+#pragma unroll
+                for (int u = 0; u < 6; ++u) {
+                    const uint64_t da = sdesc(smem_u32(sA + pi[u] * kPart));
+                    const uint64_t db = sdesc(smem_u32(sB + pj[u] * kPart));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (k >= kk) break;
+                        umma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (u | k) != 0 ? 1u : 0u);
+                    }
+                }
+                mma_issued = true;
+                umma_commit(accf);
+            }
+        }
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        ok = mbar_wait_bounded(accf, (uint32_t)tiles & 1u, status);
+        ++tiles;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        tc_fence_after();
+        // values: row r = TMEM lane (warps w and w + 4 read lanes 32 (w % 4) ..
+        // + 31), half hh takes the 32-column steps hh, hh + 2, ...; the MMAs
+        // are complete, so the rows may overwrite A and B
+        const int r = tid & (kSpM - 1), hh = tid >> 7;
+        const int qp = rowpos[r];
+        const float nq = anp[r] + anp[kSpM + r];
+        float* vr = vrows + (size_t)r * kLsVS;
+        const int sc = (kp.self_exclude && qp >= p_lo && qp < p_lo + m) ? qp - p_lo : -1;  // the query itself
+        const float neg_c = kp.neg_c;
+#pragma unroll 1
+        for (int c0 = 32 * hh; c0 < N; c0 += 64) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
+            if (c0 + 32 <= N) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float arg = fmaf(-2.f, v[j], nq + bn[c0 + j]);
+                    vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {  // N - c0 = 16
+                    const float arg = fmaf(-2.f, v[j], nq + bn[c0 + j]);
+                    vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                }
+            }
+            if (sc >= c0 && sc < c0 + 32) vr[sc] = 0.f;
+        }
+        // samples of the chunk's items: prefix[r] = samples of items < r
+        if (tid < kSpM) {
+            int x = __popcll(qmask[tid]);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((tid & 31) >= o) x += y;
+            }
+            prefix[tid + 1] = x;  // inclusive within the warp
+        }
+        __syncthreads();
+        // the 16 depth-4 node sums of row r: half hh sums nodes 8 hh .. 8 hh + 7
+        float* bt = btree + (size_t)r * 33;  // odd stride: the lanes' rows hit distinct banks
+        for (int k = 8 * hh; k < 8 * hh + 8; ++k) {
+            float acc = 0.f;
+            for (int j = bnd4[k]; j < bnd4[k + 1]; ++j) acc += vr[j];
+            bt[16 + k] = acc;
+        }
+        if (tid == 0) {  // warp totals into the prefix
+            prefix[0] = 0;
+            for (int w2 = 1; w2 < 4; ++w2) {
+                const int add = prefix[32 * w2];
+                for (int i = 32 * w2 + 1; i <= 32 * w2 + 32; ++i) prefix[i] += add;
+            }
+        }
+        __syncthreads();
+        if (hh == 0) {
+#pragma unroll
+            for (int h = 15; h >= 1; --h) bt[h] = bt[2 * h] + bt[2 * h + 1];
+        }
+        __syncthreads();
+        // descents: the chunk's samples spread over all threads
+        const int total = prefix[kSpM];
+        for (int gs = tid; gs < total; gs += kLsThreads) {
+            int lo = 0, hi = kSpM;  // item: prefix[lo] <= gs < prefix[lo + 1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (prefix[mid] <= gs) lo = mid; else hi = mid;
+            }
+            uint64_t mk = qmask[lo];
+            for (int k = gs - prefix[lo]; k > 0; --k) mk &= mk - 1ull;
+            const int l = __ffsll((long long)mk) - 1;
+            const int ip = rowpos[lo];
+            const float* vi = vrows + (size_t)lo * kLsVS;
+            uint8_t f = 0;
+            const int a = descend_bin_row(vi, btree + (size_t)lo * 33, m, dm, s0, kp.seed, (uint32_t)perm[ip],
+                                          (uint32_t)l, kp.flag_eps, f);
+            const size_t o = (size_t)ip * kp.L + l;
+            leaf_pos[o] = p_lo + a;
+            ksmp[o] = vi[a];
+            lflags[o] = f;
+        }
+        // the next chunk's copy and MMAs (async proxy) follow these accesses
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (tid == 0 && ok) {
+        unsigned long long its = 0;
+        for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) its += (unsigned long long)min(kSpM, cnt - chunk * kSpM);
+        atomicAdd(n_items, its);
+        atomicAdd(n_evals, its * (unsigned long long)m);
+    }
+    // teardown: own copies landed, own MMAs complete, then free TMEM
+    if (tid == 0) {
+        if (!ok) mbar_wait_bounded(nbar, 0u, status);
+        for (int g = ncons; g < nfill; ++g) mbar_wait_bounded(bbar, (uint32_t)g & 1u, status);
+        if (mma_issued) {
+            umma_commit(fin);
+            mbar_wait_bounded(fin, 0u, status);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
 }
 
 }  // namespace
@@ -476,11 +807,45 @@ __global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restric
 // at most one bin ends in the 32 columns of an epilogue step.
 bool kde_bins_split_supported(const fsg_tree* t) { return t->d <= kSpDim && t->n / t->nb >= 32; }
 
-// Bin boxes, tile boxes, then the tiles' images (16-byte aligned: every
-// preceding array is a multiple of 512 bytes).
-size_t split_workspace_bytes(int64_t n, int64_t nb) {
+// Bin boxes, tile boxes, the tiles' images, then (for the split leaf phase)
+// the bins' images; every array starts 16-byte aligned (the boxes are
+// multiples of 512 bytes, an image 49,920 bytes).
+size_t split_workspace_bytes(int64_t n, int64_t nb, bool bin_images) {
     const int64_t qblocks = (n + kSpM - 1) / kSpM;
-    return sizeof(float) * (size_t)(nb + qblocks) * 128 + (size_t)qblocks * kQImg;
+    return sizeof(float) * (size_t)(nb + qblocks) * 128 + (size_t)(qblocks + (bin_images ? nb : 0)) * kQImg;
+}
+
+bool leaf_split_tc_supported(const fsg_tree* t) {
+    return t->d > kMaxFmaDim && t->d <= kSpDim && t->mmax <= kSpN && kde_bins_split_supported(t);
+}
+
+cudaError_t launch_leaf_split_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (!t->sboxes || !leaf_split_tc_supported(t)) return cudaErrorInvalidValue;
+    const int64_t qblocks = (t->n + kSpM - 1) / kSpM;
+    unsigned char* bimg = reinterpret_cast<unsigned char*>(t->sboxes + (size_t)(t->nb + qblocks) * 128) +
+                          (size_t)qblocks * kQImg;
+    const size_t smem = 1024 + LsLayout::total;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(leaf_split_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    bin_images_kernel<<<t->nb, kSpM, 0, s>>>(t->Xt, t->dp, t->d, t->bnd, bimg);
+    const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
+    const int64_t chunks_per_bin = (items_est / t->nb + kSpM - 1) / kSpM + 1;
+    int64_t S = (152 * 2 * 8 + t->nb - 1) / t->nb;
+    if (S > chunks_per_bin) S = chunks_per_bin;
+    if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
+    if (S < 1) S = 1;
+    if (S > 65535) S = 65535;
+    const auto& ws = t->ws;
+    leaf_split_tc_kernel<<<dim3(t->nb, (unsigned)S), kLsThreads, smem, s>>>(
+        t->Xt, t->dp, t->d, bimg, t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, t->s0, ws.leaf_pos,
+        ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+        reinterpret_cast<unsigned long long*>(&ws.stats->n_items), t->status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {

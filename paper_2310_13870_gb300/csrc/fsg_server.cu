@@ -51,7 +51,7 @@ size_t request_bytes(const fsg_request& r) {
     size_t b = fsg::tree_bytes_estimate(r.n, r.d, r.L) + sizeof(float) * (size_t)r.n * r.d +
                (sizeof(int32_t) * 2 + sizeof(float)) * (size_t)r.n * r.L + 4096;
     if (r.params.precision == FSG_PREC_SPLIT_BF16)  // bins hold at least 32 points
-        b += fsg::split_workspace_bytes(r.n, (r.n + 31) / 32);
+        b += fsg::split_workspace_bytes(r.n, (r.n + 31) / 32, r.d > 16);
     return b;
 }
 

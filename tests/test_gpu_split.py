@@ -2,8 +2,10 @@
 BF16 split, six tensor-core products, FP32 accumulation) against the FP64
 oracle on the same spatial tree order.  Its stated bound: every degree within
 SPLIT_DEG_RTOL of the oracle's, and every sample the oracle's unless a
-decision was flagged under the mode's default tolerance (2^-10).  The leaf
-phase runs in FP32, so leaf values (and edge weights) keep FP32 accuracy."""
+decision was flagged under the mode's default tolerance (2^-10).  For d in
+17..64 the leaf phase uses the same arithmetic (the bin's points and the
+items' queries centred at the bin's centre), so leaf values and edge weights
+share the bound; for d <= 16 the leaf phase runs in FP32."""
 import math
 
 import numpy as np
@@ -67,7 +69,7 @@ def test_split_matches_oracle(fsg, n, d, sigma, L, seed):
     osmp, oflg, _ = ora.sample(X, gam, L, seed, queries=q, perm=perm)
     assert not ((g["samples"][q] != osmp) & (g["flags"][q] == 0)).any()
     assert g["stats"]["n_flagged"] <= 0.05 * n * L
-    # edge weights: FP32 leaf values and FP32 degrees of the two end points
+    # edge weights: leaf values and degrees of the two end points, each within the bound
     o = ora.build_graph(X, gam, L, seed, perm=perm)
     wo = {(min(s, t), max(s, t)): w for s, t, w in zip(o["src"].tolist(), o["dst"].tolist(), o["w"].tolist())}
     for s, t, w in zip(g["src"].tolist(), g["dst"].tolist(), g["w"].tolist()):
