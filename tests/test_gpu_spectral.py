@@ -47,10 +47,18 @@ def test_segmentation_image(fsg):
     assert ri_sparse >= 0.85 and ri_sparse >= ri_dense - 0.05, (ri_sparse, ri_dense)
 
 
-@pytest.mark.parametrize("d,split", [(10, False), (64, True)])
-def test_gaussian_mixture(fsg, d, split):
+# At d = 64 the bandwidth is 3: with sigma = 1.5 the kernel values inside a
+# blob span about nine orders of magnitude, some vertices hang on by edges
+# many orders lighter than the rest, and the normalised spectral embedding is
+# ill-conditioned for any graph of this data (the oracle's own graph, whose
+# components are exactly the 8 blobs, scores a Rand index of 0.96, and 1e-4
+# relative noise on its weights moves it between 0.96 and 0.997).  At sigma =
+# 3 the weights span two orders and the oracle's graph scores 1.0 under 1e-3
+# noise, so the check measures the graph, not the eigensolver.
+@pytest.mark.parametrize("d,split,sigma", [(10, False, 1.5), (64, True, 3.0)])
+def test_gaussian_mixture(fsg, d, split, sigma):
     X, truth = inputs.gaussian_mixture(n=5000, d=d, k=8, seed=3, return_labels=True)
-    p = fsg.params(1.5, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO)
+    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO)
     src, dst, w = fsg.fsg_build_graph_host(X, p, 16, 2)
     lab = spectral.spectral_clustering(len(X), src, dst, w, 8)
     assert spectral.rand_index(lab, truth) >= 0.99
