@@ -215,7 +215,9 @@ def run_ours(args):
     n, d, L, sigma, seed = WORKLOAD["n"], WORKLOAD["d"], WORKLOAD["L"], WORKLOAD["sigma"], WORKLOAD["seed"]
     stream = torch.cuda.Stream()
     split = args.precision == "split"
-    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO)
+    if args.kde_eps > 0 and not split:
+        raise SystemExit("--kde-eps needs --precision split (the approximate bin pass is the split form's)")
+    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO, kde_eps=args.kde_eps)
     perm = None
     if split:  # spatial tree order: computed once on the host for the fixed input, outside the timed region
         perm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
@@ -284,7 +286,8 @@ def run_ours(args):
         # split form: six BF16 products per coordinate over 64 padded coordinates,
         # for the pairs it executes (tile pairs whose values are all zero are skipped)
         pairs = st["n_bin_evals"] if split else n * n
-        achieved = (12.0 * pairs * 64 if split else 2.0 * n * n * d) / (kde_avg * 1e-3) / 1e12
+        kpad = 16 * ((d + 15) // 16)  # coordinates the split form's MMAs run (K-steps of 16)
+        achieved = (12.0 * pairs * kpad if split else 2.0 * n * n * d) / (kde_avg * 1e-3) / 1e12
         peaks = {}
         pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pf):
@@ -373,8 +376,40 @@ def run_ours(args):
         e2e = {"value": replica_throughput(n * L, world, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
                "d2h_bytes_per_step": int(8 + mm * 12), "ms_per_step": e2e_s * 1e3}
 
+    def run_approx(eps, ref):
+        # the approximate KDE (tree-pruned split bin pass) on the same input in
+        # the spatial tree order (computed on the host, outside the timed region)
+        pa = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16, kde_eps=eps)
+        sperm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
+        with torch.cuda.stream(stream):
+            t2 = fsg.fsg_build_tree(pts, perm=sperm, stream=stream)
+        fsg.fsg_build_graph(t2, pa, L, seed, bufs=bufs, stream=stream)  # warm-up
+        fsg.fsg_build_graph(t2, pa, L, seed, bufs=bufs, stream=stream)
+        ams, bin_ms = [], []
+        fsg.fsg_profile(t2, True)
+        for _ in range(max(3, args.plain_steps)):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fsg.fsg_tree_update(t2, pts, stream=stream)
+            fsg.fsg_build_graph(t2, pa, L, seed, bufs=bufs, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ams.append(e0.elapsed_time(e1))
+            bin_ms.append(fsg.fsg_profile_read(t2)[0]["kde_bins"])
+        fsg.fsg_profile(t2, False)
+        assert fsg.fsg_sync(t2, stream=stream) == 0
+        ast = fsg.stats_dict(bufs)
+        t2.close()
+        at = statistics.mean(ams)
+        return {"precision": f"approximate KDE: split form, kde_eps = {eps:.3g}, spatial tree order",
+                "value": n * L / (at * 1e-3), "unit": UNIT, "ms_per_step": at, "bin_pass_ms": statistics.mean(bin_ms),
+                "executed_pairs": int(ast["n_bin_evals"]), "skipped_fraction": 1.0 - ast["n_bin_evals"] / (n * n),
+                "flagged_samples": ast["n_flagged"], "kde_error": kde_error(bufs.deg.cpu().numpy(), ref)}
+
     cpu = None
-    err = split_cmp = None
+    err = split_cmp = approx_cmp = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ref = {}
         v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed, keep=ref)
@@ -401,6 +436,7 @@ def run_ours(args):
                          "value": n * L / (st_ms * 1e-3), "unit": UNIT, "ms_per_step": st_ms,
                          "flagged_samples": sst["n_flagged"], "flag_eps": 2.0 ** -10,
                          "kde_error": kde_error(bufs.deg.cpu().numpy(), ref)}
+            approx_cmp = run_approx(2.0 ** -20, ref)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_queries} of the {n} query points (all {L} samples each + their degrees), "
                          f"{dt:.1f} s, extrapolated per sampled edge"}
@@ -410,11 +446,12 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate" if split else "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)",
-                               **({"precision": "split (spatial tree order)"} if split else {})),
+                               **({"precision": "split (spatial tree order)"} if split else {}),
+                               **({"kde_eps": args.kde_eps} if args.kde_eps > 0 else {})),
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
-                "kde_error": err, "split_precision": split_cmp,
+                "kde_error": err, "split_precision": split_cmp, "approximate_kde": approx_cmp,
                 "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "carried_fp32_gpu": carried,
                 "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -647,6 +684,8 @@ def main():
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--plain-requests", type=int, default=40, help="serving: closed-loop burst for the plain path")
     ap.add_argument("--admission", choices=["arrival", "ratio"], default="arrival", help="serving: admission order")
+    ap.add_argument("--kde-eps", type=float, default=0.0,
+                    help="approximate KDE (tree-pruned split bin pass) with this relative error bound")
     ap.add_argument("--precision", choices=["auto", "split"], default="auto",
                     help="mixture workload, d <= 64: split-precision tensor-core bin pass on a spatial tree order")
     args = ap.parse_args()

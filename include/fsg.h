@@ -66,8 +66,10 @@ extern "C" {
 #define FSG_PREC_FP32 1         /* FP32 direct differences + ex2 on every d       */
 #define FSG_PREC_SPLIT_BF16 2   /* d <= 64: centred tiles, 3-part BF16           */
                                 /* split, six tcgen05 products, FP32 accumulate; */
-                                /* use with fsg_spatial_order (bin pass only:    */
-                                /* the leaf phase stays FP32)                    */
+                                /* use with fsg_spatial_order (the leaf phase    */
+                                /* too for d in 17..64; FP32 for d <= 16); the   */
+                                /* only form with the approximate bin pass       */
+                                /* (fsg_params.kde_eps)                          */
 #define FSG_PREC_EXACT_INT 3    /* tcgen05 BF16 on data that are k/255 exactly    */
 /* Edge semantics of Algorithm 2's set union. */
 #define FSG_EDGES_SET 0         /* one edge per unordered pair {i,j} sampled      */
@@ -104,7 +106,22 @@ typedef struct {
      * FSG_PREC_SPLIT_BF16 (whose sums carry up to about 4e-4 relative error
      * from the tensor cores' FP32 accumulation). */
     float flag_eps;
-    int32_t reserved[5];
+    /* Approximate KDE (tree-pruned bin pass), 0 = exact.  With kde_eps in
+     * (0, 0.5] the bin pass skips every point tile whose largest possible
+     * contribution to a query tile's sums, count * exp(-gamma gap^2) with gap
+     * the distance between the two tiles' bounding boxes, is at most
+     * kde_eps / T of a lower bound of those queries' degrees (their exact sums
+     * over their own tile; T = the point tiles of one query's sweep), so
+     * every degree and every node sum above the bins loses at most
+     * kde_eps * degree of its mass (a one-sided error, before rounding).
+     * Decisions on those sums are flagged with the extra tolerance
+     * kde_eps * degree, so unflagged samples still equal the exact method's.
+     * Values inside a bin are not approximated.  FSG_PREC_SPLIT_BF16 only
+     * (FSG_ERR_UNSUPPORTED otherwise); negative, non-finite or > 0.5:
+     * FSG_ERR_INVALID_ARG.  The paper's bound for the method is
+     * eps <= 1/(6 log n). */
+    float kde_eps;
+    int32_t reserved[4];
 } fsg_params;
 
 /* Device-side statistics of one fsg_build_graph call (all int64). */

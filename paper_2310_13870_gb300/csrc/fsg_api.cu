@@ -38,6 +38,7 @@ int check_params(const fsg_params* p) {
     if (p->schedule != FSG_SCHED_FUSED && p->schedule != FSG_SCHED_LEVELWISE && p->schedule != FSG_SCHED_CARRIED)
         return FSG_ERR_INVALID_ARG;
     if (!(p->flag_eps >= 0.f) || !std::isfinite(p->flag_eps) || p->flag_eps > 0.25f) return FSG_ERR_INVALID_ARG;
+    if (!(p->kde_eps >= 0.f) || !std::isfinite(p->kde_eps) || p->kde_eps > 0.5f) return FSG_ERR_INVALID_ARG;
     return FSG_OK;
 }
 
@@ -55,6 +56,7 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     // default: the relative error bound of the sums of the chosen form (the
     // split form's FP32 tensor-core accumulation adds up to about 4e-4)
     kp.flag_eps = p->flag_eps > 0.f ? p->flag_eps : (p->precision == FSG_PREC_SPLIT_BF16 ? 0x1p-10f : 0x1p-13f);
+    kp.kde_eps = p->kde_eps;
     return kp;
 }
 
@@ -127,6 +129,9 @@ int64_t bin_pass_evals(const fsg_tree* t, int precision) {
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
+    // the approximate bin pass is the split form's tile pruning
+    if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED))
+        return FSG_ERR_UNSUPPORTED;
     if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
     // the levelwise schedules are plain FP32 paths only
     if (p->schedule != FSG_SCHED_FUSED && p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32)

@@ -79,10 +79,13 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                         uint8_t f = 0;
                         int h = 1;
                         uint4 blk = make_uint4(0, 0, 0, 0);
+                        // approximate bin sums miss at most kde_eps of the exact degree
+                        // (root >= (1 - kde_eps) degree)
+                        const float abs_tol = kp.kde_eps > 0.f ? kp.kde_eps * root / (1.f - kp.kde_eps) : 0.f;
                         for (int t = 0; t < s0; ++t) {
                             if ((t & 3) == 0) blk = draw_block(kp.seed, (uint32_t)i, (uint32_t)l, (uint32_t)t);
                             h = 2 * h + descend_decide(tree[2 * h], tree[2 * h + 1], block_word(blk, (uint32_t)t),
-                                                       kp.flag_eps, f);
+                                                       kp.flag_eps, f, abs_tol);
                         }
                         binv[r] = h - nb;
                         flags[(size_t)q * L + l] = f;

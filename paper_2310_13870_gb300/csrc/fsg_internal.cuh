@@ -125,6 +125,7 @@ struct KernelParams {
     int L;
     uint64_t seed;
     float flag_eps;
+    float kde_eps;    // approximate bin pass: skipped mass <= kde_eps * degree (0 = exact)
 };
 
 int ensure_workspace(fsg_tree* t, int L, cudaStream_t s);
@@ -209,12 +210,16 @@ __device__ __forceinline__ uint32_t block_word(const uint4& b, uint32_t level) {
 // |u S - g_left| < 2 eps min(g_left, g_right) + 2^-22 S: with both sums
 // within relative error eps of the exact ones, an unflagged decision equals
 // the exact one (min(r, 1-r) >= r (1-r) bounds the ratio's error).
-__device__ __forceinline__ int descend_decide(float gl, float gr, uint32_t word, float eps, uint8_t& flag) {
+// abs_tol: a further absolute error of gl and gr together (sums that may miss
+// up to that much mass, as the approximate bin pass's do): u S - gl moves by
+// at most that much.
+__device__ __forceinline__ int descend_decide(float gl, float gr, uint32_t word, float eps, uint8_t& flag,
+                                              float abs_tol = 0.f) {
     const float S = gl + gr;
     if (!(S > 0.f)) { flag |= 2; return 1; }
     const float u = __uint2float_rz(word >> 8) * 0x1p-24f;
     const float dlt = fmaf(u, S, -gl);
-    const float tol = 2.f * eps * fminf(gl, gr) + 0x1p-22f * S;
+    const float tol = 2.f * eps * fminf(gl, gr) + 0x1p-22f * S + abs_tol;
     if (fabsf(dlt) < tol) flag |= 1;
     return dlt < 0.f ? 0 : 1;
 }

@@ -33,6 +33,8 @@
 // FSG_ERR_TIMEOUT, stops, waits (bounded) for its own MMAs and frees TMEM.
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "fsg_tc.cuh"
 
 namespace fsg {
@@ -53,6 +55,31 @@ constexpr int kSpMaxTiles = 252;      // point tiles per CTA (kept list)
 // bulk-copied by every CTA of that tile: its three swizzled parts, then the
 // centred norms of its 128 rows, then its centre.
 constexpr uint32_t kQImg = kSpParts * kPart + kSpM * 4 + kSpDim * 4;
+// log2 of "no lower bound" / "no approximation budget": far below any
+// log2(count) + neg_c * gap^2 that is not already an exact zero (> -128 - 8)
+constexpr float kNoBound = -1.0e30f;
+
+// The split form's per-tree workspace: bin boxes [nb][128], query-tile boxes
+// [qblocks][128], the query tiles' degree lower bounds (log2) [qblocks, padded
+// to 128], the query tiles' images, then the bins' images.  Every array starts
+// 16-byte aligned (the float arrays are multiples of 512 bytes, an image
+// 49,920 bytes).
+struct SplitWs {
+    float* bin_boxes;
+    float* tile_boxes;
+    float* tile_lb;
+    unsigned char* tile_img;
+    unsigned char* bin_img;
+    int64_t qblocks;
+    __host__ SplitWs(const fsg_tree* t) {
+        qblocks = (t->n + kSpM - 1) / kSpM;
+        bin_boxes = t->sboxes;
+        tile_boxes = bin_boxes + (size_t)t->nb * 128;
+        tile_lb = tile_boxes + (size_t)qblocks * 128;
+        tile_img = reinterpret_cast<unsigned char*>(tile_lb + (size_t)(qblocks + 127) / 128 * 128);
+        bin_img = tile_img + (size_t)qblocks * kQImg;
+    }
+};
 
 struct SpLayout {
     static constexpr uint32_t A = 0;                                      // [3][128 rows]
@@ -144,6 +171,7 @@ __global__ void __launch_bounds__(kSpThreads, 1)
 kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const int32_t* __restrict__ bnd, int nb,
                       int bpc, float neg_c, int self_exclude, const float* __restrict__ boxes,
                       const float* __restrict__ qboxes, const unsigned char* __restrict__ qimg,
+                      const float* __restrict__ tile_lb, float log2_budget,
                       float* __restrict__ binsum, unsigned long long* __restrict__ n_evals,
                       unsigned long long* __restrict__ n_bin_evals, int32_t* __restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
@@ -181,11 +209,17 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
     __syncthreads();
     const int pa = bnd_s[0], pe = bnd_s[nbc];
     const int ntall = (pe - pa + kSpN - 1) / kSpN;
+    // approximate bin pass: a tile whose bound count * 2^(neg_c gap^2) is at
+    // most 2^thr (= kde_eps / T of the query tile's degree lower bound) is
+    // skipped; exact pass (log2_budget = kNoBound): thr is about kNoBound
+    const float thr = log2_budget + tile_lb[blockIdx.x];
     // Point tiles whose every kernel value is exactly zero in FP32 are skipped:
     // when the gap between the query tile's box and the union of the boxes of
     // the tile's bins puts neg_c * d^2 below -128, every ex2 is below 2^-126
     // and flushes to +0 (two units of margin over the rounding of d^2), so the
-    // bin sums are the same bit for bit.  The chunk's bin boxes are staged in
+    // bin sums are the same bit for bit.  With kde_eps > 0 so are the tiles
+    // whose whole contribution is bounded by the approximation's budget.
+    // The chunk's bin boxes are staged in
     // the (not yet used) output buffer; warp w tests tiles w, w + 13, ... with
     // its lanes over the coordinates; warp 0 lists the kept tiles in order.
     float* bx = outs;  // [nbc][128]: low corner, high corner
@@ -209,7 +243,9 @@ kde_bins_split_kernel(const float* __restrict__ Xt, int dp, int d, int n, const 
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-        if (lane == 0 && t < kSpMaxTiles) tl[t] = !(neg_c * d2 < -128.f);  // keep flag, compacted below
+        const float lg = neg_c * d2;
+        if (lane == 0 && t < kSpMaxTiles)  // keep flag, compacted below
+            tl[t] = !(lg < -128.f || lg + __log2f((float)(pq - ps)) <= thr);
     }
     __syncthreads();
     if (warp == 0) {
@@ -435,11 +471,13 @@ __global__ void bin_boxes_kernel(const float* __restrict__ Xt, int dp, int d, co
 // exact, a near one is accurate), each row centred and split into three
 // swizzled BF16 parts, the rows' centred squared norms, c; rows past nv are
 // zero.  With box != nullptr also the points' bounding box (low, high corner).
+// xs [128][kImgStride] (16-byte aligned) and cen [64] are the block's shared
+// staging; xs keeps the rows (zeros past nv) on return.
+constexpr int kImgStride = kSpDim + 4;  // row stride in floats: conflict-free 16-byte stores and column reads
 __device__ __forceinline__ void write_image(const float* __restrict__ Xt, int dp, int d, int p0, int nv,
-                                            unsigned char* __restrict__ img, float* __restrict__ box) {
-    constexpr int kStride = kSpDim + 4;  // row stride in floats: conflict-free 16-byte stores and column reads
-    __shared__ __align__(16) float xs[kSpM * kStride];
-    __shared__ float cen[kSpDim];
+                                            unsigned char* __restrict__ img, float* __restrict__ box, float* xs,
+                                            float* cen) {
+    constexpr int kStride = kImgStride;
     const int r = threadIdx.x;
     float4 x[kSpDim / 4];
     load_row(Xt, dp, r < nv ? p0 + r : -1, x);
@@ -471,11 +509,55 @@ __device__ __forceinline__ void write_image(const float* __restrict__ Xt, int dp
 }
 
 // Per tile of 128 consecutive tree positions (block tb): its bounding box and
-// its image, the query operand of the bin pass.
+// its image, the query operand of the bin pass.  With lb != nullptr also a
+// lower bound of its queries' degrees for the approximate pass: the smallest
+// over its queries of the exact sum over the tile's own points (FP32 direct
+// differences; the self term under INCLUDE, not under EXCLUDE), less 2^-16 of
+// it for rounding, stored as log2 (kNoBound when it is 0).
 __global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restrict__ Xt, int dp, int d, int n,
-                                                          float* __restrict__ boxes, unsigned char* __restrict__ qimg) {
-    const int tb = blockIdx.x, p0 = tb * kSpM;
-    write_image(Xt, dp, d, p0, min(kSpM, n - p0), qimg + (size_t)tb * kQImg, boxes + (size_t)tb * 128);
+                                                          float* __restrict__ boxes, unsigned char* __restrict__ qimg,
+                                                          float* __restrict__ lb, float neg_c, int self_exclude) {
+    __shared__ __align__(16) float xs[kSpM * kImgStride];
+    __shared__ float cen[kSpDim];
+    __shared__ float wmin[kSpM / 32];
+    const int tb = blockIdx.x, p0 = tb * kSpM, nv = min(kSpM, n - p0);
+    write_image(Xt, dp, d, p0, nv, qimg + (size_t)tb * kQImg, boxes + (size_t)tb * 128, xs, cen);
+    if (!lb) return;
+    const int r = threadIdx.x;
+    constexpr int kStride = kImgStride;
+    const float* rows = xs;  // the tile's rows, staged by write_image
+    float4 x[kSpDim / 4];
+#pragma unroll
+    for (int u = 0; u < kSpDim / 4; ++u) x[u] = *reinterpret_cast<const float4*>(rows + r * kStride + 4 * u);
+    float sum = 3.0e38f;  // rows past nv take no part in the minimum
+    if (r < nv) {
+        sum = 0.f;
+        for (int j = 0; j < nv; ++j) {
+            if (j == r && self_exclude) continue;
+            float d2 = 0.f;
+#pragma unroll
+            for (int u = 0; u < kSpDim / 4; ++u) {
+                if (4 * u >= dp) break;
+                const float4 y = *reinterpret_cast<const float4*>(rows + j * kStride + 4 * u);
+                const float a = x[u].x - y.x, b = x[u].y - y.y, c = x[u].z - y.z, e = x[u].w - y.w;
+                d2 = fmaf(a, a, d2);
+                d2 = fmaf(b, b, d2);
+                d2 = fmaf(c, c, d2);
+                d2 = fmaf(e, e, d2);
+            }
+            sum += ex2_approx(neg_c * d2);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum = fminf(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+    if ((r & 31) == 0) wmin[r >> 5] = sum;
+    __syncthreads();
+    if (r == 0) {
+        float m = wmin[0];
+        for (int w = 1; w < kSpM / 32; ++w) m = fminf(m, wmin[w]);
+        m *= 1.f - 0x1p-16f;
+        lb[tb] = m > 0.f ? __log2f(m) : kNoBound;
+    }
 }
 
 // Per bin of at most 128 points (block b): its image, the point operand of
@@ -483,8 +565,10 @@ __global__ void __launch_bounds__(kSpM) split_prep_kernel(const float* __restric
 __global__ void __launch_bounds__(kSpM) bin_images_kernel(const float* __restrict__ Xt, int dp, int d,
                                                           const int32_t* __restrict__ bnd,
                                                           unsigned char* __restrict__ bimg) {
+    __shared__ __align__(16) float xs[kSpM * kImgStride];
+    __shared__ float cen[kSpDim];
     const int b = blockIdx.x, p0 = bnd[b];
-    write_image(Xt, dp, d, p0, bnd[b + 1] - p0, bimg + (size_t)b * kQImg, nullptr);
+    write_image(Xt, dp, d, p0, bnd[b + 1] - p0, bimg + (size_t)b * kQImg, nullptr, xs, cen);
 }
 
 // ---------------------------------------------------------------------------
@@ -812,7 +896,8 @@ bool kde_bins_split_supported(const fsg_tree* t) { return t->d <= kSpDim && t->n
 // multiples of 512 bytes, an image 49,920 bytes).
 size_t split_workspace_bytes(int64_t n, int64_t nb, bool bin_images) {
     const int64_t qblocks = (n + kSpM - 1) / kSpM;
-    return sizeof(float) * (size_t)(nb + qblocks) * 128 + (size_t)(qblocks + (bin_images ? nb : 0)) * kQImg;
+    return sizeof(float) * (size_t)(nb + qblocks + (qblocks + 127) / 128) * 128 +
+           (size_t)(qblocks + (bin_images ? nb : 0)) * kQImg;
 }
 
 bool leaf_split_tc_supported(const fsg_tree* t) {
@@ -821,9 +906,7 @@ bool leaf_split_tc_supported(const fsg_tree* t) {
 
 cudaError_t launch_leaf_split_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     if (!t->sboxes || !leaf_split_tc_supported(t)) return cudaErrorInvalidValue;
-    const int64_t qblocks = (t->n + kSpM - 1) / kSpM;
-    unsigned char* bimg = reinterpret_cast<unsigned char*>(t->sboxes + (size_t)(t->nb + qblocks) * 128) +
-                          (size_t)qblocks * kQImg;
+    unsigned char* bimg = SplitWs(t).bin_img;
     const size_t smem = 1024 + LsLayout::total;
     static bool attr = false;
     if (!attr) {
@@ -867,14 +950,22 @@ cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cud
         attr = true;
     }
     if (!t->sboxes) return cudaErrorInvalidValue;
-    float* qboxes = t->sboxes + (size_t)t->nb * 128;  // after the bin boxes: [qblocks][2][64]
-    unsigned char* qimg = reinterpret_cast<unsigned char*>(qboxes + (size_t)qblocks * 128);  // then the tile images
-    bin_boxes_kernel<<<t->nb, kSpDim, 0, s>>>(t->Xt, t->dp, t->d, t->bnd, t->sboxes);
-    split_prep_kernel<<<qblocks, kSpM, 0, s>>>(t->Xt, t->dp, t->d, (int)t->n, qboxes, qimg);
+    const SplitWs ws(t);
+    const bool approx = kp.kde_eps > 0.f;
+    // error budget: a query meets at most `sweep` point tiles over all chunks
+    const double sweep = (double)((t->n + kSpN - 1) / kSpN + chunks);
+    const float log2_budget = approx ? (float)(std::log2((double)kp.kde_eps) - std::log2(sweep)) : kNoBound;
+    bin_boxes_kernel<<<t->nb, kSpDim, 0, s>>>(t->Xt, t->dp, t->d, t->bnd, ws.bin_boxes);
+    split_prep_kernel<<<qblocks, kSpM, 0, s>>>(t->Xt, t->dp, t->d, (int)t->n, ws.tile_boxes, ws.tile_img,
+                                               approx ? ws.tile_lb : nullptr, kp.neg_c, kp.self_exclude);
+    if (!approx) {  // the kernel reads tile_lb[q] + kNoBound: any small finite value
+        cudaError_t e = cudaMemsetAsync(ws.tile_lb, 0, sizeof(float) * (size_t)qblocks, s);
+        if (e != cudaSuccess) return e;
+    }
     dim3 grid(qblocks, chunks);
     kde_bins_split_kernel<<<grid, kSpThreads, smem, s>>>(
-        t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc, kp.neg_c, kp.self_exclude, t->sboxes, qboxes, qimg,
-        t->ws.binsum,
+        t->Xt, t->dp, t->d, (int)t->n, t->bnd, t->nb, bpc, kp.neg_c, kp.self_exclude, ws.bin_boxes, ws.tile_boxes, ws.tile_img,
+        ws.tile_lb, log2_budget, t->ws.binsum,
         reinterpret_cast<unsigned long long*>(&t->ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&t->ws.stats->n_bin_evals), t->status);
     return cudaGetLastError();

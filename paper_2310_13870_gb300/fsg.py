@@ -60,7 +60,7 @@ class FsgError(RuntimeError):
 class fsg_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("scale_conv", ctypes.c_int32), ("self_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flag_eps", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("kde_eps", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
 
 
 class fsg_tree_opts(ctypes.Structure):
@@ -174,7 +174,8 @@ def _dptr(t):
 
 
 def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FSG_SELF_EXCLUDE,
-           precision: int = FSG_PREC_AUTO, schedule: int = FSG_SCHED_FUSED, flag_eps: float = 0.0) -> fsg_params:
+           precision: int = FSG_PREC_AUTO, schedule: int = FSG_SCHED_FUSED, flag_eps: float = 0.0,
+           kde_eps: float = 0.0) -> fsg_params:
     p = fsg_params()
     p.sigma = float(sigma)
     p.scale_conv = scale_conv
@@ -182,6 +183,7 @@ def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FS
     p.precision = precision
     p.schedule = schedule
     p.flag_eps = float(flag_eps)
+    p.kde_eps = float(kde_eps)
     return p
 
 

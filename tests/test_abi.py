@@ -67,9 +67,14 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     m = ctypes.c_int64()
     buf = (ctypes.c_float * 8)()
     for bad in (fsg.params(0.0), fsg.params(float("nan")), fsg.params(-1.0), fsg.params(0.1, self_mode=3),
-                fsg.params(0.1, scale_conv=7), fsg.params(0.1, precision=9), fsg.params(0.1, flag_eps=-1.0)):
+                fsg.params(0.1, scale_conv=7), fsg.params(0.1, precision=9), fsg.params(0.1, flag_eps=-1.0),
+                fsg.params(0.1, kde_eps=-1e-3), fsg.params(0.1, kde_eps=float("nan")), fsg.params(0.1, kde_eps=0.6)):
         rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(bad), 2, 0, 0, buf, buf, buf, 8, ctypes.byref(m), None)
         assert rc == fsg.FSG_ERR_INVALID_ARG
+    # the allocation-free degree call is the exact FP32 pass: an approximate one is not offered
+    deg = (ctypes.c_double * 4)()
+    approx = fsg.params(0.1, kde_eps=1e-3)
+    assert lib.fsg_degrees_noalloc(buf, 4, 2, ctypes.byref(approx), deg, None) == fsg.FSG_ERR_UNSUPPORTED
     # capacity below n*L is refused
     rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(p), 4, 0, 0, buf, buf, buf, 8, ctypes.byref(m), None)
     assert rc == fsg.FSG_ERR_CAPACITY
@@ -92,5 +97,6 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(fsg.fsg_request) == 120
     assert ctypes.sizeof(fsg.fsg_result) == 48
     assert ctypes.sizeof(fsg.fsg_params) == 48
+    assert fsg.fsg_params.flag_eps.offset == 24 and fsg.fsg_params.kde_eps.offset == 28
     assert ctypes.sizeof(fsg.fsg_tree_opts) == 32
     assert ctypes.sizeof(fsg.fsg_stats) == 80
