@@ -83,6 +83,13 @@ extern "C" {
 
 typedef struct fsg_tree fsg_tree; /* opaque */
 
+/* Tree order (fsg_tree_opts.order). */
+#define FSG_ORDER_IDENTITY 0    /* position p holds point p (or d_perm[p])         */
+#define FSG_ORDER_SPATIAL 1     /* computed on the GPU from the points, at build   */
+                                /* and at every fsg_tree_update: each node above   */
+                                /* 32 points split at the tree's midpoint along    */
+                                /* its widest coordinate (to one of 256 buckets)   */
+
 typedef struct {
     /* Device int32 [n]: tree position p -> original point index (a
      * permutation), or NULL for the identity order.  Copied at build time. */
@@ -91,7 +98,12 @@ typedef struct {
      * [64, 1024]); 0 selects 128 (raised automatically for very large n).
      * Smaller values run more levels through the bin pass. */
     int32_t leaf_max;
-    int32_t reserved[5];
+    /* FSG_ORDER_IDENTITY | FSG_ORDER_SPATIAL (then d_perm must be NULL).  The
+     * order changes which points share a node, not the sampling distribution
+     * (Sec. 4.1); the split form and the approximate bin pass rely on compact
+     * nodes. */
+    int32_t order;
+    int32_t reserved[4];
 } fsg_tree_opts;
 
 typedef struct {
@@ -173,6 +185,13 @@ int fsg_build_tree(const float* d_points, int64_t n, int32_t d, const fsg_tree_o
  * non-finite coordinate).
  */
 int fsg_spatial_order(const float* h_points, int64_t n, int32_t d, int32_t leaf, int32_t* h_perm);
+
+/*
+ * The tree's order: d_perm_out[p] = original index of the point at tree
+ * position p (device int32 [n], caller-owned), asynchronous on the stream.
+ * Lets a caller (or a checker) reproduce the tree of FSG_ORDER_SPATIAL.
+ */
+int fsg_tree_perm(const fsg_tree* tree, int32_t* d_perm_out, void* stream);
 void fsg_free_tree(fsg_tree* tree);
 
 /* Number of points, dimension and depth ceil(log2 n) of a tree. */

@@ -303,6 +303,9 @@ int fsg::build_tree_internal(const float* d_points, int64_t n, int32_t d, const 
     if (!d_points || n < 1 || n > (int64_t)0x7fffffff - 4096 || d < 1 || d > 4096) return FSG_ERR_INVALID_ARG;
     int leaf_max = opts && opts->leaf_max ? opts->leaf_max : 0;
     if (leaf_max && (leaf_max < 64 || leaf_max > 1024 || (leaf_max & (leaf_max - 1)))) return FSG_ERR_INVALID_ARG;
+    const int order = opts ? opts->order : FSG_ORDER_IDENTITY;
+    if (order != FSG_ORDER_IDENTITY && order != FSG_ORDER_SPATIAL) return FSG_ERR_INVALID_ARG;
+    if (order == FSG_ORDER_SPATIAL && opts->d_perm) return FSG_ERR_INVALID_ARG;
     const bool auto_leaf = leaf_max == 0;
     if (auto_leaf) leaf_max = 128;
     if (d > kMaxFmaDim && leaf_max < 128) leaf_max = 128;  // the d > 16 tiles assume bins of > 64 points
@@ -339,8 +342,11 @@ int fsg::build_tree_internal(const float* d_points, int64_t n, int32_t d, const 
     alloc((void**)&t->inv, sizeof(int32_t) * (size_t)n);
     alloc((void**)&t->bnd, sizeof(int32_t) * (size_t)(t->nb + 1));
     alloc((void**)&t->status, sizeof(int32_t) * 8);
+    if (order == FSG_ORDER_SPATIAL) alloc((void**)&t->ord, sizeof(int32_t) * 2 * (size_t)n);
+    const int32_t* perm_in = opts ? opts->d_perm : nullptr;
+    if (e == cudaSuccess && t->ord) e = launch_spatial_order(d_points, n, d, kSpatialLeaf, t->ord, &perm_in, s);
     if (e == cudaSuccess) {
-        e = launch_tree_prep(t, d_points, opts ? opts->d_perm : nullptr, s);
+        e = launch_tree_prep(t, d_points, perm_in, s);
         t->launches += 2;
     }
     int rc = status_of(e);
@@ -394,6 +400,7 @@ void fsg_free_tree(fsg_tree* t) {
     tree_free(t, t->ws.base);
     tree_free(t, t->Xtt);
     tree_free(t, t->sboxes);
+    tree_free(t, t->ord);
     if (t->Xb) cudaFree(t->Xb);
     if (t->norms) cudaFree(t->norms);
     delete t;
@@ -561,8 +568,12 @@ int fsg_tree_update(fsg_tree* t, const float* d_points, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     begin_call(t);
     PhaseScope ph(t, FSG_PHASE_TREE, s);
-    // the stored order is reused: tree_prep reads perm[p] before rewriting it
-    cudaError_t e = launch_tree_prep(t, d_points, t->perm, s);
+    // the stored order is reused (tree_prep reads perm[p] before rewriting
+    // it), or, for FSG_ORDER_SPATIAL, computed again from the new points
+    const int32_t* perm_in = t->perm;
+    cudaError_t e = cudaSuccess;
+    if (t->ord) e = launch_spatial_order(d_points, t->n, t->d, kSpatialLeaf, t->ord, &perm_in, s);
+    if (e == cudaSuccess) e = launch_tree_prep(t, d_points, perm_in, s);
     t->launches += 2;
     int rc = status_of(e);
     if (rc == FSG_OK && t->Xb) {  // refresh the tensor-core copy (exactness re-checked on the device)
@@ -570,6 +581,12 @@ int fsg_tree_update(fsg_tree* t, const float* d_points, void* stream) {
         t->launches += 1;
     }
     return rc;
+}
+
+int fsg_tree_perm(const fsg_tree* t, int32_t* d_perm_out, void* stream) {
+    if (!t || !d_perm_out) return FSG_ERR_INVALID_ARG;
+    return status_of(cudaMemcpyAsync(d_perm_out, t->perm, sizeof(int32_t) * (size_t)t->n, cudaMemcpyDeviceToDevice,
+                                     (cudaStream_t)stream));
 }
 
 int fsg_profile(fsg_tree* t, int enable) {

@@ -33,12 +33,13 @@ FSG_PREC_AUTO, FSG_PREC_FP32, FSG_PREC_SPLIT_BF16, FSG_PREC_EXACT_INT = 0, 1, 2,
 FSG_EDGES_SET, FSG_EDGES_MULTI = 0, 1
 FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE, FSG_SCHED_CARRIED = 0, 1, 2
 FSG_ADMIT_ARRIVAL, FSG_ADMIT_RESPONSE_RATIO = 0, 1
+FSG_ORDER_IDENTITY, FSG_ORDER_SPATIAL = 0, 1
 
 # Names every build of the library must export (checked by the CPU tests
 # against include/fsg.h).
 EXPORTED = [
     "fsg_version", "fsg_error_string", "fsg_build_tree", "fsg_free_tree", "fsg_tree_info", "fsg_bin_pass_evals",
-    "fsg_spatial_order",
+    "fsg_spatial_order", "fsg_tree_perm",
     "fsg_autotune", "fsg_tree_tuning",
     "fsg_degrees", "fsg_sample_edges", "fsg_build_graph", "fsg_sync", "fsg_build_graph_host",
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
@@ -64,7 +65,8 @@ class fsg_params(ctypes.Structure):
 
 
 class fsg_tree_opts(ctypes.Structure):
-    _fields_ = [("d_perm", ctypes.c_void_p), ("leaf_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+    _fields_ = [("d_perm", ctypes.c_void_p), ("leaf_max", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class fsg_batch_item(ctypes.Structure):
@@ -150,6 +152,7 @@ def load(path: str = LIB_PATH):
     lib.fsg_server_destroy.argtypes = [P]
     lib.fsg_server_destroy.restype = None
     lib.fsg_spatial_order.argtypes = [P, ctypes.c_int64, I32, I32, P]
+    lib.fsg_tree_perm.argtypes = [P, P, P]
     for name in EXPORTED:
         if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy", "fsg_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -213,8 +216,9 @@ class Tree:
         return int(dep.value)
 
 
-def fsg_build_tree(points, perm=None, leaf_max: int = 0, stream=None) -> Tree:
-    """points: CUDA float32 [n][d] contiguous; perm: optional CUDA int32 [n]."""
+def fsg_build_tree(points, perm=None, leaf_max: int = 0, stream=None, order: int = 0) -> Tree:
+    """points: CUDA float32 [n][d] contiguous; perm: optional CUDA int32 [n];
+    order: FSG_ORDER_IDENTITY or FSG_ORDER_SPATIAL (computed on the GPU)."""
     import torch
     lib = load()
     if not (points.is_cuda and points.dtype == torch.float32 and points.dim() == 2):
@@ -223,10 +227,19 @@ def fsg_build_tree(points, perm=None, leaf_max: int = 0, stream=None) -> Tree:
     opts = fsg_tree_opts()
     opts.d_perm = None if perm is None else perm.contiguous().data_ptr()
     opts.leaf_max = leaf_max
+    opts.order = order
     h = ctypes.c_void_p()
     _check(lib.fsg_build_tree(_dptr(points), points.shape[0], points.shape[1], ctypes.byref(opts),
                               _stream_ptr(stream), ctypes.byref(h)), "fsg_build_tree")
     return Tree(h, points.shape[0], points.shape[1])
+
+
+def fsg_tree_perm(tree: Tree, stream=None):
+    """The tree's order as a CUDA int32 [n] tensor (position -> original index)."""
+    import torch
+    out = torch.empty(tree.n, dtype=torch.int32, device="cuda")
+    _check(load().fsg_tree_perm(tree.handle, _dptr(out), _stream_ptr(stream)), "fsg_tree_perm")
+    return out
 
 
 def fsg_spatial_order(points: np.ndarray, leaf: int = 32) -> np.ndarray:

@@ -56,6 +56,12 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     opts.leaf_max = 100  # not a power of two
     assert lib.fsg_build_tree(fake, 10, 2, ctypes.byref(opts), None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
     assert lib.fsg_build_tree(fake, 10, 2, None, None, None) == fsg.FSG_ERR_INVALID_ARG
+    opts = fsg.fsg_tree_opts()
+    opts.order = 2  # no such order
+    assert lib.fsg_build_tree(fake, 10, 2, ctypes.byref(opts), None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    opts.order, opts.d_perm = fsg.FSG_ORDER_SPATIAL, 0x2000  # a computed order and a given one
+    assert lib.fsg_build_tree(fake, 10, 2, ctypes.byref(opts), None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_tree_perm(None, fake, None) == fsg.FSG_ERR_INVALID_ARG
     p = fsg.params(0.1)
     assert lib.fsg_degrees(None, ctypes.byref(p), fake, None) == fsg.FSG_ERR_INVALID_ARG
     assert lib.fsg_sample_edges(None, ctypes.byref(p), 8, 0, fake, None, None) == fsg.FSG_ERR_INVALID_ARG
@@ -98,5 +104,5 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(fsg.fsg_result) == 48
     assert ctypes.sizeof(fsg.fsg_params) == 48
     assert fsg.fsg_params.flag_eps.offset == 24 and fsg.fsg_params.kde_eps.offset == 28
-    assert ctypes.sizeof(fsg.fsg_tree_opts) == 32
+    assert ctypes.sizeof(fsg.fsg_tree_opts) == 32 and fsg.fsg_tree_opts.order.offset == 12
     assert ctypes.sizeof(fsg.fsg_stats) == 80
