@@ -218,12 +218,11 @@ def run_ours(args):
     if args.kde_eps > 0 and not split:
         raise SystemExit("--kde-eps needs --precision split (the approximate bin pass is the split form's)")
     p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO, kde_eps=args.kde_eps)
-    perm = None
-    if split:  # spatial tree order: computed once on the host for the fixed input, outside the timed region
-        perm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
+    # split form: the spatial tree order, computed on the GPU in every step (fsg_tree_update)
+    order = fsg.FSG_ORDER_SPATIAL if split else fsg.FSG_ORDER_IDENTITY
     with torch.cuda.stream(stream):
         pts = torch.from_numpy(X).cuda()
-        tree = fsg.fsg_build_tree(pts, perm=perm, stream=stream)
+        tree = fsg.fsg_build_tree(pts, stream=stream, order=order)
         bufs = fsg.GraphBuffers(n, L, with_aux=False)
         bufs.deg = torch.empty(n, dtype=torch.float64, device="cuda")
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -378,11 +377,10 @@ def run_ours(args):
 
     def run_approx(eps, ref):
         # the approximate KDE (tree-pruned split bin pass) on the same input in
-        # the spatial tree order (computed on the host, outside the timed region)
+        # the spatial tree order, computed on the GPU inside every timed step
         pa = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16, kde_eps=eps)
-        sperm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
         with torch.cuda.stream(stream):
-            t2 = fsg.fsg_build_tree(pts, perm=sperm, stream=stream)
+            t2 = fsg.fsg_build_tree(pts, stream=stream, order=fsg.FSG_ORDER_SPATIAL)
         fsg.fsg_build_graph(t2, pa, L, seed, bufs=bufs, stream=stream)  # warm-up
         fsg.fsg_build_graph(t2, pa, L, seed, bufs=bufs, stream=stream)
         ams, bin_ms = [], []
@@ -403,7 +401,7 @@ def run_ours(args):
         ast = fsg.stats_dict(bufs)
         t2.close()
         at = statistics.mean(ams)
-        return {"precision": f"approximate KDE: split form, kde_eps = {eps:.3g}, spatial tree order",
+        return {"precision": f"approximate KDE: split form, kde_eps = {eps:.3g}, spatial tree order (GPU, in the step)",
                 "value": n * L / (at * 1e-3), "unit": UNIT, "ms_per_step": at, "bin_pass_ms": statistics.mean(bin_ms),
                 "executed_pairs": int(ast["n_bin_evals"]), "skipped_fraction": 1.0 - ast["n_bin_evals"] / (n * n),
                 "flagged_samples": ast["n_flagged"], "kde_error": kde_error(bufs.deg.cpu().numpy(), ref)}
@@ -446,7 +444,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate" if split else "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)",
-                               **({"precision": "split (spatial tree order)"} if split else {}),
+                               **({"precision": "split (spatial tree order, GPU, in the step)"} if split else {}),
                                **({"kde_eps": args.kde_eps} if args.kde_eps > 0 else {})),
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
@@ -567,8 +565,8 @@ def run_serving(args):
     admission = {"arrival": fsg.FSG_ADMIT_ARRIVAL, "ratio": fsg.FSG_ADMIT_RESPONSE_RATIO}[args.admission]
     server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8, admission=admission)
     p = fsg.params(sigma)
-    # --precision split: the d = 64 requests take the split-precision tensor-core
-    # bin pass (identity tree order; within the mode's stated bound)
+    # --precision split: the d = 64 requests take the split form (bin pass and
+    # leaf phase on the tensor cores, spatial tree order computed on the GPU)
     p_large = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16) if args.precision == "split" else p
     owner = {}
     lat, qms, edges_done = [], [], 0

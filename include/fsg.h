@@ -464,7 +464,9 @@ int fsg_sync(fsg_tree* tree, void* stream);
 
 /*
  * End-to-end entry point on HOST buffers: copies h_points to the device,
- * builds the tree, runs fsg_build_graph, and copies the edge list back.
+ * builds the tree (FSG_ORDER_SPATIAL for FSG_PREC_SPLIT_BF16, identity
+ * otherwise), runs fsg_build_graph, and copies the edge list back.  The
+ * server builds its trees the same way.
  *   h_src, h_dst (int32 [cap]), h_w (float32 [cap]), *h_m_out (edge count).
  * Blocks until the result is on the host.  The device buffers live in an
  * internal per-thread cache that grows to the largest (n, d, L) seen.

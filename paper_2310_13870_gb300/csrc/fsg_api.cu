@@ -342,7 +342,7 @@ int fsg::build_tree_internal(const float* d_points, int64_t n, int32_t d, const 
     alloc((void**)&t->inv, sizeof(int32_t) * (size_t)n);
     alloc((void**)&t->bnd, sizeof(int32_t) * (size_t)(t->nb + 1));
     alloc((void**)&t->status, sizeof(int32_t) * 8);
-    if (order == FSG_ORDER_SPATIAL) alloc((void**)&t->ord, sizeof(int32_t) * 2 * (size_t)n);
+    if (order == FSG_ORDER_SPATIAL) alloc(&t->ord, spatial_order_scratch_bytes(n, d));
     const int32_t* perm_in = opts ? opts->d_perm : nullptr;
     if (e == cudaSuccess && t->ord) e = launch_spatial_order(d_points, n, d, kSpatialLeaf, t->ord, &perm_in, s);
     if (e == cudaSuccess) {
@@ -821,14 +821,18 @@ int fsg_build_graph_host(const float* h_points, int64_t n, int32_t d, const fsg_
     }
     e = cudaMemcpyAsync(hc.d_points, h_points, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return status_of(e);
+    // the split form takes the spatial tree order (compact tiles for its centring)
+    const bool spatial = p->precision == FSG_PREC_SPLIT_BF16;
     fsg_tree* t = hc.tree;
-    if (t && t->n == n && t->d == d) {
+    if (t && t->n == n && t->d == d && (t->ord != nullptr) == spatial) {
         rc = fsg_tree_update(t, hc.d_points, stream);
         if (rc != FSG_OK) return rc;
     } else {
         fsg_free_tree(hc.tree);
         hc.tree = nullptr;
-        rc = fsg_build_tree(hc.d_points, n, d, nullptr, stream, &t);
+        fsg_tree_opts o{};
+        o.order = spatial ? FSG_ORDER_SPATIAL : FSG_ORDER_IDENTITY;
+        rc = fsg_build_tree(hc.d_points, n, d, &o, stream, &t);
         if (rc != FSG_OK) return rc;
         hc.tree = t;
     }

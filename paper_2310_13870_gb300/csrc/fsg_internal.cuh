@@ -78,7 +78,7 @@ struct fsg_tree {
     float* Xt = nullptr;     // [n_pad][dp]     tree-ordered points
     float* Xdup = nullptr;   // [n_pad][dp][2]  same, each coordinate twice (d <= 16)
     int32_t* perm = nullptr; // [n]  position -> original index
-    int32_t* ord = nullptr;  // [2n] scratch of the GPU spatial order (FSG_ORDER_SPATIAL)
+    void* ord = nullptr;     // scratch of the GPU spatial order (FSG_ORDER_SPATIAL)
     int32_t* inv = nullptr;  // [n]  original index -> position
     int32_t* bnd = nullptr;  // [nb+1] level-s0 node boundaries
     int32_t* status = nullptr;  // device status word
@@ -159,9 +159,11 @@ bool kde_bins_split_supported(const fsg_tree* t);
 // Bytes of the split-precision pass's per-tree workspace (boxes, query-tile
 // images, and the bins' images when the split leaf phase runs).
 size_t split_workspace_bytes(int64_t n, int64_t nb, bool bin_images);
-// GPU spatial order of d_points ([n][d]) into buf (2n int32); *out = the half holding it.
-cudaError_t launch_spatial_order(const float* d_points, int64_t n, int d, int leaf, int32_t* buf,
-                                 const int32_t** out, cudaStream_t s);
+// GPU spatial order of d_points ([n][d]) in the scratch buf
+// (spatial_order_scratch_bytes); *out = the array holding it.
+size_t spatial_order_scratch_bytes(int64_t n, int d);
+cudaError_t launch_spatial_order(const float* d_points, int64_t n, int d, int leaf, void* buf, const int32_t** out,
+                                 cudaStream_t s);
 constexpr int kSpatialLeaf = 32;
 // Split-precision leaf phase on the tensor cores: d in 17..64, bins of at
 // most 128 points (after the split bin pass, whose workspace it shares).

@@ -50,8 +50,8 @@ struct Slot {
 size_t request_bytes(const fsg_request& r) {
     size_t b = fsg::tree_bytes_estimate(r.n, r.d, r.L) + sizeof(float) * (size_t)r.n * r.d +
                (sizeof(int32_t) * 2 + sizeof(float)) * (size_t)r.n * r.L + 4096;
-    if (r.params.precision == FSG_PREC_SPLIT_BF16)  // bins hold at least 32 points
-        b += fsg::split_workspace_bytes(r.n, (r.n + 31) / 32, r.d > 16);
+    if (r.params.precision == FSG_PREC_SPLIT_BF16)  // bins hold at least 32 points; the order's scratch
+        b += fsg::split_workspace_bytes(r.n, (r.n + 31) / 32, r.d > 16) + fsg::spatial_order_scratch_bytes(r.n, r.d);
     return b;
 }
 
@@ -131,7 +131,10 @@ struct fsg_server {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? FSG_ERR_OOM : FSG_ERR_CUDA;
         }
-        int rc = fsg::build_tree_internal(s.d_points, r.n, r.d, nullptr, s.stream, pool, &s.tree);
+        // split-precision requests get the spatial tree order (compact tiles for its centring)
+        fsg_tree_opts topts{};
+        topts.order = r.params.precision == FSG_PREC_SPLIT_BF16 ? FSG_ORDER_SPATIAL : FSG_ORDER_IDENTITY;
+        int rc = fsg::build_tree_internal(s.d_points, r.n, r.d, &topts, s.stream, pool, &s.tree);
         if (rc != FSG_OK) return rc;
         rc = fsg_build_graph(s.tree, &r.params, r.L, r.seed, r.edge_mode, s.d_src, s.d_dst, s.d_w, (int64_t)cap,
                              s.d_m, nullptr, nullptr, nullptr, s.d_stats, s.stream);
