@@ -29,6 +29,7 @@ _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 TWO_SIGMA_SQ, SIGMA_SQ = 0, 1
 SELF_EXCLUDE, SELF_INCLUDE = 0, 1
 EDGES_SET, EDGES_MULTI = 0, 1
+GAUSSIAN, LAPLACIAN, EXPONENTIAL = 0, 1, 2  # kernel families of Sec. 2.1
 
 _lib = None
 
@@ -63,23 +64,25 @@ def _load():
     lib.ora_uniform.restype = f64
     lib.ora_gamma.argtypes = [f64, i32]
     lib.ora_gamma.restype = f64
-    lib.ora_kernel.argtypes = [P, P, i32, f64]
+    lib.ora_scale.argtypes = [f64, i32, i32]
+    lib.ora_scale.restype = f64
+    lib.ora_kernel.argtypes = [P, P, i32, f64, i32]
     lib.ora_kernel.restype = f64
     lib.ora_split.argtypes = [i64, i64]
     lib.ora_split.restype = i64
-    lib.ora_kde.argtypes = [P, i64, i32, P, f64, i32, i64, i64, i64]
+    lib.ora_kde.argtypes = [P, i64, i32, P, f64, i32, i32, i64, i64, i64]
     lib.ora_kde.restype = f64
     lib.ora_num_threads.argtypes = [i32]
     lib.ora_num_threads.restype = i32
-    lib.ora_degrees.argtypes = [P, i64, i32, f64, i32, P, i64, P, i32]
+    lib.ora_degrees.argtypes = [P, i64, i32, f64, i32, i32, P, i64, P, i32]
     lib.ora_degrees.restype = i32
-    lib.ora_sample.argtypes = [P, i64, i32, P, f64, i32, i32, u64, P, i64, P, P, P, i32]
+    lib.ora_sample.argtypes = [P, i64, i32, P, f64, i32, i32, i32, u64, P, i64, P, P, P, i32]
     lib.ora_sample.restype = i32
-    lib.ora_path_prob.argtypes = [P, i64, i32, P, f64, i32, i64, i64]
+    lib.ora_path_prob.argtypes = [P, i64, i32, P, f64, i32, i32, i64, i64]
     lib.ora_path_prob.restype = f64
-    lib.ora_weights.argtypes = [P, i64, i32, f64, i32, P, i64, P, P, P, P]
+    lib.ora_weights.argtypes = [P, i64, i32, f64, i32, i32, P, i64, P, P, P, P]
     lib.ora_weights.restype = i32
-    lib.ora_build_graph.argtypes = [P, i64, i32, P, f64, i32, i32, u64, i32, P, P, P, i64, P, P, P, P, i32]
+    lib.ora_build_graph.argtypes = [P, i64, i32, P, f64, i32, i32, i32, u64, i32, P, P, P, i64, P, P, P, P, i32]
     lib.ora_build_graph.restype = i32
     _lib = lib
     return lib
@@ -108,6 +111,12 @@ def gamma(sigma: float, scale_conv: int = TWO_SIGMA_SQ) -> float:
     return float(_load().ora_gamma(float(sigma), int(scale_conv)))
 
 
+def scale(sigma: float, kernel: int = GAUSSIAN, scale_conv: int = TWO_SIGMA_SQ) -> float:
+    """The family's scale: gamma for the Gaussian, 1/sigma for the Laplacian
+    and exponential kernels."""
+    return float(_load().ora_scale(float(sigma), int(scale_conv), int(kernel)))
+
+
 def philox4x32_10(ctr, key):
     c = np.ascontiguousarray(ctr, dtype=np.uint32)
     k = np.ascontiguousarray(key, dtype=np.uint32)
@@ -128,30 +137,31 @@ def split(lo: int, hi: int) -> int:
     return int(_load().ora_split(lo, hi))
 
 
-def kernel(a, b, gam: float) -> float:
+def kernel(a, b, gam: float, kernel: int = GAUSSIAN) -> float:
     a = np.ascontiguousarray(a, dtype=np.float32)
     b = np.ascontiguousarray(b, dtype=np.float32)
-    return float(_load().ora_kernel(_ptr(a), _ptr(b), a.shape[0], gam))
+    return float(_load().ora_kernel(_ptr(a), _ptr(b), a.shape[0], gam, kernel))
 
 
-def kde(X, gam, i, lo, hi, perm=None, self_mode=SELF_EXCLUDE) -> float:
+def kde(X, gam, i, lo, hi, perm=None, self_mode=SELF_EXCLUDE, kernel=GAUSSIAN) -> float:
     X = _points(X)
     p = _perm(perm)
-    return float(_load().ora_kde(_ptr(X), X.shape[0], X.shape[1], _ptr(p), gam, self_mode, i, lo, hi))
+    return float(_load().ora_kde(_ptr(X), X.shape[0], X.shape[1], _ptr(p), gam, kernel, self_mode, i, lo, hi))
 
 
-def degrees(X, gam, queries=None, self_mode=SELF_EXCLUDE, nthreads=0):
+def degrees(X, gam, queries=None, self_mode=SELF_EXCLUDE, nthreads=0, kernel=GAUSSIAN):
     X = _points(X)
     q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
     nq = X.shape[0] if q is None else q.shape[0]
     out = np.zeros(nq, dtype=np.float64)
-    rc = _load().ora_degrees(_ptr(X), X.shape[0], X.shape[1], gam, self_mode, _ptr(q), nq, _ptr(out), nthreads)
+    rc = _load().ora_degrees(_ptr(X), X.shape[0], X.shape[1], gam, kernel, self_mode, _ptr(q), nq, _ptr(out),
+                             nthreads)
     if rc != 0:
         raise ValueError(f"ora_degrees failed ({rc})")
     return out
 
 
-def sample(X, gam, L, seed, queries=None, perm=None, self_mode=SELF_EXCLUDE, nthreads=0):
+def sample(X, gam, L, seed, queries=None, perm=None, self_mode=SELF_EXCLUDE, nthreads=0, kernel=GAUSSIAN):
     """Returns (samples[nq][L] int64, margin[nq][L] f64, levels[nq][L] i32)."""
     X = _points(X)
     p = _perm(perm)
@@ -160,20 +170,20 @@ def sample(X, gam, L, seed, queries=None, perm=None, self_mode=SELF_EXCLUDE, nth
     smp = np.zeros((nq, L), dtype=np.int64)
     mrg = np.zeros((nq, L), dtype=np.float64)
     lev = np.zeros((nq, L), dtype=np.int32)
-    rc = _load().ora_sample(_ptr(X), X.shape[0], X.shape[1], _ptr(p), gam, self_mode, L, seed,
+    rc = _load().ora_sample(_ptr(X), X.shape[0], X.shape[1], _ptr(p), gam, kernel, self_mode, L, seed,
                             _ptr(q), nq, _ptr(smp), _ptr(mrg), _ptr(lev), nthreads)
     if rc != 0:
         raise ValueError(f"ora_sample failed ({rc})")
     return smp, mrg, lev
 
 
-def path_prob(X, gam, i, p, perm=None, self_mode=SELF_EXCLUDE) -> float:
+def path_prob(X, gam, i, p, perm=None, self_mode=SELF_EXCLUDE, kernel=GAUSSIAN) -> float:
     X = _points(X)
     pp = _perm(perm)
-    return float(_load().ora_path_prob(_ptr(X), X.shape[0], X.shape[1], _ptr(pp), gam, self_mode, i, p))
+    return float(_load().ora_path_prob(_ptr(X), X.shape[0], X.shape[1], _ptr(pp), gam, kernel, self_mode, i, p))
 
 
-def weights(X, gam, L, deg, src, dst):
+def weights(X, gam, L, deg, src, dst, kernel=GAUSSIAN):
     """Returns (k, w) for the given pairs; deg indexed by original index."""
     X = _points(X)
     deg = np.ascontiguousarray(deg, dtype=np.float64)
@@ -181,14 +191,15 @@ def weights(X, gam, L, deg, src, dst):
     t = np.ascontiguousarray(dst, dtype=np.int64)
     k = np.zeros(s.shape[0], dtype=np.float64)
     w = np.zeros(s.shape[0], dtype=np.float64)
-    rc = _load().ora_weights(_ptr(X), X.shape[0], X.shape[1], gam, L, _ptr(deg), s.shape[0],
+    rc = _load().ora_weights(_ptr(X), X.shape[0], X.shape[1], gam, kernel, L, _ptr(deg), s.shape[0],
                              _ptr(s), _ptr(t), _ptr(k), _ptr(w))
     if rc != 0:
         raise ValueError(f"ora_weights failed ({rc})")
     return k, w
 
 
-def build_graph(X, gam, L, seed, perm=None, self_mode=SELF_EXCLUDE, edge_mode=EDGES_SET, nthreads=0):
+def build_graph(X, gam, L, seed, perm=None, self_mode=SELF_EXCLUDE, edge_mode=EDGES_SET, nthreads=0,
+                kernel=GAUSSIAN):
     """Whole of Algorithm 2.  Returns dict(src, dst, w, deg, samples, n_self)."""
     X = _points(X)
     n = X.shape[0]
@@ -201,7 +212,7 @@ def build_graph(X, gam, L, seed, perm=None, self_mode=SELF_EXCLUDE, edge_mode=ED
     deg = np.zeros(n, dtype=np.float64)
     smp = np.zeros((n, L), dtype=np.int64)
     nself = np.zeros(1, dtype=np.int64)
-    rc = _load().ora_build_graph(_ptr(X), n, X.shape[1], _ptr(p), gam, self_mode, L, seed, edge_mode,
+    rc = _load().ora_build_graph(_ptr(X), n, X.shape[1], _ptr(p), gam, kernel, self_mode, L, seed, edge_mode,
                                  _ptr(src), _ptr(dst), _ptr(w), cap, _ptr(m), _ptr(deg), _ptr(smp),
                                  _ptr(nself), nthreads)
     if rc != 0:

@@ -13,6 +13,9 @@
  *   - Gaussian kernel k(x_i,x_j) = exp(-gamma * ||x_i - x_j||^2)   [Sec. 2.1]
  *     with gamma = 1/(2 sigma^2) (default) or 1/sigma^2 (the form printed in
  *     Sec. 2.1); all arithmetic in FP64 with direct coordinate differences.
+ *   - the two other kernels Sec. 2.1 names: Laplacian exp(-c ||x_i - x_j||_1)
+ *     and exponential exp(-c ||x_i - x_j||_2), c = 1/sigma (a reading: the
+ *     paper gives the norm in the exponent, not the scale).
  *   - KDE over a contiguous range of tree positions, g_[a,b)(y_i)  [Eq. 1]
  *     with Neumaier-compensated summation.
  *   - The recursive halving descent of Algorithm 1 / Sec. 4.1: the left half
@@ -92,12 +95,22 @@ double ora_gamma(double sigma, int scale_conv) {
     return 1.0 / (2.0 * sigma * sigma);
 }
 
-double ora_kernel(const float* a, const float* b, int d, double gamma) {
+double ora_scale(double sigma, int scale_conv, int family) {
+    if (family != ORA_GAUSSIAN) return 1.0 / sigma;
+    return ora_gamma(sigma, scale_conv);
+}
+
+/* k(a, b) of the family: the exponent is -scale times the squared Euclidean
+ * distance (Gaussian), the l1 distance (Laplacian) or the Euclidean distance
+ * (exponential). */
+double ora_kernel(const float* a, const float* b, int d, double gamma, int family) {
     double s = 0.0;
     for (int t = 0; t < d; ++t) {
         double diff = (double)a[t] - (double)b[t];
-        s += diff * diff;
+        if (family == ORA_LAPLACIAN) s += fabs(diff);
+        else s += diff * diff;
     }
+    if (family == ORA_EXPONENTIAL) s = sqrt(s);
     return exp(-gamma * s);
 }
 
@@ -108,7 +121,7 @@ double ora_kernel(const float* a, const float* b, int d, double gamma) {
 int64_t ora_split(int64_t lo, int64_t hi) { return lo + (hi - lo) / 2; }
 
 /* KDE of query point i (original index) over tree positions [lo,hi) (Eq. 1). */
-double ora_kde(const float* X, int64_t n, int d, const int64_t* perm, double gamma,
+double ora_kde(const float* X, int64_t n, int d, const int64_t* perm, double gamma, int family,
                int self_mode, int64_t i, int64_t lo, int64_t hi) {
     (void)n;
     const float* xi = X + (size_t)i * (size_t)d;
@@ -116,7 +129,7 @@ double ora_kde(const float* X, int64_t n, int d, const int64_t* perm, double gam
     for (int64_t p = lo; p < hi; ++p) {
         int64_t j = perm ? perm[p] : p;
         if (j == i && self_mode == ORA_SELF_EXCLUDE) continue;
-        double v = ora_kernel(xi, X + (size_t)j * (size_t)d, d, gamma);
+        double v = ora_kernel(xi, X + (size_t)j * (size_t)d, d, gamma, family);
         double t = sum + v;
         if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
         else comp += (v - t) + sum;
@@ -170,20 +183,20 @@ static void ora_parallel_for(int64_t nq, int nthreads, ora_task_fn fn, void* ctx
 /* Degrees g_[1,n](x_i) (Algorithm 2).                                        */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    const float* X; int64_t n; int d; double gamma; int self_mode;
+    const float* X; int64_t n; int d; double gamma; int family; int self_mode;
     const int64_t* queries; double* deg;
 } ora_deg_ctx;
 
 static void ora_deg_task(void* c, int64_t q) {
     ora_deg_ctx* x = (ora_deg_ctx*)c;
     int64_t i = x->queries ? x->queries[q] : q;
-    x->deg[q] = ora_kde(x->X, x->n, x->d, NULL, x->gamma, x->self_mode, i, 0, x->n);
+    x->deg[q] = ora_kde(x->X, x->n, x->d, NULL, x->gamma, x->family, x->self_mode, i, 0, x->n);
 }
 
-int ora_degrees(const float* X, int64_t n, int d, double gamma, int self_mode,
+int ora_degrees(const float* X, int64_t n, int d, double gamma, int family, int self_mode,
                 const int64_t* queries, int64_t nq, double* deg, int nthreads) {
     if (!X || n < 1 || d < 1 || !deg || !(gamma > 0)) return -1;
-    ora_deg_ctx c = {X, n, d, gamma, self_mode, queries, deg};
+    ora_deg_ctx c = {X, n, d, gamma, family, self_mode, queries, deg};
     ora_parallel_for(nq, nthreads, ora_deg_task, &c);
     return 0;
 }
@@ -198,10 +211,10 @@ typedef struct { int64_t lo, hi; double g; } ora_memo_entry;
 typedef struct { ora_memo_entry* e; int64_t len, cap; } ora_memo;
 
 static double ora_memo_kde(ora_memo* m, const float* X, int64_t n, int d, const int64_t* perm,
-                           double gamma, int self_mode, int64_t i, int64_t lo, int64_t hi) {
+                           double gamma, int family, int self_mode, int64_t i, int64_t lo, int64_t hi) {
     for (int64_t t = 0; t < m->len; ++t)
         if (m->e[t].lo == lo && m->e[t].hi == hi) return m->e[t].g;
-    double g = ora_kde(X, n, d, perm, gamma, self_mode, i, lo, hi);
+    double g = ora_kde(X, n, d, perm, gamma, family, self_mode, i, lo, hi);
     if (m->len == m->cap) {
         m->cap = m->cap ? 2 * m->cap : 256;
         m->e = (ora_memo_entry*)realloc(m->e, (size_t)m->cap * sizeof(ora_memo_entry));
@@ -212,7 +225,7 @@ static double ora_memo_kde(ora_memo* m, const float* X, int64_t n, int d, const 
 
 typedef struct {
     const float* X; int64_t n; int d; const int64_t* perm;
-    double gamma; int self_mode; int L; uint64_t seed;
+    double gamma; int family; int self_mode; int L; uint64_t seed;
     const int64_t* queries; int64_t* samples; double* margin; int32_t* levels;
 } ora_sample_ctx;
 
@@ -220,7 +233,7 @@ static void ora_sample_task(void* c, int64_t q) {
     ora_sample_ctx* x = (ora_sample_ctx*)c;
     int64_t i = x->queries ? x->queries[q] : q;
     ora_memo memo = {NULL, 0, 0};
-    double root = ora_memo_kde(&memo, x->X, x->n, x->d, x->perm, x->gamma, x->self_mode, i, 0, x->n);
+    double root = ora_memo_kde(&memo, x->X, x->n, x->d, x->perm, x->gamma, x->family, x->self_mode, i, 0, x->n);
     for (int l = 0; l < x->L; ++l) {
         size_t o = (size_t)q * (size_t)x->L + (size_t)l;
         double mrg = INFINITY;
@@ -235,8 +248,8 @@ static void ora_sample_task(void* c, int64_t q) {
         uint32_t lev = 0;
         while (hi - lo > 1) {
             int64_t mid = ora_split(lo, hi);
-            double gl = ora_memo_kde(&memo, x->X, x->n, x->d, x->perm, x->gamma, x->self_mode, i, lo, mid);
-            double gr = ora_memo_kde(&memo, x->X, x->n, x->d, x->perm, x->gamma, x->self_mode, i, mid, hi);
+            double gl = ora_memo_kde(&memo, x->X, x->n, x->d, x->perm, x->gamma, x->family, x->self_mode, i, lo, mid);
+            double gr = ora_memo_kde(&memo, x->X, x->n, x->d, x->perm, x->gamma, x->family, x->self_mode, i, mid, hi);
             double r = gl / (gl + gr);
             double u = ora_uniform(x->seed, (uint32_t)i, (uint32_t)l, lev);
             double dm = fabs(u - r);
@@ -251,25 +264,25 @@ static void ora_sample_task(void* c, int64_t q) {
     free(memo.e);
 }
 
-int ora_sample(const float* X, int64_t n, int d, const int64_t* perm, double gamma, int self_mode,
+int ora_sample(const float* X, int64_t n, int d, const int64_t* perm, double gamma, int family, int self_mode,
                int L, uint64_t seed, const int64_t* queries, int64_t nq,
                int64_t* samples, double* margin, int32_t* levels, int nthreads) {
     if (!X || n < 1 || d < 1 || L < 1 || !samples || !(gamma > 0)) return -1;
-    ora_sample_ctx c = {X, n, d, perm, gamma, self_mode, L, seed, queries, samples, margin, levels};
+    ora_sample_ctx c = {X, n, d, perm, gamma, family, self_mode, L, seed, queries, samples, margin, levels};
     ora_parallel_for(nq, nthreads, ora_sample_task, &c);
     return 0;
 }
 
 /* Probability that the descent of query i ends at tree position p: the      */
 /* product, over the levels on the path to p, of the chosen half's share.     */
-double ora_path_prob(const float* X, int64_t n, int d, const int64_t* perm, double gamma,
+double ora_path_prob(const float* X, int64_t n, int d, const int64_t* perm, double gamma, int family,
                      int self_mode, int64_t i, int64_t p) {
     int64_t lo = 0, hi = n;
     double prob = 1.0;
     while (hi - lo > 1) {
         int64_t mid = ora_split(lo, hi);
-        double gl = ora_kde(X, n, d, perm, gamma, self_mode, i, lo, mid);
-        double gr = ora_kde(X, n, d, perm, gamma, self_mode, i, mid, hi);
+        double gl = ora_kde(X, n, d, perm, gamma, family, self_mode, i, lo, mid);
+        double gr = ora_kde(X, n, d, perm, gamma, family, self_mode, i, mid, hi);
         if (gl + gr <= 0.0) return 0.0;
         if (p < mid) { prob *= gl / (gl + gr); hi = mid; }
         else { prob *= gr / (gl + gr); lo = mid; }
@@ -282,13 +295,13 @@ double ora_path_prob(const float* X, int64_t n, int d, const int64_t* perm, doub
 /* deg is indexed by original point index and holds g_[1,n] for every point  */
 /* that appears in src or dst.                                               */
 /* ------------------------------------------------------------------------ */
-int ora_weights(const float* X, int64_t n, int d, double gamma, int L, const double* deg,
+int ora_weights(const float* X, int64_t n, int d, double gamma, int family, int L, const double* deg,
                 int64_t m, const int64_t* src, const int64_t* dst, double* k_out, double* w_out) {
     (void)n;
     if (!X || !deg || (m > 0 && (!src || !dst || !w_out))) return -1;
     for (int64_t e = 0; e < m; ++e) {
         int64_t i = src[e], j = dst[e];
-        double k = ora_kernel(X + (size_t)i * (size_t)d, X + (size_t)j * (size_t)d, d, gamma);
+        double k = ora_kernel(X + (size_t)i * (size_t)d, X + (size_t)j * (size_t)d, d, gamma, family);
         double pi = fmin((double)L * k / deg[i], 1.0);
         double pj = fmin((double)L * k / deg[j], 1.0);
         double ph = pi + pj - pi * pj;
@@ -313,7 +326,7 @@ static int ora_cmp_pair(const void* a, const void* b) {
     return 0;
 }
 
-int ora_build_graph(const float* X, int64_t n, int d, const int64_t* perm, double gamma,
+int ora_build_graph(const float* X, int64_t n, int d, const int64_t* perm, double gamma, int family,
                     int self_mode, int L, uint64_t seed, int edge_mode,
                     int64_t* src, int64_t* dst, double* w, int64_t cap, int64_t* m_out,
                     double* deg_out, int64_t* samples_out, int64_t* n_self_out, int nthreads) {
@@ -321,8 +334,8 @@ int ora_build_graph(const float* X, int64_t n, int d, const int64_t* perm, doubl
     double* deg = (double*)malloc((size_t)n * sizeof(double));
     int64_t* smp = (int64_t*)malloc((size_t)n * (size_t)L * sizeof(int64_t));
     if (!deg || !smp) { free(deg); free(smp); return -2; }
-    ora_degrees(X, n, d, gamma, self_mode, NULL, n, deg, nthreads);
-    ora_sample(X, n, d, perm, gamma, self_mode, L, seed, NULL, n, smp, NULL, NULL, nthreads);
+    ora_degrees(X, n, d, gamma, family, self_mode, NULL, n, deg, nthreads);
+    ora_sample(X, n, d, perm, gamma, family, self_mode, L, seed, NULL, n, smp, NULL, NULL, nthreads);
     int64_t cnt = 0, nself = 0;
     int64_t* pairs = (int64_t*)malloc((size_t)n * (size_t)L * 2 * sizeof(int64_t));
     if (!pairs) { free(deg); free(smp); return -2; }
@@ -356,7 +369,7 @@ int ora_build_graph(const float* X, int64_t n, int d, const int64_t* perm, doubl
         rc = -3;
     } else {
         for (int64_t e = 0; e < cnt; ++e) { src[e] = pairs[2 * e]; dst[e] = pairs[2 * e + 1]; }
-        ora_weights(X, n, d, gamma, L, deg, cnt, src, dst, NULL, w);
+        ora_weights(X, n, d, gamma, family, L, deg, cnt, src, dst, NULL, w);
     }
     *m_out = cnt;
     if (deg_out) memcpy(deg_out, deg, (size_t)n * sizeof(double));

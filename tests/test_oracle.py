@@ -305,3 +305,67 @@ def test_golden_two_moons_regression():
     np.testing.assert_array_equal(g["src"], gold["src"])
     np.testing.assert_array_equal(g["dst"], gold["dst"])
     np.testing.assert_allclose(g["w"], gold["w"], rtol=1e-14)
+
+
+# ---- the other kernels of Sec. 2.1: Laplacian (l1 norm in the exponent) and
+# exponential (l2 norm), k = exp(-c ||x - y||), c = 1/sigma
+
+def _family_matrix(X, c, family):
+    X = np.asarray(X, dtype=np.float64)
+    metric = {ora.GAUSSIAN: "sqeuclidean", ora.LAPLACIAN: "cityblock", ora.EXPONENTIAL: "euclidean"}[family]
+    return np.exp(-c * cdist(X, X, metric))
+
+
+def test_kernel_families_closed_form():
+    # a 3-4-5 triangle: squared l2 25, l1 7, l2 5 give three different values
+    a = np.zeros(4, np.float32)
+    b = np.array([3.0, 0.0, -4.0, 0.0], np.float32)
+    sigma = 2.5
+    assert math.isclose(ora.scale(sigma, ora.LAPLACIAN), 0.4, rel_tol=1e-15)
+    assert math.isclose(ora.scale(sigma, ora.EXPONENTIAL), 0.4, rel_tol=1e-15)
+    assert math.isclose(ora.scale(sigma, ora.GAUSSIAN), 1.0 / (2 * 2.5 * 2.5), rel_tol=1e-15)
+    assert math.isclose(ora.kernel(a, b, 0.4, ora.LAPLACIAN), math.exp(-0.4 * 7.0), rel_tol=1e-15)
+    assert math.isclose(ora.kernel(a, b, 0.4, ora.EXPONENTIAL), math.exp(-0.4 * 5.0), rel_tol=1e-15)
+    assert math.isclose(ora.kernel(a, b, 0.4, ora.GAUSSIAN), math.exp(-0.4 * 25.0), rel_tol=1e-15)
+    for f in (ora.LAPLACIAN, ora.EXPONENTIAL):
+        assert ora.kernel(a, a, 0.4, f) == 1.0
+
+
+@pytest.mark.parametrize("family", [ora.LAPLACIAN, ora.EXPONENTIAL])
+def test_family_degrees_match_bruteforce(family):
+    rng = np.random.default_rng(11)
+    X = rng.normal(size=(61, 5)).astype(np.float32)
+    c = 0.9
+    K = _family_matrix(X, c, family)
+    np.fill_diagonal(K, 0.0)
+    np.testing.assert_allclose(ora.degrees(X, c, kernel=family), K.sum(1), rtol=1e-13)
+
+
+@pytest.mark.parametrize("family", [ora.LAPLACIAN, ora.EXPONENTIAL])
+@pytest.mark.parametrize("n", [3, 8, 13])
+def test_family_path_probability_telescopes_to_target(family, n):
+    # Lemma 1's telescoping holds for any non-negative kernel: the path product
+    # is k(x_i, x_j) / deg(x_i) for every (i, j)
+    rng = np.random.default_rng(100 + n)
+    X = (rng.normal(size=(n, 3)) * 0.8).astype(np.float32)
+    c = 1.1
+    perm = rng.permutation(n)
+    pos = np.empty(n, dtype=np.int64)
+    pos[perm] = np.arange(n)
+    K = _family_matrix(X, c, family)
+    np.fill_diagonal(K, 0.0)
+    for i in range(n):
+        want = K[i] / K[i].sum()
+        got = np.array([ora.path_prob(X, c, i, pos[j], perm=perm, kernel=family) for j in range(n)])
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("family", [ora.LAPLACIAN, ora.EXPONENTIAL])
+def test_family_weights_and_graph(family):
+    # Eq. 2 with the family's k; two points: p_hat = 1, w = k
+    X = np.array([[0.0, 0.0], [0.6, -0.8]], np.float32)  # l1 1.4, l2 1.0
+    c = 0.5
+    g = ora.build_graph(X, c, 4, 0, kernel=family)
+    k = math.exp(-c * (1.4 if family == ora.LAPLACIAN else 1.0))
+    assert len(g["w"]) == 1 and math.isclose(g["w"][0], k, rel_tol=1e-7)
+    np.testing.assert_allclose(g["deg"], [k, k], rtol=1e-7)
