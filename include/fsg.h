@@ -71,6 +71,16 @@ extern "C" {
                                 /* only form with the approximate bin pass       */
                                 /* (fsg_params.kde_eps)                          */
 #define FSG_PREC_EXACT_INT 3    /* tcgen05 BF16 on data that are k/255 exactly    */
+/* Kernel family (Sec. 2.1): the exponent of k(x, y) is minus the scale times
+ * the squared Euclidean distance (Gaussian, scale gamma of scale_conv), the
+ * l1 distance (Laplacian, scale 1/sigma) or the Euclidean distance
+ * (exponential, scale 1/sigma).  The Laplacian and exponential kernels run on
+ * the fused FP32 path for d <= 16 with bins of 65..128 points (the default
+ * tree for most n from 65 to 262,144 at d <= 16); elsewhere
+ * FSG_ERR_UNSUPPORTED. */
+#define FSG_KERNEL_GAUSSIAN 0
+#define FSG_KERNEL_LAPLACIAN 1
+#define FSG_KERNEL_EXPONENTIAL 2
 /* Edge semantics of Algorithm 2's set union. */
 #define FSG_EDGES_SET 0         /* one edge per unordered pair {i,j} sampled      */
 #define FSG_EDGES_MULTI 1       /* one edge per (non-self) sample                 */
@@ -133,7 +143,8 @@ typedef struct {
      * FSG_ERR_INVALID_ARG.  The paper's bound for the method is
      * eps <= 1/(6 log n). */
     float kde_eps;
-    int32_t reserved[4];
+    int32_t kernel;        /* FSG_KERNEL_* (0: Gaussian)                         */
+    int32_t reserved[3];
 } fsg_params;
 
 /* Device-side statistics of one fsg_build_graph call (all int64). */

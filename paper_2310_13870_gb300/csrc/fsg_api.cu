@@ -39,12 +39,17 @@ int check_params(const fsg_params* p) {
         return FSG_ERR_INVALID_ARG;
     if (!(p->flag_eps >= 0.f) || !std::isfinite(p->flag_eps) || p->flag_eps > 0.25f) return FSG_ERR_INVALID_ARG;
     if (!(p->kde_eps >= 0.f) || !std::isfinite(p->kde_eps) || p->kde_eps > 0.5f) return FSG_ERR_INVALID_ARG;
+    if (p->kernel != FSG_KERNEL_GAUSSIAN && p->kernel != FSG_KERNEL_LAPLACIAN && p->kernel != FSG_KERNEL_EXPONENTIAL)
+        return FSG_ERR_INVALID_ARG;
     return FSG_OK;
 }
 
 KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
-    const double gamma = p->scale_conv == FSG_SIGMA_SQ ? 1.0 / (p->sigma * p->sigma)
-                                                       : 1.0 / (2.0 * p->sigma * p->sigma);
+    // Gaussian: gamma of the bandwidth convention; Laplacian and exponential:
+    // 1/sigma times their distance
+    const double gamma = p->kernel != FSG_KERNEL_GAUSSIAN ? 1.0 / p->sigma
+                         : p->scale_conv == FSG_SIGMA_SQ  ? 1.0 / (p->sigma * p->sigma)
+                                                          : 1.0 / (2.0 * p->sigma * p->sigma);
     KernelParams kp;
     kp.precision = p->precision;
     kp.gamma = (float)gamma;
@@ -57,6 +62,7 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     // split form's FP32 tensor-core accumulation adds up to about 4e-4)
     kp.flag_eps = p->flag_eps > 0.f ? p->flag_eps : (p->precision == FSG_PREC_SPLIT_BF16 ? 0x1p-10f : 0x1p-13f);
     kp.kde_eps = p->kde_eps;
+    kp.family = p->kernel;
     return kp;
 }
 
@@ -129,6 +135,12 @@ int64_t bin_pass_evals(const fsg_tree* t, int precision) {
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
+    // the Laplacian and exponential kernels: the fused FP32 path of the
+    // symmetric bin pass and the 128-point leaf kernel
+    if (p->kernel != FSG_KERNEL_GAUSSIAN &&
+        (t->d > kMaxFmaDim || (p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32) ||
+         p->schedule != FSG_SCHED_FUSED || !kde_bins_sym_supported(t) || !use_leaf128(t)))
+        return FSG_ERR_UNSUPPORTED;
     // the approximate bin pass is the split form's tile pruning
     if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED))
         return FSG_ERR_UNSUPPORTED;

@@ -546,8 +546,8 @@ constexpr int kLC = 128;  // items per chunk = threads per CTA
 constexpr int kLV = 31;   // kept node sums per item (node h at h - 1), odd row stride
 
 // Kernel values of the point at Pr for two queries (packed lanes), the point
-// dropped for a query whose own local index it is.
-template <int D, bool SELF>
+// dropped for a query whose own local index it is.  F: the kernel family.
+template <int D, int F, bool SELF>
 __device__ __forceinline__ uint64_t leaf_kv2(const uint64_t (&qd)[D], const float4* __restrict__ Pr, uint64_t nc2,
                                              int r, int sa, int sb) {
     constexpr int DH = (D + 1) / 2;
@@ -556,14 +556,14 @@ __device__ __forceinline__ uint64_t leaf_kv2(const uint64_t (&qd)[D], const floa
     for (int u = 0; u < DH; ++u) {
         const float4 c4 = Pr[u];
         uint64_t dd = f2_sub(qd[2 * u], f2_pack(c4.x, c4.y));
-        s2 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s2);
+        s2 = u == 0 ? fam_first2<F>(dd) : fam_acc2<F>(dd, s2);
         if (2 * u + 1 < D) {
             dd = f2_sub(qd[2 * u + 1], f2_pack(c4.z, c4.w));
-            s3 = u == 0 ? f2_mul(dd, dd) : f2_fma(dd, dd, s3);
+            s3 = u == 0 ? fam_first2<F>(dd) : fam_acc2<F>(dd, s3);
         }
     }
     if (D > 1) s2 = f2_add(s2, s3);
-    const float2 sv = f2_unpack(f2_mul(s2, nc2));
+    const float2 sv = f2_unpack(f2_mul(fam_fin2<F>(s2), nc2));
     float ka = ex2_approx(sv.x), kb = ex2_approx(sv.y);
     if (SELF) {
         if (r == sa) ka = 0.f;
@@ -573,7 +573,7 @@ __device__ __forceinline__ uint64_t leaf_kv2(const uint64_t (&qd)[D], const floa
 }
 
 // One lane of leaf_kv2, operation for operation.
-template <int D>
+template <int D, int F>
 __device__ __forceinline__ float leaf_kv1(const float (&x)[D], const float4* __restrict__ Pr, float neg_c) {
     constexpr int DH = (D + 1) / 2;
     float s2 = 0.f, s3 = 0.f;
@@ -581,18 +581,18 @@ __device__ __forceinline__ float leaf_kv1(const float (&x)[D], const float4* __r
     for (int u = 0; u < DH; ++u) {
         const float4 c4 = Pr[u];
         float dd = __fsub_rn(x[2 * u], c4.x);
-        s2 = u == 0 ? __fmul_rn(dd, dd) : __fmaf_rn(dd, dd, s2);
+        s2 = u == 0 ? fam_first1<F>(dd) : fam_acc1<F>(dd, s2);
         if (2 * u + 1 < D) {
             dd = __fsub_rn(x[2 * u + 1], c4.z);
-            s3 = u == 0 ? __fmul_rn(dd, dd) : __fmaf_rn(dd, dd, s3);
+            s3 = u == 0 ? fam_first1<F>(dd) : fam_acc1<F>(dd, s3);
         }
     }
     if (D > 1) s2 = __fadd_rn(s2, s3);
-    return ex2_approx(__fmul_rn(s2, neg_c));
+    return ex2_approx(__fmul_rn(fam_fin1<F>(s2), neg_c));
 }
 
 // Sums of the eight depth-5 nodes of quarter w for the lane's two items.
-template <int D, bool SELF>
+template <int D, int F, bool SELF>
 __device__ __forceinline__ void leaf_quarter(const uint64_t (&qd)[D], const float4* __restrict__ P2,
                                              const int32_t* __restrict__ r5, int w, uint64_t nc2, int sa, int sb,
                                              uint64_t (&n5)[8]) {
@@ -600,11 +600,11 @@ __device__ __forceinline__ void leaf_quarter(const uint64_t (&qd)[D], const floa
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int r0 = r5[8 * w + j], c = r5[8 * w + j + 1] - r0;  // 2..4 points
-        uint64_t v = f2_add(leaf_kv2<D, SELF>(qd, P2 + (size_t)r0 * DH, nc2, r0, sa, sb),
-                            leaf_kv2<D, SELF>(qd, P2 + (size_t)(r0 + 1) * DH, nc2, r0 + 1, sa, sb));
+        uint64_t v = f2_add(leaf_kv2<D, F, SELF>(qd, P2 + (size_t)r0 * DH, nc2, r0, sa, sb),
+                            leaf_kv2<D, F, SELF>(qd, P2 + (size_t)(r0 + 1) * DH, nc2, r0 + 1, sa, sb));
         if (c > 2) {
-            uint64_t v2 = leaf_kv2<D, SELF>(qd, P2 + (size_t)(r0 + 2) * DH, nc2, r0 + 2, sa, sb);
-            if (c > 3) v2 = f2_add(v2, leaf_kv2<D, SELF>(qd, P2 + (size_t)(r0 + 3) * DH, nc2, r0 + 3, sa, sb));
+            uint64_t v2 = leaf_kv2<D, F, SELF>(qd, P2 + (size_t)(r0 + 2) * DH, nc2, r0 + 2, sa, sb);
+            if (c > 3) v2 = f2_add(v2, leaf_kv2<D, F, SELF>(qd, P2 + (size_t)(r0 + 3) * DH, nc2, r0 + 3, sa, sb));
             v = f2_add(v, v2);
         }
         n5[j] = v;
@@ -626,7 +626,7 @@ struct Leaf128Layout {
     static constexpr size_t total = V + (size_t)kLC * kLV * 4;
 };
 
-template <int D>
+template <int D, int F>
 __global__ void __launch_bounds__(kLC)
 leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, const int32_t* __restrict__ bnd,
                int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
@@ -703,8 +703,8 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
             const bool self_here = kp.self_exclude &&
                                    __any_sync(0xffffffffu, (sa >= lo && sa < hi) || (sb >= lo && sb < hi));
             uint64_t n5[8];
-            if (self_here) leaf_quarter<D, true>(qd, P2, r5, w, nc2, sa, sb, n5);
-            else leaf_quarter<D, false>(qd, P2, r5, w, nc2, sa, sb, n5);
+            if (self_here) leaf_quarter<D, F, true>(qd, P2, r5, w, nc2, sa, sb, n5);
+            else leaf_quarter<D, F, false>(qd, P2, r5, w, nc2, sa, sb, n5);
             uint64_t n4[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) n4[i] = f2_add(n5[2 * i], n5[2 * i + 1]);
@@ -761,7 +761,7 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     lf[k] = 0.f;
-                    if (k < cnt4 && a0 + k != s_self) lf[k] = leaf_kv1<D>(x, P2 + (size_t)(a0 + k) * DH, kp.neg_c);
+                    if (k < cnt4 && a0 + k != s_self) lf[k] = leaf_kv1<D, F>(x, P2 + (size_t)(a0 + k) * DH, kp.neg_c);
                 }
                 for (int t = 4; t < 7; ++t) {
                     if (c - a < 2) break;
@@ -801,11 +801,8 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
     }
 }
 
-bool use_leaf128(const fsg_tree* t) {
-    return t->dm == 7 && t->d <= kMaxFmaDim && t->n / t->nb >= 65;  // every bin holds 65..128 points
-}
 
-template <int D>
+template <int D, int F>
 cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     int64_t S = leaf_default_splits(t, kp.L);
     if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
@@ -816,12 +813,12 @@ cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStre
     constexpr size_t smem = Leaf128Layout<D>::total;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf128_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(leaf128_kernel<D, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    leaf128_kernel<D><<<grid, kLC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
+    leaf128_kernel<D, F><<<grid, kLC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
                                               kp, ws.leaf_pos, ws.ksmp, ws.lflags,
                                               reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
                                               reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
@@ -829,6 +826,10 @@ cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStre
 }
 
 }  // namespace
+
+bool use_leaf128(const fsg_tree* t) {
+    return t->dm == 7 && t->d <= kMaxFmaDim && t->n / t->nb >= 65;  // every bin holds 65..128 points
+}
 
 // CTAs per bin of the d <= 16 leaf kernels: a few waves over the expected
 // items (one per (query, bin) reached, at most min(L, nb) per query).
@@ -883,25 +884,34 @@ cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_
     return cudaGetLastError();
 }
 
+template <int F>
+cudaError_t launch_leaf128_family(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    switch (t->d) {
+        case 1: return launch_leaf128_d<1, F>(t, kp, s);
+        case 2: return launch_leaf128_d<2, F>(t, kp, s);
+        case 3: return launch_leaf128_d<3, F>(t, kp, s);
+        case 4: return launch_leaf128_d<4, F>(t, kp, s);
+        case 5: return launch_leaf128_d<5, F>(t, kp, s);
+        case 6: return launch_leaf128_d<6, F>(t, kp, s);
+        case 7: return launch_leaf128_d<7, F>(t, kp, s);
+        case 8: return launch_leaf128_d<8, F>(t, kp, s);
+        case 9: return launch_leaf128_d<9, F>(t, kp, s);
+        case 10: return launch_leaf128_d<10, F>(t, kp, s);
+        case 11: return launch_leaf128_d<11, F>(t, kp, s);
+        case 12: return launch_leaf128_d<12, F>(t, kp, s);
+        case 13: return launch_leaf128_d<13, F>(t, kp, s);
+        case 14: return launch_leaf128_d<14, F>(t, kp, s);
+        case 15: return launch_leaf128_d<15, F>(t, kp, s);
+        default: return launch_leaf128_d<16, F>(t, kp, s);
+    }
+}
+
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     if (use_leaf128(t)) {
-        switch (t->d) {
-            case 1: return launch_leaf128_d<1>(t, kp, s);
-            case 2: return launch_leaf128_d<2>(t, kp, s);
-            case 3: return launch_leaf128_d<3>(t, kp, s);
-            case 4: return launch_leaf128_d<4>(t, kp, s);
-            case 5: return launch_leaf128_d<5>(t, kp, s);
-            case 6: return launch_leaf128_d<6>(t, kp, s);
-            case 7: return launch_leaf128_d<7>(t, kp, s);
-            case 8: return launch_leaf128_d<8>(t, kp, s);
-            case 9: return launch_leaf128_d<9>(t, kp, s);
-            case 10: return launch_leaf128_d<10>(t, kp, s);
-            case 11: return launch_leaf128_d<11>(t, kp, s);
-            case 12: return launch_leaf128_d<12>(t, kp, s);
-            case 13: return launch_leaf128_d<13>(t, kp, s);
-            case 14: return launch_leaf128_d<14>(t, kp, s);
-            case 15: return launch_leaf128_d<15>(t, kp, s);
-            default: return launch_leaf128_d<16>(t, kp, s);
+        switch (kp.family) {
+            case kFamLaplace: return launch_leaf128_family<kFamLaplace>(t, kp, s);
+            case kFamExp: return launch_leaf128_family<kFamExp>(t, kp, s);
+            default: return launch_leaf128_family<kFamGauss>(t, kp, s);
         }
     }
     const int qt = leaf_queries_per_tile(t);

@@ -127,6 +127,7 @@ struct KernelParams {
     uint64_t seed;
     float flag_eps;
     float kde_eps;    // approximate bin pass: skipped mass <= kde_eps * degree (0 = exact)
+    int family;       // FSG_KERNEL_*
 };
 
 int ensure_workspace(fsg_tree* t, int L, cudaStream_t s);
@@ -145,6 +146,8 @@ cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 int leaf_queries_per_tile(const fsg_tree* t);
 int64_t leaf_default_splits(const fsg_tree* t, int L);
+// The 128-point leaf kernel applies: d <= 16, every bin of 65..128 points.
+bool use_leaf128(const fsg_tree* t);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
                          int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
@@ -255,6 +258,41 @@ __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
 }
 __device__ __forceinline__ float2 f2_unpack(uint64_t v) {
     float2 r; asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v)); return r;
+}
+
+// Kernel families (Sec. 2.1): the exponent is neg_c times the squared
+// Euclidean distance (Gaussian), the l1 distance (Laplacian) or the Euclidean
+// distance (exponential).  A distance is accumulated term by term from the
+// coordinate differences dd (first, acc) and finished (fin) before the scale;
+// the packed (two lanes) and the scalar forms round identically per lane.
+constexpr int kFamGauss = FSG_KERNEL_GAUSSIAN;
+constexpr int kFamLaplace = FSG_KERNEL_LAPLACIAN;
+constexpr int kFamExp = FSG_KERNEL_EXPONENTIAL;
+__device__ __forceinline__ uint64_t f2_abs(uint64_t a) { return a & 0x7fffffff7fffffffull; }
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <int F> __device__ __forceinline__ uint64_t fam_first2(uint64_t dd) {
+    return F == kFamLaplace ? f2_abs(dd) : f2_mul(dd, dd);
+}
+template <int F> __device__ __forceinline__ uint64_t fam_acc2(uint64_t dd, uint64_t s) {
+    return F == kFamLaplace ? f2_add(s, f2_abs(dd)) : f2_fma(dd, dd, s);
+}
+template <int F> __device__ __forceinline__ uint64_t fam_fin2(uint64_t s) {
+    if (F != kFamExp) return s;
+    const float2 v = f2_unpack(s);
+    return f2_pack(sqrt_approx(v.x), sqrt_approx(v.y));
+}
+template <int F> __device__ __forceinline__ float fam_first1(float dd) {
+    return F == kFamLaplace ? fabsf(dd) : __fmul_rn(dd, dd);
+}
+template <int F> __device__ __forceinline__ float fam_acc1(float dd, float s) {
+    return F == kFamLaplace ? __fadd_rn(s, fabsf(dd)) : __fmaf_rn(dd, dd, s);
+}
+template <int F> __device__ __forceinline__ float fam_fin1(float s) {
+    return F == kFamExp ? sqrt_approx(s) : s;
 }
 
 // --- mbarrier + 1-D bulk copy (TMA engine) --------------------------------

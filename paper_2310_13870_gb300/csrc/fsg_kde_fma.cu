@@ -286,8 +286,8 @@ struct SymOccupancy {
 };
 
 // Kernel values of one point against the lane's four queries; adds them to
-// the row accumulators and returns their sum.
-template <int D, bool MASK>
+// the row accumulators and returns their sum.  F: the kernel family.
+template <int D, int F, bool MASK>
 __device__ __forceinline__ float sym_point(const float* __restrict__ tp, int p, int gpos, const uint64_t (&q)[2][D],
                                            const int32_t (&qmask)[4], uint64_t nc2, uint64_t (&acc)[2]) {
     constexpr int DP = (D + 3) & ~3;
@@ -304,19 +304,19 @@ __device__ __forceinline__ float sym_point(const float* __restrict__ tp, int p, 
     for (int k = 0; k < 2; ++k) {
         // two interleaved accumulation chains (even / odd coordinates)
         uint64_t dd = f2_sub(q[k][0], c[0]);
-        uint64_t s = f2_mul(dd, dd);
+        uint64_t s = fam_first2<F>(dd);
         uint64_t s1 = 0ull;
         if (D > 1) {
             dd = f2_sub(q[k][1], c[1]);
-            s1 = f2_mul(dd, dd);
+            s1 = fam_first2<F>(dd);
         }
 #pragma unroll
         for (int t = 2; t < D; ++t) {
             dd = f2_sub(q[k][t], c[t]);
-            if (t & 1) s1 = f2_fma(dd, dd, s1); else s = f2_fma(dd, dd, s);
+            if (t & 1) s1 = fam_acc2<F>(dd, s1); else s = fam_acc2<F>(dd, s);
         }
         if (D > 1) s = f2_add(s, s1);
-        s = f2_mul(s, nc2);
+        s = f2_mul(fam_fin2<F>(s), nc2);
         const float2 sv = f2_unpack(s);
         float e0 = ex2_approx(sv.x);
         float e1 = ex2_approx(sv.y);
@@ -358,7 +358,7 @@ struct SymWarp {
 };
 
 // One batch of points (FULL: a whole batch, no bounds tests).
-template <int D, bool MIRROR, bool FULL>
+template <int D, int F, bool MIRROR, bool FULL>
 __device__ __forceinline__ void sym_batch(const float* __restrict__ tp, int pb, int nbat, int gp0,
                                           const uint64_t (&q)[2][D], const int32_t (&qmask)[4], uint64_t nc2,
                                           uint64_t (&acc)[2], const SymWarp& sw, float* mrow, int lane) {
@@ -367,7 +367,7 @@ __device__ __forceinline__ void sym_batch(const float* __restrict__ tp, int pb, 
 #pragma unroll
     for (int j = 0; j < B; ++j) {
         float tot = 0.f;
-        if (FULL || j < nbat) tot = sym_point<D, !MIRROR>(tp, pb + j, gp0 + j, q, qmask, nc2, acc);
+        if (FULL || j < nbat) tot = sym_point<D, F, !MIRROR>(tp, pb + j, gp0 + j, q, qmask, nc2, acc);
         colE[j] = sw.mid ? 0.f : tot;
         colM[j] = sw.mid ? tot : 0.f;
     }
@@ -389,7 +389,7 @@ __device__ __forceinline__ void sym_batch(const float* __restrict__ tp, int pb, 
 }
 
 // The point-bin loop of one CTA.  Returns false if a bounded wait ran out.
-template <int D, bool MIRROR>
+template <int D, int F, bool MIRROR>
 __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars, const float* __restrict__ Xdup,
                                          const int32_t* pbn, int np, const uint64_t (&q)[2][D],
                                          const int32_t (&qmask)[4], const int32_t (&qpos)[4], uint64_t nc2,
@@ -412,8 +412,8 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
         constexpr int B = SymBatch<D>::B;
         int pb = 0;
         for (; pb + B <= cnt; pb += B)
-            sym_batch<D, MIRROR, true>(tp, pb, B, t0 + pb, q, qmask, nc2, acc, sw, mrow, lane);
-        if (pb < cnt) sym_batch<D, MIRROR, false>(tp, pb, cnt - pb, t0 + pb, q, qmask, nc2, acc, sw, mrow, lane);
+            sym_batch<D, F, MIRROR, true>(tp, pb, B, t0 + pb, q, qmask, nc2, acc, sw, mrow, lane);
+        if (pb < cnt) sym_batch<D, F, MIRROR, false>(tp, pb, cnt - pb, t0 + pb, q, qmask, nc2, acc, sw, mrow, lane);
         {   // this point bin's row sums of the lane's queries
             const float2 v0 = f2_unpack(acc[0]), v1 = f2_unpack(acc[1]);
             const float vv[4] = {v0.x, v0.y, v1.x, v1.y};
@@ -439,7 +439,7 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
     return true;
 }
 
-template <int D>
+template <int D, int F>
 __global__ void __launch_bounds__(kSymThreads, SymOccupancy<D>::value)
 kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, const int32_t* __restrict__ bnd,
                     int nb, int G, float neg_c, int self_exclude, float* __restrict__ binsum,
@@ -515,10 +515,10 @@ kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt
 #pragma unroll
     for (int h = 0; h < 4; ++h) qmask[h] = (!mirror && self_exclude) ? qpos[h] : -1;
     if (mirror)
-        sym_bins<D, true>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
+        sym_bins<D, F, true>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
                           pn0, qn0, nq);
     else
-        sym_bins<D, false>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
+        sym_bins<D, F, false>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
                            pn0, qn0, nq);
 }
 
@@ -530,7 +530,7 @@ int sym_block_bins(const fsg_tree* t) {
     return g;
 }
 
-template <int D>
+template <int D, int F>
 cudaError_t launch_sym_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     constexpr int DP = (D + 3) & ~3;
     const int G = sym_block_bins(t);
@@ -539,13 +539,13 @@ cudaError_t launch_sym_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t
                         kSymStages * 8 + 3 * (kSymNodes + 1) * 4;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kde_bins_sym_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(kde_bins_sym_kernel<D, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid(nblk, nblk);
-    kde_bins_sym_kernel<D><<<grid, kSymThreads, smem, s>>>(t->Xdup, t->Xt, t->bnd, t->nb, G, kp.neg_c,
+    kde_bins_sym_kernel<D, F><<<grid, kSymThreads, smem, s>>>(t->Xdup, t->Xt, t->bnd, t->nb, G, kp.neg_c,
                                                           kp.self_exclude, t->ws.binsum, t->status);
     return cudaGetLastError();
 }
@@ -579,25 +579,36 @@ int64_t kde_bins_sym_evals(const fsg_tree* t) {
     return (t->n * t->n + sq) / 2;
 }
 
-cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+namespace {
+template <int F>
+cudaError_t launch_sym_family(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     switch (t->d) {
-        case 1: return launch_sym_d<1>(t, kp, s);
-        case 2: return launch_sym_d<2>(t, kp, s);
-        case 3: return launch_sym_d<3>(t, kp, s);
-        case 4: return launch_sym_d<4>(t, kp, s);
-        case 5: return launch_sym_d<5>(t, kp, s);
-        case 6: return launch_sym_d<6>(t, kp, s);
-        case 7: return launch_sym_d<7>(t, kp, s);
-        case 8: return launch_sym_d<8>(t, kp, s);
-        case 9: return launch_sym_d<9>(t, kp, s);
-        case 10: return launch_sym_d<10>(t, kp, s);
-        case 11: return launch_sym_d<11>(t, kp, s);
-        case 12: return launch_sym_d<12>(t, kp, s);
-        case 13: return launch_sym_d<13>(t, kp, s);
-        case 14: return launch_sym_d<14>(t, kp, s);
-        case 15: return launch_sym_d<15>(t, kp, s);
-        case 16: return launch_sym_d<16>(t, kp, s);
+        case 1: return launch_sym_d<1, F>(t, kp, s);
+        case 2: return launch_sym_d<2, F>(t, kp, s);
+        case 3: return launch_sym_d<3, F>(t, kp, s);
+        case 4: return launch_sym_d<4, F>(t, kp, s);
+        case 5: return launch_sym_d<5, F>(t, kp, s);
+        case 6: return launch_sym_d<6, F>(t, kp, s);
+        case 7: return launch_sym_d<7, F>(t, kp, s);
+        case 8: return launch_sym_d<8, F>(t, kp, s);
+        case 9: return launch_sym_d<9, F>(t, kp, s);
+        case 10: return launch_sym_d<10, F>(t, kp, s);
+        case 11: return launch_sym_d<11, F>(t, kp, s);
+        case 12: return launch_sym_d<12, F>(t, kp, s);
+        case 13: return launch_sym_d<13, F>(t, kp, s);
+        case 14: return launch_sym_d<14, F>(t, kp, s);
+        case 15: return launch_sym_d<15, F>(t, kp, s);
+        case 16: return launch_sym_d<16, F>(t, kp, s);
         default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    switch (kp.family) {
+        case kFamLaplace: return launch_sym_family<kFamLaplace>(t, kp, s);
+        case kFamExp: return launch_sym_family<kFamExp>(t, kp, s);
+        default: return launch_sym_family<kFamGauss>(t, kp, s);
     }
 }
 

@@ -66,7 +66,10 @@ extern "C" int fsg_degrees_noalloc(const float* d_points, int64_t n, int32_t d, 
     if (p->scale_conv != FSG_TWO_SIGMA_SQ && p->scale_conv != FSG_SIGMA_SQ) return FSG_ERR_INVALID_ARG;
     if (p->self_mode != FSG_SELF_EXCLUDE && p->self_mode != FSG_SELF_INCLUDE) return FSG_ERR_INVALID_ARG;
     if (!(p->kde_eps >= 0.f) || !std::isfinite(p->kde_eps) || p->kde_eps > 0.5f) return FSG_ERR_INVALID_ARG;
-    if (d > fsg::kMaxFmaDim || p->kde_eps > 0.f) return FSG_ERR_UNSUPPORTED;  // exact FP32 only
+    if (p->kernel != FSG_KERNEL_GAUSSIAN && p->kernel != FSG_KERNEL_LAPLACIAN && p->kernel != FSG_KERNEL_EXPONENTIAL)
+        return FSG_ERR_INVALID_ARG;
+    // the exact FP32 pass of the Gaussian kernel only
+    if (d > fsg::kMaxFmaDim || p->kde_eps > 0.f || p->kernel != FSG_KERNEL_GAUSSIAN) return FSG_ERR_UNSUPPORTED;
     // Geometry: 16 bins (or fewer for tiny n) only to spread the bin pass over
     // the GPU; the degree is the sum of a query's bins.
     int s0 = 0;

@@ -34,6 +34,7 @@ FSG_EDGES_SET, FSG_EDGES_MULTI = 0, 1
 FSG_SCHED_FUSED, FSG_SCHED_LEVELWISE, FSG_SCHED_CARRIED = 0, 1, 2
 FSG_ADMIT_ARRIVAL, FSG_ADMIT_RESPONSE_RATIO = 0, 1
 FSG_ORDER_IDENTITY, FSG_ORDER_SPATIAL = 0, 1
+FSG_KERNEL_GAUSSIAN, FSG_KERNEL_LAPLACIAN, FSG_KERNEL_EXPONENTIAL = 0, 1, 2
 
 # Names every build of the library must export (checked by the CPU tests
 # against include/fsg.h).
@@ -61,7 +62,7 @@ class FsgError(RuntimeError):
 class fsg_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("scale_conv", ctypes.c_int32), ("self_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flag_eps", ctypes.c_float),
-                ("kde_eps", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+                ("kde_eps", ctypes.c_float), ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class fsg_tree_opts(ctypes.Structure):
@@ -178,7 +179,7 @@ def _dptr(t):
 
 def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FSG_SELF_EXCLUDE,
            precision: int = FSG_PREC_AUTO, schedule: int = FSG_SCHED_FUSED, flag_eps: float = 0.0,
-           kde_eps: float = 0.0) -> fsg_params:
+           kde_eps: float = 0.0, kernel: int = 0) -> fsg_params:
     p = fsg_params()
     p.sigma = float(sigma)
     p.scale_conv = scale_conv
@@ -187,6 +188,7 @@ def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FS
     p.schedule = schedule
     p.flag_eps = float(flag_eps)
     p.kde_eps = float(kde_eps)
+    p.kernel = int(kernel)
     return p
 
 

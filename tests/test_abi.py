@@ -74,7 +74,8 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     buf = (ctypes.c_float * 8)()
     for bad in (fsg.params(0.0), fsg.params(float("nan")), fsg.params(-1.0), fsg.params(0.1, self_mode=3),
                 fsg.params(0.1, scale_conv=7), fsg.params(0.1, precision=9), fsg.params(0.1, flag_eps=-1.0),
-                fsg.params(0.1, kde_eps=-1e-3), fsg.params(0.1, kde_eps=float("nan")), fsg.params(0.1, kde_eps=0.6)):
+                fsg.params(0.1, kde_eps=-1e-3), fsg.params(0.1, kde_eps=float("nan")), fsg.params(0.1, kde_eps=0.6),
+                fsg.params(0.1, kernel=3), fsg.params(0.1, kernel=-1)):
         rc = lib.fsg_build_graph_host(buf, 4, 2, ctypes.byref(bad), 2, 0, 0, buf, buf, buf, 8, ctypes.byref(m), None)
         assert rc == fsg.FSG_ERR_INVALID_ARG
     # the allocation-free degree call is the exact FP32 pass: an approximate one is not offered
@@ -104,5 +105,6 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(fsg.fsg_result) == 48
     assert ctypes.sizeof(fsg.fsg_params) == 48
     assert fsg.fsg_params.flag_eps.offset == 24 and fsg.fsg_params.kde_eps.offset == 28
+    assert fsg.fsg_params.kernel.offset == 32
     assert ctypes.sizeof(fsg.fsg_tree_opts) == 32 and fsg.fsg_tree_opts.order.offset == 12
     assert ctypes.sizeof(fsg.fsg_stats) == 80
