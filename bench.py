@@ -406,8 +406,35 @@ def run_ours(args):
                 "executed_pairs": int(ast["n_bin_evals"]), "skipped_fraction": 1.0 - ast["n_bin_evals"] / (n * n),
                 "flagged_samples": ast["n_flagged"], "kde_error": kde_error(bufs.deg.cpu().numpy(), ref)}
 
+    def run_family(fam, ofam, nq=1024):
+        # the same input and path under another kernel of Sec. 2.1 (same sigma)
+        import oracle as ora
+        pf = fsg.params(sigma, kernel=fam)
+        fsg.fsg_build_graph(tree, pf, L, seed, bufs=bufs, stream=stream)  # warm-up
+        fms = []
+        for _ in range(max(3, args.plain_steps)):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fsg.fsg_tree_update(tree, pts, stream=stream)
+            fsg.fsg_build_graph(tree, pf, L, seed, bufs=bufs, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            fms.append(e0.elapsed_time(e1))
+        assert fsg.fsg_sync(tree, stream=stream) == 0
+        fst = fsg.stats_dict(bufs)
+        q = np.random.Generator(np.random.PCG64(7)).choice(n, size=min(nq, n), replace=False)
+        want = ora.degrees(X, ora.scale(sigma, ofam), queries=q, kernel=ofam)
+        got = bufs.deg.cpu().numpy()[q]
+        rel = np.abs(got - want) / want
+        ft = statistics.mean(fms)
+        return {"value": n * L / (ft * 1e-3), "unit": UNIT, "ms_per_step": ft, "flagged_samples": fst["n_flagged"],
+                "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(q.size),
+                              "kind": "degrees vs the FP64 oracle of the same kernel"}}
+
     cpu = None
-    err = split_cmp = approx_cmp = None
+    err = split_cmp = approx_cmp = families = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ref = {}
         v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed, keep=ref)
@@ -435,6 +462,8 @@ def run_ours(args):
                          "flagged_samples": sst["n_flagged"], "flag_eps": 2.0 ** -10,
                          "kde_error": kde_error(bufs.deg.cpu().numpy(), ref)}
             approx_cmp = run_approx(2.0 ** -20, ref)
+            families = {name: run_family(fam, ofam) for name, fam, ofam in
+                        (("laplacian", fsg.FSG_KERNEL_LAPLACIAN, 1), ("exponential", fsg.FSG_KERNEL_EXPONENTIAL, 2))}
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_queries} of the {n} query points (all {L} samples each + their degrees), "
                          f"{dt:.1f} s, extrapolated per sampled edge"}
@@ -450,6 +479,7 @@ def run_ours(args):
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
                 "kde_error": err, "split_precision": split_cmp, "approximate_kde": approx_cmp,
+                "kernel_families": families,
                 "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "carried_fp32_gpu": carried,
                 "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
