@@ -27,7 +27,7 @@
  *   - Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random
  *     numbers: as easy as 1, 2, 3"), written from that paper's definition.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent (the project's design notes list each):
  *   - self term: EXCLUDE (default) omits j == i from every sum, matching the
  *     fully connected graph of Sec. 2.1 which has no self loops; INCLUDE keeps
  *     it (k(i,i) = 1) as literally written in Algorithm 1;

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (derivation in the design doc):
+Tolerances (derived from the FP32 arithmetic of each path):
   * KDE / degree:  |g_gpu - g_ora| <= 1e-5 g_ora + n 2^-126 (FP32 evaluations
     with direct differences, ex2.approx, runs of <= 64 terms, pairwise bins);
   * samples: identical to the oracle's unless the GPU flagged the sample (a
