@@ -40,8 +40,8 @@ def _requests():
 
 
 def _params(fsg, X, sigma, split):
-    if split and X.shape[1] > 16:  # d = 64 requests in split precision
-        return fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16)
+    if split and X.shape[1] > 16:  # d = 64 requests in split precision (approximate KDE too for "approx")
+        return fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16, kde_eps=1e-3 if split == "approx" else 0.0)
     return fsg.params(sigma)
 
 
@@ -61,7 +61,8 @@ def _drain(server, expect, timeout_s=120):
 
 
 @pytest.mark.parametrize("budget_mb,slots,admission,split", [(8192, 8, 0, False), (64, 2, 0, False),
-                                                           (8192, 8, 1, False), (64, 1, 1, False), (8192, 8, 0, True)])
+                                                           (8192, 8, 1, False), (64, 1, 1, False), (8192, 8, 0, True),
+                                                           (8192, 8, 0, "approx")])
 def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots, admission, split):
     reqs = _requests()
     want = [_alone(fsg, *r, split=split) for r in reqs]
