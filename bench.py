@@ -298,6 +298,20 @@ def run_ours(args):
                 **({"executed_pairs": int(pairs), "skipped_fraction": 1.0 - pairs / (n * n)} if split else {}),
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": "measured cuBLAS BF16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
+        if split:
+            # the split form's other bound: one ex2 per executed pair on the
+            # MUFU units (16 per SM per clock); with few K-steps (small d) it
+            # needs more time than the tensor work and is the binding unit
+            mufu_peak = 152 * 16 * 2.07  # G ex2/s at 2,070 MHz
+            t_tensor = 12.0 * pairs * kpad / (peak * 1e12)
+            t_mufu = pairs / (mufu_peak * 1e9)
+            if t_mufu > t_tensor:
+                ach = pairs / (kde_avg * 1e-3) / 1e9
+                roof = {"bound": "alu", "kernel": "kde_bins_split_kernel", "achieved": ach, "peak": mufu_peak,
+                        "executed_pairs": int(pairs), "skipped_fraction": 1.0 - pairs / (n * n),
+                        "unit": "G ex2/s (one per executed pair)", "frac": ach / mufu_peak,
+                        "peak_basis": "152 SMs x 16 ex2/clk (MUFU) x 2070 MHz",
+                        "tensor_frac": achieved / peak}
     else:
         # executed evaluations of the bin pass; the symmetric kernel adds each
         # value to two rows (2d+3 FP32 lane operations), the plain one to one (2d+2)
