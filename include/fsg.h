@@ -468,6 +468,16 @@ int fsg_server_info(fsg_server* server, int64_t* pending, int64_t* in_flight, in
 void fsg_server_destroy(fsg_server* server);
 
 /*
+ * Self-test of the failure path: launches a kernel that waits, the way every
+ * pipeline of the library does, on an mbarrier that nothing completes, with
+ * a wall-clock limit of limit_ns (1e3 .. 1e10).  Returns FSG_ERR_TIMEOUT when
+ * the wait ran out and the kernel reported it through its status word as
+ * designed (no trap; the context stays usable), FSG_OK if the wait completed
+ * (a failure of the test), INVALID_ARG or CUDA otherwise.  Synchronous.
+ */
+int fsg_selftest_wait_timeout(int64_t limit_ns, void* stream);
+
+/*
  * Waits for the stream and returns the tree's device status word
  * (FSG_OK or FSG_ERR_TIMEOUT), then clears it.  Errors: CUDA.
  */

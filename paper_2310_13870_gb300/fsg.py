@@ -46,7 +46,7 @@ EXPORTED = [
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
     "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
     "fsg_server_create", "fsg_server_submit", "fsg_server_poll", "fsg_server_cancel", "fsg_server_info",
-    "fsg_server_destroy",
+    "fsg_server_destroy", "fsg_selftest_wait_timeout",
 ]
 FSG_NUM_PHASES = 8
 PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "unused"]
@@ -154,6 +154,7 @@ def load(path: str = LIB_PATH):
     lib.fsg_server_destroy.restype = None
     lib.fsg_spatial_order.argtypes = [P, ctypes.c_int64, I32, I32, P]
     lib.fsg_tree_perm.argtypes = [P, P, P]
+    lib.fsg_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
     for name in EXPORTED:
         if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy", "fsg_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int

@@ -62,6 +62,7 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     opts.order, opts.d_perm = fsg.FSG_ORDER_SPATIAL, 0x2000  # a computed order and a given one
     assert lib.fsg_build_tree(fake, 10, 2, ctypes.byref(opts), None, ctypes.byref(h)) == fsg.FSG_ERR_INVALID_ARG
     assert lib.fsg_tree_perm(None, fake, None) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_selftest_wait_timeout(10, None) == fsg.FSG_ERR_INVALID_ARG  # limit below 1 us
     p = fsg.params(0.1)
     assert lib.fsg_degrees(None, ctypes.byref(p), fake, None) == fsg.FSG_ERR_INVALID_ARG
     assert lib.fsg_sample_edges(None, ctypes.byref(p), 8, 0, fake, None, None) == fsg.FSG_ERR_INVALID_ARG
