@@ -294,7 +294,13 @@ int fsg_degrees(fsg_tree* tree, const fsg_params* params, double* d_deg, void* s
  * (cudaGetSymbolAddress, with the device current); make that first call
  * before any stream capture.  Every call, on any stream, shares the one
  * array and leaves its contents behind: calls that overlap on the GPU race
- * and give wrong results, so serialize them (one stream, or events).
+ * and give wrong results, so serialize them (one stream, or events).  Each
+ * call clears what it reads before writing it (the status word and the
+ * position map) and overwrites every partial sum it uses, so a call does not
+ * depend on what an earlier one left.
+ * Device-side failure: there is no tree whose status word fsg_sync could
+ * read, so when a bounded wait of the bin pass runs out (the condition the
+ * other calls report as FSG_ERR_TIMEOUT) every entry of d_deg is set to NaN.
  * No cudaMalloc, cudaFree or allocating library routine is called.
  * Errors: INVALID_ARG, UNSUPPORTED (d > 16), SCRATCH, CUDA.
  */

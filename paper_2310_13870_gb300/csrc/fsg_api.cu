@@ -164,6 +164,23 @@ void tree_free(fsg_tree* t, void* p) {
 
 }  // namespace
 
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<const void*, int>, size_t> g_attr_set;  // (kernel, device) -> limit set
+}  // namespace
+
+cudaError_t set_smem_limit_fn(const void* kernel, size_t bytes) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    size_t& cur = g_attr_set[{kernel, dev}];
+    if (cur >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 // Byte sizes of the workspace carve-outs, in carve order (shared by the
 // allocation and the server's admission estimate).
 namespace {

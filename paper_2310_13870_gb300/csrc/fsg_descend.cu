@@ -509,12 +509,9 @@ template <int D, bool FROM_GLOBAL = false>
 cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cudaStream_t s) {
     constexpr int DH = (D + 1) / 2;
     const size_t smem = LeafSmem(1 << t->dm, DH, qc).total;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_finish_kernel<D, FROM_GLOBAL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    {
+        const cudaError_t e = set_smem_limit(leaf_finish_kernel<D, FROM_GLOBAL>, 200 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     int64_t S = leaf_default_splits(t, kp.L);
     if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
@@ -811,12 +808,9 @@ cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStre
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
     constexpr size_t smem = Leaf128Layout<D>::total;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf128_kernel<D, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    {
+        const cudaError_t e = set_smem_limit(leaf128_kernel<D, F>, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     leaf128_kernel<D, F><<<grid, kLC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
                                               kp, ws.leaf_pos, ws.ksmp, ws.lflags,
@@ -855,12 +849,9 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
     int warps = 8;
     while (warps > 1 && (size_t)warps * 8 * t->nb > 96 * 1024) warps >>= 1;
     const size_t smem = (size_t)warps * 8 * t->nb;  // per warp: 2 nb tree nodes (later nb bin masks)
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(descend_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(smem < 48 * 1024 ? 48 * 1024 : smem));
+    {
+        const cudaError_t e = set_smem_limit(descend_top_kernel, smem < 48 * 1024 ? 48 * 1024 : smem);
         if (e != cudaSuccess) return e;
-        attr = smem;
     }
     int64_t blocks = (t->n + warps - 1) / warps;
     if (blocks > 152 * 16) blocks = 152 * 16;

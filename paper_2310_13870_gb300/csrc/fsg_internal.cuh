@@ -130,6 +130,15 @@ struct KernelParams {
     int family;       // FSG_KERNEL_*
 };
 
+// Raises the dynamic shared-memory limit of `kernel` on the current device to
+// at least `bytes` (cudaFuncSetAttribute), once per (kernel, device) and
+// value; safe to call from several threads and for several devices.
+cudaError_t set_smem_limit_fn(const void* kernel, size_t bytes);
+template <typename K>
+inline cudaError_t set_smem_limit(K* kernel, size_t bytes) {
+    return set_smem_limit_fn(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 int ensure_workspace(fsg_tree* t, int L, cudaStream_t s);
 int build_tree_internal(const float* d_points, int64_t n, int32_t d, const fsg_tree_opts* opts, cudaStream_t s,
                         cudaMemPool_t pool, fsg_tree** out);

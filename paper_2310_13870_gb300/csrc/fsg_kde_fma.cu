@@ -197,12 +197,9 @@ cudaError_t launch_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) 
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = (size_t)kStagesA * kTileA * DP * 2 * 4 + kStagesA * 8 + ((bpc + 1 + 3) & ~3) * 4 +
                         (size_t)QCTA * bpc * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kde_bins_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             96 * 1024);
+    {
+        const cudaError_t e = set_smem_limit(kde_bins_kernel<D>, 96 * 1024);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     dim3 grid(qblocks, chunks);
     kde_bins_kernel<D><<<grid, kThreadsA, smem, s>>>(t->Xdup, t->Xt, (int)t->n, t->bnd, t->nb, bpc, kp.neg_c,
@@ -537,12 +534,9 @@ cudaError_t launch_sym_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t
     const int nblk = (t->nb + G - 1) / G;
     const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymNodes * 4 +
                         kSymStages * 8 + 3 * (kSymNodes + 1) * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kde_bins_sym_kernel<D, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    {
+        const cudaError_t e = set_smem_limit(kde_bins_sym_kernel<D, F>, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     dim3 grid(nblk, nblk);
     kde_bins_sym_kernel<D, F><<<grid, kSymThreads, smem, s>>>(t->Xdup, t->Xt, t->bnd, t->nb, G, kp.neg_c,

@@ -567,12 +567,9 @@ int64_t kde_bins_generic_sym_evals(const fsg_tree* t) {
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     if (kde_bins_generic_sym_supported(t)) {
         const size_t smem = 2 * kSymGenSmem + 2 * sizeof(uint64_t);  // two stages and their mbarriers
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(kde_bins_generic_sym_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        {
+            const cudaError_t e = set_smem_limit(kde_bins_generic_sym_kernel, (int)smem);
             if (e != cudaSuccess) return e;
-            attr = true;
         }
         const int64_t T = (t->n + kST - 1) / kST;
         const int dpc = (t->dp + kSK - 1) / kSK * kSK;
@@ -760,12 +757,9 @@ cudaError_t launch_leaf_fused_generic(const fsg_tree* t, const KernelParams& kp,
     if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_fused_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kLfSmem);
+    {
+        const cudaError_t e = set_smem_limit(leaf_fused_generic_kernel, (int)kLfSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const auto& ws = t->ws;
     leaf_fused_generic_kernel<<<dim3(t->nb, (unsigned)S), kGT, kLfSmem, s>>>(
@@ -784,12 +778,10 @@ cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const bool wide = (1 << t->dm) > 64;
-    static bool attr[2] = {false, false};
-    if (!attr[wide]) {
-        cudaError_t e = cudaFuncSetAttribute(wide ? leaf_values_generic_kernel<2> : leaf_values_generic_kernel<1>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymGenSmem);
+    {
+        const cudaError_t e =
+            set_smem_limit(wide ? leaf_values_generic_kernel<2> : leaf_values_generic_kernel<1>, kSymGenSmem);
         if (e != cudaSuccess) return e;
-        attr[wide] = true;
     }
     if (wide)
         leaf_values_generic_kernel<2><<<grid, kGT, kSymGenSmem, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off,

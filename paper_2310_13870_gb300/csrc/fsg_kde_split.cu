@@ -908,12 +908,9 @@ cudaError_t launch_leaf_split_tc(const fsg_tree* t, const KernelParams& kp, cuda
     if (!t->sboxes || !leaf_split_tc_supported(t)) return cudaErrorInvalidValue;
     unsigned char* bimg = SplitWs(t).bin_img;
     const size_t smem = 1024 + LsLayout::total;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_split_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    {
+        const cudaError_t e = set_smem_limit(leaf_split_tc_kernel, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     bin_images_kernel<<<t->nb, kSpM, 0, s>>>(t->Xt, t->dp, t->d, t->bnd, bimg);
     const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
@@ -942,12 +939,9 @@ cudaError_t launch_kde_bins_split(const fsg_tree* t, const KernelParams& kp, cud
     if (((int64_t)bpc * t->mmax + kSpN - 1) / kSpN > kSpMaxTiles) return cudaErrorInvalidValue;
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = 1024 + SpLayout::total(bpc);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kde_bins_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+    {
+        const cudaError_t e = set_smem_limit(kde_bins_split_kernel, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     if (!t->sboxes) return cudaErrorInvalidValue;
     const SplitWs ws(t);

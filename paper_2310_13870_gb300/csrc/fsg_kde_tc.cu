@@ -331,12 +331,9 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
     if (t->tune.tc_bins > 0 && t->tune.tc_bins < bpc) bpc = t->tune.tc_bins;
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = tc_bins_smem(kTcEpiWarps, bpc);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(kde_bins_tc_kernel<kTcEpiWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(227 * 1024));
+    {
+        const cudaError_t e = set_smem_limit(kde_bins_tc_kernel<kTcEpiWarps>, (int)(227 * 1024));
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     // integer units: ||255 x - 255 y||^2 = 255^2 ||x - y||^2
     const float nc = kp.neg_c / (255.f * 255.f);
@@ -676,12 +673,9 @@ cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cud
     const int nmax = (t->mmax + 15) & ~15;  // point rows of the largest bin, rounded to the TMA box
     if (nmax > 256) return cudaErrorInvalidValue;
     const size_t smem = 1024 + LvLayout(nmax).total;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_values_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+    {
+        const cudaError_t e = set_smem_limit(leaf_values_tc_kernel, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
     const int64_t chunks_per_bin = (items_est / t->nb + 127) / 128 + 1;

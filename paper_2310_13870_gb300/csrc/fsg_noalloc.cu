@@ -41,6 +41,15 @@ int noalloc_scratch(void** out) {
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The caller's only view of a device-side failure: when a bounded wait of the
+// bin pass ran out (status word set), every degree of the call becomes NaN.
+__global__ void noalloc_finish_kernel(const int32_t* __restrict__ status, int64_t n, double* __restrict__ d_deg) {
+    if (status[0] == FSG_OK) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d_deg[i] = nan;
+}
+
 // Scratch layout for n points of dimension d with nb bins.
 struct NoallocLayout {
     size_t xt, xdup, perm, inv, bnd, binsum, degf, status, total;
@@ -107,7 +116,9 @@ extern "C" int fsg_degrees_noalloc(const float* d_points, int64_t n, int32_t d, 
 
     const double gamma = p->scale_conv == FSG_SIGMA_SQ ? 1.0 / (p->sigma * p->sigma)
                                                        : 1.0 / (2.0 * p->sigma * p->sigma);
-    fsg::KernelParams kp;
+    fsg::KernelParams kp{};
+    kp.family = FSG_KERNEL_GAUSSIAN;
+    kp.kde_eps = 0.f;
     kp.precision = FSG_PREC_FP32;
     kp.gamma = (float)gamma;
     kp.neg_c = (float)(-gamma * 1.4426950408889634073599246810019);
@@ -119,10 +130,16 @@ extern "C" int fsg_degrees_noalloc(const float* d_points, int64_t n, int32_t d, 
 
     cudaStream_t s = (cudaStream_t)stream;
     // tree_prep clears the inverse map and the status word it reuses; the bin
-    // pass writes every (query, bin) entry and descend_top every degree.
+    // pass writes every (query, bin) entry and descend_top every degree; the
+    // last kernel turns a timed-out bin pass into NaN degrees.
     cudaError_t e = fsg::launch_tree_prep(&t, d_points, nullptr, s);
     if (e == cudaSuccess) e = fsg::launch_kde_bins(&t, kp, s);
     if (e == cudaSuccess) e = fsg::launch_descend_top(&t, kp, d_deg, 0, s);
+    if (e == cudaSuccess) {
+        const int64_t blocks = (n + 255) / 256;
+        noalloc_finish_kernel<<<(int)(blocks < 1024 ? blocks : 1024), 256, 0, s>>>(t.status, n, d_deg);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? FSG_ERR_OOM : FSG_ERR_CUDA;

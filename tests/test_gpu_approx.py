@@ -113,3 +113,44 @@ def test_approx_refused_outside_the_split_form(fsg):
             fsg.fsg_degrees(tree, fsg.params(1.5, precision=prec, kde_eps=1e-3))
         assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
     tree.close()
+
+
+def test_approx_sample_frequencies_within_the_bound(fsg):
+    # Chi-square of the sampled frequencies at the paper's eps = 1/(6 ln n)
+    # (Lemma 1, App. A).  The approximate bin pass only removes mass from bin
+    # sums (at most eps of the degree in all) and every node sum above the
+    # bins is a sum of those, so the probability of reaching bin b is
+    # g'_b / sum g', within total variation eps / (1 - eps) of the exact
+    # g_b / deg; inside a bin the values are exact.  The split form's own
+    # arithmetic (sums within about 4e-4) adds at most 1e-3.  The test is the
+    # chi-square against the exact k(x_i, x_j) / deg(x_i) (FP64) widened by
+    # that total variation: the smallest statistic over all distributions
+    # within the bound must stay below the chi-square quantile.
+    from scipy.spatial.distance import cdist
+    from chisq_tv import tv_chi_square_pvalue
+    n, d, L = 3000, 4, 64
+    X = inputs.gaussian_mixture(n=n, d=d, k=6, box=4.0, seed=12)
+    sigma = 1.0
+    eps = 1.0 / (6.0 * math.log(n))
+    delta = eps / (1.0 - eps) + 1e-3
+    gam = ora.gamma(sigma)
+    perm = torch.from_numpy(fsg.fsg_spatial_order(X)).cuda()
+    tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda(), perm=perm)
+    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16, kde_eps=eps)
+    pe = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16)
+    # the pass prunes on this input
+    assert fsg.fsg_build_graph(tree, p, L, 0).stats.cpu()[8] < fsg.fsg_build_graph(tree, pe, L, 0).stats.cpu()[8]
+    queries = [5, 900, 1700, 2999]
+    counts = np.zeros((len(queries), n))
+    for seed in range(3000, 3500):
+        smp, _ = fsg.fsg_sample_edges(tree, p, L, seed)
+        s = smp[queries].cpu().numpy()
+        for r in range(len(queries)):
+            counts[r] += np.bincount(s[r], minlength=n)
+    assert fsg.fsg_sync(tree) == 0
+    tree.close()
+    K = np.exp(-gam * cdist(X.astype(np.float64), X.astype(np.float64), "sqeuclidean"))
+    np.fill_diagonal(K, 0.0)
+    for r, i in enumerate(queries):
+        pv = tv_chi_square_pvalue(counts[r], K[i] / K[i].sum(), delta)
+        assert pv > 0.01 / len(queries), (i, pv)

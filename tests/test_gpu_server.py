@@ -80,6 +80,37 @@ def test_results_equal_alone_in_the_mix(fsg, budget_mb, slots, admission, split)
     server.close()
 
 
+def test_in_mix_results_match_the_oracle(fsg):
+    # Results taken from the mix (eight slots, all requests in flight together)
+    # against the FP64 oracle's Algorithm 2 directly, for one request of each
+    # d: a flagged sample may move one edge, so the edge sets differ in at
+    # most two pairs per flagged sample; every edge both have carries the
+    # oracle's weight (Eq. 2, which pins both endpoints' degrees) within 1e-4.
+    import math
+    import oracle as ora
+    reqs = _requests()
+    server = fsg.Server(hbm_budget_bytes=8192 << 20, max_slots=8)
+    ids = [server.submit(X, fsg.params(s), L, seed) for X, s, L, seed in reqs]
+    got = _drain(server, len(ids))
+    server.close()
+    checked = set()
+    for k in sorted(range(len(reqs)), key=lambda k: reqs[k][0].shape[0]):
+        X, sigma, L, seed = reqs[k]
+        if X.shape[1] in checked:
+            continue
+        checked.add(X.shape[1])
+        rec, (gs, gd, gw) = got[ids[k]]
+        assert rec["status"] == fsg.FSG_OK
+        o = ora.build_graph(X, ora.gamma(sigma), L, seed)
+        eg = {(min(a, b), max(a, b)): w for a, b, w in zip(gs.tolist(), gd.tolist(), gw.tolist())}
+        eo = {(min(a, b), max(a, b)): w for a, b, w in zip(o["src"].tolist(), o["dst"].tolist(), o["w"].tolist())}
+        assert len(eg) == len(gs)  # SET: no pair twice
+        assert len(set(eg) ^ set(eo)) <= 2 * rec["n_flagged"], (X.shape, rec["n_flagged"])
+        for key in set(eg) & set(eo):
+            assert math.isclose(eg[key], eo[key], rel_tol=1e-4), (X.shape, key, eg[key], eo[key])
+    assert checked == {2, 10, 64}
+
+
 def test_response_ratio_lets_short_requests_overtake(fsg):
     # one slot: a long request (200k points) is admitted first, then three long
     # and three short requests queue behind it; by response ratio the short

@@ -3,11 +3,16 @@
 It exists for callers that must not allocate device memory -- an application
 whose pool allocator owns the whole GPU, or a latency-critical caller that
 cannot pay for cudaMalloc/cudaFree -- and keeps its scratch in one fixed
-array inside the library.  This file checks, through the C ABI, that it gives
-the same degrees as the tree-based entry point (fsg_degrees) within the
-degree tolerance of the other GPU tests, on two calls in a row (the second
-call must not be disturbed by what the first left in the shared scratch), and
-that a problem too large for the scratch is refused before any GPU work.
+array inside the library.  This file checks, through the C ABI:
+
+* that it gives the degrees of the tree-based entry point (fsg_degrees) within
+  the degree tolerance of the other GPU tests, and the FP64 oracle's degrees
+  of Algorithm 2 on sampled points, on two calls in a row;
+* that the second call is not disturbed by what an earlier call left in the
+  shared scratch: between the two compared calls another call runs on a
+  different problem (more points, another dimension, the other self mode), so
+  stale position maps, partial sums or status words would show;
+* that a problem too large for the scratch is refused before any GPU work.
 
 The file is named to be collected last, and it builds the library itself, so
 it passes alone in a fresh process as well as after the other tests.
@@ -49,23 +54,59 @@ def _noalloc(fsg, pts, p):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("case", ["two_moons", "mixture_d10", "mixture_d3_include"])
-def test_noalloc_matches_tree_entry_point_on_two_calls(fsg, case):
-    if case == "two_moons":
-        X, p = inputs.two_moons(n=3001, seed=4), fsg.params(0.1)
-    elif case == "mixture_d10":
-        X, p = inputs.gaussian_mixture(n=60_000, d=10, seed=2), fsg.params(1.5)
-    else:
-        X, p = inputs.gaussian_mixture(n=7_777, d=3, k=4, box=2.0, seed=1), fsg.params(0.5, self_mode=1)
-    n = X.shape[0]
-    pts = torch.from_numpy(X).cuda()
+def _tree_degrees(fsg, pts, p):
     tree = fsg.fsg_build_tree(pts)
     ref = fsg.fsg_degrees(tree, p).cpu().numpy()
+    fsg.fsg_sync(tree)
     tree.close()
-    for _ in range(2):
+    return ref
+
+
+def _close(got, want, n):
+    err = np.abs(got - want)
+    ok = np.isfinite(got).all() and (err <= DEG_RTOL * want + n * TINY).all()
+    return ok, float(np.max(err / np.maximum(want, 1e-300)))
+
+
+CASES = {
+    "two_moons": lambda fsg: (inputs.two_moons(n=3001, seed=4), fsg.params(0.1), 0.1, 0),
+    "mixture_d10": lambda fsg: (inputs.gaussian_mixture(n=60_000, d=10, seed=2), fsg.params(1.5), 1.5, 0),
+    "mixture_d3_include": lambda fsg: (inputs.gaussian_mixture(n=7_777, d=3, k=4, box=2.0, seed=1),
+                                       fsg.params(0.5, self_mode=1), 0.5, 1),
+}
+# the call placed between the two compared ones: more points, another d, the other self mode
+OTHER = {
+    "two_moons": lambda fsg: (inputs.gaussian_mixture(n=90_001, d=7, seed=9), fsg.params(1.2, self_mode=1)),
+    "mixture_d10": lambda fsg: (inputs.gaussian_mixture(n=80_000, d=16, seed=3), fsg.params(2.0, self_mode=1)),
+    "mixture_d3_include": lambda fsg: (inputs.two_moons(n=100_000, seed=5), fsg.params(0.1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_noalloc_matches_tree_entry_point_and_oracle_on_two_calls(fsg, case):
+    import oracle as ora
+    X, p, sigma, self_mode = CASES[case](fsg)
+    n = X.shape[0]
+    pts = torch.from_numpy(X).cuda()
+    ref = _tree_degrees(fsg, pts, p)
+    q = np.random.Generator(np.random.PCG64(11)).choice(n, size=min(n, 256), replace=False)
+    want = ora.degrees(X, ora.gamma(sigma), queries=q, self_mode=self_mode)
+    ok, worst = _close(ref[q], want, n)
+    assert ok, f"tree entry point vs oracle: {worst}"
+
+    Xo, po = OTHER[case](fsg)
+    for call in range(2):
         got = _noalloc(fsg, pts, p)
-        err = np.abs(got - ref)
-        assert (err <= DEG_RTOL * ref + n * TINY).all(), float(np.max(err / np.maximum(ref, 1e-300)))
+        ok, worst = _close(got, ref, n)
+        assert ok, f"call {call}: vs fsg_degrees {worst}"
+        ok, worst = _close(got[q], want, n)
+        assert ok, f"call {call}: vs the oracle {worst}"
+        if call == 0:
+            # a different problem in between, itself checked against the tree entry point
+            other = torch.from_numpy(Xo).cuda()
+            got_o = _noalloc(fsg, other, po)
+            ok, worst = _close(got_o, _tree_degrees(fsg, other, po), Xo.shape[0])
+            assert ok, f"intervening call: {worst}"
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch(fsg):
