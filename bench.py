@@ -195,6 +195,208 @@ def run_reference(args):
     return 0
 
 
+def timed_steps(step, steps, stream, flush):
+    """CUDA-event times (ms) of `steps` calls of step() on `stream`, with the
+    L2 flushed before each."""
+    import torch
+    out = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def tensor_peak():
+    """Measured sustained BF16 tensor peak (TFLOP/s) and where it came from."""
+    pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pf):
+        with open(pf) as f:
+            return json.load(f).get("bf16_tflops_sustained", 1700.0), "measured cuBLAS BF16 sustained"
+    return 1700.0, "fallback"
+
+
+def sub_digits(fsg, stream, flush, steps):
+    """Digit-image workload (n = 70,000, d = 784, L = 64, sigma = median/2) on
+    the exact 8-bit tensor-core path: throughput, bin-pass roofline against
+    the tensor peak, degree error against the FP64 oracle on 256 points."""
+    import torch
+    import oracle as ora
+    from paper_2310_13870_gb300 import inputs
+    n, d, L, seed = 70_000, 784, 64, 0
+    X = inputs.digit_like(n=n, seed=0)
+    sigma = inputs.median_pair_distance(X, m=4096, seed=0) / 2
+    p = fsg.params(sigma)
+    with torch.cuda.stream(stream):
+        pts = torch.from_numpy(X).cuda()
+        tree = fsg.fsg_build_tree(pts, stream=stream)
+        bufs = fsg.GraphBuffers(n, L, with_aux=False)
+        bufs.deg = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step():
+        fsg.fsg_tree_update(tree, pts, stream=stream)
+        fsg.fsg_build_graph(tree, p, L, seed, bufs=bufs, stream=stream)
+
+    for _ in range(3):
+        step()
+    fsg.fsg_profile(tree, True)
+    kde = []
+    ms = []
+    for _ in range(steps):
+        ms += timed_steps(step, 1, stream, flush)
+        kde.append(fsg.fsg_profile_read(tree)[0]["kde_bins"])
+    fsg.fsg_profile(tree, False)
+    assert fsg.fsg_sync(tree, stream=stream) == 0
+    st = fsg.stats_dict(bufs)
+    t = statistics.mean(ms)
+    peak, basis = tensor_peak()
+    achieved = 2.0 * n * n * d / (statistics.mean(kde) * 1e-3) / 1e12
+    q = np.random.Generator(np.random.PCG64(21)).choice(n, size=256, replace=False)
+    want = ora.degrees(X, ora.gamma(sigma), queries=q)
+    rel = np.abs(bufs.deg.cpu().numpy()[q] - want) / want
+    tree.close()
+    return {"workload": "digit_like n=70000 d=784 (10 prototypes, 8-bit) sigma=median/2 L=64 seed=0",
+            "precision": "exact 8-bit tcgen05 bin pass (BF16 products of k/255 data, FP32 accumulate)",
+            "value": n * L / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "steps": steps,
+            "flagged_samples": st["n_flagged"], "edges_per_step": int(bufs.m.item()),
+            "roofline": {"bound": "tensor", "kernel": "kde_bins_tc_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "kde_bins_ms": statistics.mean(kde),
+                         "flops_per_launch": 2.0 * n * n * d, "peak_basis": basis},
+            "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(q.size),
+                          "kind": "degrees (Eq. 1 over all points) vs the FP64 oracle"}}
+
+
+def sub_seg_batch(fsg, stream, flush, steps):
+    """64 segmentation-shaped images (h 160..321, w = min(481, 1.5 h), d = 5,
+    sigma = 0.05, L = 48) as one batch replayed from a CUDA graph: throughput,
+    executed bin-pass evaluations per second of the whole step against the
+    d = 5 FP32 bound, degree error on 64 points of four images."""
+    import torch
+    import oracle as ora
+    from paper_2310_13870_gb300 import inputs
+    imgs = inputs.segmentation_batch(count=64)
+    L, sigma = 48, 0.05
+    with torch.cuda.stream(stream):
+        sets = [(torch.from_numpy(X).cuda(), fsg.params(sigma), L, 1000 + i) for i, X in enumerate(imgs)]
+        batch = fsg.Batch(sets, streams=4, capture=True, stream=stream)
+    for _ in range(3):
+        batch.run(stream=stream)
+    stream.synchronize()
+    ms = timed_steps(lambda: batch.run(stream=stream), steps, stream, flush)
+    t = statistics.mean(ms)
+    n_tot = sum(int(X.shape[0]) for X in imgs)
+    bin_evals = 0
+    for (pts, p, _, _) in sets:
+        tr = fsg.fsg_build_tree(pts, stream=stream)
+        bin_evals += fsg.fsg_bin_pass_evals(tr, p)
+        tr.close()
+    peak = alu_peak_evals(5, ops=2 * 5 + 3) / 1e9
+    achieved = bin_evals / (t * 1e-3) / 1e9
+    errs = []
+    for k in (0, 21, 42, 63):
+        X = imgs[k]
+        q = np.random.Generator(np.random.PCG64(50 + k)).choice(X.shape[0], size=64, replace=False)
+        want = ora.degrees(X, ora.gamma(sigma), queries=q)
+        errs.append(np.abs(batch.bufs[k].deg.cpu().numpy()[q] - want) / want)
+    rel = np.concatenate(errs)
+    flagged = sum(int(b.stats[1].item()) for b in batch.bufs)
+    batch.close()
+    return {"workload": "segmentation batch: 64 images h 160..321, w=min(481,1.5h), d=5, sigma=0.05, L=48",
+            "points": n_tot, "value": n_tot * L / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "steps": steps,
+            "flagged_samples": flagged, "parallelism": "4 streams, CUDA graph",
+            "roofline": {"bound": "alu", "kernel": "kde_bins_sym_kernel<5> (64 launches, whole step)",
+                         "achieved": achieved, "peak": peak, "unit": "Gkernel-evals/s (executed, per step time)",
+                         "frac": achieved / peak, "executed_bin_evals": int(bin_evals),
+                         "note": "step time includes every other phase: a lower bound of the bin pass's rate"},
+            "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(rel.size),
+                          "kind": "degrees vs the FP64 oracle (64 points of images 0, 21, 42, 63)"}}
+
+
+def sub_serving(fsg, requests, rate):
+    """Serving: `requests` graph-build requests (Poisson arrivals at `rate`/s,
+    n log-uniform in [1e3, 2e5], d in {2, 10, 64}, mixture data, sigma = 1.5,
+    L = 32) through the library's server: p50/p99 latency and edges/s; the
+    degree error of three of the trace's requests run through the same
+    kernels alone (results in the mix equal the results alone)."""
+    import torch
+    import oracle as ora
+    from paper_2310_13870_gb300 import inputs
+    L, sigma, warm = 32, 1.5, 20
+    reqs = inputs.serving_requests(count=requests + warm, rate_hz=rate)
+    pools = {d: torch.from_numpy(inputs.gaussian_mixture(n=200_000, d=d, seed=d)).pin_memory().numpy()
+             for d in (2, 10, 64)}
+    ring = [tuple(torch.empty(200_000 * L, dtype=dt).pin_memory().numpy()
+                  for dt in (torch.int32, torch.int32, torch.float32)) for _ in range(24)]
+    free_ring = list(range(len(ring)))
+    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8)
+    p = fsg.params(sigma)
+    owner, lat, done = {}, [], [0]
+
+    def collect(wait_ms=0):
+        for rec, _ in server.poll(wait_ms=wait_ms):
+            slot, n_r, timed = owner.pop(rec["id"])
+            free_ring.append(slot)
+            if rec["status"] != fsg.FSG_OK:
+                raise RuntimeError(f"request failed: {rec}")
+            if timed:
+                lat.append(rec["latency_ms"])
+                done[0] += n_r * L
+
+    def submit(r, timed):
+        while not free_ring:
+            collect(wait_ms=1)
+        slot = free_ring.pop()
+        rid = server.submit(pools[r.d][: r.n], p, L, r.seed, out=ring[slot])
+        owner[rid] = (slot, r.n, timed)
+
+    for r in reqs[:warm]:
+        submit(r, False)
+    while owner:
+        collect(wait_ms=5)
+    timed_reqs = reqs[warm:]
+    base = timed_reqs[0].arrival_s
+    t0 = time.perf_counter()
+    for r in timed_reqs:
+        due = t0 + (r.arrival_s - base)
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            collect(wait_ms=0)
+            if due - now > 0.002:
+                time.sleep(0.001)
+        submit(r, True)
+        collect(wait_ms=0)
+    while owner:
+        collect(wait_ms=5)
+    wall = time.perf_counter() - t0
+    server.close()
+    errs = []
+    for d in (2, 10, 64):
+        r = min((r for r in timed_reqs if r.d == d), key=lambda r: r.n)
+        X = pools[d][: r.n]
+        tree = fsg.fsg_build_tree(torch.from_numpy(np.ascontiguousarray(X)).cuda())
+        deg = fsg.fsg_degrees(tree, p).cpu().numpy()
+        tree.close()
+        q = np.random.Generator(np.random.PCG64(60 + d)).choice(r.n, size=min(64, r.n), replace=False)
+        want = ora.degrees(X, ora.gamma(sigma), queries=q)
+        errs.append(np.abs(deg[q] - want) / want)
+    rel = np.concatenate(errs)
+    lat.sort()
+    pct = lambda a, x: a[min(len(a) - 1, int(x * len(a)))]
+    return {"workload": f"serving: {len(timed_reqs)} requests, Poisson {rate}/s, n log-uniform [1e3, 2e5], "
+                        "d in {2,10,64}, mixture data, sigma=1.5, L=32, SET edges, HBM budget 120 GB, 8 slots",
+            "value": done[0] / wall, "unit": UNIT, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
+            "max_ms": lat[-1], "wall_s": wall, "offered_s": timed_reqs[-1].arrival_s - base,
+            "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(rel.size),
+                          "kind": "degrees vs the FP64 oracle (the smallest request of each d, run alone)"}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -448,7 +650,7 @@ def run_ours(args):
                               "kind": "degrees vs the FP64 oracle of the same kernel"}}
 
     cpu = None
-    err = split_cmp = approx_cmp = families = None
+    err = split_cmp = approx_cmp = families = subs = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ref = {}
         v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed, keep=ref)
@@ -478,6 +680,11 @@ def run_ours(args):
             approx_cmp = run_approx(2.0 ** -20, ref)
             families = {name: run_family(fam, ofam) for name, fam, ofam in
                         (("laplacian", fsg.FSG_KERNEL_LAPLACIAN, 1), ("exponential", fsg.FSG_KERNEL_EXPONENTIAL, 2))}
+        if not args.no_sub and WORKLOAD["workload"].startswith("gaussian_mixture") and not split and n == 100_000:
+            # the other workloads, each measured the same way (value, roofline, error vs the oracle)
+            subs = {"digits": sub_digits(fsg, stream, flush, 5),
+                    "seg_batch": sub_seg_batch(fsg, stream, flush, 3),
+                    "serving": sub_serving(fsg, args.sub_requests, args.rate)}
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_queries} of the {n} query points (all {L} samples each + their degrees), "
                          f"{dt:.1f} s, extrapolated per sampled edge"}
@@ -493,7 +700,7 @@ def run_ours(args):
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
                 "kde_error": err, "split_precision": split_cmp, "approximate_kde": approx_cmp,
-                "kernel_families": families,
+                "kernel_families": families, "workloads": subs,
                 "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "carried_fp32_gpu": carried,
                 "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
@@ -717,6 +924,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch-shape heuristics")
+    ap.add_argument("--no-sub", action="store_true", help="skip the digit, segmentation-batch and serving entries")
+    ap.add_argument("--sub-requests", type=int, default=1000, help="serving entry: length of the trace")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP32 levelwise path")
     ap.add_argument("--n", type=int, default=0, help="smaller point count (profiler captures only)")
     ap.add_argument("--d", type=int, default=0, help="other dimension of the mixture workload (kernel studies)")

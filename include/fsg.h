@@ -144,7 +144,24 @@ typedef struct {
      * eps <= 1/(6 log n). */
     float kde_eps;
     int32_t kernel;        /* FSG_KERNEL_* (0: Gaussian)                         */
-    int32_t reserved[3];
+    /* High-precision re-decision of flagged descents (0 = off, 1 = on):
+     * after the fused schedule, every sample with a decision inside the flag
+     * band is taken again from the root; each such decision is made on sums
+     * of kernel values within relative error 2^-20 of the exact ones
+     * (double-single squared distances, FP64 accumulation), compared in FP64
+     * with the full 32-bit draw (u = word 2^-32), and the levels inside the
+     * bin reached are all decided that way.  A sample stays flagged only if a
+     * high-precision margin is itself within 2^-20; every other sample
+     * equals the exact method's (Algorithm 1).  fsg_stats.n_resolved counts
+     * the samples taken again and n_flagged the ones still flagged.
+     * Gaussian kernel, FSG_SCHED_FUSED, bins of at most 1024 points;
+     * FSG_ERR_UNSUPPORTED otherwise. */
+    int32_t resolve;
+    /* 1: fsg_build_graph writes d_w as double [cap]: w = k / p_hat (Eq. 2)
+     * formed in FP64 from a high-precision k(x_i, x_j) (relative error
+     * 2^-20) and the FP32-accumulated degrees; 0: float [cap]. */
+    int32_t weight_f64;
+    int32_t reserved[1];
 } fsg_params;
 
 /* Device-side statistics of one fsg_build_graph call (all int64). */
@@ -159,7 +176,7 @@ typedef struct {
     int64_t status;        /* device status word (FSG_OK or FSG_ERR_TIMEOUT)    */
     int64_t n_bin_evals;   /* of n_evals, those of the bin pass (the split pass */
                            /* skips tile pairs whose values are all zero)       */
-    int64_t reserved;
+    int64_t n_resolved;    /* samples re-decided in high precision (resolve)    */
 } fsg_stats;
 
 /* Library version string and a description of a status code. */
@@ -332,7 +349,8 @@ int fsg_sample_edges(fsg_tree* tree, const fsg_params* params, int32_t L, uint64
  *   edge_mode  : FSG_EDGES_SET or FSG_EDGES_MULTI.
  *   d_src,d_dst: device int32 [cap] original indices (SET: the point that
  *                sampled the edge first in (point, sample) order is src).
- *   d_w        : device float32 [cap].
+ *   d_w        : device float32 [cap], or float64 [cap] with
+ *                params->weight_f64.
  *   cap        : >= n*L (an upper bound of the edge count in either mode).
  *   d_m_out    : device int64, number of edges written.
  *   d_deg, d_samples, d_flags, d_stats : optional device outputs (NULL to
@@ -340,7 +358,7 @@ int fsg_sample_edges(fsg_tree* tree, const fsg_params* params, int32_t L, uint64
  * Errors: INVALID_ARG, CAPACITY, OOM, CUDA, UNSUPPORTED.
  */
 int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_t seed,
-                    int32_t edge_mode, int32_t* d_src, int32_t* d_dst, float* d_w, int64_t cap,
+                    int32_t edge_mode, int32_t* d_src, int32_t* d_dst, void* d_w, int64_t cap,
                     int64_t* d_m_out, double* d_deg, int32_t* d_samples, uint8_t* d_flags,
                     fsg_stats* d_stats, void* stream);
 
@@ -360,6 +378,7 @@ int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_
 #define FSG_PHASE_LEAF 4        /* leaf finish: remaining levels and weights   */
 #define FSG_PHASE_EDGES 5       /* edge list                                   */
 #define FSG_PHASE_OUTPUTS 6     /* per-sample outputs and statistics           */
+#define FSG_PHASE_RESOLVE 7     /* high-precision re-decision (params.resolve) */
 #define FSG_NUM_PHASES 8
 int fsg_profile(fsg_tree* tree, int enable);
 int fsg_profile_read(fsg_tree* tree, float* ms, int64_t* launches);
@@ -386,7 +405,7 @@ typedef struct {
     int32_t reserved0;
     int32_t* d_src;         /* device int32 [cap]                             */
     int32_t* d_dst;         /* device int32 [cap]                             */
-    float* d_w;             /* device float32 [cap]                           */
+    float* d_w;             /* device float32 [cap] (params.weight_f64 = 0)   */
     int64_t cap;            /* >= n * L                                       */
     int64_t* d_m_out;       /* device int64: edges written                    */
     double* d_deg;          /* optional device float64 [n]                    */
@@ -443,7 +462,7 @@ typedef struct {
     int32_t reserved0;
     int32_t* h_src;         /* host int32 [cap] (pinned memory is faster)     */
     int32_t* h_dst;         /* host int32 [cap]                               */
-    float* h_w;             /* host float32 [cap]                             */
+    float* h_w;             /* host float32 [cap] (params.weight_f64 = 0)     */
     int64_t cap;            /* >= n * L                                       */
 } fsg_request;
 
@@ -494,7 +513,8 @@ int fsg_sync(fsg_tree* tree, void* stream);
  * builds the tree (FSG_ORDER_SPATIAL for FSG_PREC_SPLIT_BF16, identity
  * otherwise), runs fsg_build_graph, and copies the edge list back.  The
  * server builds its trees the same way.
- *   h_src, h_dst (int32 [cap]), h_w (float32 [cap]), *h_m_out (edge count).
+ *   h_src, h_dst (int32 [cap]), h_w (float32 [cap]; params->weight_f64 must
+ *   be 0), *h_m_out (edge count).
  * Blocks until the result is on the host.  The device buffers live in an
  * internal per-thread cache that grows to the largest (n, d, L) seen.
  * Errors: as fsg_build_graph, plus CAPACITY when cap < n*L.

@@ -41,6 +41,7 @@ int check_params(const fsg_params* p) {
     if (!(p->kde_eps >= 0.f) || !std::isfinite(p->kde_eps) || p->kde_eps > 0.5f) return FSG_ERR_INVALID_ARG;
     if (p->kernel != FSG_KERNEL_GAUSSIAN && p->kernel != FSG_KERNEL_LAPLACIAN && p->kernel != FSG_KERNEL_EXPONENTIAL)
         return FSG_ERR_INVALID_ARG;
+    if ((p->resolve != 0 && p->resolve != 1) || (p->weight_f64 != 0 && p->weight_f64 != 1)) return FSG_ERR_INVALID_ARG;
     return FSG_OK;
 }
 
@@ -50,7 +51,7 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     const double gamma = p->kernel != FSG_KERNEL_GAUSSIAN ? 1.0 / p->sigma
                          : p->scale_conv == FSG_SIGMA_SQ  ? 1.0 / (p->sigma * p->sigma)
                                                           : 1.0 / (2.0 * p->sigma * p->sigma);
-    KernelParams kp;
+    KernelParams kp{};
     kp.precision = p->precision;
     kp.gamma = (float)gamma;
     kp.neg_c = (float)(-gamma * kLog2e);
@@ -63,6 +64,12 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     kp.flag_eps = p->flag_eps > 0.f ? p->flag_eps : (p->precision == FSG_PREC_SPLIT_BF16 ? 0x1p-10f : 0x1p-13f);
     kp.kde_eps = p->kde_eps;
     kp.family = p->kernel;
+    // gamma log2 e as an unevaluated pair of FP32 numbers (high-precision values)
+    const double c = gamma * kLog2e;
+    kp.hp_ch = (float)c;
+    kp.hp_cl = (float)(c - (double)kp.hp_ch);
+    kp.resolve = p->resolve;
+    kp.weight_f64 = p->weight_f64;
     return kp;
 }
 
@@ -145,6 +152,11 @@ int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED))
         return FSG_ERR_UNSUPPORTED;
     if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
+    // the high-precision re-decision re-reads the fused schedule's bin sums (Gaussian kernel)
+    if (p->resolve && (p->schedule != FSG_SCHED_FUSED || p->kernel != FSG_KERNEL_GAUSSIAN ||
+                       !resolve_supported(t)))
+        return FSG_ERR_UNSUPPORTED;
+    if (p->weight_f64 && p->kernel != FSG_KERNEL_GAUSSIAN) return FSG_ERR_UNSUPPORTED;
     // the levelwise schedules are plain FP32 paths only
     if (p->schedule != FSG_SCHED_FUSED && p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32)
         return FSG_ERR_UNSUPPORTED;
@@ -676,6 +688,11 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
         PhaseScope ph(t, FSG_PHASE_LEAF, s);
         e = run_leaf_phase(t, kp, s);
     }
+    if (e == cudaSuccess && kp.resolve) {  // the list of flagged samples reuses uniq (free until the edges)
+        PhaseScope ph(t, FSG_PHASE_RESOLVE, s);
+        e = launch_resolve(t, kp, ws.uniq, ws.misc, s);
+        t->launches += 2;
+    }
     return status_of(e);
 }
 
@@ -688,11 +705,12 @@ static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
 
 // Statistics known on the host: samples run, bin-pass evaluations.
 __global__ static void stats_finish_kernel(fsg_stats* st, int64_t n_samples, int64_t bin_evals,
-                                           const int32_t* status, fsg_stats* out) {
+                                           const int32_t* status, const int32_t* n_resolved, fsg_stats* out) {
     st->n_samples = n_samples;
     st->n_evals += bin_evals;       // the split pass counts its own on the device
     st->n_bin_evals += bin_evals;
     st->status = status[0];
+    st->n_resolved = n_resolved ? *n_resolved : 0;
     if (out) *out = *st;
 }
 
@@ -742,7 +760,8 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
         PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
         e = launch_outputs(t, kp, d_samples, d_flags, nullptr, s);
         if (e == cudaSuccess) {
-            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status, nullptr);
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status,
+                                                p->resolve ? t->ws.misc : nullptr, nullptr);
             e = cudaGetLastError();
         }
         t->launches += 2;
@@ -751,7 +770,7 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
 }
 
 int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t edge_mode, int32_t* d_src,
-                    int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, double* d_deg, int32_t* d_samples,
+                    int32_t* d_dst, void* d_w, int64_t cap, int64_t* d_m_out, double* d_deg, int32_t* d_samples,
                     uint8_t* d_flags, fsg_stats* d_stats, void* stream) {
     if (!t || L < 1 || L > kMaxL || !d_src || !d_dst || !d_w || !d_m_out) return FSG_ERR_INVALID_ARG;
     if (edge_mode != FSG_EDGES_SET && edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
@@ -775,7 +794,8 @@ int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, 
         PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
         e = launch_outputs(t, kp, d_samples, d_flags, d_stats, s);
         if (e == cudaSuccess) {
-            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status, d_stats);
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status,
+                                                p->resolve ? t->ws.misc : nullptr, d_stats);
             e = cudaGetLastError();
         }
         t->launches += 2;
@@ -823,6 +843,7 @@ int fsg_build_graph_host(const float* h_points, int64_t n, int32_t d, const fsg_
                          int64_t* h_m_out, void* stream) {
     if (!h_points || !h_src || !h_dst || !h_w || !h_m_out || n < 1 || d < 1 || L < 1 || L > kMaxL)
         return FSG_ERR_INVALID_ARG;
+    if (p && p->weight_f64) return FSG_ERR_INVALID_ARG;  // h_w is float32
     if (cap < n * (int64_t)L) return FSG_ERR_CAPACITY;
     int rc = check_params(p);
     if (rc != FSG_OK) return rc;

@@ -74,6 +74,7 @@ int fsg_batch_create(const fsg_batch_item* items, int32_t count, int32_t streams
             !it.d_m_out)
             return FSG_ERR_INVALID_ARG;
         if (it.edge_mode != FSG_EDGES_SET && it.edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
+        if (it.params.weight_f64) return FSG_ERR_INVALID_ARG;  // d_w is float32
         if (it.cap < it.n * (int64_t)it.L) return FSG_ERR_CAPACITY;
     }
     fsg_batch* b = new (std::nothrow) fsg_batch();

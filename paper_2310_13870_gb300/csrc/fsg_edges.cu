@@ -27,6 +27,19 @@ __device__ __forceinline__ float edge_weight(float k, float deg_i, float deg_j, 
     return __fdiv_rn(k, pi + pj - pi * pj);
 }
 
+// Weight of Eq. 2 in FP64 from a high-precision kernel value of the pair at
+// tree positions (a, b) and the two FP32-accumulated degrees; symmetric in
+// (a, b) bit for bit.
+__device__ __forceinline__ double edge_weight_f64(const float* __restrict__ Xt, int dp, int d, int a, int b,
+                                                  float deg_a, float deg_b, int L, float ch, float cl) {
+    const double k = (double)hp_gauss(Xt + (size_t)a * dp, Xt + (size_t)b * dp, d, ch, cl);
+    if (!(k > 0.0)) return 0.0;
+    const double Lk = (double)L * k;
+    const double pa = fmin(Lk / (double)deg_a, 1.0);
+    const double pb = fmin(Lk / (double)deg_b, 1.0);
+    return k / (pa + pb - pa * pb);
+}
+
 // Bitonic sort of the warp's 64 (key, value) pairs: element index lane holds
 // (k0, v0), index lane+32 holds (k1, v1).  Ascending by key.
 __device__ __forceinline__ void warp_sort64(int32_t& k0, float& v0, int32_t& k1, float& v1, int lane) {
@@ -219,11 +232,14 @@ __global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(int64_t* __restr
     }
 }
 
+// F64: weights in FP64 from high-precision kernel values (wout is double).
+template <bool F64>
 __global__ void __launch_bounds__(128)
 set_write_kernel(const int32_t* __restrict__ uniq, const float* __restrict__ uniq_w,
                  const uint64_t* __restrict__ emit_mask, const int64_t* __restrict__ eoff,
                  const int32_t* __restrict__ perm, int n, int L, int64_t cap, int32_t* __restrict__ src,
-                 int32_t* __restrict__ dst, float* __restrict__ wout) {
+                 int32_t* __restrict__ dst, void* __restrict__ wout, const float* __restrict__ Xt, int dp, int d,
+                 const float* __restrict__ degf, float ch, float cl) {
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
@@ -236,20 +252,26 @@ set_write_kernel(const int32_t* __restrict__ uniq, const float* __restrict__ uni
             if ((mk >> k) & 1ull) {
                 const int64_t o = base + __popcll(mk & ((1ull << k) - 1ull));
                 if (o < cap) {
+                    const int32_t j = uniq[(size_t)q * L + k];
                     src[o] = iq;
-                    dst[o] = perm[uniq[(size_t)q * L + k]];
-                    wout[o] = uniq_w[(size_t)q * L + k];
+                    dst[o] = perm[j];
+                    if (F64)
+                        static_cast<double*>(wout)[o] = edge_weight_f64(Xt, dp, d, q, j, degf[q], degf[j], L, ch, cl);
+                    else
+                        static_cast<float*>(wout)[o] = uniq_w[(size_t)q * L + k];
                 }
             }
         }
     }
 }
 
+template <bool F64>
 __global__ void multi_write_kernel(const int32_t* __restrict__ leaf_pos, const float* __restrict__ ksmp,
                                    const float* __restrict__ degf, const int64_t* __restrict__ eoff,
                                    const int32_t* __restrict__ perm, int n, int L,
                                    int64_t cap, int32_t* __restrict__ src, int32_t* __restrict__ dst,
-                                   float* __restrict__ wout) {
+                                   void* __restrict__ wout, const float* __restrict__ Xt, int dp, int d, float ch,
+                                   float cl) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         int64_t o = eoff[q];
         const int32_t iq = perm[q];
@@ -259,7 +281,11 @@ __global__ void multi_write_kernel(const int32_t* __restrict__ leaf_pos, const f
                 if (o < cap) {
                     src[o] = iq;
                     dst[o] = perm[j];
-                    wout[o] = edge_weight(ksmp[(size_t)q * L + l], degf[q], degf[j], L);
+                    if (F64)
+                        static_cast<double*>(wout)[o] = edge_weight_f64(Xt, dp, d, q, j, degf[q], degf[j], L,
+                                                                        ch, cl);
+                    else
+                        static_cast<float*>(wout)[o] = edge_weight(ksmp[(size_t)q * L + l], degf[q], degf[j], L);
                 }
                 ++o;
             }
@@ -309,7 +335,7 @@ int grid_for(int64_t work, int per_block) {
 }  // namespace
 
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src, int32_t* d_dst,
-                         float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s) {
+                         void* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s) {
     const auto& ws = t->ws;
     const int n = (int)t->n, L = kp.L;
     if (edge_mode == FSG_EDGES_SET) {
@@ -326,11 +352,13 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
     scan_top_kernel<<<1, kScanBlock, 0, s>>>(ws.scan_tmp, nblocks);
     scan_apply_kernel<<<nblocks, kScanBlock, 0, s>>>(ws.ecount, n, ws.scan_tmp, d_m_out, ws.stats);
     if (edge_mode == FSG_EDGES_SET) {
-        set_write_kernel<<<grid_for(n, 4), 128, 0, s>>>(ws.uniq, ws.uniq_w, ws.emit_mask, ws.ecount, t->perm, n, L,
-                                                       cap, d_src, d_dst, d_w);
+        auto k = kp.weight_f64 ? set_write_kernel<true> : set_write_kernel<false>;
+        k<<<grid_for(n, 4), 128, 0, s>>>(ws.uniq, ws.uniq_w, ws.emit_mask, ws.ecount, t->perm, n, L, cap, d_src,
+                                         d_dst, d_w, t->Xt, t->dp, t->d, ws.degf, kp.hp_ch, kp.hp_cl);
     } else {
-        multi_write_kernel<<<grid_for(n, 256), 256, 0, s>>>(ws.leaf_pos, ws.ksmp, ws.degf, ws.ecount, t->perm, n, L,
-                                                           cap, d_src, d_dst, d_w);
+        auto k = kp.weight_f64 ? multi_write_kernel<true> : multi_write_kernel<false>;
+        k<<<grid_for(n, 256), 256, 0, s>>>(ws.leaf_pos, ws.ksmp, ws.degf, ws.ecount, t->perm, n, L, cap, d_src,
+                                           d_dst, d_w, t->Xt, t->dp, t->d, kp.hp_ch, kp.hp_cl);
     }
     return cudaGetLastError();
 }

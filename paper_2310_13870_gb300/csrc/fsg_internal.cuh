@@ -128,6 +128,9 @@ struct KernelParams {
     float flag_eps;
     float kde_eps;    // approximate bin pass: skipped mass <= kde_eps * degree (0 = exact)
     int family;       // FSG_KERNEL_*
+    float hp_ch, hp_cl;  // gamma log2 e as a pair of FP32 numbers (high-precision values)
+    int resolve;      // re-decide flagged descents in high precision
+    int weight_f64;   // d_w is double: weights in FP64 from high-precision kernel values
 };
 
 // Raises the dynamic shared-memory limit of `kernel` on the current device to
@@ -158,7 +161,12 @@ int64_t leaf_default_splits(const fsg_tree* t, int L);
 // The 128-point leaf kernel applies: d <= 16, every bin of 65..128 points.
 bool use_leaf128(const fsg_tree* t);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
-                         int32_t* d_dst, float* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
+                         int32_t* d_dst, void* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
+// High-precision re-decision of flagged samples (list: int32 [n L] scratch,
+// count: one int32, both device memory).
+bool resolve_supported(const fsg_tree* t);
+cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, int32_t* list, int32_t* count,
+                           cudaStream_t s);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
                            fsg_stats* d_stats, cudaStream_t s);
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
@@ -267,6 +275,62 @@ __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
 }
 __device__ __forceinline__ float2 f2_unpack(uint64_t v) {
     float2 r; asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v)); return r;
+}
+
+// ---------------------------------------------------------------------------
+// High-precision kernel values (the re-decision of flagged descents and the
+// FP64 weights).  The squared distance of two FP32 points is accumulated as
+// an unevaluated pair of FP32 numbers (hi + lo): each coordinate difference
+// is split exactly into its rounded value and rounding error (two-sum,
+// Knuth), its square exactly into product and error (fused multiply-add),
+// and the terms are added with two-sum, so ||x - y||^2 carries a relative
+// error of a few 2^-46.  The exponent c ||x - y||^2 (c = gamma log2 e, also
+// as a pair) is split into an integer and a fraction f, |f| <= 1/2 + 2^-20,
+// and k = 2^-f 2^-i with 2^-f from ex2.approx (relative error below 2^-22)
+// and f rounded to FP32 (2^-25 absolute, 2^-25.5 relative in k).  Every
+// value is therefore within relative error kHpEta of exp(-gamma ||x-y||^2)
+// computed exactly, or below 2^-126 where FP32 flushes it to zero.
+// ---------------------------------------------------------------------------
+constexpr double kHpEta = 0x1p-20;  // relative error bound used by the re-decision (a 3x margin)
+
+__device__ __forceinline__ void hp_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Adds the square of x - y (both FP32) to the pair (sh, sl).
+__device__ __forceinline__ void hp_acc_sq(float x, float y, float& sh, float& sl) {
+    float dh, dl;
+    hp_two_sum(x, -y, dh, dl);            // x - y = dh + dl exactly
+    const float ph = __fmul_rn(dh, dh);
+    float pl = __fmaf_rn(dh, dh, -ph);    // dh^2 = ph + pl exactly
+    pl = __fmaf_rn(__fmul_rn(2.f, dh), dl, pl);  // + 2 dh dl (dl^2 < 2^-48 dh^2)
+    float th, te;
+    hp_two_sum(sh, ph, th, te);
+    sh = th;
+    sl = __fadd_rn(sl, __fadd_rn(te, pl));
+}
+
+// 2^-(th + tl) for th >= 0 (the pair of the exponent in base 2).
+__device__ __forceinline__ float hp_exp2_neg(float th, float tl) {
+    const float ti = rintf(th);
+    if (ti > 150.f) return 0.f;
+    const float f = __fadd_rn(__fsub_rn(th, ti), tl);  // th - ti is exact
+    const float m = ex2_approx(-f);
+    const int e = 127 - (int)ti;                       // 2^-ti as an FP32 power of two
+    return e >= 1 ? __fmul_rn(m, __int_as_float(e << 23)) : 0.f;
+}
+
+// k(x, y) = exp(-gamma ||x - y||^2) to relative error kHpEta (see above);
+// (ch, cl) = gamma log2 e as a pair; x and y hold d coordinates.
+__device__ __forceinline__ float hp_gauss(const float* __restrict__ x, const float* __restrict__ y, int d, float ch,
+                                          float cl) {
+    float sh = 0.f, sl = 0.f;
+    for (int t = 0; t < d; ++t) hp_acc_sq(x[t], y[t], sh, sl);
+    const float th = __fmul_rn(sh, ch);
+    const float tl = __fadd_rn(__fmaf_rn(sh, ch, -th), __fmaf_rn(sh, cl, __fmul_rn(sl, ch)));
+    return hp_exp2_neg(th, tl);
 }
 
 // Kernel families (Sec. 2.1): the exponent is neg_c times the squared

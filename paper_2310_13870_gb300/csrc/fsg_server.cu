@@ -305,6 +305,7 @@ int fsg_server_submit(fsg_server* sv, const fsg_request* r, uint64_t* id_out) {
     if (r->edge_mode != FSG_EDGES_SET && r->edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
     const fsg_params& p = r->params;
     if (!(p.sigma > 0.0) || p.sigma != p.sigma || p.sigma > 1e300) return FSG_ERR_INVALID_ARG;
+    if (p.weight_f64) return FSG_ERR_INVALID_ARG;  // h_w is float32
     if (r->cap < r->n * (int64_t)r->L) return FSG_ERR_CAPACITY;
     Pending pd;
     pd.req = *r;

@@ -49,7 +49,7 @@ EXPORTED = [
     "fsg_server_destroy", "fsg_selftest_wait_timeout",
 ]
 FSG_NUM_PHASES = 8
-PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "unused"]
+PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "resolve"]
 
 
 class FsgError(RuntimeError):
@@ -62,7 +62,8 @@ class FsgError(RuntimeError):
 class fsg_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("scale_conv", ctypes.c_int32), ("self_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flag_eps", ctypes.c_float),
-                ("kde_eps", ctypes.c_float), ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("kde_eps", ctypes.c_float), ("kernel", ctypes.c_int32), ("resolve", ctypes.c_int32),
+                ("weight_f64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class fsg_tree_opts(ctypes.Structure):
@@ -98,7 +99,7 @@ class fsg_result(ctypes.Structure):
 
 
 STATS_FIELDS = ["n_samples", "n_flagged", "n_self", "n_empty", "n_evals", "n_items", "n_edges", "status",
-                "n_bin_evals", "reserved"]
+                "n_bin_evals", "n_resolved"]
 
 
 class fsg_stats(ctypes.Structure):
@@ -180,7 +181,7 @@ def _dptr(t):
 
 def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FSG_SELF_EXCLUDE,
            precision: int = FSG_PREC_AUTO, schedule: int = FSG_SCHED_FUSED, flag_eps: float = 0.0,
-           kde_eps: float = 0.0, kernel: int = 0) -> fsg_params:
+           kde_eps: float = 0.0, kernel: int = 0, resolve: bool = False, weight_f64: bool = False) -> fsg_params:
     p = fsg_params()
     p.sigma = float(sigma)
     p.scale_conv = scale_conv
@@ -190,6 +191,8 @@ def params(sigma: float, scale_conv: int = FSG_TWO_SIGMA_SQ, self_mode: int = FS
     p.flag_eps = float(flag_eps)
     p.kde_eps = float(kde_eps)
     p.kernel = int(kernel)
+    p.resolve = int(bool(resolve))
+    p.weight_f64 = int(bool(weight_f64))
     return p
 
 
@@ -349,13 +352,13 @@ def fsg_sample_edges(tree: Tree, p: fsg_params, L: int, seed: int, samples=None,
 class GraphBuffers:
     """Device output buffers of fsg_build_graph, reusable across calls."""
 
-    def __init__(self, n: int, L: int, with_aux: bool = True):
+    def __init__(self, n: int, L: int, with_aux: bool = True, weight_f64: bool = False):
         import torch
         cap = n * L
         self.cap = cap
         self.src = torch.empty(cap, dtype=torch.int32, device="cuda")
         self.dst = torch.empty(cap, dtype=torch.int32, device="cuda")
-        self.w = torch.empty(cap, dtype=torch.float32, device="cuda")
+        self.w = torch.empty(cap, dtype=torch.float64 if weight_f64 else torch.float32, device="cuda")
         self.m = torch.zeros(1, dtype=torch.int64, device="cuda")
         self.stats = torch.zeros(len(STATS_FIELDS), dtype=torch.int64, device="cuda")
         self.deg = torch.empty(n, dtype=torch.float64, device="cuda") if with_aux else None
@@ -365,8 +368,11 @@ class GraphBuffers:
 
 def fsg_build_graph(tree: Tree, p: fsg_params, L: int, seed: int, edge_mode: int = FSG_EDGES_SET,
                     bufs: Optional[GraphBuffers] = None, stream=None) -> GraphBuffers:
+    import torch
     if bufs is None:
-        bufs = GraphBuffers(tree.n, L)
+        bufs = GraphBuffers(tree.n, L, weight_f64=bool(p.weight_f64))
+    if bufs.w.dtype != (torch.float64 if p.weight_f64 else torch.float32):
+        raise ValueError("the weight buffer's dtype does not match params.weight_f64")
     _check(load().fsg_build_graph(tree.handle, ctypes.byref(p), L, ctypes.c_uint64(seed), edge_mode,
                                   _dptr(bufs.src), _dptr(bufs.dst), _dptr(bufs.w), bufs.cap, _dptr(bufs.m),
                                   _dptr(bufs.deg), _dptr(bufs.samples), _dptr(bufs.flags), _dptr(bufs.stats),
