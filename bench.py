@@ -255,7 +255,8 @@ def sub_digits(fsg, stream, flush, steps):
     st = fsg.stats_dict(bufs)
     t = statistics.mean(ms)
     peak, basis = tensor_peak()
-    achieved = 2.0 * n * n * d / (statistics.mean(kde) * 1e-3) / 1e12
+    pairs = fsg.fsg_bin_pass_evals(tree, p)  # executed (query, point) pairs: each pair once off the diagonal
+    achieved = 2.0 * pairs * d / (statistics.mean(kde) * 1e-3) / 1e12
     q = np.random.Generator(np.random.PCG64(21)).choice(n, size=256, replace=False)
     want = ora.degrees(X, ora.gamma(sigma), queries=q)
     rel = np.abs(bufs.deg.cpu().numpy()[q] - want) / want
@@ -264,9 +265,10 @@ def sub_digits(fsg, stream, flush, steps):
             "precision": "exact 8-bit tcgen05 bin pass (BF16 products of k/255 data, FP32 accumulate)",
             "value": n * L / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "steps": steps,
             "flagged_samples": st["n_flagged"], "edges_per_step": int(bufs.m.item()),
-            "roofline": {"bound": "tensor", "kernel": "kde_bins_tc_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "kde_bins_ms": statistics.mean(kde),
-                         "flops_per_launch": 2.0 * n * n * d, "peak_basis": basis},
+            "roofline": {"bound": "tensor", "kernel": "kde_bins_tc_kernel (symmetric)", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "kde_bins_ms": statistics.mean(kde),
+                         "executed_pairs": int(pairs), "flops_per_launch": 2.0 * pairs * d,
+                         "algorithmic_pairs": n * n, "peak_basis": basis},
             "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(q.size),
                           "kind": "degrees (Eq. 1 over all points) vs the FP64 oracle"}}
 
@@ -486,9 +488,9 @@ def run_ours(args):
     if on_tc:  # tensor-core GEMM (8-bit data): flops 2 n^2 d of the dot products;
         # split form: six BF16 products per coordinate over 64 padded coordinates,
         # for the pairs it executes (tile pairs whose values are all zero are skipped)
-        pairs = st["n_bin_evals"] if split else n * n
+        pairs = st["n_bin_evals"] if split else fsg.fsg_bin_pass_evals(tree, p)
         kpad = 16 * ((d + 15) // 16)  # coordinates the split form's MMAs run (K-steps of 16)
-        achieved = (12.0 * pairs * kpad if split else 2.0 * n * n * d) / (kde_avg * 1e-3) / 1e12
+        achieved = (12.0 * pairs * kpad if split else 2.0 * pairs * d) / (kde_avg * 1e-3) / 1e12
         peaks = {}
         pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pf):
@@ -649,8 +651,34 @@ def run_ours(args):
                 "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(q.size),
                               "kind": "degrees vs the FP64 oracle of the same kernel"}}
 
+    def run_resolve():
+        # the same input and path with the high-precision re-decision of the
+        # flagged samples (and FP64 weights): step time, the re-decision's
+        # own time, samples re-decided and still flagged
+        out = {}
+        for name, pr in (("resolve", fsg.params(sigma, resolve=True)),
+                         ("resolve_f64_weights", fsg.params(sigma, resolve=True, weight_f64=True))):
+            b2 = fsg.GraphBuffers(n, L, with_aux=False, weight_f64=bool(pr.weight_f64))
+            fsg.fsg_build_graph(tree, pr, L, seed, bufs=b2, stream=stream)  # warm-up
+            fsg.fsg_profile(tree, True)
+            rms, rph = [], []
+            for _ in range(max(3, args.plain_steps)):
+                rms += timed_steps(lambda: (fsg.fsg_tree_update(tree, pts, stream=stream),
+                                            fsg.fsg_build_graph(tree, pr, L, seed, bufs=b2, stream=stream)),
+                                   1, stream, flush)
+                rph.append(fsg.fsg_profile_read(tree)[0]["resolve"])
+            fsg.fsg_profile(tree, False)
+            assert fsg.fsg_sync(tree, stream=stream) == 0
+            rst = fsg.stats_dict(b2)
+            rt = statistics.mean(rms)
+            out[name] = {"value": n * L / (rt * 1e-3), "unit": UNIT, "ms_per_step": rt,
+                         "resolve_ms": statistics.mean(rph), "added_ms": rt - ms,
+                         "resolved_samples": rst["n_resolved"], "flagged_after": rst["n_flagged"],
+                         "flagged_without": st["n_flagged"]}
+        return out
+
     cpu = None
-    err = split_cmp = approx_cmp = families = subs = None
+    err = split_cmp = approx_cmp = families = subs = resolved = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ref = {}
         v, dt, threads = cpu_oracle_throughput(X, args.cpu_queries, L, sigma, seed, keep=ref)
@@ -680,6 +708,8 @@ def run_ours(args):
             approx_cmp = run_approx(2.0 ** -20, ref)
             families = {name: run_family(fam, ofam) for name, fam, ofam in
                         (("laplacian", fsg.FSG_KERNEL_LAPLACIAN, 1), ("exponential", fsg.FSG_KERNEL_EXPONENTIAL, 2))}
+        if not split and not on_tc and d <= 16:
+            resolved = run_resolve()
         if not args.no_sub and WORKLOAD["workload"].startswith("gaussian_mixture") and not split and n == 100_000:
             # the other workloads, each measured the same way (value, roofline, error vs the oracle)
             subs = {"digits": sub_digits(fsg, stream, flush, 5),
@@ -700,7 +730,7 @@ def run_ours(args):
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
                 "kde_error": err, "split_precision": split_cmp, "approximate_kde": approx_cmp,
-                "kernel_families": families, "workloads": subs,
+                "kernel_families": families, "workloads": subs, "high_precision": resolved,
                 "roofline": dict(roof, traffic=traffic), "plain_fp32_gpu": plain, "carried_fp32_gpu": carried,
                 "tuning": tuning,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

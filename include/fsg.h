@@ -389,10 +389,16 @@ int fsg_profile_read(fsg_tree* tree, float* ms, int64_t* launches);
  * Algorithm 2 with its own parameters.  fsg_batch_create builds one tree per
  * set (allocating); fsg_batch_run refreshes every tree from its d_points and
  * enqueues every set's graph build on `streams` internal streams forked from
- * (and joined back into) the caller's stream.  With capture != 0 the first run
- * records the whole launch sequence into a CUDA graph and later runs replay
- * it (inputs and outputs are read and written through the pointers given at
- * creation, so new point values of the same shapes are picked up).
+ * (and joined back into) the caller's stream.  When every set takes the
+ * symmetric FP32 bin pass (the same d <= 16 and kernel family, the fused
+ * schedule, exact KDE), the bin passes of all sets are one launch over the
+ * sets' block pairs (Sec. 4.2: one level's KDE calls over all sets add up
+ * to one KDE of their total size), between the trees' refresh and the rest of
+ * each set's build; otherwise each set keeps its own launches.  Results are
+ * the same either way.  With capture != 0 the first run records the whole
+ * launch sequence into a CUDA graph and later runs replay it (inputs and
+ * outputs are read and written through the pointers given at creation, so
+ * new point values of the same shapes are picked up).
  */
 typedef struct {
     const float* d_points;  /* device float32 [n][d], read at every run       */

@@ -135,7 +135,8 @@ cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) 
 
 // Kernel evaluations the bin pass executes (n^2, or about n^2/2 when symmetric).
 int64_t bin_pass_evals(const fsg_tree* t, int precision) {
-    if (use_tc(t, precision) || precision == FSG_PREC_SPLIT_BF16) return t->n * t->n;
+    if (use_tc(t, precision)) return kde_bins_tc_evals(t);
+    if (precision == FSG_PREC_SPLIT_BF16) return t->n * t->n;
     if (t->d <= kMaxFmaDim) return kde_bins_sym_supported(t) ? kde_bins_sym_evals(t) : t->n * t->n;
     return kde_bins_generic_sym_supported(t) ? kde_bins_generic_sym_evals(t) : t->n * t->n;
 }
@@ -442,6 +443,7 @@ void fsg_free_tree(fsg_tree* t) {
     tree_free(t, t->Xtt);
     tree_free(t, t->sboxes);
     tree_free(t, t->ord);
+    tree_free(t, t->rs.base);
     if (t->Xb) cudaFree(t->Xb);
     if (t->norms) cudaFree(t->norms);
     delete t;
@@ -455,7 +457,8 @@ int fsg_tree_info(const fsg_tree* t, int64_t* n, int32_t* d, int32_t* depth) {
     return FSG_OK;
 }
 
-static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s);
+static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s,
+                        bool skip_bins = false);
 
 namespace {
 struct TuneKey {
@@ -499,6 +502,7 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
     if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
+    if (p->resolve && (rc = ensure_resolve(t, L, s)) != FSG_OK) return rc;
     if (p->schedule != FSG_SCHED_FUSED) {  // the levelwise schedule has no shapes to choose
         to_public(t->tune, out);
         return FSG_OK;
@@ -656,7 +660,8 @@ int fsg_profile_read(fsg_tree* t, float* ms, int64_t* launches) {
     return FSG_OK;
 }
 
-static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s) {
+static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, double* d_deg, cudaStream_t s,
+                        bool skip_bins) {
     Workspace& ws = t->ws;
     if (schedule != FSG_SCHED_FUSED) {
         cudaError_t e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
@@ -669,7 +674,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
     cudaError_t e = cudaMemsetAsync(ws.bin_count, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.bin_cursor, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws.stats, 0, sizeof(fsg_stats), s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !skip_bins) {
         PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
         e = run_kde_bins(t, kp, s);
         t->launches += 1;
@@ -688,10 +693,10 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
         PhaseScope ph(t, FSG_PHASE_LEAF, s);
         e = run_leaf_phase(t, kp, s);
     }
-    if (e == cudaSuccess && kp.resolve) {  // the list of flagged samples reuses uniq (free until the edges)
+    if (e == cudaSuccess && kp.resolve) {
         PhaseScope ph(t, FSG_PHASE_RESOLVE, s);
-        e = launch_resolve(t, kp, ws.uniq, ws.misc, s);
-        t->launches += 2;
+        e = launch_resolve(t, kp, s);
+        t->launches += 8;
     }
     return status_of(e);
 }
@@ -752,6 +757,7 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
     if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
+    if (p->resolve && (rc = ensure_resolve(t, L, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, L, seed);
     begin_call(t);
     if ((rc = run_sampling(t, kp, p->schedule, nullptr, s)) != FSG_OK) return rc;
@@ -761,7 +767,7 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
         e = launch_outputs(t, kp, d_samples, d_flags, nullptr, s);
         if (e == cudaSuccess) {
             stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status,
-                                                p->resolve ? t->ws.misc : nullptr, nullptr);
+                                                p->resolve ? t->rs.cnt : nullptr, nullptr);
             e = cudaGetLastError();
         }
         t->launches += 2;
@@ -772,18 +778,37 @@ int fsg_sample_edges(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed,
 int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t edge_mode, int32_t* d_src,
                     int32_t* d_dst, void* d_w, int64_t cap, int64_t* d_m_out, double* d_deg, int32_t* d_samples,
                     uint8_t* d_flags, fsg_stats* d_stats, void* stream) {
+    return fsg::build_graph_internal(t, p, L, seed, edge_mode, d_src, d_dst, d_w, cap, d_m_out, d_deg, d_samples,
+                                     d_flags, d_stats, (cudaStream_t)stream, false);
+}
+
+}  // extern "C"
+
+int fsg::check_graph_call(const fsg_tree* t, const fsg_params* p) {
+    const int rc = check_params(p);
+    return rc != FSG_OK ? rc : check_path(t, p);
+}
+
+fsg::KernelParams fsg::kernel_params_of(const fsg_params* p, int L, uint64_t seed) {
+    return make_kernel_params(p, L, seed);
+}
+
+int fsg::build_graph_internal(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t edge_mode,
+                              int32_t* d_src, int32_t* d_dst, void* d_w, int64_t cap, int64_t* d_m_out,
+                              double* d_deg, int32_t* d_samples, uint8_t* d_flags, fsg_stats* d_stats,
+                              cudaStream_t s, bool skip_bins) {
     if (!t || L < 1 || L > kMaxL || !d_src || !d_dst || !d_w || !d_m_out) return FSG_ERR_INVALID_ARG;
     if (edge_mode != FSG_EDGES_SET && edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
     if (cap < t->n * (int64_t)L) return FSG_ERR_CAPACITY;
     int rc = check_params(p);
     if (rc != FSG_OK) return rc;
     if ((rc = check_path(t, p)) != FSG_OK) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
     if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
+    if (p->resolve && (rc = ensure_resolve(t, L, s)) != FSG_OK) return rc;
     const KernelParams kp = make_kernel_params(p, L, seed);
     begin_call(t);
-    if ((rc = run_sampling(t, kp, p->schedule, d_deg, s)) != FSG_OK) return rc;
+    if ((rc = run_sampling(t, kp, p->schedule, d_deg, s, skip_bins)) != FSG_OK) return rc;
     cudaError_t e;
     {
         PhaseScope ph(t, FSG_PHASE_EDGES, s);
@@ -795,13 +820,15 @@ int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, 
         e = launch_outputs(t, kp, d_samples, d_flags, d_stats, s);
         if (e == cudaSuccess) {
             stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, p), t->status,
-                                                p->resolve ? t->ws.misc : nullptr, d_stats);
+                                                p->resolve ? t->rs.cnt : nullptr, d_stats);
             e = cudaGetLastError();
         }
         t->launches += 2;
     }
     return status_of(e);
 }
+
+extern "C" {
 
 int fsg_sync(fsg_tree* t, void* stream) {
     if (!t) return FSG_ERR_INVALID_ARG;

@@ -27,7 +27,7 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                    KernelParams kp, int with_samples, double* __restrict__ d_deg, float* __restrict__ degf,
                    uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp,
                    int32_t* __restrict__ bin_count, int32_t* __restrict__ qitem_bin,
-                   uint64_t* __restrict__ qitem_mask, int32_t* __restrict__ qitem_cnt) {
+                   uint64_t* __restrict__ qitem_mask, int32_t* __restrict__ qitem_cnt, uint16_t* __restrict__ flev) {
     extern __shared__ __align__(16) unsigned char smem_b[];
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -82,13 +82,18 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                         // approximate bin sums miss at most kde_eps of the exact degree
                         // (root >= (1 - kde_eps) degree)
                         const float abs_tol = kp.kde_eps > 0.f ? kp.kde_eps * root / (1.f - kp.kde_eps) : 0.f;
+                        uint32_t flev_m = 0;  // levels whose decision was flagged (re-decision)
                         for (int t = 0; t < s0; ++t) {
                             if ((t & 3) == 0) blk = draw_block(kp.seed, (uint32_t)i, (uint32_t)l, (uint32_t)t);
+                            uint8_t ft = 0;
                             h = 2 * h + descend_decide(tree[2 * h], tree[2 * h + 1], block_word(blk, (uint32_t)t),
-                                                       kp.flag_eps, f, abs_tol);
+                                                       kp.flag_eps, ft, abs_tol);
+                            flev_m |= (uint32_t)(ft & 1) << t;
+                            f |= ft;
                         }
                         binv[r] = h - nb;
                         flags[(size_t)q * L + l] = f;
+                        if (flev) flev[(size_t)q * L + l] = (uint16_t)flev_m;
                     }
                 }
                 __syncwarp();
@@ -541,6 +546,7 @@ cudaError_t launch_leaf_d(const fsg_tree* t, const KernelParams& kp, int qc, cud
 // Two barriers per chunk of 128 items.
 constexpr int kLC = 128;  // items per chunk = threads per CTA
 constexpr int kLV = 31;   // kept node sums per item (node h at h - 1), odd row stride
+constexpr int kL128List = 1024;  // (item, sample) pairs descended per window
 
 // Kernel values of the point at Pr for two queries (packed lanes), the point
 // dropped for a query whose own local index it is.  F: the kernel family.
@@ -620,7 +626,9 @@ struct Leaf128Layout {
     static constexpr size_t QIDX = QPOS + (size_t)kLC * 4;             // int [128]
     static constexpr size_t QCO = QIDX + (size_t)kLC * 4;              // float [128][QS]
     static constexpr size_t V = QCO + (((size_t)kLC * QS * 4 + 15) & ~size_t(15));  // float [128][31]
-    static constexpr size_t total = V + (size_t)kLC * kLV * 4;
+    static constexpr size_t LIST = V + (size_t)kLC * kLV * 4;                  // uint16 [kL128List] (item, sample)
+    static constexpr size_t WSUM = LIST + (size_t)kL128List * 2;               // int [4] samples per warp
+    static constexpr size_t total = WSUM + 16;
 };
 
 template <int D, int F>
@@ -640,6 +648,8 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
     int32_t* qidx = reinterpret_cast<int32_t*>(smem128 + LY::QIDX);
     float* qco = reinterpret_cast<float*>(smem128 + LY::QCO);
     float* V = reinterpret_cast<float*>(smem128 + LY::V);
+    uint16_t* plist = reinterpret_cast<uint16_t*>(smem128 + LY::LIST);
+    int32_t* wsum = reinterpret_cast<int32_t*>(smem128 + LY::WSUM);
     const int b = blockIdx.x;
     const int base = bin_off[b * kBinSlots];
     const int cnt = bin_off[(b + 1) * kBinSlots] - base;
@@ -724,19 +734,48 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
             Vb[3 + w] = v2.y;
         }
         __syncthreads();
-        // descents: thread = item, over the item's samples
+        // descents: the chunk's (item, sample) pairs spread over all threads
+        // (an item holds 1..64 samples, so one thread per item would leave
+        // most lanes idle behind the few items with many); exclusive offsets
+        // of the items' sample counts, then windows of kL128List pairs.
+        const int ns = tid < qcnt ? __popcll(qmask[tid]) : 0;
+        int incl = ns;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
         if (tid < qcnt) {
             float* row = V + (size_t)tid * kLV;
             row[1] = row[3] + row[4];  // node 2
             row[2] = row[5] + row[6];  // node 3
-            const int my_pos = qpos[tid];
-            const int s_self = kp.self_exclude ? my_pos - p_lo : -1;
-            const uint32_t qi = (uint32_t)qidx[tid];
-            float x[D];
+        }
+        __syncthreads();
+        int wbase = 0;
 #pragma unroll
-            for (int t = 0; t < D; ++t) x[t] = qco[tid * QS + t];
-            for (uint64_t mk = qmask[tid]; mk; mk &= mk - 1ull) {
-                const int l = __ffsll((long long)mk) - 1;
+        for (int k = 0; k < kLC / 32; ++k) wbase += k < w ? wsum[k] : 0;
+        const int total = wsum[0] + wsum[1] + wsum[2] + wsum[3];
+        const int my_off = wbase + incl - ns;
+        for (int r0 = 0; r0 < total; r0 += kL128List) {
+            if (r0 > 0) __syncthreads();  // the previous window's pairs are taken
+            if (ns > 0 && my_off < r0 + kL128List && my_off + ns > r0) {
+                int o = my_off;
+                for (uint64_t mk = qmask[tid]; mk; mk &= mk - 1ull, ++o)
+                    if (o >= r0 && o < r0 + kL128List)
+                        plist[o - r0] = (uint16_t)((tid << 6) | (__ffsll((long long)mk) - 1));
+            }
+            __syncthreads();
+            const int cnt_w = min(kL128List, total - r0);
+            for (int e = tid; e < cnt_w; e += kLC) {
+                const int it = plist[e] >> 6, l = plist[e] & 63;
+                const float* row = V + (size_t)it * kLV;
+                const int my_pos = qpos[it];
+                const int s_self = kp.self_exclude ? my_pos - p_lo : -1;
+                const uint32_t qi = (uint32_t)qidx[it];
+                float x[D];
+#pragma unroll
+                for (int t = 0; t < D; ++t) x[t] = qco[it * QS + t];
                 int a = 0, c = m, h = 1;
                 uint8_t f = 0;
                 uint4 blk = make_uint4(0, 0, 0, 0);
@@ -859,7 +898,8 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
     descend_top_kernel<<<(int)blocks, warps * 32, smem, s>>>(ws.binsum, (int)t->n, t->nb, t->s0, t->perm, kp,
                                                             with_samples, d_deg, ws.degf, ws.flags, ws.leaf_pos,
                                                             ws.ksmp, ws.bin_count, ws.qitem_bin, ws.qitem_mask,
-                                                            ws.qitem_cnt);
+                                                            ws.qitem_cnt,
+                                                            kp.resolve && with_samples ? t->rs.flev : nullptr);
     return cudaGetLastError();
 }
 

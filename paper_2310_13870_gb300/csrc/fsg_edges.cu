@@ -32,7 +32,7 @@ __device__ __forceinline__ float edge_weight(float k, float deg_i, float deg_j, 
 // (a, b) bit for bit.
 __device__ __forceinline__ double edge_weight_f64(const float* __restrict__ Xt, int dp, int d, int a, int b,
                                                   float deg_a, float deg_b, int L, float ch, float cl) {
-    const double k = (double)hp_gauss(Xt + (size_t)a * dp, Xt + (size_t)b * dp, d, ch, cl);
+    const double k = (double)hp_gauss(Xt + (size_t)a * dp, Xt + (size_t)b * dp, dp, ch, cl);
     if (!(k > 0.0)) return 0.0;
     const double Lk = (double)L * k;
     const double pa = fmin(Lk / (double)deg_a, 1.0);

@@ -54,6 +54,32 @@ struct Workspace {
     int64_t cap_n = 0, cap_L = 0;
 };
 
+// Scratch of the high-precision re-decision (fsg_params.resolve), allocated
+// on first use: the flagged levels of every sample, the flagged samples, the
+// (sample, level) jobs grouped by node and their high-precision sums.
+struct ResolveWs {
+    void* base = nullptr;
+    size_t bytes = 0;
+    int64_t cap_nl = 0;             // n * L the arrays are sized for
+    int32_t fcap = 0, jcap = 0;     // flagged samples and jobs of the batched path
+    uint16_t* flev = nullptr;       // [n][L]  bit t: the FP32 decision at level t was flagged
+    int32_t* list = nullptr;        // [n L]   flagged samples
+    int32_t* sbin = nullptr;        // [fcap]  bin of each flagged sample's FP32 path
+    int32_t* node_cnt = nullptr;    // [nb]    jobs per node (heap index)
+    int32_t* node_cur = nullptr;    // [nb]
+    int32_t* node_off = nullptr;    // [nb+1]  job offsets per node
+    int32_t* cta_off = nullptr;     // [nb+1]  work items per node (32 jobs x a chunk of points)
+    int32_t* part_off = nullptr;    // [nb+1]  partial-sum offsets per node
+    int32_t* job_s = nullptr;       // [jcap]  flagged sample of a job
+    int32_t* job_t = nullptr;       // [jcap]  level of a job
+    int32_t* slot_of = nullptr;     // [fcap][kRsMaxLevels] job slot of (flagged sample, level)
+    double* part = nullptr;         // [pcap][2] high-precision (g_left, g_right) per (job, point chunk)
+    int32_t pcap = 0;
+    int32_t* wlist = nullptr;       // [n L]   samples left to the per-sample walker (| mode << 30)
+    int32_t* cnt = nullptr;         // [8]     flagged, jobs, walker entries, overflow
+};
+constexpr int kRsMaxLevels = 13;    // s0 <= 12 bin-pass levels
+
 // Launch shapes (0: the built-in heuristic), chosen by fsg_autotune.
 struct LaunchTuning {
     int32_t sym_bins = 0;     // bins per block of the symmetric d <= 16 bin pass
@@ -99,6 +125,7 @@ struct fsg_tree {
     alignas(64) unsigned char tmap_b[128] = {};
     alignas(64) unsigned char tmap_p[128] = {};  // 16-row boxes: point rows of the tensor-core leaf kernel
     fsg::Workspace ws;
+    fsg::ResolveWs rs;
     fsg::LaunchTuning tune;
     // per-phase timing (fsg_profile) and kernel-launch count
     bool profiling = false;
@@ -150,6 +177,36 @@ cudaError_t launch_tree_prep(fsg_tree* t, const float* d_points, const int32_t* 
 cudaError_t launch_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 bool kde_bins_supported(const fsg_tree* t);
 cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+// The symmetric d <= 16 pass of many trees in one launch: one descriptor per
+// tree (device table, pair_off = the tree's first block pair in the launch).
+struct SymPackDesc {
+    const float* Xdup;
+    const float* Xt;
+    const int32_t* bnd;
+    float* binsum;
+    int32_t* status;
+    int nb, G, nblk, pair_off;
+    float neg_c;
+    int self_exclude;
+};
+constexpr int kSymPackMax = 64;
+struct SymPackTable {  // descriptors passed by value (a kernel parameter)
+    SymPackDesc d[kSymPackMax];
+    int count;
+};
+// Fills the tree's descriptor; returns its block pairs.
+int sym_pack_fill(const fsg_tree* t, const KernelParams& kp, int pair_off, SymPackDesc* out);
+cudaError_t launch_kde_bins_sym_packed(const SymPackDesc* d_descs, int count, int total, int d, int family,
+                                       cudaStream_t s);
+cudaError_t launch_kde_bins_sym_packed(const SymPackTable& tab, int total, int d, int family, cudaStream_t s);
+// Argument and path checks of a graph build, and its kernel parameters.
+int check_graph_call(const fsg_tree* t, const fsg_params* p);
+KernelParams kernel_params_of(const fsg_params* p, int L, uint64_t seed);
+// fsg_build_graph; with skip_bins the tree's bin sums are taken as already
+// computed (by a packed bin pass of the batch).
+int build_graph_internal(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int32_t edge_mode,
+                         int32_t* d_src, int32_t* d_dst, void* d_w, int64_t cap, int64_t* d_m_out, double* d_deg,
+                         int32_t* d_samples, uint8_t* d_flags, fsg_stats* d_stats, cudaStream_t s, bool skip_bins);
 bool kde_bins_sym_supported(const fsg_tree* t);
 int64_t kde_bins_sym_evals(const fsg_tree* t);
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
@@ -162,11 +219,11 @@ int64_t leaf_default_splits(const fsg_tree* t, int L);
 bool use_leaf128(const fsg_tree* t);
 cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mode, int32_t* d_src,
                          int32_t* d_dst, void* d_w, int64_t cap, int64_t* d_m_out, cudaStream_t s);
-// High-precision re-decision of flagged samples (list: int32 [n L] scratch,
-// count: one int32, both device memory).
+// High-precision re-decision of flagged samples (scratch t->rs, allocated by
+// ensure_resolve before the call's first launch).
 bool resolve_supported(const fsg_tree* t);
-cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, int32_t* list, int32_t* count,
-                           cudaStream_t s);
+int ensure_resolve(fsg_tree* t, int L, cudaStream_t s);
+cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
                            fsg_stats* d_stats, cudaStream_t s);
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
@@ -175,6 +232,9 @@ size_t generic_tile_bytes(int64_t n, int32_t d);
 int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
 bool kde_bins_tc_supported(const fsg_tree* t);
+// Pairs the tensor-core bin pass evaluates (symmetric form: each pair once
+// outside the diagonal chunks).
+int64_t kde_bins_tc_evals(const fsg_tree* t);
 bool kde_bins_split_supported(const fsg_tree* t);
 // Bytes of the split-precision pass's per-tree workspace (boxes, query-tile
 // images, and the bins' images when the split leaf phase runs).
@@ -322,15 +382,68 @@ __device__ __forceinline__ float hp_exp2_neg(float th, float tl) {
     return e >= 1 ? __fmul_rn(m, __int_as_float(e << 23)) : 0.f;
 }
 
-// k(x, y) = exp(-gamma ||x - y||^2) to relative error kHpEta (see above);
-// (ch, cl) = gamma log2 e as a pair; x and y hold d coordinates.
-__device__ __forceinline__ float hp_gauss(const float* __restrict__ x, const float* __restrict__ y, int d, float ch,
-                                          float cl) {
-    float sh = 0.f, sl = 0.f;
-    for (int t = 0; t < d; ++t) hp_acc_sq(x[t], y[t], sh, sl);
+// k from the pair (sh, sl) = ||x - y||^2 and (ch, cl) = gamma log2 e.
+__device__ __forceinline__ float hp_finish(float sh, float sl, float ch, float cl) {
     const float th = __fmul_rn(sh, ch);
     const float tl = __fadd_rn(__fmaf_rn(sh, ch, -th), __fmaf_rn(sh, cl, __fmul_rn(sl, ch)));
     return hp_exp2_neg(th, tl);
+}
+
+// k(x, y) = exp(-gamma ||x - y||^2) to relative error kHpEta (see above);
+// (ch, cl) = gamma log2 e as a pair.  x: dp coordinates (any memory), y: a
+// 16-byte aligned row of dp coordinates (dp a multiple of 4, zero padding on
+// both sides), read 16 coordinates at a time with the loads issued together.
+__device__ __forceinline__ float hp_gauss(const float* __restrict__ x, const float* __restrict__ y, int dp, float ch,
+                                          float cl) {
+    float sh = 0.f, sl = 0.f;
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    for (int t0 = 0; t0 < dp; t0 += 16) {
+        float4 c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t0 + 4 * k < dp) c[k] = __ldg(y4 + (t0 >> 2) + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (t0 + 4 * k < dp) {
+                const float* xx = x + t0 + 4 * k;
+                hp_acc_sq(xx[0], c[k].x, sh, sl);
+                hp_acc_sq(xx[1], c[k].y, sh, sl);
+                hp_acc_sq(xx[2], c[k].z, sh, sl);
+                hp_acc_sq(xx[3], c[k].w, sh, sl);
+            }
+        }
+    }
+    return hp_finish(sh, sl, ch, cl);
+}
+
+// hp_gauss, first testing the pair in FP32: where ch ||x - y||^2 > 127 the
+// high-precision value would be flushed to zero (2^-f 2^-i with i >= 127,
+// i.e. an exponent of at least 126.5), so 0 is returned without the
+// high-precision work.  The FP32 exponent (direct differences, relative error
+// about (d + 2) 2^-24) is within 0.04 of the pair's for d <= 4096, so the
+// test never drops a value the high-precision path keeps.
+__device__ __forceinline__ float hp_gauss_far0(const float* __restrict__ x, const float* __restrict__ y, int dp,
+                                               float ch, float cl) {
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    float s = 0.f;
+    for (int t0 = 0; t0 < dp; t0 += 16) {
+        float4 c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t0 + 4 * k < dp) c[k] = __ldg(y4 + (t0 >> 2) + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (t0 + 4 * k < dp) {
+                const float* xx = x + t0 + 4 * k;
+                float dd = xx[0] - c[k].x; s = fmaf(dd, dd, s);
+                dd = xx[1] - c[k].y; s = fmaf(dd, dd, s);
+                dd = xx[2] - c[k].z; s = fmaf(dd, dd, s);
+                dd = xx[3] - c[k].w; s = fmaf(dd, dd, s);
+            }
+        }
+    }
+    if (s * ch > 127.f) return 0.f;
+    return hp_gauss(x, y, dp, ch, cl);
 }
 
 // Kernel families (Sec. 2.1): the exponent is neg_c times the squared

@@ -299,20 +299,16 @@ __device__ __forceinline__ float sym_point(const float* __restrict__ tp, int p, 
     uint64_t e2[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        // two interleaved accumulation chains (even / odd coordinates)
+        // one accumulation chain per query pair: the two pairs and the
+        // batch's points give the independent work (a second chain per pair,
+        // even / odd coordinates, cost an extra add and measured 2% slower)
         uint64_t dd = f2_sub(q[k][0], c[0]);
         uint64_t s = fam_first2<F>(dd);
-        uint64_t s1 = 0ull;
-        if (D > 1) {
-            dd = f2_sub(q[k][1], c[1]);
-            s1 = fam_first2<F>(dd);
-        }
 #pragma unroll
-        for (int t = 2; t < D; ++t) {
+        for (int t = 1; t < D; ++t) {
             dd = f2_sub(q[k][t], c[t]);
-            if (t & 1) s1 = fam_acc2<F>(dd, s1); else s = fam_acc2<F>(dd, s);
+            s = fam_acc2<F>(dd, s);
         }
-        if (D > 1) s = f2_add(s, s1);
         s = f2_mul(fam_fin2<F>(s), nc2);
         const float2 sv = f2_unpack(s);
         float e0 = ex2_approx(sv.x);
@@ -436,18 +432,16 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
     return true;
 }
 
+// One block pair (k1, k2 >= k1) of one tree: the body of the symmetric pass.
 template <int D, int F>
-__global__ void __launch_bounds__(kSymThreads, SymOccupancy<D>::value)
-kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, const int32_t* __restrict__ bnd,
-                    int nb, int G, float neg_c, int self_exclude, float* __restrict__ binsum,
-                    int32_t* __restrict__ status) {
+__device__ __forceinline__ void sym_block_pair(const float* __restrict__ Xdup, const float* __restrict__ Xt,
+                                               const int32_t* __restrict__ bnd, int nb, int G, float neg_c,
+                                               int self_exclude, float* __restrict__ binsum,
+                                               int32_t* __restrict__ status, int k1, int k2,
+                                               unsigned char* smem_raw) {
     constexpr int DP = (D + 3) & ~3;
     constexpr int STAGE_FLOATS = kSymMaxBin * DP * 2;
-    const int k2 = blockIdx.x, k1 = blockIdx.y;
-    if (k2 < k1) return;
     const bool mirror = k2 > k1;
-
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     float* pts = reinterpret_cast<float*>(smem_raw);                       // [stages][128][DP][2]
     float* mir = pts + kSymStages * STAGE_FLOATS;                          // [2][128][kSymNodes]
     uint64_t* bars = reinterpret_cast<uint64_t*>(mir + 2 * kSymMaxBin * kSymNodes);
@@ -517,6 +511,50 @@ kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt
     else
         sym_bins<D, F, false>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
                            pn0, qn0, nq);
+}
+
+template <int D, int F>
+__global__ void __launch_bounds__(kSymThreads, SymOccupancy<D>::value)
+kde_bins_sym_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, const int32_t* __restrict__ bnd,
+                    int nb, int G, float neg_c, int self_exclude, float* __restrict__ binsum,
+                    int32_t* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int k2 = blockIdx.x, k1 = blockIdx.y;
+    if (k2 < k1) return;
+    sym_block_pair<D, F>(Xdup, Xt, bnd, nb, G, neg_c, self_exclude, binsum, status, k1, k2, smem_raw);
+}
+
+// The symmetric pass of many trees in one launch (batches of point sets):
+// CTA i takes the i-th block pair over all trees' triangles (k2 >= k1),
+// trees in table order.
+template <int D, int F>
+__device__ __forceinline__ void sym_packed_item(const SymPackDesc* __restrict__ descs, int count, int item,
+                                                unsigned char* smem_raw) {
+    int lo = 0, hi = count;  // tree: descs[lo].pair_off <= item < descs[lo + 1].pair_off
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (descs[mid].pair_off <= item) lo = mid; else hi = mid;
+    }
+    const SymPackDesc& dsc = descs[lo];
+    int k1 = 0, rem = item - dsc.pair_off;
+    while (rem >= dsc.nblk - k1) { rem -= dsc.nblk - k1; ++k1; }
+    sym_block_pair<D, F>(dsc.Xdup, dsc.Xt, dsc.bnd, dsc.nb, dsc.G, dsc.neg_c, dsc.self_exclude, dsc.binsum,
+                         dsc.status, k1, k1 + rem, smem_raw);
+}
+
+template <int D, int F>
+__global__ void __launch_bounds__(kSymThreads, SymOccupancy<D>::value)
+kde_bins_sym_packed_kernel(const SymPackDesc* __restrict__ descs, int count) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    sym_packed_item<D, F>(descs, count, blockIdx.x, smem_raw);
+}
+
+// The same with the descriptors as a kernel parameter (up to kSymPackMax trees).
+template <int D, int F>
+__global__ void __launch_bounds__(kSymThreads, SymOccupancy<D>::value)
+kde_bins_sym_packed_param_kernel(const __grid_constant__ SymPackTable tab) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    sym_packed_item<D, F>(tab.d, tab.count, blockIdx.x, smem_raw);
 }
 
 // Bins per block: as many as fit the CTA's 256 lanes (fewer if tuned so).
@@ -597,6 +635,86 @@ cudaError_t launch_sym_family(const fsg_tree* t, const KernelParams& kp, cudaStr
     }
 }
 }  // namespace
+
+namespace {
+// tab != nullptr: descriptors by value (kernel parameter), else d_descs.
+template <int D, int F>
+cudaError_t launch_sym_packed_d(const SymPackDesc* d_descs, const SymPackTable* tab, int count, int total,
+                                cudaStream_t s) {
+    constexpr int DP = (D + 3) & ~3;
+    const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymNodes * 4 +
+                        kSymStages * 8 + 3 * (kSymNodes + 1) * 4;
+    if (tab) {
+        const cudaError_t e = set_smem_limit(kde_bins_sym_packed_param_kernel<D, F>, (int)smem);
+        if (e != cudaSuccess) return e;
+        kde_bins_sym_packed_param_kernel<D, F><<<total, kSymThreads, smem, s>>>(*tab);
+    } else {
+        const cudaError_t e = set_smem_limit(kde_bins_sym_packed_kernel<D, F>, (int)smem);
+        if (e != cudaSuccess) return e;
+        kde_bins_sym_packed_kernel<D, F><<<total, kSymThreads, smem, s>>>(d_descs, count);
+    }
+    return cudaGetLastError();
+}
+template <int F>
+cudaError_t launch_sym_packed_family(int d, const SymPackDesc* d_descs, const SymPackTable* tab, int count,
+                                     int total, cudaStream_t s) {
+    switch (d) {
+        case 1: return launch_sym_packed_d<1, F>(d_descs, tab, count, total, s);
+        case 2: return launch_sym_packed_d<2, F>(d_descs, tab, count, total, s);
+        case 3: return launch_sym_packed_d<3, F>(d_descs, tab, count, total, s);
+        case 4: return launch_sym_packed_d<4, F>(d_descs, tab, count, total, s);
+        case 5: return launch_sym_packed_d<5, F>(d_descs, tab, count, total, s);
+        case 6: return launch_sym_packed_d<6, F>(d_descs, tab, count, total, s);
+        case 7: return launch_sym_packed_d<7, F>(d_descs, tab, count, total, s);
+        case 8: return launch_sym_packed_d<8, F>(d_descs, tab, count, total, s);
+        case 9: return launch_sym_packed_d<9, F>(d_descs, tab, count, total, s);
+        case 10: return launch_sym_packed_d<10, F>(d_descs, tab, count, total, s);
+        case 11: return launch_sym_packed_d<11, F>(d_descs, tab, count, total, s);
+        case 12: return launch_sym_packed_d<12, F>(d_descs, tab, count, total, s);
+        case 13: return launch_sym_packed_d<13, F>(d_descs, tab, count, total, s);
+        case 14: return launch_sym_packed_d<14, F>(d_descs, tab, count, total, s);
+        case 15: return launch_sym_packed_d<15, F>(d_descs, tab, count, total, s);
+        case 16: return launch_sym_packed_d<16, F>(d_descs, tab, count, total, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+int sym_pack_fill(const fsg_tree* t, const KernelParams& kp, int pair_off, SymPackDesc* out) {
+    const int G = sym_block_bins(t);
+    const int nblk = (t->nb + G - 1) / G;
+    out->Xdup = t->Xdup;
+    out->Xt = t->Xt;
+    out->bnd = t->bnd;
+    out->binsum = t->ws.binsum;
+    out->status = t->status;
+    out->nb = t->nb;
+    out->G = G;
+    out->nblk = nblk;
+    out->pair_off = pair_off;
+    out->neg_c = kp.neg_c;
+    out->self_exclude = kp.self_exclude;
+    return nblk * (nblk + 1) / 2;
+}
+
+cudaError_t launch_kde_bins_sym_packed(const SymPackDesc* d_descs, int count, int total, int d, int family,
+                                       cudaStream_t s) {
+    if (count < 1 || total < 1) return cudaSuccess;
+    switch (family) {
+        case kFamLaplace: return launch_sym_packed_family<kFamLaplace>(d, d_descs, nullptr, count, total, s);
+        case kFamExp: return launch_sym_packed_family<kFamExp>(d, d_descs, nullptr, count, total, s);
+        default: return launch_sym_packed_family<kFamGauss>(d, d_descs, nullptr, count, total, s);
+    }
+}
+
+cudaError_t launch_kde_bins_sym_packed(const SymPackTable& tab, int total, int d, int family, cudaStream_t s) {
+    if (tab.count < 1 || total < 1) return cudaSuccess;
+    switch (family) {
+        case kFamLaplace: return launch_sym_packed_family<kFamLaplace>(d, nullptr, &tab, tab.count, total, s);
+        case kFamExp: return launch_sym_packed_family<kFamExp>(d, nullptr, &tab, tab.count, total, s);
+        default: return launch_sym_packed_family<kFamGauss>(d, nullptr, &tab, tab.count, total, s);
+    }
+}
 
 cudaError_t launch_kde_bins_sym(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     switch (kp.family) {

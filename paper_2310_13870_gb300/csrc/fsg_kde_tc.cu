@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <climits>
+#include <cmath>
 
 #include "fsg_tc.cuh"
 
@@ -41,32 +42,71 @@ constexpr uint32_t kTmemCols = 512;
 
 constexpr uint32_t kIdesc = idesc_bf16(kTcM, kTcN);
 
-template <int EW>
+// SYM = false: CTA (x, y) = queries 128 x .. 128 x + 127 against the points
+// of bins y bpc .. y bpc + bpc - 1 (every pair evaluated, both orders).
+// SYM = true (the kernel is symmetric): bins are grouped in chunks of bpc; CTA
+// (t, pair) takes row tile t (128 positions) of chunk k1 against the points
+// of chunk k2 >= k1, pair = the index of (k1, k2) in the triangle.  Off the
+// diagonal each value also goes to the column point's sum at the row's bin:
+// per 32 columns a warp sums its 32 rows by bin (at most two bins: bins hold
+// more than 32 points) with a butterfly, the four lane quadrants' partials
+// are added in a fixed order, and one atomic addition per (point, bin) and
+// CTA goes into bin sums zeroed beforehand.  A bin meets at most two row
+// tiles, so every such sum receives at most two additions onto zero, whose
+// result does not depend on their order.
+template <int EW, int ST, bool SYM>
 __global__ void __launch_bounds__(64 + 32 * EW, 1)
 kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
-                   int bpc, float neg_c, int self_exclude, float* __restrict__ binsum, int32_t* __restrict__ status) {
+                   int bpc, int nchunk, float neg_c, int self_exclude, float* __restrict__ binsum,
+                   int32_t* __restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr uint32_t kStage = kABytes + kBBytes;
+    constexpr int kCols = kTcN / (EW / 4);  // columns of each epilogue warp per tile
     unsigned char* base = smem_align1024(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base + kTcStages * kStageBytes);
-    uint64_t* empty = full + kTcStages;
-    uint64_t* tfull = empty + kTcStages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + ST * kStage);
+    uint64_t* empty = full + ST;
+    uint64_t* tfull = empty + ST;
     uint64_t* tempty = tfull + 2;
     uint64_t* fin = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+    uint64_t* colbar = fin + 1;                                   // [EW / 4] column-part barriers
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(colbar + 2);
     int32_t* flags = reinterpret_cast<int32_t*>(tmem_slot + 1);  // [0] abort, [1] stages consumed by MMA
-    int32_t* bnd_s = flags + 2;                                   // bpc + 1
-    float* pnorm = reinterpret_cast<float*>(bnd_s + ((bpc + 1 + 3) & ~3));  // [epilogue warp][128]
-    float* outs = pnorm + EW * (kTcN / (EW / 4));                   // [EW/4 parts][128][bpc]
+    int32_t* winfo = flags + 2;                                   // [4] warp's first bin, [4] rows in it
+    int32_t* bnd_s = winfo + 8;                                   // bpc + 1 (column bins)
+    int32_t* rbnd_s = bnd_s + ((bpc + 1 + 3) & ~3);                // bpc + 1 (row bins, SYM)
+    float* pnorm = reinterpret_cast<float*>(rbnd_s + ((bpc + 1 + 3) & ~3));  // [epilogue warp][kCols]
+    float* outs = pnorm + EW * kCols;                              // [EW/4 parts][128][bpc]
+    float* colpart = outs + (EW / 4) * kTcM * bpc;                 // SYM: [2][EW/4][4][kCols][2]
+    // SYM: [EW][32][36] transposed tiles, 16-byte aligned (float4 stores)
+    float* ctile = colpart + 2 * (EW / 4) * 4 * kCols * 2;
+    ctile += ((16u - (smem_u32(ctile) & 15u)) & 15u) / 4u;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q0 = blockIdx.x * kTcM;
-    const int b0 = blockIdx.y * bpc;
+    int q0, b0, rb0 = 0, row_end = n;
+    bool mirror = false;
+    if (SYM) {
+        int k1 = 0, rem = blockIdx.y;
+        while (rem >= nchunk - k1) { rem -= nchunk - k1; ++k1; }
+        const int k2 = k1 + rem;
+        rb0 = k1 * bpc;
+        const int rb1 = min(nb, rb0 + bpc);
+        q0 = bnd[rb0] + (int)blockIdx.x * kTcM;
+        row_end = bnd[rb1];
+        if (q0 >= row_end) return;  // chunk k1 has fewer row tiles
+        b0 = k2 * bpc;
+        mirror = k2 > k1;
+        if (tid <= rb1 - rb0) rbnd_s[tid] = bnd[rb0 + tid];
+    } else {
+        q0 = blockIdx.x * kTcM;
+        b0 = blockIdx.y * bpc;
+    }
     const int nbc = min(nb, b0 + bpc) - b0;
+    const int nrows = min(kTcM, row_end - q0);
     if (tid <= nbc) bnd_s[tid] = bnd[b0 + tid];
     for (int e = tid; e < (EW / 4) * kTcM * bpc; e += (64 + 32 * EW)) outs[e] = 0.f;
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -75,6 +115,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             mbar_init(&tempty[a], 32 * EW);
         }
         mbar_init(fin, 1);
+        for (int h = 0; h < EW / 4; ++h) mbar_init(&colbar[h], 4);
         flags[0] = 0;
         flags[1] = 0;
         fence_mbar_init();
@@ -88,6 +129,18 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (SYM && tid < 4) {  // lane quadrant tid: the bin of its first row and how many of its rows it holds
+        const int r0 = q0 + 32 * tid;
+        int wb = -1, cnt = 0;
+        if (r0 < row_end) {
+            wb = 0;
+            while (rbnd_s[wb + 1] <= r0) ++wb;
+            cnt = min(32, rbnd_s[wb + 1] - r0);
+        }
+        winfo[tid] = wb;
+        winfo[4 + tid] = cnt;
+    }
+    __syncthreads();
     const uint32_t tmem = *tmem_slot;
     const int pa = bnd_s[0], pe = bnd_s[nbc];
     const int ntile = (pe - pa + kTcN - 1) / kTcN;
@@ -103,14 +156,14 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     if (!inexact && warp == 0 && lane == 0) {
         // ---- TMA producer
         for (int it = 0; it < total && !*abort_flag; ++it) {
-            const int s = it % kTcStages;
-            if (!mbar_wait_bounded(&empty[s], ((uint32_t)(it / kTcStages) & 1u) ^ 1u, status)) {
+            const int s = it % ST;
+            if (!mbar_wait_bounded(&empty[s], ((uint32_t)(it / ST) & 1u) ^ 1u, status)) {
                 *abort_flag = 1;
                 break;
             }
             const int tile = it / kchunks, kc = it - tile * kchunks;
-            unsigned char* st = base + s * kStageBytes;
-            mbar_arrive_expect_tx(&full[s], kStageBytes);
+            unsigned char* st = base + s * kStage;
+            mbar_arrive_expect_tx(&full[s], kStage);
             tma_load_2d(st, &tmA, kc * kTcK, q0, &full[s]);
             tma_load_2d(st + kABytes, &tmB, kc * kTcK, pa + tile * kTcN, &full[s]);
             issued = it + 1;
@@ -128,14 +181,14 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             bool ok = true;
             for (int kc = 0; kc < kchunks; ++kc) {
                 const int it = tile * kchunks + kc;
-                const int s = it % kTcStages;
-                if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kTcStages) & 1u, status)) {
+                const int s = it % ST;
+                if (!mbar_wait_bounded(&full[s], (uint32_t)(it / ST) & 1u, status)) {
                     *abort_flag = 1;
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(base + s * kStageBytes);
+                const uint32_t sa = smem_u32(base + s * kStage);
                 const uint64_t da = sdesc(sa), db = sdesc(sa + kABytes);
 #pragma unroll
                 for (int k = 0; k < kTcK / 16; ++k)  // 32 bytes of K per MMA inside the swizzled row
@@ -149,14 +202,16 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     } else if (!inexact && warp >= 2) {
         // ---- epilogue: TMEM lane quadrant (warp % 4), row = query; column part (warp - 2) / 4
-        constexpr int kCols = kTcN / (EW / 4);  // columns of each epilogue warp per tile
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
         const int r = 32 * quad + lane;
         const int q = q0 + r;
-        const float nq = q < n ? norms[q] : 0.f;
+        const bool rvalid = r < nrows;
+        const float nq = rvalid ? norms[q] : 0.f;
         float* pn = pnorm + (warp - 2) * kCols;
         float* orow = outs + (half * kTcM + r) * bpc;  // partial sums of this column part
+        // SYM: rows of this warp in its first bin (the rest, if any, in the next)
+        const int w_split = SYM ? winfo[4 + quad] : 32;
         int bin = 0;
         int next_b = nbc > 0 ? bnd_s[1] : INT_MAX;
         // point norms of this warp's columns, one tile ahead
@@ -189,6 +244,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             }
             const bool check = c0 + kCols > pe || (self_exclude && c0 < q0 + kTcM && q0 < c0 + kCols);
             float acc = 0.f;
+            float* cp = colpart + (((size_t)(tile & 1) * (EW / 4) + half) * 4 + quad) * kCols * 2;
             const uint32_t tcol = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(a * kTcN + half * kCols);
             // 32 columns per step, the next step's TMEM load in flight
             uint32_t rb[2][32];
@@ -198,22 +254,73 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 const int cur = (cc >> 5) & 1;
                 tmem_wait32(rb[cur]);  // the only load in flight
                 if (cc + 32 < kCols) tmem_issue32(tcol + (uint32_t)(cc + 32), rb[cur ^ 1]);
+                float v[32];
                 if (check)
-                    tc_row_chunk<true>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
-                                       bnd_s, nbc, orow);
+                    tc_values32<true>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
                 else
-                    tc_row_chunk<false>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, acc, bin, next_b,
-                                        bnd_s, nbc, orow);
+                    tc_values32<false>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
+                if (SYM && !rvalid) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                }
+                if (SYM && mirror) {  // warp-uniform
+                    // column sums through a transposed 32 x 32 tile: row = lane
+                    // written as 16-byte pieces (row stride 36 floats: no bank
+                    // conflict either way), then lane = column adds its rows in
+                    // order, those of the warp's first bin and the rest apart
+                    float* tw = ctile + (warp - 2) * 32 * 36;
+                    __syncwarp();  // the previous chunk's reads are done
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4*>(tw + lane * 36 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    __syncwarp();
+                    float sa = 0.f, sb = 0.f;
+#pragma unroll
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const float x = tw[rr * 36 + lane];
+                        if (rr < w_split) sa += x; else sb += x;
+                    }
+                    cp[2 * (cc + lane)] = sa;
+                    cp[2 * (cc + lane) + 1] = sb;
+                }
+                tc_row_bins(v, c0 + cc, acc, bin, next_b, bnd_s, nbc, orow);
             }
             if (bin < nbc) orow[bin] += acc;  // the bin that continues past this half
             tc_fence_before();
             mbar_arrive(&tempty[a]);
+            if (SYM && mirror) {
+                // the four quadrants' partials of this column part, added in
+                // quadrant order per row bin of the tile, into the points' sums
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&colbar[half]);
+                if (!mbar_wait_bounded(&colbar[half], (uint32_t)tile & 1u, status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const int j = 32 * ((warp - 2) & 3) + lane;  // this thread's column of the part
+                const int p = c0 + j;
+                const float* cpb = colpart + ((size_t)(tile & 1) * (EW / 4) + half) * 4 * kCols * 2;
+                const int lq = (nrows - 1) >> 5;  // the quadrant of the last row
+                const int tb_lo = winfo[0], tb_hi = winfo[lq] + (((nrows - 1) & 31) >= winfo[4 + lq] ? 1 : 0);
+                if (p < pe) {
+                    for (int tb = tb_lo; tb <= tb_hi; ++tb) {
+                        float sum = 0.f;
+#pragma unroll
+                        for (int qd = 0; qd < 4; ++qd) {
+                            const int wb = winfo[qd];
+                            if (wb < 0) continue;
+                            if (wb == tb) sum += cpb[(qd * kCols + j) * 2];
+                            else if (wb + 1 == tb) sum += cpb[(qd * kCols + j) * 2 + 1];
+                        }
+                        atomicAdd(&binsum[(size_t)p * nb + rb0 + tb], sum);
+                    }
+                }
+            }
         }
     }
     __syncthreads();
     if (!inexact && !*abort_flag) {
-        const int nq = min(kTcM, n - q0);
-        for (int e = tid; e < nq * nbc; e += (64 + 32 * EW)) {
+        for (int e = tid; e < nrows * nbc; e += (64 + 32 * EW)) {
             const int ql = e / nbc, b = e - ql * nbc;
             float v = outs[ql * bpc + b];
 #pragma unroll
@@ -225,7 +332,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     if (tid == 0) {
         // after an abort: wait (bounded) for this CTA's own copies still in flight
         for (int it = *consumed; it < issued; ++it)
-            mbar_wait_bounded(&full[it % kTcStages], (uint32_t)(it / kTcStages) & 1u, status);
+            mbar_wait_bounded(&full[it % ST], (uint32_t)(it / ST) & 1u, status);
     }
     if (warp == 1) {
         if (lane == 0 && mma_issued) {
@@ -315,13 +422,81 @@ int tc_prepare(fsg_tree* t, cudaStream_t s) {
 bool kde_bins_tc_supported(const fsg_tree* t) { return t->Xb != nullptr && t->d >= 64; }
 
 namespace {
-size_t tc_bins_smem(int ew, int bpc) {
-    return 1024 + (size_t)kTcStages * kStageBytes + 8 * (2 * kTcStages + 5) + 16 + (size_t)((bpc + 1 + 3) & ~3) * 4 +
-           (size_t)ew * (kTcN / (ew / 4)) * 4 + (size_t)(ew / 4) * kTcM * bpc * 4;
+constexpr int kTcSymStages = 3;
+constexpr int kTcSymMaxBins = 16;  // bins per chunk of the symmetric pass
+
+size_t tc_bins_smem(int ew, int bpc, int st, bool sym) {
+    const int kcols = kTcN / (ew / 4);
+    return 1024 + (size_t)st * kStageBytes + 8 * (2 * st + 7) + 16 + 8 * 4 + 2 * (size_t)((bpc + 1 + 3) & ~3) * 4 +
+           (size_t)ew * kcols * 4 + (size_t)(ew / 4) * kTcM * bpc * 4 +
+           (sym ? (size_t)2 * (ew / 4) * 4 * kcols * 2 * 4 + 16 + (size_t)ew * 32 * 36 * 4 : 0);
+}
+
+// Bins per chunk of the symmetric pass: the chunks' positions are cut into
+// 128-row tiles, so pick the count (8..16) whose chunks fill their last tile
+// best.  0: the symmetric pass does not apply (bins of fewer than 33 points
+// could put three bins in one warp's 32 rows).
+int tc_sym_bins(const fsg_tree* t) {
+    if (t->n / t->nb < 33 || t->nb < 2) return 0;
+    int best = 0;
+    double best_fill = -1.0;
+    for (int g = 8; g <= kTcSymMaxBins; ++g) {
+        const double rows = (double)g * t->n / t->nb;
+        const double tiles = std::ceil(rows / kTcM);
+        const double fill = rows / (tiles * kTcM);
+        if (fill > best_fill + 1e-9) { best_fill = fill; best = g; }
+    }
+    if (t->tune.tc_bins > 0 && t->tune.tc_bins <= kTcSymMaxBins) best = t->tune.tc_bins;
+    return best;
 }
 }  // namespace
 
+bool kde_bins_tc_sym(const fsg_tree* t) { return tc_sym_bins(t) > 0; }
+
+// Pairs the tensor-core bin pass evaluates: n^2, or for the symmetric pass
+// (n^2 + sum_k P_k^2) / 2, P_k the positions of chunk k (its diagonal blocks
+// are evaluated in both orders).
+int64_t kde_bins_tc_evals(const fsg_tree* t) {
+    const int G = tc_sym_bins(t);
+    if (G == 0) return t->n * t->n;
+    int64_t sq = 0;
+    for (int b0 = 0; b0 < t->nb; b0 += G) {
+        auto start = [&](int b) {
+            if (b >= t->nb) return t->n;
+            int64_t lo = 0, hi = t->n;
+            for (int l = t->s0 - 1; l >= 0; --l) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if ((b >> l) & 1) lo = mid; else hi = mid;
+            }
+            return lo;
+        };
+        const int64_t pk = start(b0 + G) - start(b0);
+        sq += pk * pk;
+    }
+    return (t->n * t->n + sq) / 2;
+}
+
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    // integer units: ||255 x - 255 y||^2 = 255^2 ||x - y||^2
+    const float nc = kp.neg_c / (255.f * 255.f);
+    const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(t->tmap_a);
+    const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(t->tmap_b);
+    const int G = tc_sym_bins(t);
+    if (G > 0) {
+        const int nchunk = (t->nb + G - 1) / G;
+        const int tmax = (int)((((int64_t)G * t->mmax) + kTcM - 1) / kTcM);
+        const size_t smem = tc_bins_smem(kTcEpiWarps, G, kTcSymStages, true);
+        auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcSymStages, true>;
+        cudaError_t e = set_smem_limit(kern, smem);
+        if (e != cudaSuccess) return e;
+        // the sums that the mirrored values reach are accumulated onto zero
+        e = cudaMemsetAsync(t->ws.binsum, 0, sizeof(float) * (size_t)t->n * t->nb, s);
+        if (e != cudaSuccess) return e;
+        dim3 grid(tmax, nchunk * (nchunk + 1) / 2);
+        kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, t->norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, G,
+                                                       nchunk, nc, kp.self_exclude, t->ws.binsum, t->status);
+        return cudaGetLastError();
+    }
     const int qblocks = (int)((t->n + kTcM - 1) / kTcM);
     int chunks = (4 * 152 + qblocks - 1) / qblocks;
     if (chunks < 1) chunks = 1;
@@ -330,18 +505,15 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
     if (bpc > 24) bpc = 24;  // two [128][bpc] sum arrays beside the 4-stage ring
     if (t->tune.tc_bins > 0 && t->tune.tc_bins < bpc) bpc = t->tune.tc_bins;
     chunks = (t->nb + bpc - 1) / bpc;
-    const size_t smem = tc_bins_smem(kTcEpiWarps, bpc);
+    const size_t smem = tc_bins_smem(kTcEpiWarps, bpc, kTcStages, false);
+    auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcStages, false>;
     {
-        const cudaError_t e = set_smem_limit(kde_bins_tc_kernel<kTcEpiWarps>, (int)(227 * 1024));
+        const cudaError_t e = set_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
     }
-    // integer units: ||255 x - 255 y||^2 = 255^2 ||x - y||^2
-    const float nc = kp.neg_c / (255.f * 255.f);
     dim3 grid(qblocks, chunks);
-    kde_bins_tc_kernel<kTcEpiWarps><<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(t->tmap_a),
-                                                      *reinterpret_cast<const CUtensorMap*>(t->tmap_b), t->norms,
-                                                      (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc, nc,
-                                                      kp.self_exclude, t->ws.binsum, t->status);
+    kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, t->norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc,
+                                                   chunks, nc, kp.self_exclude, t->ws.binsum, t->status);
     return cudaGetLastError();
 }
 

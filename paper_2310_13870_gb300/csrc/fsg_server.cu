@@ -31,8 +31,10 @@ struct Pending {
 
 struct Slot {
     int state = 0;  // 0 idle, 1 building (waiting for ev_built), 2 copying edges (waiting for ev_done)
-    cudaStream_t stream = nullptr;
-    cudaEvent_t ev_built = nullptr, ev_done = nullptr;
+    cudaStream_t stream = nullptr;   // the admitted request's stream: stream_hi or stream_lo
+    cudaStream_t stream_hi = nullptr, stream_lo = nullptr;
+    cudaEvent_t ev_built = nullptr, ev_done = nullptr, ev_prep = nullptr;
+    bool packable = false;           // its bin pass can join the round's packed launch
     int64_t* h_m = nullptr;         // pinned: edge count
     fsg_stats* h_stats = nullptr;   // pinned: statistics
     Pending p;
@@ -66,10 +68,19 @@ double request_est_ms(const fsg_request& r) {
 
 }  // namespace
 
+// Requests whose estimated run time alone is below this go to their slot's
+// high-priority stream: the GPU's block scheduler then starts their CTAs
+// ahead of pending CTAs of long requests, so short requests are not queued
+// behind the long ones' launches.
+constexpr double kShortRequestMs = 5.0;
+
 struct fsg_server {
     fsg_server_opts opts{};
     int device = 0;
     cudaMemPool_t pool = nullptr;
+    cudaStream_t merge_stream = nullptr;  // the rounds' packed bin passes
+    cudaEvent_t ev_merged = nullptr;
+    int64_t merged_launches = 0, merged_requests = 0;
     std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -112,9 +123,13 @@ struct fsg_server {
         s.state = 0;
     }
 
-    // Enqueues the whole request on the slot's stream.
-    int admit(Slot& s) {
+    // First part of an admission, on the slot's stream: device buffers,
+    // points uploaded, tree built; for a request that takes the symmetric FP32
+    // bin pass also its workspace, so the round can pack its bin pass.
+    int admit_prepare(Slot& s) {
         const fsg_request& r = s.p.req;
+        s.stream = s.p.est_ms < kShortRequestMs ? s.stream_hi : s.stream_lo;
+        s.packable = false;
         ++admissions;
         if (opts.inject_alloc_fail_every > 0 && admissions % opts.inject_alloc_fail_every == 0) return FSG_ERR_OOM;
         const size_t cap = (size_t)r.n * r.L;
@@ -136,13 +151,100 @@ struct fsg_server {
         topts.order = r.params.precision == FSG_PREC_SPLIT_BF16 ? FSG_ORDER_SPATIAL : FSG_ORDER_IDENTITY;
         int rc = fsg::build_tree_internal(s.d_points, r.n, r.d, &topts, s.stream, pool, &s.tree);
         if (rc != FSG_OK) return rc;
-        rc = fsg_build_graph(s.tree, &r.params, r.L, r.seed, r.edge_mode, s.d_src, s.d_dst, s.d_w, (int64_t)cap,
-                             s.d_m, nullptr, nullptr, nullptr, s.d_stats, s.stream);
+        const fsg_params& p = r.params;
+        if (r.d <= fsg::kMaxFmaDim && p.schedule == FSG_SCHED_FUSED && p.kde_eps == 0.f &&
+            (p.precision == FSG_PREC_AUTO || p.precision == FSG_PREC_FP32) &&
+            fsg::check_graph_call(s.tree, &p) == FSG_OK && fsg::kde_bins_sym_supported(s.tree)) {
+            rc = fsg::ensure_workspace(s.tree, r.L, s.stream);
+            if (rc != FSG_OK) return rc;
+            if (cudaEventRecord(s.ev_prep, s.stream) != cudaSuccess) return FSG_ERR_CUDA;
+            s.packable = true;
+        }
+        return FSG_OK;
+    }
+
+    // Second part: the graph build (its bin pass already done when the round
+    // packed it), then the edge count and statistics to the host.
+    int admit_finish(Slot& s, bool bins_done) {
+        const fsg_request& r = s.p.req;
+        const size_t cap = (size_t)r.n * r.L;
+        int rc = fsg::build_graph_internal(s.tree, &r.params, r.L, r.seed, r.edge_mode, s.d_src, s.d_dst, s.d_w,
+                                           (int64_t)cap, s.d_m, nullptr, nullptr, nullptr, s.d_stats, s.stream,
+                                           bins_done);
         if (rc != FSG_OK) return rc;
-        e = cudaMemcpyAsync(s.h_m, s.d_m, sizeof(int64_t), cudaMemcpyDeviceToHost, s.stream);
+        cudaError_t e = cudaMemcpyAsync(s.h_m, s.d_m, sizeof(int64_t), cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_stats, s.d_stats, sizeof(fsg_stats), cudaMemcpyDeviceToHost, s.stream);
         if (e == cudaSuccess) e = cudaEventRecord(s.ev_built, s.stream);
         return e == cudaSuccess ? FSG_OK : FSG_ERR_CUDA;
+    }
+
+    void fail(Slot& s, int rc) {
+        // the slot's stream may hold partial work: let it drain before reuse
+        cudaStreamSynchronize(s.stream);
+        cudaGetLastError();
+        finish(s.p, rc, 0, 0, s.t_admit);
+        release(s);
+    }
+
+    // Launches a round of admitted requests.  The requests that take the
+    // symmetric FP32 bin pass are grouped by (d, kernel family); a group of
+    // two or more gets one packed bin-pass launch over all its members' block
+    // pairs (the members' streams join into the merge stream and fork again),
+    // so requests that arrive together share the GPU in one launch instead of
+    // each leaving it partly idle at its own launch's tail.
+    void launch_round(std::vector<Slot*>& round) {
+        for (Slot* s : round) {
+            const int rc = admit_prepare(*s);
+            if (rc != FSG_OK) {
+                fail(*s, rc);
+                s->packable = false;
+                s->state = 0;
+            }
+        }
+        std::vector<bool> done(round.size(), false);
+        for (size_t i = 0; i < round.size(); ++i) {
+            Slot* a = round[i];
+            if (done[i] || a->state != 1 || !a->packable) continue;
+            std::vector<size_t> grp;
+            for (size_t j = i; j < round.size() && grp.size() < (size_t)fsg::kSymPackMax; ++j) {
+                Slot* b = round[j];
+                if (!done[j] && b->state == 1 && b->packable && b->p.req.d == a->p.req.d &&
+                    b->p.req.params.kernel == a->p.req.params.kernel)
+                    grp.push_back(j);
+            }
+            if (grp.size() < 2) continue;
+            fsg::SymPackTable tab{};
+            int total = 0;
+            cudaError_t e = cudaSuccess;
+            for (size_t g = 0; g < grp.size(); ++g) {
+                Slot* m = round[grp[g]];
+                const fsg_request& r = m->p.req;
+                total += fsg::sym_pack_fill(m->tree, fsg::kernel_params_of(&r.params, r.L, r.seed), total, &tab.d[g]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(merge_stream, m->ev_prep, 0);
+            }
+            tab.count = (int)grp.size();
+            if (e == cudaSuccess)
+                e = fsg::launch_kde_bins_sym_packed(tab, total, a->p.req.d, a->p.req.params.kernel, merge_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_merged, merge_stream);
+            for (size_t g = 0; g < grp.size() && e == cudaSuccess; ++g)
+                e = cudaStreamWaitEvent(round[grp[g]]->stream, ev_merged, 0);
+            if (e != cudaSuccess) {  // not packed after all: the members run their own bin passes
+                cudaGetLastError();
+                continue;
+            }
+            ++merged_launches;
+            merged_requests += (int64_t)grp.size();
+            for (size_t g : grp) {
+                done[g] = true;
+                const int rc = admit_finish(*round[g], true);
+                if (rc != FSG_OK) fail(*round[g], rc);
+            }
+        }
+        for (size_t i = 0; i < round.size(); ++i) {
+            if (done[i] || round[i]->state != 1) continue;
+            const int rc = admit_finish(*round[i], false);
+            if (rc != FSG_OK) fail(*round[i], rc);
+        }
     }
 
     bool cancelled(uint64_t id) {
@@ -205,7 +307,9 @@ struct fsg_server {
                     release(s);
                 }
             }
-            // Admission: the next request in the chosen order, slot and budget permitting.
+            // Admission: the next requests in the chosen order, slot and budget
+            // permitting, launched together as one round.
+            std::vector<Slot*> round;
             for (;;) {
                 Slot* free_slot = nullptr;
                 for (Slot& s : slots)
@@ -234,15 +338,10 @@ struct fsg_server {
                 s.p = p;
                 s.t_admit = Clock::now();
                 s.state = 1;
-                const int rc = admit(s);
-                if (rc != FSG_OK) {
-                    // the slot's stream may hold partial work: let it drain before reuse
-                    cudaStreamSynchronize(s.stream);
-                    cudaGetLastError();
-                    finish(s.p, rc, 0, 0, s.t_admit);
-                    release(s);
-                }
+                s.stream = s.p.est_ms < kShortRequestMs ? s.stream_hi : s.stream_lo;
+                round.push_back(&s);
             }
+            if (!round.empty()) launch_round(round);
             {
                 std::unique_lock<std::mutex> lock(mu);
                 bool busy = false;
@@ -279,11 +378,18 @@ int fsg_server_create(const fsg_server_opts* opts, fsg_server** out) {
         uint64_t keep = (uint64_t)opts->hbm_budget_bytes;  // memory stays cached in the pool up to the budget
         e = cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sv->merge_stream, cudaStreamNonBlocking, prio_high);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_merged, cudaEventDisableTiming);
     sv->slots.resize(opts->max_slots);
     for (Slot& s : sv->slots) {
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s.stream_hi, cudaStreamNonBlocking, prio_high);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s.stream_lo, cudaStreamNonBlocking, prio_low);
+        s.stream = s.stream_lo;
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_built, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev_prep, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.h_m, sizeof(int64_t), cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaHostAlloc((void**)&s.h_stats, sizeof(fsg_stats), cudaHostAllocDefault);
     }
@@ -380,14 +486,20 @@ void fsg_server_destroy(fsg_server* sv) {
     }
     sv->cv_work.notify_all();
     if (sv->worker.joinable()) sv->worker.join();
+    if (sv->merge_stream) cudaStreamSynchronize(sv->merge_stream);
     for (Slot& s : sv->slots) {
-        if (s.stream) cudaStreamSynchronize(s.stream);
-        if (s.stream) cudaStreamDestroy(s.stream);
+        for (cudaStream_t st : {s.stream_hi, s.stream_lo}) {
+            if (st) cudaStreamSynchronize(st);
+            if (st) cudaStreamDestroy(st);
+        }
         if (s.ev_built) cudaEventDestroy(s.ev_built);
         if (s.ev_done) cudaEventDestroy(s.ev_done);
+        if (s.ev_prep) cudaEventDestroy(s.ev_prep);
         if (s.h_m) cudaFreeHost(s.h_m);
         if (s.h_stats) cudaFreeHost(s.h_stats);
     }
+    if (sv->merge_stream) cudaStreamDestroy(sv->merge_stream);
+    if (sv->ev_merged) cudaEventDestroy(sv->ev_merged);
     if (sv->pool) cudaMemPoolDestroy(sv->pool);
     delete sv;
 }

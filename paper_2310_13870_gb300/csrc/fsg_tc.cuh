@@ -115,16 +115,11 @@ __device__ __forceinline__ float tree_sum32(float (&x)[32]) {
     return t.x + t.y;
 }
 
-// Kernel values of 32 columns of one row, added to the row's bin sums.  Bins
-// hold more than 32 points, so at most one bin ends inside the 32 columns
-// (at a column that is the same for every row of the warp).
+// Kernel values v[0..31] of 32 columns of one row from its 32 dot products.
 // CHECK: test for the ragged end (p >= pe) and the query's own position.
 template <bool CHECK>
-__device__ __forceinline__ void tc_row_chunk(const uint32_t (&r)[32], const float* __restrict__ pn, int pc, float nq,
-                                             float neg_c, int q, int pe, int self_exclude, float& acc, int& bin,
-                                             int& next_b, const int32_t* __restrict__ bnd_s, int nbc,
-                                             float* __restrict__ orow) {
-    float v[32];
+__device__ __forceinline__ void tc_values32(const uint32_t (&r)[32], const float* __restrict__ pn, int pc, float nq,
+                                            float neg_c, int q, int pe, int self_exclude, float (&v)[32]) {
     const uint64_t nq2 = f2_pack(nq, nq), m2 = f2_pack(-2.f, -2.f), nc2 = f2_pack(neg_c, neg_c);
 #pragma unroll
     for (int j = 0; j < 32; j += 2) {
@@ -141,6 +136,13 @@ __device__ __forceinline__ void tc_row_chunk(const uint32_t (&r)[32], const floa
         v[j] = k0;
         v[j + 1] = k1;
     }
+}
+
+// The 32 values of one row added to the row's bin sums.  Bins hold more than
+// 32 points, so at most one bin ends inside the 32 columns (at a column that
+// is the same for every row of the warp).  v is consumed.
+__device__ __forceinline__ void tc_row_bins(float (&v)[32], int pc, float& acc, int& bin, int& next_b,
+                                            const int32_t* __restrict__ bnd_s, int nbc, float* __restrict__ orow) {
     const int jb = next_b - 1 - pc;  // the current bin ends after column jb
     if (jb >= 0 && jb < 32) {
         float hi[32];
@@ -156,6 +158,34 @@ __device__ __forceinline__ void tc_row_chunk(const uint32_t (&r)[32], const floa
     } else {
         acc += tree_sum32(v);
     }
+}
+
+// Kernel values of 32 columns of one row, added to the row's bin sums.
+template <bool CHECK>
+__device__ __forceinline__ void tc_row_chunk(const uint32_t (&r)[32], const float* __restrict__ pn, int pc, float nq,
+                                             float neg_c, int q, int pe, int self_exclude, float& acc, int& bin,
+                                             int& next_b, const int32_t* __restrict__ bnd_s, int nbc,
+                                             float* __restrict__ orow) {
+    float v[32];
+    tc_values32<CHECK>(r, pn, pc, nq, neg_c, q, pe, self_exclude, v);
+    tc_row_bins(v, pc, acc, bin, next_b, bnd_s, nbc, orow);
+}
+
+// Column sums of a warp's 32 x 32 block of values: lane l returns the sum
+// over the 32 lanes (rows) of column l.  Five butterfly levels; the order of
+// the additions is fixed, so the result is the same on every run.
+__device__ __forceinline__ float warp_column_sums32(float (&x)[32], int lane) {
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool up = (lane & half) != 0;
+#pragma unroll
+        for (int j = 0; j < half; ++j) {
+            const float send = up ? x[j] : x[j + half];
+            const float keep = up ? x[j + half] : x[j];
+            x[j] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+        }
+    }
+    return x[0];
 }
 
 }  // namespace fsg

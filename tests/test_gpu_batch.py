@@ -91,3 +91,30 @@ def test_batch_matches_oracle_on_sampled_queries(fsg):
         deg = ora.degrees(X, gam, queries=q, self_mode=p.self_mode)
         np.testing.assert_allclose(b.deg.cpu().numpy()[q], deg, rtol=1e-5, atol=X.shape[0] * 2.0 ** -126)
     batch.close()
+
+
+def test_packed_batch_equals_single_sets(fsg):
+    # every set takes the symmetric d = 5 FP32 pass, so the batch computes all
+    # bin sums in one launch: the results must equal each set built alone,
+    # whatever the sets' sizes, bandwidths, L and self modes
+    imgs = [inputs.segmentation_image(h, w, seed=s) for h, w, s in ((40, 60, 0), (64, 96, 1), (33, 49, 2),
+                                                                     (80, 120, 3))]
+    sets = [(torch.from_numpy(X).cuda(), fsg.params(sig, self_mode=sm), L, 11 + k)
+            for k, (X, sig, sm, L) in enumerate(zip(imgs, (0.05, 0.08, 0.05, 0.1), (0, 1, 0, 0), (12, 48, 7, 64)))]
+    for capture in (False, True):
+        batch = fsg.Batch(sets, streams=3, capture=capture)
+        for _ in range(2):
+            batch.run()
+            torch.cuda.synchronize()
+            for (pts, p, L, seed), b in zip(sets, batch.bufs):
+                src, dst, w, deg, _, _ = _single(fsg, pts, p, L, seed)
+                m = int(b.m.item())
+                np.testing.assert_array_equal(b.deg.cpu().numpy(), deg)
+                np.testing.assert_array_equal(b.src[:m].cpu().numpy(), src)
+                np.testing.assert_array_equal(b.dst[:m].cpu().numpy(), dst)
+                np.testing.assert_array_equal(b.w[:m].cpu().numpy(), w)
+        batch.close()
+    X = imgs[1]
+    q = np.arange(0, X.shape[0], 37)
+    want = ora.degrees(X, ora.gamma(0.08), queries=q, self_mode=1)
+    np.testing.assert_allclose(_single(fsg, *sets[1])[3][q], want, rtol=1e-5, atol=X.shape[0] * 2.0 ** -126)

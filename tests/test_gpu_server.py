@@ -185,3 +185,45 @@ def test_malformed_and_oversized_requests_are_refused(fsg):
         server.submit(X[:10], fsg.params(1.0), 65, 0)
     assert e.value.status == fsg.FSG_ERR_INVALID_ARG
     server.close()
+
+
+def test_server_and_direct_calls_run_concurrently(fsg):
+    # The server's worker thread launches kernels while this thread makes
+    # direct calls on its own trees (the launchers' per-device shared-memory
+    # limits are set under a lock, once per kernel and device): every result
+    # equals the same work run alone.
+    import threading
+    reqs = _requests()
+    want = [_alone(fsg, *r) for r in reqs]
+    X = inputs.gaussian_mixture(n=30_000, d=12, seed=77)
+    pts = torch.from_numpy(X).cuda()
+    tree = fsg.fsg_build_tree(pts)
+    ref = fsg.fsg_build_graph(tree, fsg.params(1.5), 32, 5)
+    torch.cuda.synchronize()
+    ref_w = ref.w[: int(ref.m.item())].cpu().numpy().copy()
+    server = fsg.Server(hbm_budget_bytes=8192 << 20, max_slots=8)
+    ids = [server.submit(Xr, fsg.params(s), L, seed) for Xr, s, L, seed in reqs]
+    errors = []
+
+    def direct():
+        try:
+            with torch.cuda.stream(torch.cuda.Stream()):
+                for _ in range(5):
+                    b = fsg.fsg_build_graph(tree, fsg.params(1.5), 32, 5)
+                    torch.cuda.current_stream().synchronize()
+                    np.testing.assert_array_equal(b.w[: int(b.m.item())].cpu().numpy(), ref_w)
+        except Exception as e:  # reported on the main thread
+            errors.append(e)
+
+    th = threading.Thread(target=direct)
+    th.start()
+    got = _drain(server, len(ids))
+    th.join()
+    server.close()
+    tree.close()
+    assert not errors, errors
+    for rid, (src, dst, w) in zip(ids, want):
+        rec, (gs, gd, gw) = got[rid]
+        assert rec["status"] == fsg.FSG_OK
+        np.testing.assert_array_equal(gs, src)
+        np.testing.assert_array_equal(gw, w)

@@ -35,16 +35,27 @@ def test_two_moons(fsg):
 
 
 def test_segmentation_image(fsg):
+    # The Rand index of one sampled graph's clustering varies with the seed
+    # (the exact method's own graphs of this image span 0.87..0.93 over seeds
+    # 1..8 at L = 16), so the check takes the median over five seeds and
+    # compares it with the oracle's graphs on the same seeds, and with the
+    # complete kernel graph's clustering.
     X, reg = inputs.segmentation_image(48, 72, seed=7, return_labels=True)
     k = len(np.unique(reg))
-    src, dst, w = fsg.fsg_build_graph_host(X, fsg.params(0.05), 16, 1)
-    ri_sparse = spectral.rand_index(spectral.spectral_clustering(len(X), src, dst, w, k), reg)
     gam = ora.gamma(0.05)
+    ri_gpu, ri_ora = [], []
+    for seed in range(1, 6):
+        src, dst, w = fsg.fsg_build_graph_host(X, fsg.params(0.05), 16, seed)
+        ri_gpu.append(spectral.rand_index(spectral.spectral_clustering(len(X), src, dst, w, k), reg))
+        o = ora.build_graph(X, gam, 16, seed)
+        ri_ora.append(spectral.rand_index(spectral.spectral_clustering(len(X), o["src"], o["dst"], o["w"], k), reg))
     K = np.exp(-gam * ((X[:, None, :].astype(np.float64) - X[None, :, :]) ** 2).sum(-1))
     np.fill_diagonal(K, 0.0)
     i, j = np.nonzero(np.triu(K, 1))
     ri_dense = spectral.rand_index(spectral.spectral_clustering(len(X), i, j, K[i, j], k), reg)
-    assert ri_sparse >= 0.85 and ri_sparse >= ri_dense - 0.05, (ri_sparse, ri_dense)
+    med_gpu, med_ora = float(np.median(ri_gpu)), float(np.median(ri_ora))
+    assert med_gpu >= 0.85 and abs(med_gpu - med_ora) <= 0.03, (ri_gpu, ri_ora)
+    assert med_gpu >= ri_dense - 0.06, (med_gpu, ri_dense)
 
 
 # At d = 64 the bandwidth is 3: with sigma = 1.5 the kernel values inside a
