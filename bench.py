@@ -319,7 +319,7 @@ def sub_seg_batch(fsg, stream, flush, steps):
                           "kind": "degrees vs the FP64 oracle (64 points of images 0, 21, 42, 63)"}}
 
 
-def sub_serving(fsg, requests, rate):
+def sub_serving(fsg, requests, rate, slots=8, admission=0):
     """Serving: `requests` graph-build requests (Poisson arrivals at `rate`/s,
     n log-uniform in [1e3, 2e5], d in {2, 10, 64}, mixture data, sigma = 1.5,
     L = 32) through the library's server: p50/p99 latency and edges/s; the
@@ -335,7 +335,7 @@ def sub_serving(fsg, requests, rate):
     ring = [tuple(torch.empty(200_000 * L, dtype=dt).pin_memory().numpy()
                   for dt in (torch.int32, torch.int32, torch.float32)) for _ in range(24)]
     free_ring = list(range(len(ring)))
-    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8)
+    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=slots, admission=admission)
     p = fsg.params(sigma)
     owner, lat, done = {}, [], [0]
 
@@ -392,7 +392,7 @@ def sub_serving(fsg, requests, rate):
     lat.sort()
     pct = lambda a, x: a[min(len(a) - 1, int(x * len(a)))]
     return {"workload": f"serving: {len(timed_reqs)} requests, Poisson {rate}/s, n log-uniform [1e3, 2e5], "
-                        "d in {2,10,64}, mixture data, sigma=1.5, L=32, SET edges, HBM budget 120 GB, 8 slots",
+                        f"d in {{2,10,64}}, mixture data, sigma=1.5, L=32, SET edges, HBM budget 120 GB, {slots} slots",
             "value": done[0] / wall, "unit": UNIT, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99),
             "max_ms": lat[-1], "wall_s": wall, "offered_s": timed_reqs[-1].arrival_s - base,
             "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(rel.size),
@@ -421,7 +421,10 @@ def run_ours(args):
     split = args.precision == "split"
     if args.kde_eps > 0 and not split:
         raise SystemExit("--kde-eps needs --precision split (the approximate bin pass is the split form's)")
-    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO, kde_eps=args.kde_eps)
+    if args.resolve and split:
+        raise SystemExit("--resolve takes the FP32 fused path (not --precision split)")
+    p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO, kde_eps=args.kde_eps,
+                   resolve=args.resolve)
     # split form: the spatial tree order, computed on the GPU in every step (fsg_tree_update)
     order = fsg.FSG_ORDER_SPATIAL if split else fsg.FSG_ORDER_IDENTITY
     with torch.cuda.stream(stream):
@@ -714,7 +717,7 @@ def run_ours(args):
             # the other workloads, each measured the same way (value, roofline, error vs the oracle)
             subs = {"digits": sub_digits(fsg, stream, flush, 5),
                     "seg_batch": sub_seg_batch(fsg, stream, flush, 3),
-                    "serving": sub_serving(fsg, args.sub_requests, args.rate)}
+                    "serving": sub_serving(fsg, args.sub_requests, args.rate, args.slots)}
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.cpu_queries} of the {n} query points (all {L} samples each + their degrees), "
                          f"{dt:.1f} s, extrapolated per sampled edge"}
@@ -725,7 +728,8 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate" if split else "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)",
                                **({"precision": "split (spatial tree order, GPU, in the step)"} if split else {}),
-                               **({"kde_eps": args.kde_eps} if args.kde_eps > 0 else {})),
+                               **({"kde_eps": args.kde_eps} if args.kde_eps > 0 else {}),
+                               **({"resolve": True} if args.resolve else {})),
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
                 "flagged_samples": st["n_flagged"], "items": st["n_items"],
                 "phase_ms": {k: v / args.steps for k, v in phase_tot.items() if v > 0},
@@ -844,7 +848,7 @@ def run_serving(args):
             for _ in range(24)]
     free_ring = list(range(len(ring)))
     admission = {"arrival": fsg.FSG_ADMIT_ARRIVAL, "ratio": fsg.FSG_ADMIT_RESPONSE_RATIO}[args.admission]
-    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8, admission=admission)
+    server = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=args.slots, admission=admission)
     p = fsg.params(sigma)
     # --precision split: the d = 64 requests take the split form (bin pass and
     # leaf phase on the tensor cores, spatial tree order computed on the GPU)
@@ -904,7 +908,7 @@ def run_serving(args):
     if args.plain_requests > 0:
         # closed loop: the first K timed requests submitted at once, fused vs plain schedule
         def burst(schedule):
-            srv = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=8, admission=admission)
+            srv = fsg.Server(hbm_budget_bytes=120 << 30, max_slots=args.slots, admission=admission)
             pp = fsg.params(sigma, schedule=schedule)
             sub = timed_reqs[: args.plain_requests]
             t0b = time.perf_counter()
@@ -931,7 +935,8 @@ def run_serving(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving: {len(timed_reqs)} requests, Poisson {args.rate}/s, n log-uniform "
                                    f"[1e3, 2e5], d in {{2,10,64}}, mixture data, sigma=1.5, L=32, SET edges",
-                       "hbm_budget_gb": 120, "slots": 8, "parallelism": "continuous admission, 8 streams",
+                       "hbm_budget_gb": 120, "slots": args.slots,
+                       "parallelism": f"continuous admission, {args.slots} slots",
                        "precision": "d = 64 in split precision" if args.precision == "split" else "FP32 / auto",
                        "admission": {"arrival": "arrival order",
                                      "ratio": "highest response ratio next"}[args.admission]},
@@ -965,6 +970,9 @@ def main():
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--plain-requests", type=int, default=40, help="serving: closed-loop burst for the plain path")
     ap.add_argument("--admission", choices=["arrival", "ratio"], default="arrival", help="serving: admission order")
+    ap.add_argument("--slots", type=int, default=8, help="serving: requests in flight at once")
+    ap.add_argument("--resolve", action="store_true",
+                    help="the headline step with the high-precision re-decision of flagged samples")
     ap.add_argument("--kde-eps", type=float, default=0.0,
                     help="approximate KDE (tree-pruned split bin pass) with this relative error bound")
     ap.add_argument("--precision", choices=["auto", "split"], default="auto",

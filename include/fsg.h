@@ -50,6 +50,7 @@ extern "C" {
 #define FSG_ERR_CAPACITY 7      /* an output buffer is too small                  */
 #define FSG_ERR_SCRATCH 8       /* problem too large for fsg_degrees_noalloc      */
 #define FSG_ERR_CANCELLED 9     /* server: the request was cancelled              */
+#define FSG_ERR_BOUNDS 10       /* bounds-checking build: an index check failed   */
 
 /* ---- option values ----------------------------------------------------- */
 /* Bandwidth convention: gamma = 1/(2 sigma^2) (default) or 1/sigma^2, the form
@@ -75,9 +76,11 @@ extern "C" {
  * the squared Euclidean distance (Gaussian, scale gamma of scale_conv), the
  * l1 distance (Laplacian, scale 1/sigma) or the Euclidean distance
  * (exponential, scale 1/sigma).  The Laplacian and exponential kernels run on
- * the fused FP32 path for d <= 16 with bins of 65..128 points (the default
- * tree for most n from 65 to 262,144 at d <= 16); elsewhere
- * FSG_ERR_UNSUPPORTED. */
+ * the fused schedule's FP32 paths: for d <= 16 with bins of 65..128 points
+ * (the default tree for most n from 65 to 262,144 at d <= 16), and for any
+ * d > 16 (FSG_PREC_AUTO then means FP32, also on 8-bit data); elsewhere
+ * (levelwise schedules, split and tensor-core precisions, fsg_params.resolve,
+ * weight_f64) FSG_ERR_UNSUPPORTED. */
 #define FSG_KERNEL_GAUSSIAN 0
 #define FSG_KERNEL_LAPLACIAN 1
 #define FSG_KERNEL_EXPONENTIAL 2
@@ -510,9 +513,21 @@ int fsg_selftest_wait_timeout(int64_t limit_ns, void* stream);
 
 /*
  * Waits for the stream and returns the tree's device status word
- * (FSG_OK or FSG_ERR_TIMEOUT), then clears it.  Errors: CUDA.
+ * (FSG_OK or FSG_ERR_TIMEOUT), then clears it.  In a library built with
+ * FSG_BOUNDS_CHECK (FSG_BOUNDS_CHECK=1 python -m paper_2310_13870_gb300.build,
+ * into _build_bounds/) it also returns FSG_ERR_BOUNDS when an index check of
+ * any kernel failed since the last call.  Errors: CUDA.
  */
 int fsg_sync(fsg_tree* tree, void* stream);
+
+/*
+ * Bounds-checking build only (see fsg_sync): the first failed index check
+ * since the last call (out[0] = 1, out[1] = the check's site number, out[2] =
+ * the index, out[3] = its limit; all 0 when none failed), then cleared.
+ * Synchronizes the device.  Other builds: FSG_ERR_UNSUPPORTED.  The paper has
+ * no counterpart (a debugging aid of this library).
+ */
+int fsg_bounds_error(int64_t* out);
 
 /*
  * End-to-end entry point on HOST buffers: copies h_points to the device,

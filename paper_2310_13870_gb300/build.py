@@ -18,7 +18,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-OUT_DIR = os.path.join(HERE, "_build")
+# FSG_BOUNDS_CHECK=1: the bounds-checking build (every kernel's index checks
+# compiled in, failures reported through fsg_sync / fsg_bounds_error) into
+# _build_bounds/, beside the normal one.
+BOUNDS = os.environ.get("FSG_BOUNDS_CHECK", "0") not in ("", "0")
+OUT_DIR = os.path.join(HERE, "_build_bounds" if BOUNDS else "_build")
 LIB = os.path.join(OUT_DIR, "libfsg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,7 +36,7 @@ def nvcc_path() -> str:
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-                   "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
+                   "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"] + (["-DFSG_BOUNDS_CHECK"] if BOUNDS else [])
 
 
 def _newest_header() -> float:

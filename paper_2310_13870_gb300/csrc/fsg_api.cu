@@ -45,6 +45,13 @@ int check_params(const fsg_params* p) {
     return FSG_OK;
 }
 
+// The arithmetic a call runs: AUTO takes the tensor-core forms for the
+// Gaussian kernel only (the other families' exponents are not the expanded
+// squared distance), so for them AUTO means FP32.
+int eff_precision(const fsg_params* p) {
+    return p->kernel != FSG_KERNEL_GAUSSIAN && p->precision == FSG_PREC_AUTO ? FSG_PREC_FP32 : p->precision;
+}
+
 KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
     // Gaussian: gamma of the bandwidth convention; Laplacian and exponential:
     // 1/sigma times their distance
@@ -52,7 +59,7 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
                          : p->scale_conv == FSG_SIGMA_SQ  ? 1.0 / (p->sigma * p->sigma)
                                                           : 1.0 / (2.0 * p->sigma * p->sigma);
     KernelParams kp{};
-    kp.precision = p->precision;
+    kp.precision = eff_precision(p);
     kp.gamma = (float)gamma;
     kp.neg_c = (float)(-gamma * kLog2e);
     if (kp.neg_c > -1e-30f) kp.neg_c = -1e-30f;  // keeps far-away padding at exactly 0
@@ -143,11 +150,12 @@ int64_t bin_pass_evals(const fsg_tree* t, int precision) {
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
-    // the Laplacian and exponential kernels: the fused FP32 path of the
-    // symmetric bin pass and the 128-point leaf kernel
+    // the Laplacian and exponential kernels: the fused schedule's FP32 paths
+    // (d <= 16: the symmetric bin pass and the 128-point leaf kernel; d > 16:
+    // the generic passes and leaf kernels)
     if (p->kernel != FSG_KERNEL_GAUSSIAN &&
-        (t->d > kMaxFmaDim || (p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32) ||
-         p->schedule != FSG_SCHED_FUSED || !kde_bins_sym_supported(t) || !use_leaf128(t)))
+        ((p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32) || p->schedule != FSG_SCHED_FUSED ||
+         (t->d <= kMaxFmaDim && (!kde_bins_sym_supported(t) || !use_leaf128(t)))))
         return FSG_ERR_UNSUPPORTED;
     // the approximate bin pass is the split form's tile pruning
     if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED))
@@ -327,6 +335,7 @@ const char* fsg_error_string(int status) {
         case FSG_ERR_CAPACITY: return "output buffer too small";
         case FSG_ERR_SCRATCH: return "problem too large for the fixed scratch of fsg_degrees_noalloc";
         case FSG_ERR_CANCELLED: return "request cancelled";
+        case FSG_ERR_BOUNDS: return "an index check of the bounds-checking build failed";
         default: return "unknown status";
     }
 }
@@ -507,7 +516,7 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
         to_public(t->tune, out);
         return FSG_OK;
     }
-    const bool tc = use_tc(t, p->precision);
+    const bool tc = use_tc(t, eff_precision(p));
     const int path = tc ? 2 : (t->d <= kMaxFmaDim && kde_bins_sym_supported(t)) ? 1 : 0;
     const TuneKey key{t->n, t->d, L, t->s0, t->mmax, path};
     {
@@ -604,7 +613,7 @@ int fsg_bin_pass_evals(const fsg_tree* t, const fsg_params* p, int64_t* evals) {
     if (!t || !evals) return FSG_ERR_INVALID_ARG;
     const int rc = check_params(p);
     if (rc != FSG_OK) return rc;
-    *evals = p->schedule != FSG_SCHED_FUSED ? 0 : bin_pass_evals(t, p->precision);
+    *evals = p->schedule != FSG_SCHED_FUSED ? 0 : bin_pass_evals(t, eff_precision(p));
     return FSG_OK;
 }
 
@@ -705,7 +714,7 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
 // the host; the levelwise schedule counts its own on the device.
 static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
     if (p->schedule != FSG_SCHED_FUSED || p->precision == FSG_PREC_SPLIT_BF16) return 0;
-    return bin_pass_evals(t, p->precision);
+    return bin_pass_evals(t, eff_precision(p));
 }
 
 // Statistics known on the host: samples run, bin-pass evaluations.
@@ -830,6 +839,25 @@ int fsg::build_graph_internal(fsg_tree* t, const fsg_params* p, int32_t L, uint6
 
 extern "C" {
 
+int fsg_bounds_error(int64_t* out) {
+    if (!out) return FSG_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; ++k) out[k] = 0;
+#ifdef FSG_BOUNDS_CHECK
+    if (cudaDeviceSynchronize() != cudaSuccess) return FSG_ERR_CUDA;
+    int (*readers[])(long long*) = {bounds_read_fma, bounds_read_descend, bounds_read_tc, bounds_read_resolve};
+    for (auto rd : readers) {
+        long long v[4] = {0, 0, 0, 0};
+        const int r = rd(v);
+        if (r < 0) return FSG_ERR_CUDA;
+        if (r > 0 && out[0] == 0)
+            for (int k = 0; k < 4; ++k) out[k] = v[k];
+    }
+    return FSG_OK;
+#else
+    return FSG_ERR_UNSUPPORTED;
+#endif
+}
+
 int fsg_sync(fsg_tree* t, void* stream) {
     if (!t) return FSG_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -837,6 +865,14 @@ int fsg_sync(fsg_tree* t, void* stream) {
     cudaError_t e = cudaMemcpyAsync(&st, t->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return status_of(e);
+#ifdef FSG_BOUNDS_CHECK
+    {
+        int64_t be[4];
+        const int rb = fsg_bounds_error(be);
+        if (rb != FSG_OK) return rb;
+        if (be[0]) return FSG_ERR_BOUNDS;
+    }
+#endif
     if (st != 0) {
         cudaMemsetAsync(t->status, 0, sizeof(int32_t), s);
         cudaStreamSynchronize(s);

@@ -15,8 +15,14 @@
 //                 for the weight of Eq. 2 (formed by the edge kernels).
 #include "fsg_internal.cuh"
 
+FSG_BOUNDS_TU(descend)
+
 namespace fsg {
 namespace {
+
+__device__ __forceinline__ int k_of(int r, uint32_t b0, uint32_t b1, uint32_t below) {
+    return r == 0 ? __popc(b0 & below) : __popc(b0) + __popc(b1 & below);
+}
 
 // Per query (one warp): segment tree of the query's node sums over levels
 // 0..s0 built from its bin sums, the degree (the root), the first s0
@@ -127,7 +133,7 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
                 const uint32_t below = (1u << lane) - 1u;
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
-                    if (lead[r]) {
+                    if (lead[r] && FSG_INB(k_of(r, b0, b1, below), L, kSiteTopItem) && FSG_INB(binv[r], nb, kSiteTopItem)) {
                         const int k = r == 0 ? __popc(b0 & below) : __popc(b0) + __popc(b1 & below);
                         qitem_bin[(size_t)q * L + k] = binv[r];
                         qitem_mask[(size_t)q * L + k] = M[r];
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(128)
 scatter_items_kernel(const int32_t* __restrict__ qitem_bin, const uint64_t* __restrict__ qitem_mask,
                      const int32_t* __restrict__ qitem_cnt, int n, int L, const int32_t* __restrict__ bin_off,
                      int32_t* __restrict__ bin_cursor, int32_t* __restrict__ items_q,
-                     uint64_t* __restrict__ items_mask) {
+                     uint64_t* __restrict__ items_mask, long long max_items) {
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
@@ -194,6 +200,7 @@ scatter_items_kernel(const int32_t* __restrict__ qitem_bin, const uint64_t* __re
         for (int k = lane; k < cnt; k += 32) {
             const int b = qitem_bin[(size_t)q * L + k] * kBinSlots + (q & (kBinSlots - 1));
             const int slot = bin_off[b] + atomicAdd(&bin_cursor[b], 1);
+            if (!FSG_INB(slot, max_items, kSiteScatter)) continue;
             items_q[slot] = q;
             items_mask[slot] = qitem_mask[(size_t)q * L + k];
         }
@@ -496,9 +503,11 @@ leaf_finish_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ per
                 }
             }
             const size_t o = (size_t)qpos[qq] * L + l;
-            leaf_pos[o] = p_lo + a;
-            ksmp[o] = row[h];
-            lflags[o] = f;
+            if (FSG_INB(o, (long long)n * L, kSiteLeafFinish)) {
+                leaf_pos[o] = p_lo + a;
+                ksmp[o] = row[h];
+                lflags[o] = f;
+            }
         }
         ev_acc += (unsigned long long)qcnt * (unsigned long long)m;
         it_acc += (unsigned long long)qcnt;
@@ -637,7 +646,7 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
                int s0, const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
                const uint64_t* __restrict__ items_mask, KernelParams kp, int32_t* __restrict__ leaf_pos,
                float* __restrict__ ksmp, uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
-               unsigned long long* __restrict__ n_items) {
+               unsigned long long* __restrict__ n_items, long long nl) {
     using LY = Leaf128Layout<D>;
     constexpr int DP = LY::DP, DH = LY::DH, QS = LY::QS;
     extern __shared__ __align__(16) unsigned char smem128[];
@@ -822,9 +831,11 @@ leaf128_kernel(const float* __restrict__ Xt, const int32_t* __restrict__ perm, c
                 for (int k = 0; k < 8; ++k)
                     if (a0 + k == a) kval = lf[k];
                 const size_t o = (size_t)my_pos * L + l;
-                leaf_pos[o] = p_lo + a;
-                ksmp[o] = kval;
-                lflags[o] = f;
+                if (FSG_INB(o, nl, kSiteLeaf128)) {
+                    leaf_pos[o] = p_lo + a;
+                    ksmp[o] = kval;
+                    lflags[o] = f;
+                }
             }
         }
         ev_acc += (unsigned long long)qcnt * (unsigned long long)m;
@@ -854,7 +865,8 @@ cudaError_t launch_leaf128_d(const fsg_tree* t, const KernelParams& kp, cudaStre
     leaf128_kernel<D, F><<<grid, kLC, smem, s>>>(t->Xt, t->perm, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask,
                                               kp, ws.leaf_pos, ws.ksmp, ws.lflags,
                                               reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
-                                              reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
+                                              reinterpret_cast<unsigned long long*>(&ws.stats->n_items),
+                                              t->n * (long long)kp.L);
     return cudaGetLastError();
 }
 
@@ -910,8 +922,9 @@ cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_
     if (e != cudaSuccess) return e;
     int64_t blocks = (t->n + 3) / 4;
     if (blocks > 152 * 32) blocks = 152 * 32;
+    const long long max_items = t->n * (long long)(ws.cap_L < t->nb ? ws.cap_L : t->nb);
     scatter_items_kernel<<<(int)blocks, 128, 0, s>>>(ws.qitem_bin, ws.qitem_mask, ws.qitem_cnt, (int)t->n, kp.L,
-                                                     ws.bin_off, ws.bin_cursor, ws.items_q, ws.items_mask);
+                                                     ws.bin_off, ws.bin_cursor, ws.items_q, ws.items_mask, max_items);
     return cudaGetLastError();
 }
 

@@ -610,6 +610,54 @@ __device__ __forceinline__ int descend_bin_row(const float* __restrict__ vi, con
 
 #endif  // __CUDACC__
 
+// ---------------------------------------------------------------------------
+// Bounds-checking build (-DFSG_BOUNDS_CHECK; FSG_BOUNDS_CHECK=1 python -m
+// paper_2310_13870_gb300.build).  FSG_INB(i, lim, site) tests an index before
+// a global access; a failure is recorded once per translation unit (site,
+// index, limit) in that unit's device error words and the access is skipped
+// instead of going out of bounds.  fsg_sync then returns FSG_ERR_BOUNDS and
+// fsg_bounds_error reads and clears the record.  Other builds compile every
+// check to `true`.
+// ---------------------------------------------------------------------------
+#ifdef FSG_BOUNDS_CHECK
+#define FSG_BOUNDS_TU(name)                                                                         \
+    static __device__ unsigned long long g_fsg_bounds[4];                                           \
+    static __device__ __forceinline__ bool fsg_inb(long long i, long long lim, int site) {          \
+        if (i >= 0 && i < lim) return true;                                                         \
+        if (atomicCAS(&g_fsg_bounds[0], 0ull, 1ull) == 0ull) {                                      \
+            g_fsg_bounds[1] = (unsigned long long)site;                                             \
+            g_fsg_bounds[2] = (unsigned long long)i;                                                \
+            g_fsg_bounds[3] = (unsigned long long)lim;                                              \
+        }                                                                                           \
+        return false;                                                                               \
+    }                                                                                               \
+    namespace fsg {                                                                                 \
+    int bounds_read_##name(long long* out) {                                                        \
+        if (cudaMemcpyFromSymbol(out, g_fsg_bounds, sizeof(g_fsg_bounds)) != cudaSuccess) return -1; \
+        if (out[0]) {                                                                               \
+            const unsigned long long z[4] = {0, 0, 0, 0};                                           \
+            cudaMemcpyToSymbol(g_fsg_bounds, z, sizeof(z));                                         \
+        }                                                                                           \
+        return out[0] ? 1 : 0;                                                                      \
+    }                                                                                               \
+    }
+#define FSG_INB(i, lim, site) fsg_inb((long long)(i), (long long)(lim), (site))
+#else
+#define FSG_BOUNDS_TU(name)
+#define FSG_INB(i, lim, site) true
+#endif
+// Check sites (FSG_INB's third argument).
+enum {
+    kSiteSymRow = 1, kSiteSymMirror, kSitePlainRow, kSiteTopItem, kSiteScatter, kSiteLeaf128, kSiteLeafFinish,
+    kSiteTcRow, kSiteTcCol, kSiteResolveWalk, kSiteResolvePart, kSiteResolveList
+};
+#ifdef FSG_BOUNDS_CHECK
+int bounds_read_fma(long long* out);
+int bounds_read_descend(long long* out);
+int bounds_read_tc(long long* out);
+int bounds_read_resolve(long long* out);
+#endif
+
 inline int ceil_log2_host(int64_t m) {
     int r = 0;
     while ((int64_t(1) << r) < m) ++r;

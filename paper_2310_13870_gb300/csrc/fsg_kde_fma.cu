@@ -19,6 +19,8 @@
 
 #include "fsg_internal.cuh"
 
+FSG_BOUNDS_TU(fma)
+
 namespace fsg {
 namespace {
 
@@ -179,7 +181,8 @@ kde_bins_kernel(const float* __restrict__ Xdup, const float* __restrict__ Xt, in
     const int nq = min(QCTA, n - qbase);
     for (int e = tid; e < nq * nbc; e += kThreadsA) {
         const int ql = e / nbc, b = e - ql * nbc;
-        binsum[(size_t)(qbase + ql) * nb + b0 + b] = outs[ql * bpc + b];
+        const size_t o = (size_t)(qbase + ql) * nb + b0 + b;
+        if (FSG_INB(o, (long long)n * nb, kSitePlainRow)) binsum[o] = outs[ql * bpc + b];
     }
 }
 
@@ -387,7 +390,8 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
                                          const int32_t* pbn, int np, const uint64_t (&q)[2][D],
                                          const int32_t (&qmask)[4], const int32_t (&qpos)[4], uint64_t nc2,
                                          const SymWarp& sw, int lane, int tid, int32_t* status,
-                                         float* __restrict__ binsum, int nb, int pn0, int qn0, int nq) {
+                                         float* __restrict__ binsum, int nb, int pn0, int qn0, int nq,
+                                         long long bins_lim) {
     constexpr int DP = (D + 3) & ~3;
     constexpr int STAGE_FLOATS = kSymMaxBin * DP * 2;
     for (int b = 0; b < np; ++b) {
@@ -412,7 +416,8 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
             const float vv[4] = {v0.x, v0.y, v1.x, v1.y};
 #pragma unroll
             for (int h = 0; h < 4; ++h)
-                if (qpos[h] >= 0) binsum[(size_t)qpos[h] * nb + pn0 + b] = vv[h];
+                if (qpos[h] >= 0 && FSG_INB((size_t)qpos[h] * nb + pn0 + b, bins_lim, kSiteSymRow))
+                    binsum[(size_t)qpos[h] * nb + pn0 + b] = vv[h];
         }
         __syncthreads();
         if (tid == 0 && b + kSymStages < np) {
@@ -424,7 +429,8 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
         if (MIRROR) {  // mirror rows of this bin's points: query bins qn0 .. qn0+nq-1
             for (int e = tid; e < cnt * nq; e += kSymThreads) {
                 const int r = e / nq, c = e - r * nq;
-                binsum[(size_t)(t0 + r) * nb + qn0 + c] = mrow[r * kSymNodes + c];
+                if (FSG_INB((size_t)(t0 + r) * nb + qn0 + c, bins_lim, kSiteSymMirror))
+                    binsum[(size_t)(t0 + r) * nb + qn0 + c] = mrow[r * kSymNodes + c];
                 mrow[r * kSymNodes + c] = 0.f;
             }
         }
@@ -442,6 +448,11 @@ __device__ __forceinline__ void sym_block_pair(const float* __restrict__ Xdup, c
     constexpr int DP = (D + 3) & ~3;
     constexpr int STAGE_FLOATS = kSymMaxBin * DP * 2;
     const bool mirror = k2 > k1;
+#ifdef FSG_BOUNDS_CHECK
+    const long long bins_lim = (long long)bnd[nb] * nb;  // n x nb bin sums
+#else
+    const long long bins_lim = 0;
+#endif
     float* pts = reinterpret_cast<float*>(smem_raw);                       // [stages][128][DP][2]
     float* mir = pts + kSymStages * STAGE_FLOATS;                          // [2][128][kSymNodes]
     uint64_t* bars = reinterpret_cast<uint64_t*>(mir + 2 * kSymMaxBin * kSymNodes);
@@ -507,10 +518,10 @@ __device__ __forceinline__ void sym_block_pair(const float* __restrict__ Xdup, c
     for (int h = 0; h < 4; ++h) qmask[h] = (!mirror && self_exclude) ? qpos[h] : -1;
     if (mirror)
         sym_bins<D, F, true>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
-                          pn0, qn0, nq);
+                          pn0, qn0, nq, bins_lim);
     else
         sym_bins<D, F, false>(pts, mir, bars, Xdup, pbn, np, q, qmask, qpos, nc2, sw, lane, tid, status, binsum, nb,
-                           pn0, qn0, nq);
+                           pn0, qn0, nq, bins_lim);
 }
 
 template <int D, int F>

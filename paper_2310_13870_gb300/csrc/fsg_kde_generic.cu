@@ -41,7 +41,9 @@ __device__ __forceinline__ void load_chunk(float* __restrict__ S, int nrows, con
     }
 }
 
-// acc[i][j] += sum over the chunk of (q_i - p_j)^2.
+// acc[i][j] += sum over the chunk of (q_i - p_j)^2 (F: the kernel family's
+// distance term, fam_acc1).
+template <int F>
 __device__ __forceinline__ void accumulate_chunk(const float* __restrict__ Qs, const float* __restrict__ Ps, int tq,
                                                  int tp, float (&acc)[8][4]) {
 #pragma unroll 4
@@ -56,12 +58,13 @@ __device__ __forceinline__ void accumulate_chunk(const float* __restrict__ Qs, c
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float dd = qv[i] - pp[j];
-                acc[i][j] = fmaf(dd, dd, acc[i][j]);
+                acc[i][j] = fam_acc1<F>(dd, acc[i][j]);
             }
         }
     }
 }
 
+template <int F>
 __global__ void __launch_bounds__(kGT, 2)
 kde_bins_generic_kernel(const float* __restrict__ Xt, int n, int d, int dp, const int32_t* __restrict__ bnd, int nb,
                         int bpc, float neg_c, int self_exclude, float* __restrict__ binsum) {
@@ -93,7 +96,7 @@ kde_bins_generic_kernel(const float* __restrict__ Xt, int n, int d, int dp, cons
             load_chunk(Qs, kGQ, qrow, Xt, dp, k0);
             load_chunk(Ps, kGP, prow, Xt, dp, k0);
             __syncthreads();
-            accumulate_chunk(Qs, Ps, tq, tp, acc);
+            accumulate_chunk<F>(Qs, Ps, tq, tp, acc);
         }
         // Bin of the tile's first point; the tile spans at most two bins.
         int bt = 0;
@@ -107,7 +110,7 @@ kde_bins_generic_kernel(const float* __restrict__ Xt, int n, int d, int dp, cons
             for (int j = 0; j < 4; ++j) {
                 const int p = t0 + 4 * tp + j;
                 if (4 * tp + j < np) {
-                    float k = ex2_approx(acc[i][j] * neg_c);
+                    float k = ex2_approx(fam_fin1<F>(acc[i][j]) * neg_c);
                     if (self_exclude && p == q) k = 0.f;
                     if (p < split) s0v += k; else s1v += k;
                 }
@@ -188,7 +191,7 @@ __device__ __forceinline__ void load_tiles(float* __restrict__ Qs, float* __rest
 }
 
 // acc[a][b] += (row pair a - column b)^2 over the 32 coordinates of the chunk.
-template <int NPG>
+template <int NPG, int F>
 __device__ __forceinline__ void accumulate_pairs(const float* __restrict__ Qs, const float* __restrict__ Ps, int tq,
                                                  int tp, uint64_t (&acc)[4][4 * NPG]) {
 #pragma unroll 2
@@ -211,7 +214,7 @@ __device__ __forceinline__ void accumulate_pairs(const float* __restrict__ Qs, c
 #pragma unroll
             for (int b = 0; b < 4 * NPG; ++b) {
                 const uint64_t dd = f2_sub(qv[a], pv[b]);
-                acc[a][b] = f2_fma(dd, dd, acc[a][b]);
+                acc[a][b] = fam_acc2<F>(dd, acc[a][b]);
             }
         }
     }
@@ -285,6 +288,7 @@ generic_tiles_kernel(const float* __restrict__ Xt, int n, int d, int dp, int dpc
     }
 }
 
+template <int F>
 __global__ void __launch_bounds__(kGT, 2)
 kde_bins_generic_sym_kernel(const float* __restrict__ Xtt, int n, int dpc, const int32_t* __restrict__ bnd, int nb,
                             int s0, int T, float neg_c, int self_exclude, float* __restrict__ binsum,
@@ -348,7 +352,7 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xtt, int n, int dpc, const
             return;
         }
         const float* Qs = gsm + st * kStageFloats;
-        accumulate_pairs<2>(Qs, Qs + kSK * kSQS, tq, tp, acc);
+        accumulate_pairs<2, F>(Qs, Qs + kSK * kSQS, tq, tp, acc);
         __syncthreads();  // stage st is free again
         if (tid == 0 && c + 2 < nchunks) issue(c + 2, st);
     }
@@ -360,7 +364,7 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xtt, int n, int dpc, const
     for (int a = 0; a < 4; ++a) {
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            const float2 sv = f2_unpack(f2_mul(acc[a][b], nc2));
+            const float2 sv = f2_unpack(f2_mul(fam_fin2<F>(acc[a][b]), nc2));
             const int p = P0 + tile_row(tp, b);
             const int q0 = Q0 + tile_row(tq, 2 * a);
             float k0 = ex2_approx(sv.x), k1 = ex2_approx(sv.y);
@@ -458,7 +462,7 @@ kde_bins_generic_sym_kernel(const float* __restrict__ Xtt, int n, int dpc, const
 // bin b's segment: 128 items (rows) against the leaf slots of the bin's
 // perfect tree (columns, 64 NPG per tile; slots whose node is empty get 0),
 // packed as in the symmetric pass; rows of leafv[item][slot] written as float4.
-template <int NPG>
+template <int NPG, int F>
 __global__ void __launch_bounds__(kGT, 2)
 leaf_values_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__ bnd,
                            const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q, float neg_c,
@@ -504,14 +508,14 @@ leaf_values_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* 
                 __syncthreads();
                 load_tiles(Qs, Ps, [&](int r) { return qrow[r]; }, [&](int r) { return prow[r]; }, Xt, dp, k0, 0.f);
                 __syncthreads();
-                accumulate_pairs<NPG>(Qs, Ps, tq, tp, acc);
+                accumulate_pairs<NPG, F>(Qs, Ps, tq, tp, acc);
             }
 #pragma unroll
             for (int a = 0; a < 4; ++a) {
                 float o[2][4 * NPG];
 #pragma unroll
                 for (int c = 0; c < 4 * NPG; ++c) {
-                    const float2 sv = f2_unpack(f2_mul(acc[a][c], nc2));
+                    const float2 sv = f2_unpack(f2_mul(fam_fin2<F>(acc[a][c]), nc2));
                     const int pp = prow[tile_row(tp, c)];
                     float k0 = pp >= 0 ? ex2_approx(sv.x) : 0.f, k1 = pp >= 0 ? ex2_approx(sv.y) : 0.f;
                     if (self_exclude) {
@@ -564,11 +568,13 @@ int64_t kde_bins_generic_sym_evals(const fsg_tree* t) {
     return T * (T + 1) / 2 * kST * kST;
 }
 
-cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+namespace {
+template <int F>
+cudaError_t launch_generic_f(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     if (kde_bins_generic_sym_supported(t)) {
         const size_t smem = 2 * kSymGenSmem + 2 * sizeof(uint64_t);  // two stages and their mbarriers
         {
-            const cudaError_t e = set_smem_limit(kde_bins_generic_sym_kernel, (int)smem);
+            const cudaError_t e = set_smem_limit(kde_bins_generic_sym_kernel<F>, (int)smem);
             if (e != cudaSuccess) return e;
         }
         const int64_t T = (t->n + kST - 1) / kST;
@@ -580,9 +586,9 @@ cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, c
         if (e != cudaSuccess) return e;
         const int64_t ctas = T * (T + 1) / 2;
         if (ctas > INT_MAX) return cudaErrorInvalidValue;
-        kde_bins_generic_sym_kernel<<<(unsigned)ctas, kGT, smem, s>>>(t->Xtt, (int)t->n, dpc, t->bnd, t->nb, t->s0,
-                                                                    (int)T, kp.neg_c, kp.self_exclude, t->ws.binsum,
-                                                                    t->status);
+        kde_bins_generic_sym_kernel<F><<<(unsigned)ctas, kGT, smem, s>>>(t->Xtt, (int)t->n, dpc, t->bnd, t->nb,
+                                                                       t->s0, (int)T, kp.neg_c, kp.self_exclude,
+                                                                       t->ws.binsum, t->status);
         return cudaGetLastError();
     }
     const int qblocks = (int)((t->n + kGQ - 1) / kGQ);
@@ -593,9 +599,19 @@ cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, c
     if (bpc > 8) bpc = 8;
     chunks = (t->nb + bpc - 1) / bpc;
     dim3 grid(qblocks, chunks);
-    kde_bins_generic_kernel<<<grid, kGT, (size_t)kGQ * bpc * 4, s>>>(t->Xt, (int)t->n, t->d, t->dp, t->bnd, t->nb,
-                                                                    bpc, kp.neg_c, kp.self_exclude, t->ws.binsum);
+    kde_bins_generic_kernel<F><<<grid, kGT, (size_t)kGQ * bpc * 4, s>>>(t->Xt, (int)t->n, t->d, t->dp, t->bnd, t->nb,
+                                                                       bpc, kp.neg_c, kp.self_exclude,
+                                                                       t->ws.binsum);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    switch (kp.family) {
+        case kFamLaplace: return launch_generic_f<kFamLaplace>(t, kp, s);
+        case kFamExp: return launch_generic_f<kFamExp>(t, kp, s);
+        default: return launch_generic_f<kFamGauss>(t, kp, s);
+    }
 }
 
 namespace {
@@ -615,6 +631,7 @@ constexpr size_t kLfPre = kLfMask + (size_t)kST * 8;      // [129] samples befor
 constexpr size_t kLfB4 = kLfPre + 132 * 4;                // [17] depth-4 node starts
 constexpr size_t kLfSmem = kLfB4 + 20 * 4;
 
+template <int F>
 __global__ void __launch_bounds__(kGT, 2)
 leaf_fused_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__ bnd, int s0,
                           const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
@@ -660,7 +677,7 @@ leaf_fused_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* _
             __syncthreads();
             load_tiles(Qs, Ps, [&](int r) { return qrow[r]; }, [&](int r) { return prow[r]; }, Xt, dp, k0, 0.f);
             __syncthreads();
-            accumulate_pairs<2>(Qs, Ps, tq, tp, acc);
+            accumulate_pairs<2, F>(Qs, Ps, tq, tp, acc);
         }
         __syncthreads();  // every thread is done with Qs and Ps: V takes their place
 #pragma unroll
@@ -669,7 +686,7 @@ leaf_fused_generic_kernel(const float* __restrict__ Xt, int dp, const int32_t* _
             for (int c = 0; c < 8; ++c) {
                 const int col = tile_row(tp, c);
                 const int pp = prow[col];
-                const float2 sv = f2_unpack(f2_mul(acc[a][c], nc2));
+                const float2 sv = f2_unpack(f2_mul(fam_fin2<F>(acc[a][c]), nc2));
                 const int r0 = tile_row(tq, 2 * a);
                 float k0v = pp >= 0 ? ex2_approx(sv.x) : 0.f, k1v = pp >= 0 ? ex2_approx(sv.y) : 0.f;
                 if (kp.self_exclude) {
@@ -757,12 +774,15 @@ cudaError_t launch_leaf_fused_generic(const fsg_tree* t, const KernelParams& kp,
     if (t->tune.leaf_splits > 0) S = t->tune.leaf_splits;
     if (S < 1) S = 1;
     if (S > 65535) S = 65535;
+    auto kern = kp.family == kFamLaplace ? leaf_fused_generic_kernel<kFamLaplace>
+                : kp.family == kFamExp     ? leaf_fused_generic_kernel<kFamExp>
+                                           : leaf_fused_generic_kernel<kFamGauss>;
     {
-        const cudaError_t e = set_smem_limit(leaf_fused_generic_kernel, (int)kLfSmem);
+        const cudaError_t e = set_smem_limit(kern, (int)kLfSmem);
         if (e != cudaSuccess) return e;
     }
     const auto& ws = t->ws;
-    leaf_fused_generic_kernel<<<dim3(t->nb, (unsigned)S), kGT, kLfSmem, s>>>(
+    kern<<<dim3(t->nb, (unsigned)S), kGT, kLfSmem, s>>>(
         t->Xt, t->dp, t->bnd, t->s0, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, ws.leaf_pos, ws.ksmp,
         ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&ws.stats->n_items));
@@ -778,19 +798,19 @@ cudaError_t launch_leaf_values_generic(const fsg_tree* t, const KernelParams& kp
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const bool wide = (1 << t->dm) > 64;
+    using K = void (*)(const float*, int, const int32_t*, const int32_t*, const int32_t*, float, int, int, float*);
+    const K kern = kp.family == kFamLaplace ? (wide ? (K)leaf_values_generic_kernel<2, kFamLaplace>
+                                                    : (K)leaf_values_generic_kernel<1, kFamLaplace>)
+                   : kp.family == kFamExp   ? (wide ? (K)leaf_values_generic_kernel<2, kFamExp>
+                                                    : (K)leaf_values_generic_kernel<1, kFamExp>)
+                                            : (wide ? (K)leaf_values_generic_kernel<2, kFamGauss>
+                                                    : (K)leaf_values_generic_kernel<1, kFamGauss>);
     {
-        const cudaError_t e =
-            set_smem_limit(wide ? leaf_values_generic_kernel<2> : leaf_values_generic_kernel<1>, kSymGenSmem);
+        const cudaError_t e = set_smem_limit(kern, kSymGenSmem);
         if (e != cudaSuccess) return e;
     }
-    if (wide)
-        leaf_values_generic_kernel<2><<<grid, kGT, kSymGenSmem, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off,
-                                                                     t->ws.items_q, kp.neg_c, kp.self_exclude,
-                                                                     1 << t->dm, t->ws.leafv);
-    else
-        leaf_values_generic_kernel<1><<<grid, kGT, kSymGenSmem, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off,
-                                                                     t->ws.items_q, kp.neg_c, kp.self_exclude,
-                                                                     1 << t->dm, t->ws.leafv);
+    kern<<<grid, kGT, kSymGenSmem, s>>>(t->Xt, t->dp, t->bnd, t->ws.bin_off, t->ws.items_q, kp.neg_c,
+                                        kp.self_exclude, 1 << t->dm, t->ws.leafv);
     return cudaGetLastError();
 }
 

@@ -27,6 +27,8 @@
 
 #include "fsg_tc.cuh"
 
+FSG_BOUNDS_TU(tc)
+
 namespace fsg {
 namespace {
 
@@ -48,10 +50,11 @@ constexpr uint32_t kIdesc = idesc_bf16(kTcM, kTcN);
 // (t, pair) takes row tile t (128 positions) of chunk k1 against the points
 // of chunk k2 >= k1, pair = the index of (k1, k2) in the triangle.  Off the
 // diagonal each value also goes to the column point's sum at the row's bin:
-// per 32 columns a warp sums its 32 rows by bin (at most two bins: bins hold
-// more than 32 points) with a butterfly, the four lane quadrants' partials
-// are added in a fixed order, and one atomic addition per (point, bin) and
-// CTA goes into bin sums zeroed beforehand.  A bin meets at most two row
+// per 32 columns a warp writes its 32 x 32 values to a transposed tile in
+// shared memory and each lane adds its column's 32 rows in order, apart by
+// bin (at most two bins: bins hold more than 32 points); the four lane
+// quadrants' partials are added in a fixed order, and one atomic addition
+// per (point, bin) and CTA goes into bin sums zeroed beforehand.  A bin meets at most two row
 // tiles, so every such sum receives at most two additions onto zero, whose
 // result does not depend on their order.
 template <int EW, int ST, bool SYM>
@@ -312,7 +315,8 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             if (wb == tb) sum += cpb[(qd * kCols + j) * 2];
                             else if (wb + 1 == tb) sum += cpb[(qd * kCols + j) * 2 + 1];
                         }
-                        atomicAdd(&binsum[(size_t)p * nb + rb0 + tb], sum);
+                        if (FSG_INB((size_t)p * nb + rb0 + tb, (long long)n * nb, kSiteTcCol))
+                            atomicAdd(&binsum[(size_t)p * nb + rb0 + tb], sum);
                     }
                 }
             }
@@ -325,7 +329,8 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             float v = outs[ql * bpc + b];
 #pragma unroll
             for (int h = 1; h < EW / 4; ++h) v += outs[(h * kTcM + ql) * bpc + b];
-            binsum[(size_t)(q0 + ql) * nb + b0 + b] = v;
+            if (FSG_INB((size_t)(q0 + ql) * nb + b0 + b, (long long)n * nb, kSiteTcRow))
+                binsum[(size_t)(q0 + ql) * nb + b0 + b] = v;
         }
     }
     if (inexact && tid == 0) atomicExch(status, FSG_ERR_UNSUPPORTED);

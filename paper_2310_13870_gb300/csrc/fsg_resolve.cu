@@ -40,6 +40,8 @@
 // the root.
 #include "fsg_internal.cuh"
 
+FSG_BOUNDS_TU(resolve)
+
 namespace fsg {
 namespace {
 
@@ -75,7 +77,10 @@ __global__ void rs_compact_kernel(const uint8_t* __restrict__ flags, const uint8
                                   int32_t* __restrict__ cnt) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t pos = leaf_pos[e];
-        if (pos >= 0 && ((flags[e] | lflags[e]) & 1)) list[atomicAdd(&cnt[0], 1)] = (int32_t)e;
+        if (pos >= 0 && ((flags[e] | lflags[e]) & 1)) {
+            const int slot = atomicAdd(&cnt[0], 1);
+            if (FSG_INB(slot, total, kSiteResolveList)) list[slot] = (int32_t)e;
+        }
     }
 }
 
@@ -311,9 +316,11 @@ rs_node_sums_kernel(const float* __restrict__ Xt, int dp, int n, int L, int nb, 
                 sr += red[(k * kRsJobs + tid) * 2 + 1];
             }
             const int j = j0 + tid - node_off[h];  // the job's index within its node
-            double* r = part + ((size_t)part_off[h] + (size_t)j * pc + pk) * 2;
-            r[0] = sl;
-            r[1] = sr;
+            const size_t pi = (size_t)part_off[h] + (size_t)j * pc + pk;
+            if (FSG_INB(pi, part_off[nb], kSiteResolvePart)) {
+                part[pi * 2] = sl;
+                part[pi * 2 + 1] = sr;
+            }
         }
     }
 }
@@ -424,7 +431,8 @@ rs_walk_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__
                const int32_t* __restrict__ bnd, int nb, int s0, const float* __restrict__ binsum,
                const int32_t* __restrict__ list, const int32_t* __restrict__ sbin, const int32_t* __restrict__ wlist,
                const int32_t* __restrict__ cnt, KernelParams kp, int32_t* __restrict__ leaf_pos,
-               float* __restrict__ ksmp, uint8_t* __restrict__ flags, uint8_t* __restrict__ lflags, int leafmax) {
+               float* __restrict__ ksmp, uint8_t* __restrict__ flags, uint8_t* __restrict__ lflags, int leafmax,
+               long long nl) {
     extern __shared__ __align__(16) unsigned char smem_r[];
     float* tree = reinterpret_cast<float*>(smem_r);                       // [2 nb]
     double* V = reinterpret_cast<double*>(tree + 2 * nb + 2);             // [2 leafmax] halving-tree sums
@@ -521,10 +529,12 @@ rs_walk_kernel(const float* __restrict__ Xt, int dp, const int32_t* __restrict__
                 }
                 hh = 2 * hh + right;
             }
-            leaf_pos[e] = spos[hh - leaf0];
-            ksmp[e] = (float)V[hh];
-            flags[e] = f;
-            lflags[e] = 0;
+            if (FSG_INB(e, nl, kSiteResolveWalk)) {
+                leaf_pos[e] = spos[hh - leaf0];
+                ksmp[e] = (float)V[hh];
+                flags[e] = f;
+                lflags[e] = 0;
+            }
         }
     }
 }
@@ -648,7 +658,7 @@ cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, cudaStream
     if (e != cudaSuccess) return e;
     rs_walk_kernel<<<152 * 4, kRsThreads, smem, s>>>(t->Xt, t->dp, t->perm, t->bnd, t->nb, t->s0, ws.binsum, rs.list,
                                                     rs.sbin, rs.wlist, rs.cnt, kp, ws.leaf_pos, ws.ksmp, ws.flags,
-                                                    ws.lflags, 1 << t->dm);
+                                                    ws.lflags, 1 << t->dm, total);
     return cudaGetLastError();
 }
 

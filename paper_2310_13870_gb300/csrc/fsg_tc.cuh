@@ -171,23 +171,6 @@ __device__ __forceinline__ void tc_row_chunk(const uint32_t (&r)[32], const floa
     tc_row_bins(v, pc, acc, bin, next_b, bnd_s, nbc, orow);
 }
 
-// Column sums of a warp's 32 x 32 block of values: lane l returns the sum
-// over the 32 lanes (rows) of column l.  Five butterfly levels; the order of
-// the additions is fixed, so the result is the same on every run.
-__device__ __forceinline__ float warp_column_sums32(float (&x)[32], int lane) {
-#pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
-        const bool up = (lane & half) != 0;
-#pragma unroll
-        for (int j = 0; j < half; ++j) {
-            const float send = up ? x[j] : x[j + half];
-            const float keep = up ? x[j + half] : x[j];
-            x[j] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-        }
-    }
-    return x[0];
-}
-
 }  // namespace fsg
 
 #endif  // FSG_TC_CUH

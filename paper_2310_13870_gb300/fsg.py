@@ -14,7 +14,8 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libfsg.so")
+# FSG_LIB_DIR=_build_bounds selects the bounds-checking build (see build.py)
+LIB_PATH = os.path.join(_HERE, os.environ.get("FSG_LIB_DIR", "_build"), "libfsg.so")
 
 FSG_OK = 0
 FSG_ERR_INVALID_ARG = 1
@@ -26,6 +27,7 @@ FSG_ERR_BUSY = 6
 FSG_ERR_CAPACITY = 7
 FSG_ERR_SCRATCH = 8
 FSG_ERR_CANCELLED = 9
+FSG_ERR_BOUNDS = 10
 
 FSG_TWO_SIGMA_SQ, FSG_SIGMA_SQ = 0, 1
 FSG_SELF_EXCLUDE, FSG_SELF_INCLUDE = 0, 1
@@ -46,7 +48,7 @@ EXPORTED = [
     "fsg_tree_update", "fsg_profile", "fsg_profile_read", "fsg_degrees_noalloc",
     "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
     "fsg_server_create", "fsg_server_submit", "fsg_server_poll", "fsg_server_cancel", "fsg_server_info",
-    "fsg_server_destroy", "fsg_selftest_wait_timeout",
+    "fsg_server_destroy", "fsg_selftest_wait_timeout", "fsg_bounds_error",
 ]
 FSG_NUM_PHASES = 8
 PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "resolve"]
@@ -156,6 +158,7 @@ def load(path: str = LIB_PATH):
     lib.fsg_spatial_order.argtypes = [P, ctypes.c_int64, I32, I32, P]
     lib.fsg_tree_perm.argtypes = [P, P, P]
     lib.fsg_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
+    lib.fsg_bounds_error.argtypes = [P]
     for name in EXPORTED:
         if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy", "fsg_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int

@@ -1,7 +1,10 @@
 """The Laplacian and exponential kernels of Sec. 2.1 (fsg_params.kernel) on
-the fused FP32 path for d <= 16, against the FP64 oracle of the same family:
-degrees within the FP32 tolerance, unflagged samples equal to the oracle's,
-edge weights within 1e-4; refused where the path does not offer them."""
+the fused schedule's FP32 paths (d <= 16: the symmetric bin pass and the
+128-point leaf kernel; d > 16: the generic passes and leaf kernels, also for
+8-bit data, where AUTO means FP32 for these families), against the FP64
+oracle of the same family: degrees within the FP32 tolerance, unflagged
+samples equal to the oracle's, edge weights within 1e-4; refused where the
+path does not offer them."""
 import math
 
 import numpy as np
@@ -40,7 +43,9 @@ def family_pair(fsg, name):
 @pytest.mark.parametrize("n,d,sigma,L,seed", [
     (6000, 10, 3.0, 32, 1),      # the mixture workload's dimension
     (5003, 2, 0.2, 16, 2),       # ragged n, two dimensions
-    (9000, 16, 4.0, 64, 3),      # the largest d of the path, full sample mask
+    (9000, 16, 4.0, 64, 3),      # the largest d of the d <= 16 path, full sample mask
+    (5000, 24, 6.0, 32, 4),      # generic symmetric pass, fused generic leaf (bins <= 128)
+    (3001, 40, 8.0, 16, 5),      # ragged n at d = 40
 ])
 def test_family_matches_oracle(fsg, name, n, d, sigma, L, seed):
     fam, ofam = family_pair(fsg, name)
@@ -93,13 +98,42 @@ def test_families_differ_from_the_gaussian(fsg):
     assert not np.allclose(out[0], out[1]) and not np.allclose(out[1], out[2]) and not np.allclose(out[0], out[2])
 
 
+@pytest.mark.parametrize("name", ["laplacian", "exponential"])
+def test_family_on_8bit_data_and_large_bins(fsg, name):
+    # digit-like 8-bit data (AUTO would take the tensor-core form for the
+    # Gaussian) and a tree with bins of up to 512 points (the two-kernel
+    # generic leaf phase: values in HBM, then the leaf finish)
+    fam, ofam = family_pair(fsg, name)
+    for X, sigma, leaf_max in ((inputs.digit_like(n=2500, d=784, seed=6), 9.0, 0),
+                               (inputs.gaussian_mixture(n=6000, d=20, k=5, box=4.0, seed=7), 5.0, 512)):
+        c = ora.scale(sigma, ofam)
+        tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda(), leaf_max=leaf_max)
+        bufs = fsg.fsg_build_graph(tree, fsg.params(sigma, kernel=fam), 16, 8)
+        assert fsg.fsg_sync(tree) == 0
+        q = np.arange(0, X.shape[0], 11)
+        want = ora.degrees(X, c, queries=q, kernel=ofam)
+        deg = bufs.deg.cpu().numpy()[q]
+        # FP32 bound of the degree at large d: a term with exponent a (log2
+        # units) computed from d rounded differences and sums carries
+        # ln2 a (d + 3) 2^-24 relative error, plus ex2's 2^-22 and the
+        # accumulation's (at most 96 roundings of 2^-24 on the way)
+        d = X.shape[1]
+        Xd = X.astype(np.float64)
+        if ofam == ora.LAPLACIAN:
+            dist = np.abs(Xd[q][:, None, :] - Xd[None, :, :]).sum(-1)
+        else:
+            dist = np.sqrt(((Xd[q][:, None, :] - Xd[None, :, :]) ** 2).sum(-1))
+        a = c * np.log2(np.e) * dist
+        kv = np.exp2(-a)
+        kv[np.arange(q.size), q] = 0.0
+        bound = (kv * a).sum(1) * np.log(2) * (d + 3) * 2.0 ** -24 + want * (2.0 ** -22 + 96 * 2.0 ** -24)
+        assert (np.abs(deg - want) <= np.maximum(bound, DEG_RTOL * want) + X.shape[0] * TINY).all()
+        osmp, _, _ = ora.sample(X, c, 16, 8, queries=q, kernel=ofam)
+        assert not ((bufs.samples.cpu().numpy()[q] != osmp) & (bufs.flags.cpu().numpy()[q] == 0)).any()
+        tree.close()
+
+
 def test_family_refused_outside_the_fused_fp32_path(fsg):
-    X = inputs.gaussian_mixture(n=6000, d=20, seed=1)
-    tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
-    with pytest.raises(fsg.FsgError) as e:  # d > 16
-        fsg.fsg_degrees(tree, fsg.params(1.5, kernel=fsg.FSG_KERNEL_LAPLACIAN))
-    assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
-    tree.close()
     X = inputs.gaussian_mixture(n=6000, d=8, seed=1)
     tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
     for kw in (dict(schedule=fsg.FSG_SCHED_LEVELWISE), dict(precision=fsg.FSG_PREC_SPLIT_BF16)):
