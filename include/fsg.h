@@ -78,8 +78,10 @@ extern "C" {
  * (exponential, scale 1/sigma).  The Laplacian and exponential kernels run on
  * the fused schedule's FP32 paths: for d <= 16 with bins of 65..128 points
  * (the default tree for most n from 65 to 262,144 at d <= 16), and for any
- * d > 16 (FSG_PREC_AUTO then means FP32, also on 8-bit data); elsewhere
- * (levelwise schedules, split and tensor-core precisions, fsg_params.resolve,
+ * d > 16.  The exponential also runs on the exact 8-bit tensor-core path
+ * (FSG_PREC_EXACT_INT, or AUTO on 8-bit data with d >= 64: the square root of
+ * the exact integer squared distance); for the Laplacian AUTO means FP32.
+ * Elsewhere (levelwise schedules, the split precision, fsg_params.resolve,
  * weight_f64) FSG_ERR_UNSUPPORTED. */
 #define FSG_KERNEL_GAUSSIAN 0
 #define FSG_KERNEL_LAPLACIAN 1

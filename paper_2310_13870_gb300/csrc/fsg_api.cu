@@ -45,11 +45,12 @@ int check_params(const fsg_params* p) {
     return FSG_OK;
 }
 
-// The arithmetic a call runs: AUTO takes the tensor-core forms for the
-// Gaussian kernel only (the other families' exponents are not the expanded
-// squared distance), so for them AUTO means FP32.
+// The arithmetic a call runs.  The tensor-core forms get the squared
+// distance from the expanded dot product: the Gaussian's exponent, and the
+// exponential's after a square root (exact integers on 8-bit data).  The
+// Laplacian's l1 distance has no such form, so for it AUTO means FP32.
 int eff_precision(const fsg_params* p) {
-    return p->kernel != FSG_KERNEL_GAUSSIAN && p->precision == FSG_PREC_AUTO ? FSG_PREC_FP32 : p->precision;
+    return p->kernel == FSG_KERNEL_LAPLACIAN && p->precision == FSG_PREC_AUTO ? FSG_PREC_FP32 : p->precision;
 }
 
 KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
@@ -152,10 +153,12 @@ int check_path(const fsg_tree* t, const fsg_params* p) {
     if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
     // the Laplacian and exponential kernels: the fused schedule's FP32 paths
     // (d <= 16: the symmetric bin pass and the 128-point leaf kernel; d > 16:
-    // the generic passes and leaf kernels)
+    // the generic passes and leaf kernels); the exponential also on the exact
+    // 8-bit tensor-core path
     if (p->kernel != FSG_KERNEL_GAUSSIAN &&
-        ((p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32) || p->schedule != FSG_SCHED_FUSED ||
-         (t->d <= kMaxFmaDim && (!kde_bins_sym_supported(t) || !use_leaf128(t)))))
+        ((p->precision != FSG_PREC_AUTO && p->precision != FSG_PREC_FP32 &&
+          !(p->precision == FSG_PREC_EXACT_INT && p->kernel == FSG_KERNEL_EXPONENTIAL)) ||
+         p->schedule != FSG_SCHED_FUSED || (t->d <= kMaxFmaDim && (!kde_bins_sym_supported(t) || !use_leaf128(t)))))
         return FSG_ERR_UNSUPPORTED;
     // the approximate bin pass is the split form's tile pruning
     if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED))

@@ -3,7 +3,8 @@
 // coordinates are integers 0..255, exact in BF16, so every product of the
 // dot-product GEMM is exact and only its FP32 accumulation rounds:
 //   ||x - y||^2 = ||x||^2 + ||y||^2 - 2 x.y   (integer units, exact norms),
-//   k = ex2(neg_c / 255^2 * ||x - y||^2).
+//   k = ex2(neg_c / 255^2 * ||x - y||^2),
+// or for the exponential kernel k = ex2(neg_c / 255 * sqrt(||255 x - 255 y||^2)).
 //
 // CTA = one block of 128 queries x one chunk of bins (their points), 10 warps:
 //   warp 0 (one thread): TMA producer, 4-stage ring of {A: 128 query rows,
@@ -57,7 +58,7 @@ constexpr uint32_t kIdesc = idesc_bf16(kTcM, kTcN);
 // per (point, bin) and CTA goes into bin sums zeroed beforehand.  A bin meets at most two row
 // tiles, so every such sum receives at most two additions onto zero, whose
 // result does not depend on their order.
-template <int EW, int ST, bool SYM>
+template <int EW, int ST, bool SYM, bool EXPD>
 __global__ void __launch_bounds__(64 + 32 * EW, 1)
 kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
@@ -259,9 +260,9 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 if (cc + 32 < kCols) tmem_issue32(tcol + (uint32_t)(cc + 32), rb[cur ^ 1]);
                 float v[32];
                 if (check)
-                    tc_values32<true>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
+                    tc_values32<true, EXPD>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
                 else
-                    tc_values32<false>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
+                    tc_values32<false, EXPD>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
                 if (SYM && !rvalid) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = 0.f;
@@ -481,9 +482,16 @@ int64_t kde_bins_tc_evals(const fsg_tree* t) {
     return (t->n * t->n + sq) / 2;
 }
 
-cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    // integer units: ||255 x - 255 y||^2 = 255^2 ||x - y||^2
-    const float nc = kp.neg_c / (255.f * 255.f);
+// The scale of the exponent in integer units: ||255 x - 255 y||^2 = 255^2
+// ||x - y||^2 for the Gaussian, its square root 255 ||x - y|| for the
+// exponential kernel.
+static float tc_neg_c(const KernelParams& kp) {
+    return kp.family == kFamExp ? kp.neg_c / 255.f : kp.neg_c / (255.f * 255.f);
+}
+
+template <bool EXPD>
+cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    const float nc = tc_neg_c(kp);
     const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(t->tmap_a);
     const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(t->tmap_b);
     const int G = tc_sym_bins(t);
@@ -491,7 +499,7 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
         const int nchunk = (t->nb + G - 1) / G;
         const int tmax = (int)((((int64_t)G * t->mmax) + kTcM - 1) / kTcM);
         const size_t smem = tc_bins_smem(kTcEpiWarps, G, kTcSymStages, true);
-        auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcSymStages, true>;
+        auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcSymStages, true, EXPD>;
         cudaError_t e = set_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
         // the sums that the mirrored values reach are accumulated onto zero
@@ -511,7 +519,7 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
     if (t->tune.tc_bins > 0 && t->tune.tc_bins < bpc) bpc = t->tune.tc_bins;
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = tc_bins_smem(kTcEpiWarps, bpc, kTcStages, false);
-    auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcStages, false>;
+    auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcStages, false, EXPD>;
     {
         const cudaError_t e = set_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
@@ -520,6 +528,10 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
     kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, t->norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc,
                                                    chunks, nc, kp.self_exclude, t->ws.binsum, t->status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    return kp.family == kFamExp ? launch_kde_bins_tc_f<true>(t, kp, s) : launch_kde_bins_tc_f<false>(t, kp, s);
 }
 
 }  // namespace fsg
@@ -586,6 +598,7 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
                       uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
                       unsigned long long* __restrict__ n_items, int32_t* __restrict__ status) {
     const int self_exclude = kp.self_exclude;
+    const bool expd = kp.family == kFamExp;  // exponential kernel: the distance, not its square
     const int b = blockIdx.x;
     const int seg = bin_off[b * kBinSlots];
     const int cnt = bin_off[(b + 1) * kBinSlots] - seg;
@@ -749,14 +762,14 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
             if (c0 + 32 <= N) {
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float arg = fmaf(-2.f, v[j], nq + pnorm[c0 + j]);
-                    vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                    const float arg = fmaxf(fmaf(-2.f, v[j], nq + pnorm[c0 + j]), 0.f);
+                    vr[c0 + j] = ex2_approx((expd ? sqrt_approx(arg) : arg) * neg_c);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {  // N - c0 = 16
-                    const float arg = fmaf(-2.f, v[j], nq + pnorm[c0 + j]);
-                    vr[c0 + j] = ex2_approx(fmaxf(arg, 0.f) * neg_c);
+                    const float arg = fmaxf(fmaf(-2.f, v[j], nq + pnorm[c0 + j]), 0.f);
+                    vr[c0 + j] = ex2_approx((expd ? sqrt_approx(arg) : arg) * neg_c);
                 }
             }
             if (sc >= c0 && sc < c0 + 32) vr[sc] = 0.f;
@@ -865,7 +878,7 @@ cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cud
     const auto& ws = t->ws;
     leaf_values_tc_kernel<<<grid, kLvThreads, smem, s>>>(
         *reinterpret_cast<const CUtensorMap*>(t->tmap_p), reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms,
-        t->dpad, nmax, t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, kp.neg_c / (255.f * 255.f), t->s0,
+        t->dpad, nmax, t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, tc_neg_c(kp), t->s0,
         ws.leaf_pos, ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
         reinterpret_cast<unsigned long long*>(&ws.stats->n_items), t->status);
     return cudaGetLastError();

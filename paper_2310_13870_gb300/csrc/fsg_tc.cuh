@@ -117,7 +117,9 @@ __device__ __forceinline__ float tree_sum32(float (&x)[32]) {
 
 // Kernel values v[0..31] of 32 columns of one row from its 32 dot products.
 // CHECK: test for the ragged end (p >= pe) and the query's own position.
-template <bool CHECK>
+// EXPD: the exponential kernel (Sec. 2.1), whose exponent scales the
+// Euclidean distance, the square root of the exact integer squared distance.
+template <bool CHECK, bool EXPD = false>
 __device__ __forceinline__ void tc_values32(const uint32_t (&r)[32], const float* __restrict__ pn, int pc, float nq,
                                             float neg_c, int q, int pe, int self_exclude, float (&v)[32]) {
     const uint64_t nq2 = f2_pack(nq, nq), m2 = f2_pack(-2.f, -2.f), nc2 = f2_pack(neg_c, neg_c);
@@ -127,7 +129,12 @@ __device__ __forceinline__ void tc_values32(const uint32_t (&r)[32], const float
         const uint64_t arg = f2_fma(m2, f2_pack(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
                                     f2_add(nq2, f2_pack(pn[j], pn[j + 1])));
         const float2 a = f2_unpack(arg);
-        const float2 e = f2_unpack(f2_mul(f2_pack(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f)), nc2));
+        float x0 = fmaxf(a.x, 0.f), x1 = fmaxf(a.y, 0.f);
+        if (EXPD) {
+            x0 = sqrt_approx(x0);
+            x1 = sqrt_approx(x1);
+        }
+        const float2 e = f2_unpack(f2_mul(f2_pack(x0, x1), nc2));
         float k0 = ex2_approx(e.x), k1 = ex2_approx(e.y);
         if (CHECK) {
             if (pc + j >= pe || (self_exclude && pc + j == q)) k0 = 0.f;

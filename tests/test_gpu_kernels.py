@@ -1,10 +1,11 @@
 """The Laplacian and exponential kernels of Sec. 2.1 (fsg_params.kernel) on
 the fused schedule's FP32 paths (d <= 16: the symmetric bin pass and the
 128-point leaf kernel; d > 16: the generic passes and leaf kernels, also for
-8-bit data, where AUTO means FP32 for these families), against the FP64
-oracle of the same family: degrees within the FP32 tolerance, unflagged
-samples equal to the oracle's, edge weights within 1e-4; refused where the
-path does not offer them."""
+8-bit data under the Laplacian, where AUTO means FP32) and, for the
+exponential, the exact 8-bit tensor-core path, against the FP64 oracle of the
+same family: degrees within the FP32 tolerance, unflagged samples equal to
+the oracle's, edge weights within 1e-4; refused where the path does not
+offer them."""
 import math
 
 import numpy as np
@@ -100,9 +101,10 @@ def test_families_differ_from_the_gaussian(fsg):
 
 @pytest.mark.parametrize("name", ["laplacian", "exponential"])
 def test_family_on_8bit_data_and_large_bins(fsg, name):
-    # digit-like 8-bit data (AUTO would take the tensor-core form for the
-    # Gaussian) and a tree with bins of up to 512 points (the two-kernel
-    # generic leaf phase: values in HBM, then the leaf finish)
+    # digit-like 8-bit data (AUTO takes the FP32 generic passes for the
+    # Laplacian, the tensor-core form for the exponential) and a tree with
+    # bins of up to 512 points (the two-kernel generic leaf phase: values in
+    # HBM, then the leaf finish)
     fam, ofam = family_pair(fsg, name)
     for X, sigma, leaf_max in ((inputs.digit_like(n=2500, d=784, seed=6), 9.0, 0),
                                (inputs.gaussian_mixture(n=6000, d=20, k=5, box=4.0, seed=7), 5.0, 512)):
@@ -133,6 +135,48 @@ def test_family_on_8bit_data_and_large_bins(fsg, name):
         tree.close()
 
 
+@pytest.mark.parametrize("n,d,sigma,L,seed", [
+    (3000, 784, 9.0, 32, 1),     # the digit workload's dimension
+    (2311, 64, 4.0, 16, 2),      # ragged n, the smallest d of the tensor-core path
+])
+def test_exponential_on_the_tensor_core_path(fsg, n, d, sigma, L, seed):
+    # 8-bit data: AUTO takes the exact tensor-core path for the exponential
+    # kernel (the square root of the exact integer squared distance), the
+    # same result as FSG_PREC_EXACT_INT, near the FP32 path's and the oracle's
+    fam, ofam = family_pair(fsg, "exponential")
+    X = inputs.digit_like(n=n, d=d, seed=seed)
+    c = ora.scale(sigma, ofam)
+    tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
+    p_auto = fsg.params(sigma, kernel=fam)
+    p_int = fsg.params(sigma, kernel=fam, precision=fsg.FSG_PREC_EXACT_INT)
+    p_fp32 = fsg.params(sigma, kernel=fam, precision=fsg.FSG_PREC_FP32)
+    assert fsg.fsg_bin_pass_evals(tree, p_auto) == fsg.fsg_bin_pass_evals(tree, p_int)
+    assert fsg.fsg_bin_pass_evals(tree, p_auto) != fsg.fsg_bin_pass_evals(tree, p_fp32)
+    out = {}
+    for name, p in (("auto", p_auto), ("int", p_int), ("fp32", p_fp32)):
+        b = fsg.fsg_build_graph(tree, p, L, seed)
+        assert fsg.fsg_sync(tree) == 0
+        m = int(b.m.item())
+        out[name] = (b.deg.cpu().numpy(), b.samples.cpu().numpy(), b.flags.cpu().numpy(),
+                     b.src[:m].cpu().numpy(), b.dst[:m].cpu().numpy(), b.w[:m].cpu().numpy(), fsg.stats_dict(b))
+    tree.close()
+    deg, samples, flags, src, dst, w, st = out["auto"]
+    assert st["status"] == 0
+    np.testing.assert_array_equal(deg, out["int"][0])
+    np.testing.assert_array_equal(samples, out["int"][1])
+    np.testing.assert_allclose(deg, out["fp32"][0], rtol=2 * DEG_RTOL)
+    q = np.arange(0, n, 5)
+    want = ora.degrees(X, c, queries=q, kernel=ofam)
+    assert (np.abs(deg[q] - want) <= DEG_RTOL * want + n * TINY).all(), float((np.abs(deg[q] - want) / want).max())
+    osmp, _, _ = ora.sample(X, c, L, seed, queries=q, kernel=ofam)
+    assert not ((samples[q] != osmp) & (flags[q] == 0)).any()
+    assert st["n_flagged"] <= 0.01 * n * L
+    sel = np.arange(0, src.size, max(1, src.size // 2000))
+    odeg = ora.degrees(X, c, kernel=ofam)
+    _, ow = ora.weights(X, c, L, odeg, src[sel], dst[sel], kernel=ofam)
+    np.testing.assert_allclose(w[sel], ow, rtol=W_RTOL)
+
+
 def test_family_refused_outside_the_fused_fp32_path(fsg):
     X = inputs.gaussian_mixture(n=6000, d=8, seed=1)
     tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
@@ -140,4 +184,10 @@ def test_family_refused_outside_the_fused_fp32_path(fsg):
         with pytest.raises(fsg.FsgError) as e:
             fsg.fsg_degrees(tree, fsg.params(1.5, kernel=fsg.FSG_KERNEL_EXPONENTIAL, **kw))
         assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
+    tree.close()
+    # the Laplacian's l1 distance has no dot-product form: no tensor-core path
+    tree = fsg.fsg_build_tree(torch.from_numpy(inputs.digit_like(n=2000, d=784, seed=2)).cuda())
+    with pytest.raises(fsg.FsgError) as e:
+        fsg.fsg_degrees(tree, fsg.params(9.0, kernel=fsg.FSG_KERNEL_LAPLACIAN, precision=fsg.FSG_PREC_EXACT_INT))
+    assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
     tree.close()
