@@ -260,6 +260,38 @@ def sub_digits(fsg, stream, flush, steps):
     q = np.random.Generator(np.random.PCG64(21)).choice(n, size=256, replace=False)
     want = ora.degrees(X, ora.gamma(sigma), queries=q)
     rel = np.abs(bufs.deg.cpu().numpy()[q] - want) / want
+    # the same input in split precision (three-part BF16 operands, six
+    # products per coordinate, the FP32-data form at d > 64)
+    ps = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16)
+
+    def step_split():
+        fsg.fsg_tree_update(tree, pts, stream=stream)
+        fsg.fsg_build_graph(tree, ps, L, seed, bufs=bufs, stream=stream)
+
+    for _ in range(3):
+        step_split()
+    fsg.fsg_profile(tree, True)
+    skde, sms = [], []
+    for _ in range(steps):
+        sms += timed_steps(step_split, 1, stream, flush)
+        skde.append(fsg.fsg_profile_read(tree)[0]["kde_bins"])
+    fsg.fsg_profile(tree, False)
+    assert fsg.fsg_sync(tree, stream=stream) == 0
+    sst = fsg.stats_dict(bufs)
+    srel = np.abs(bufs.deg.cpu().numpy()[q] - want) / want
+    dpad = 64 * ((d + 63) // 64)
+    spairs = sst["n_bin_evals"]
+    sflops = 12.0 * dpad * spairs  # six BF16 products over the padded coordinates, per executed pair
+    sach = sflops / (statistics.mean(skde) * 1e-3) / 1e12
+    st_split = {"precision": "split: three-part BF16 operands, six tcgen05 products per coordinate (FP32 data form)",
+                "value": n * L / (statistics.mean(sms) * 1e-3), "unit": UNIT, "ms_per_step": statistics.mean(sms),
+                "flagged_samples": sst["n_flagged"], "flag_eps": 2.0 ** -10,
+                "roofline": {"bound": "tensor", "kernel": "kde_bins_tc_kernel (symmetric, split operands)",
+                             "achieved": sach, "peak": peak, "unit": "TFLOP/s", "frac": sach / peak,
+                             "kde_bins_ms": statistics.mean(skde), "executed_pairs": int(spairs),
+                             "flops_per_launch": sflops, "peak_basis": basis},
+                "kde_error": {"max_rel": float(srel.max()), "mean_rel": float(srel.mean()), "queries": int(q.size),
+                              "kind": "degrees vs the FP64 oracle"}}
     tree.close()
     return {"workload": "digit_like n=70000 d=784 (10 prototypes, 8-bit) sigma=median/2 L=64 seed=0",
             "precision": "exact 8-bit tcgen05 bin pass (BF16 products of k/255 data, FP32 accumulate)",
@@ -270,7 +302,8 @@ def sub_digits(fsg, stream, flush, steps):
                          "executed_pairs": int(pairs), "flops_per_launch": 2.0 * pairs * d,
                          "algorithmic_pairs": n * n, "peak_basis": basis},
             "kde_error": {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "queries": int(q.size),
-                          "kind": "degrees (Eq. 1 over all points) vs the FP64 oracle"}}
+                          "kind": "degrees (Eq. 1 over all points) vs the FP64 oracle"},
+            "split_precision": st_split}
 
 
 def sub_seg_batch(fsg, stream, flush, steps):
@@ -425,8 +458,9 @@ def run_ours(args):
         raise SystemExit("--resolve takes the FP32 fused path (not --precision split)")
     p = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16 if split else fsg.FSG_PREC_AUTO, kde_eps=args.kde_eps,
                    resolve=args.resolve)
-    # split form: the spatial tree order, computed on the GPU in every step (fsg_tree_update)
-    order = fsg.FSG_ORDER_SPATIAL if split else fsg.FSG_ORDER_IDENTITY
+    # split form at d <= 64: the spatial tree order (its tiles are centred),
+    # computed on the GPU in every step (fsg_tree_update); d > 64 needs none
+    order = fsg.FSG_ORDER_SPATIAL if split and d <= 64 else fsg.FSG_ORDER_IDENTITY
     with torch.cuda.stream(stream):
         pts = torch.from_numpy(X).cuda()
         tree = fsg.fsg_build_tree(pts, stream=stream, order=order)
@@ -492,7 +526,8 @@ def run_ours(args):
         # split form: six BF16 products per coordinate over 64 padded coordinates,
         # for the pairs it executes (tile pairs whose values are all zero are skipped)
         pairs = st["n_bin_evals"] if split else fsg.fsg_bin_pass_evals(tree, p)
-        kpad = 16 * ((d + 15) // 16)  # coordinates the split form's MMAs run (K-steps of 16)
+        # coordinates the split form's MMAs run: K-steps of 16 (d <= 64), K chunks of 64 (d > 64)
+        kpad = 16 * ((d + 15) // 16) if d <= 64 else 64 * ((d + 63) // 64)
         achieved = (12.0 * pairs * kpad if split else 2.0 * pairs * d) / (kde_avg * 1e-3) / 1e12
         peaks = {}
         pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -500,9 +535,11 @@ def run_ours(args):
             with open(pf) as f:
                 peaks = json.load(f)
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "kernel": "kde_bins_split_kernel" if split else "kde_bins_tc_kernel",
+        roof = {"bound": "tensor", "kernel": "kde_bins_split_kernel" if split and d <= 64 else "kde_bins_tc_kernel",
                 "achieved": achieved, "peak": peak,
-                **({"executed_pairs": int(pairs), "skipped_fraction": 1.0 - pairs / (n * n)} if split else {}),
+                **({"executed_pairs": int(pairs), "skipped_fraction": 1.0 - pairs / (n * n)} if split and d <= 64
+                   else {"executed_pairs": int(pairs), "note": "symmetric pass: each pair once off the diagonal"}
+                   if split else {}),
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_basis": "measured cuBLAS BF16 sustained (MEASURED_PEAKS.json)" if peaks else "fallback"}
         if split:
@@ -727,7 +764,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16x3 split, f32 accumulate" if split else "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, parallelism=f"replicas x{world} (independent point sets)",
-                               **({"precision": "split (spatial tree order, GPU, in the step)"} if split else {}),
+                               **({"precision": "split (spatial tree order, GPU, in the step)" if d <= 64 else
+                                   "split (three-part BF16 operands, identity tree order)"} if split else {}),
                                **({"kde_eps": args.kde_eps} if args.kde_eps > 0 else {}),
                                **({"resolve": True} if args.resolve else {})),
                 "gkernel_evals_per_s": gevals, "evals_per_step": evals_per_step, "edges_per_step": m,
@@ -976,7 +1014,8 @@ def main():
     ap.add_argument("--kde-eps", type=float, default=0.0,
                     help="approximate KDE (tree-pruned split bin pass) with this relative error bound")
     ap.add_argument("--precision", choices=["auto", "split"], default="auto",
-                    help="mixture workload, d <= 64: split-precision tensor-core bin pass on a spatial tree order")
+                    help="split-precision tensor-core bin pass (d <= 64: centred tiles on a spatial tree order; "
+                         "d > 64, e.g. --workload digits: three-part operands)")
     args = ap.parse_args()
     if args.n:
         set_size(args.n)

@@ -105,8 +105,11 @@ void begin_call(fsg_tree* t) {
 bool use_tc(const fsg_tree* t, int precision) {
     return precision == FSG_PREC_EXACT_INT || (precision == FSG_PREC_AUTO && kde_bins_tc_supported(t));
 }
+// The split form at d > 64: the tensor-core kernels on the three-part image.
+bool use_splitk(const fsg_tree* t, int precision) { return precision == FSG_PREC_SPLIT_BF16 && t->d > 64; }
 
 cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+    if (use_splitk(t, kp.precision)) return launch_kde_bins_tc(t, kp, s);
     if (kp.precision == FSG_PREC_SPLIT_BF16) return launch_kde_bins_split(t, kp, s);
     if (use_tc(t, kp.precision)) return launch_kde_bins_tc(t, kp, s);
     if (t->d > kMaxFmaDim) return launch_kde_bins_generic(t, kp, s);
@@ -119,7 +122,7 @@ cudaError_t run_kde_bins(const fsg_tree* t, const KernelParams& kp, cudaStream_t
 // other d > 16 bins: leaf values, then the leaf finish; d <= 16: the leaf
 // finish evaluates its own values.
 cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    if (t->d > kMaxFmaDim && use_tc(t, kp.precision) && (1 << t->dm) <= 256) {
+    if (t->d > kMaxFmaDim && (use_tc(t, kp.precision) || use_splitk(t, kp.precision)) && (1 << t->dm) <= 256) {
         t->launches += 1;
         return launch_leaf_values_tc(t, kp, s);
     }
@@ -143,14 +146,15 @@ cudaError_t run_leaf_phase(fsg_tree* t, const KernelParams& kp, cudaStream_t s) 
 
 // Kernel evaluations the bin pass executes (n^2, or about n^2/2 when symmetric).
 int64_t bin_pass_evals(const fsg_tree* t, int precision) {
-    if (use_tc(t, precision)) return kde_bins_tc_evals(t);
+    if (use_tc(t, precision) || use_splitk(t, precision)) return kde_bins_tc_evals(t);
     if (precision == FSG_PREC_SPLIT_BF16) return t->n * t->n;
     if (t->d <= kMaxFmaDim) return kde_bins_sym_supported(t) ? kde_bins_sym_evals(t) : t->n * t->n;
     return kde_bins_generic_sym_supported(t) ? kde_bins_generic_sym_evals(t) : t->n * t->n;
 }
 
 int check_path(const fsg_tree* t, const fsg_params* p) {
-    if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t)) return FSG_ERR_UNSUPPORTED;
+    if (p->precision == FSG_PREC_SPLIT_BF16 && !kde_bins_split_supported(t) && !splitk_supported(t))
+        return FSG_ERR_UNSUPPORTED;
     // the Laplacian and exponential kernels: the fused schedule's FP32 paths
     // (d <= 16: the symmetric bin pass and the 128-point leaf kernel; d > 16:
     // the generic passes and leaf kernels); the exponential also on the exact
@@ -160,8 +164,9 @@ int check_path(const fsg_tree* t, const fsg_params* p) {
           !(p->precision == FSG_PREC_EXACT_INT && p->kernel == FSG_KERNEL_EXPONENTIAL)) ||
          p->schedule != FSG_SCHED_FUSED || (t->d <= kMaxFmaDim && (!kde_bins_sym_supported(t) || !use_leaf128(t)))))
         return FSG_ERR_UNSUPPORTED;
-    // the approximate bin pass is the split form's tile pruning
-    if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED))
+    // the approximate bin pass is the split form's tile pruning (d <= 64)
+    if (p->kde_eps > 0.f && (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED ||
+                             !kde_bins_split_supported(t)))
         return FSG_ERR_UNSUPPORTED;
     if (p->precision == FSG_PREC_EXACT_INT && !kde_bins_tc_supported(t)) return FSG_ERR_UNSUPPORTED;
     // the high-precision re-decision re-reads the fused schedule's bin sums (Gaussian kernel)
@@ -241,10 +246,33 @@ void workspace_sizes(int64_t n, int d, int dm, int nb, int64_t Lc, size_t (&sz)[
 }
 }  // namespace
 
-// The split-precision pass's workspace: bin and tile boxes, the query tiles'
-// split images (allocated on first use).
+// The split-precision pass's workspace (allocated on first use): for d <= 64
+// bin and tile boxes and the query tiles' split images; for d > 64 the
+// three-part image of the points (refilled by fsg_tree_update).
 int ensure_split(fsg_tree* t, const fsg_params* p, cudaStream_t s) {
-    if (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED || t->sboxes) return FSG_OK;
+    if (p->precision != FSG_PREC_SPLIT_BF16 || p->schedule != FSG_SCHED_FUSED) return FSG_OK;
+    if (t->d > 64) {
+        if (t->Xs) return FSG_OK;
+        const int dpad = (t->d + 63) / 64 * 64;
+        const size_t xbytes = sizeof(uint16_t) * 3 * (size_t)dpad * (size_t)t->n_pad;
+        if (tree_malloc(t, &t->Xs, xbytes, s) != cudaSuccess ||
+            tree_malloc(t, (void**)&t->snorms, sizeof(float) * (size_t)t->n_pad, s) != cudaSuccess) {
+            cudaGetLastError();
+            tree_free(t, t->Xs);
+            t->Xs = nullptr;
+            return FSG_ERR_OOM;
+        }
+        if (cudaMemsetAsync(t->Xs, 0, xbytes, s) != cudaSuccess) return FSG_ERR_CUDA;
+        const int rc = splitk_prepare(t, s);
+        if (rc != FSG_OK) {
+            tree_free(t, t->Xs);
+            tree_free(t, t->snorms);
+            t->Xs = nullptr;
+            t->snorms = nullptr;
+        }
+        return rc;
+    }
+    if (t->sboxes) return FSG_OK;
     if (tree_malloc(t, (void**)&t->sboxes, split_workspace_bytes(t->n, t->nb, leaf_split_tc_supported(t)), s) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -456,6 +484,8 @@ void fsg_free_tree(fsg_tree* t) {
     tree_free(t, t->sboxes);
     tree_free(t, t->ord);
     tree_free(t, t->rs.base);
+    tree_free(t, t->Xs);
+    tree_free(t, t->snorms);
     if (t->Xb) cudaFree(t->Xb);
     if (t->norms) cudaFree(t->norms);
     delete t;
@@ -519,8 +549,9 @@ int fsg_autotune(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, int
         to_public(t->tune, out);
         return FSG_OK;
     }
-    const bool tc = use_tc(t, eff_precision(p));
-    const int path = tc ? 2 : (t->d <= kMaxFmaDim && kde_bins_sym_supported(t)) ? 1 : 0;
+    const bool tc = use_tc(t, eff_precision(p)) || use_splitk(t, eff_precision(p));
+    const int path = use_splitk(t, eff_precision(p)) ? 3 : tc ? 2
+                     : (t->d <= kMaxFmaDim && kde_bins_sym_supported(t)) ? 1 : 0;
     const TuneKey key{t->n, t->d, L, t->s0, t->mmax, path};
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -637,6 +668,10 @@ int fsg_tree_update(fsg_tree* t, const float* d_points, void* stream) {
         rc = tc_prepare(t, s);
         t->launches += 1;
     }
+    if (rc == FSG_OK && t->Xs) {  // refresh the split form's three-part image
+        rc = splitk_prepare(t, s);
+        t->launches += 1;
+    }
     return rc;
 }
 
@@ -714,9 +749,11 @@ static int run_sampling(fsg_tree* t, const KernelParams& kp, int schedule, doubl
 }
 
 // Evaluations of the bin pass (every query against every point), counted on
-// the host; the levelwise schedule counts its own on the device.
+// the host; the levelwise schedule and the split pass for d <= 64 (which
+// skips tiles) count their own on the device.
 static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
-    if (p->schedule != FSG_SCHED_FUSED || p->precision == FSG_PREC_SPLIT_BF16) return 0;
+    if (p->schedule != FSG_SCHED_FUSED || (p->precision == FSG_PREC_SPLIT_BF16 && !use_splitk(t, p->precision)))
+        return 0;
     return bin_pass_evals(t, eff_precision(p));
 }
 
@@ -724,7 +761,7 @@ static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
 __global__ static void stats_finish_kernel(fsg_stats* st, int64_t n_samples, int64_t bin_evals,
                                            const int32_t* status, const int32_t* n_resolved, fsg_stats* out) {
     st->n_samples = n_samples;
-    st->n_evals += bin_evals;       // the split pass counts its own on the device
+    st->n_evals += bin_evals;       // the split pass for d <= 64 counts its own on the device
     st->n_bin_evals += bin_evals;
     st->status = status[0];
     st->n_resolved = n_resolved ? *n_resolved : 0;

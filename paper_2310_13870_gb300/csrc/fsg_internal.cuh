@@ -124,6 +124,15 @@ struct fsg_tree {
     alignas(64) unsigned char tmap_a[128] = {};
     alignas(64) unsigned char tmap_b[128] = {};
     alignas(64) unsigned char tmap_p[128] = {};  // 16-row boxes: point rows of the tensor-core leaf kernel
+    // split-precision tensor-core path for d > 64 (FSG_PREC_SPLIT_BF16, made
+    // on first use): every coordinate as three BF16 parts, [n_pad][3 dpad]
+    // (all hi, then all mid, then all lo), the squared norms (FP64 sums
+    // rounded once) and TMA descriptors with the same boxes as above
+    void* Xs = nullptr;
+    float* snorms = nullptr;
+    alignas(64) unsigned char tmap_sa[128] = {};
+    alignas(64) unsigned char tmap_sb[128] = {};
+    alignas(64) unsigned char tmap_sp[128] = {};
     fsg::Workspace ws;
     fsg::ResolveWs rs;
     fsg::LaunchTuning tune;
@@ -231,6 +240,12 @@ bool kde_bins_generic_sym_supported(const fsg_tree* t);
 size_t generic_tile_bytes(int64_t n, int32_t d);
 int64_t kde_bins_generic_sym_evals(const fsg_tree* t);
 int tc_prepare(fsg_tree* t, cudaStream_t s);
+// The three-part BF16 image of the points for the split form at d > 64
+// (allocated and described on the first call, refilled on every call).
+int splitk_prepare(fsg_tree* t, cudaStream_t s);
+// The split form at d > 64 runs the tensor-core bin pass and leaf kernel on
+// the three-part image (bins of at least 33 points).
+bool splitk_supported(const fsg_tree* t);
 bool kde_bins_tc_supported(const fsg_tree* t);
 // Pairs the tensor-core bin pass evaluates (symmetric form: each pair once
 // outside the diagonal chunks).

@@ -19,6 +19,16 @@
 //                        and added half 0 + half 1 at the end.
 // Every mbarrier wait is bounded; on a timeout the CTA records
 // FSG_ERR_TIMEOUT, stops, waits (bounded) for its MMAs and frees TMEM.
+//
+// The same kernels serve the split precision (FSG_PREC_SPLIT_BF16) for FP32
+// data at d > 64.  Each coordinate is held as three BF16 parts, x = hi + mid
+// + lo exactly (each part the BF16 rounding of what the previous ones leave),
+// in one row of 3 dpad values; x.y is accumulated in FP32 in TMEM from six of
+// the nine part products, the small ones first (lo.hi, hi.lo, mid.mid,
+// mid.hi, hi.mid, hi.hi: the three left out lie below 2^-24 of |x||y|), each
+// an exact BF16 product.  The K loop simply runs over 6 dpad / 64 chunks, the
+// chunk's A and B columns taken from the parts of the product it belongs
+// to; the epilogue is the 8-bit path's with data-unit norms.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -45,6 +55,23 @@ constexpr uint32_t kTmemCols = 512;
 
 constexpr uint32_t kIdesc = idesc_bf16(kTcM, kTcN);
 
+// Split form: the parts (0 hi, 1 mid, 2 lo) of A and of B in product j of a
+// K chunk's six, one nibble per product, small products first.
+constexpr uint32_t kSplitPartA = 0x001102u;  // lo, hi, mid, mid, hi, hi
+constexpr uint32_t kSplitPartB = 0x010120u;  // hi, lo, mid, hi, mid, hi
+// Column of virtual K chunk v (of kv = 6 kchunks in the split form, else v
+// itself) in the A and B rows.
+__device__ __forceinline__ void split_cols(int v, int kchunks, bool split, int& xa, int& xb) {
+    if (!split) {
+        xa = xb = v * kTcK;
+        return;
+    }
+    const int j = v / kchunks, k = v - j * kchunks;
+    const int dpad = kchunks * kTcK;
+    xa = (int)((kSplitPartA >> (4 * j)) & 0xFu) * dpad + k * kTcK;
+    xb = (int)((kSplitPartB >> (4 * j)) & 0xFu) * dpad + k * kTcK;
+}
+
 // SYM = false: CTA (x, y) = queries 128 x .. 128 x + 127 against the points
 // of bins y bpc .. y bpc + bpc - 1 (every pair evaluated, both orders).
 // SYM = true (the kernel is symmetric): bins are grouped in chunks of bpc; CTA
@@ -63,7 +90,7 @@ __global__ void __launch_bounds__(64 + 32 * EW, 1)
 kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
                    int bpc, int nchunk, float neg_c, int self_exclude, float* __restrict__ binsum,
-                   int32_t* __restrict__ status) {
+                   int32_t* __restrict__ status, int split) {
     extern __shared__ unsigned char smem_raw[];
     constexpr uint32_t kStage = kABytes + kBBytes;
     constexpr int kCols = kTcN / (EW / 4);  // columns of each epilogue warp per tile
@@ -148,14 +175,16 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const uint32_t tmem = *tmem_slot;
     const int pa = bnd_s[0], pe = bnd_s[nbc];
     const int ntile = (pe - pa + kTcN - 1) / kTcN;
-    const int total = ntile * kchunks;
+    const int kv = split ? 6 * kchunks : kchunks;  // K chunks of one tile
+    const int total = ntile * kv;
     volatile int32_t* abort_flag = flags;
     volatile int32_t* consumed = flags + 1;
     int mma_issued = 0;
     int issued = 0;  // TMA stages issued (producer thread)
 
-    // The points must be exact 8-bit values (checked when the tree is built or updated).
-    const bool inexact = status[1] != 0;
+    // The 8-bit form needs exact 8-bit values (checked when the tree is built
+    // or updated); the split form takes any FP32 data.
+    const bool inexact = !split && status[1] != 0;
 
     if (!inexact && warp == 0 && lane == 0) {
         // ---- TMA producer
@@ -165,11 +194,13 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 *abort_flag = 1;
                 break;
             }
-            const int tile = it / kchunks, kc = it - tile * kchunks;
+            const int tile = it / kv, kc = it - tile * kv;
+            int xa, xb;
+            split_cols(kc, kchunks, split != 0, xa, xb);
             unsigned char* st = base + s * kStage;
             mbar_arrive_expect_tx(&full[s], kStage);
-            tma_load_2d(st, &tmA, kc * kTcK, q0, &full[s]);
-            tma_load_2d(st + kABytes, &tmB, kc * kTcK, pa + tile * kTcN, &full[s]);
+            tma_load_2d(st, &tmA, xa, q0, &full[s]);
+            tma_load_2d(st + kABytes, &tmB, xb, pa + tile * kTcN, &full[s]);
             issued = it + 1;
         }
     } else if (!inexact && warp == 1 && lane == 0) {
@@ -183,8 +214,8 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             tc_fence_after();
             const uint32_t dt = tmem + (uint32_t)(a * kTcN);
             bool ok = true;
-            for (int kc = 0; kc < kchunks; ++kc) {
-                const int it = tile * kchunks + kc;
+            for (int kc = 0; kc < kv; ++kc) {
+                const int it = tile * kv + kc;
                 const int s = it % ST;
                 if (!mbar_wait_bounded(&full[s], (uint32_t)(it / ST) & 1u, status)) {
                     *abort_flag = 1;
@@ -370,6 +401,32 @@ __global__ void tc_prep_kernel(const float* __restrict__ Xt, int64_t n, int d, i
     }
 }
 
+// Split form: the three BF16 parts of every coordinate (x = hi + mid + lo:
+// each residual is exact in FP32, and the last one fits in eight bits) in
+// rows of 3 dpad values, and the squared norms summed in FP64 and rounded
+// once.  One warp per point.
+__global__ void splitk_prep_kernel(const float* __restrict__ Xt, int64_t n, int d, int dp, int dpad,
+                                   __nv_bfloat16* __restrict__ Xs, float* __restrict__ norms) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.y + threadIdx.y; p < n; p += (int64_t)gridDim.x * blockDim.y) {
+        double sq = 0.0;
+        __nv_bfloat16* row = Xs + (size_t)p * 3 * dpad;
+        for (int t = threadIdx.x; t < dpad; t += 32) {
+            const float x = t < d ? Xt[p * dp + t] : 0.f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const float r1 = __fsub_rn(x, __bfloat162float(hi));
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float r2 = __fsub_rn(r1, __bfloat162float(mid));
+            row[t] = hi;
+            row[dpad + t] = mid;
+            row[2 * dpad + t] = __float2bfloat16_rn(r2);
+            sq = fma((double)x, (double)x, sq);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (threadIdx.x == 0) norms[p] = (float)sq;
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -426,6 +483,43 @@ int tc_prepare(fsg_tree* t, cudaStream_t s) {
 }
 
 bool kde_bins_tc_supported(const fsg_tree* t) { return t->Xb != nullptr && t->d >= 64; }
+
+// Bins of at least 33 points: at most one bin ends in the 32 columns of an
+// epilogue step (or a single bin).
+bool splitk_supported(const fsg_tree* t) { return t->d > 64 && (t->nb == 1 || t->n / t->nb >= 33); }
+
+// Describes (every call: host-only) and fills the split form's image; Xs and
+// snorms are allocated by the caller ([n_pad][3 dpad] BF16, [n_pad] floats,
+// the padding rows zero).
+int splitk_prepare(fsg_tree* t, cudaStream_t s) {
+    const int dpad = (t->d + kTcK - 1) / kTcK * kTcK;
+    if (!t->Xs || !t->snorms) return FSG_ERR_INVALID_ARG;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (!enc) return FSG_ERR_UNSUPPORTED;
+    const cuuint64_t gdim[2] = {(cuuint64_t)(3 * dpad), (cuuint64_t)t->n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(3 * dpad) * 2};
+    const cuuint32_t estride[2] = {1, 1};
+    const cuuint32_t boxA[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
+    const cuuint32_t boxB[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcN};
+    const cuuint32_t boxP[2] = {(cuuint32_t)kTcK, 16u};
+    CUresult r1 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_sa), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xs, gdim,
+                      gstride, boxA, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_sb), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xs, gdim,
+                      gstride, boxB, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r3 = enc(reinterpret_cast<CUtensorMap*>(t->tmap_sp), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, t->Xs, gdim,
+                      gstride, boxP, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS) return FSG_ERR_UNSUPPORTED;
+    t->dpad = dpad;
+    dim3 block(32, 8);
+    int64_t g = (t->n + 7) / 8;
+    if (g > 152 * 64) g = 152 * 64;
+    splitk_prep_kernel<<<(int)g, block, 0, s>>>(t->Xt, t->n, t->d, t->dp, dpad,
+                                                reinterpret_cast<__nv_bfloat16*>(t->Xs), t->snorms);
+    return cudaGetLastError() == cudaSuccess ? FSG_OK : FSG_ERR_CUDA;
+}
 
 namespace {
 constexpr int kTcSymStages = 3;
@@ -486,14 +580,18 @@ int64_t kde_bins_tc_evals(const fsg_tree* t) {
 // ||x - y||^2 for the Gaussian, its square root 255 ||x - y|| for the
 // exponential kernel.
 static float tc_neg_c(const KernelParams& kp) {
+    if (kp.precision == FSG_PREC_SPLIT_BF16) return kp.neg_c;  // data units
     return kp.family == kFamExp ? kp.neg_c / 255.f : kp.neg_c / (255.f * 255.f);
 }
 
 template <bool EXPD>
 cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const float nc = tc_neg_c(kp);
-    const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(t->tmap_a);
-    const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(t->tmap_b);
+    const int split = kp.precision == FSG_PREC_SPLIT_BF16 ? 1 : 0;
+    if (split && !t->Xs) return cudaErrorInvalidValue;
+    const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(split ? t->tmap_sa : t->tmap_a);
+    const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(split ? t->tmap_sb : t->tmap_b);
+    const float* norms = split ? t->snorms : t->norms;
     const int G = tc_sym_bins(t);
     if (G > 0) {
         const int nchunk = (t->nb + G - 1) / G;
@@ -506,8 +604,8 @@ cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cuda
         e = cudaMemsetAsync(t->ws.binsum, 0, sizeof(float) * (size_t)t->n * t->nb, s);
         if (e != cudaSuccess) return e;
         dim3 grid(tmax, nchunk * (nchunk + 1) / 2);
-        kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, t->norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, G,
-                                                       nchunk, nc, kp.self_exclude, t->ws.binsum, t->status);
+        kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, G,
+                                                       nchunk, nc, kp.self_exclude, t->ws.binsum, t->status, split);
         return cudaGetLastError();
     }
     const int qblocks = (int)((t->n + kTcM - 1) / kTcM);
@@ -525,8 +623,8 @@ cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cuda
         if (e != cudaSuccess) return e;
     }
     dim3 grid(qblocks, chunks);
-    kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, t->norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc,
-                                                   chunks, nc, kp.self_exclude, t->ws.binsum, t->status);
+    kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc,
+                                                   chunks, nc, kp.self_exclude, t->ws.binsum, t->status, split);
     return cudaGetLastError();
 }
 
@@ -596,7 +694,7 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
                       const uint64_t* __restrict__ items_mask, const int32_t* __restrict__ perm, KernelParams kp,
                       float neg_c, int s0, int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp,
                       uint8_t* __restrict__ lflags, unsigned long long* __restrict__ n_evals,
-                      unsigned long long* __restrict__ n_items, int32_t* __restrict__ status) {
+                      unsigned long long* __restrict__ n_items, int32_t* __restrict__ status, int split) {
     const int self_exclude = kp.self_exclude;
     const bool expd = kp.family == kFamExp;  // exponential kernel: the distance, not its square
     const int b = blockIdx.x;
@@ -633,6 +731,8 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int kchunks = dpad / 64;
+    const int kv = split ? 6 * kchunks : kchunks;    // K chunks of one accumulation
+    const size_t rstride = split ? 3 * (size_t)dpad : (size_t)dpad;  // BF16 values per point row
     if (tid == 0) {
         for (int s = 0; s < kLvStages; ++s) {
             mbar_init(&done[s], 1);
@@ -669,14 +769,16 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     // (empty rows are 0), the point rows by TMA (one thread)
     auto fill = [&](int kc, int s) {
         unsigned char* st = base + s * ly.stage;
+        int xa, xb;
+        split_cols(kc, kchunks, split != 0, xa, xb);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            cp_async16(st + gdst + i * 4096, gsrc[i] + kc * 64, ((gbytes >> i) & 1u) ? 16 : 0);
+            cp_async16(st + gdst + i * 4096, gsrc[i] + xa, ((gbytes >> i) & 1u) ? 16 : 0);
         asm volatile("cp.async.commit_group;" ::: "memory");
         if (tid == 0) {
             mbar_arrive_expect_tx(&full[s], (uint32_t)N * 128u);
             for (int j = 0; j < N; j += kLvBox)
-                tma_load_2d(st + kA + (uint32_t)j * 128u, &tmP, kc * 64, p_lo + j, &full[s]);
+                tma_load_2d(st + kA + (uint32_t)j * 128u, &tmP, xb, p_lo + j, &full[s]);
             ++nfill;
         }
     };
@@ -698,17 +800,17 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int pos = rowpos[(tid >> 3) + 32 * i];
-            gsrc[i] = Xb + (size_t)(pos >= 0 ? pos : 0) * dpad + (tid & 7) * 8;
+            gsrc[i] = Xb + (size_t)(pos >= 0 ? pos : 0) * rstride + (tid & 7) * 8;
             gbytes |= (pos >= 0 ? 1u : 0u) << i;
         }
-        const int pre = min(kLvStages - 1, kchunks);
+        const int pre = min(kLvStages - 1, kv);
         for (int kc = 0; kc < pre; ++kc) {
             if (ok) ok = stage_free(g + kc);
             if (ok) fill(kc, (g + kc) % kLvStages);
         }
-        for (int kc = 0; kc < kchunks; ++kc) {
+        for (int kc = 0; kc < kv; ++kc) {
             const int gs = g + kc, s = gs % kLvStages;
-            if (kc + pre < kchunks) {
+            if (kc + pre < kv) {
                 if (ok) ok = stage_free(g + kc + pre);
                 if (ok) fill(kc + pre, (g + kc + pre) % kLvStages);
                 asm volatile("cp.async.wait_group %0;" ::"n"(kLvStages - 1) : "memory");
@@ -735,12 +837,12 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
                     }
                     mma_issued = true;
                     umma_commit(&done[s]);
-                    if (kc == kchunks - 1) umma_commit(accf);
+                    if (kc == kv - 1) umma_commit(accf);
                 }
             }
         }
         if (__syncthreads_or(!ok)) { ok = false; break; }
-        g += kchunks;
+        g += kv;
         // epilogue: item row r = TMEM lane (warps w and w + 4 read lanes
         // 32 (w % 4) .. + 31), half hh of the thread pair takes the 32-column
         // steps hh, hh + 2, ...
@@ -876,11 +978,14 @@ cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cud
     if (S > 65535) S = 65535;
     dim3 grid(t->nb, (unsigned)S);
     const auto& ws = t->ws;
+    const int split = kp.precision == FSG_PREC_SPLIT_BF16 ? 1 : 0;
+    if (split && !t->Xs) return cudaErrorInvalidValue;
     leaf_values_tc_kernel<<<grid, kLvThreads, smem, s>>>(
-        *reinterpret_cast<const CUtensorMap*>(t->tmap_p), reinterpret_cast<const __nv_bfloat16*>(t->Xb), t->norms,
-        t->dpad, nmax, t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, tc_neg_c(kp), t->s0,
-        ws.leaf_pos, ws.ksmp, ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
-        reinterpret_cast<unsigned long long*>(&ws.stats->n_items), t->status);
+        *reinterpret_cast<const CUtensorMap*>(split ? t->tmap_sp : t->tmap_p),
+        reinterpret_cast<const __nv_bfloat16*>(split ? t->Xs : t->Xb), split ? t->snorms : t->norms, t->dpad, nmax,
+        t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, tc_neg_c(kp), t->s0, ws.leaf_pos, ws.ksmp,
+        ws.lflags, reinterpret_cast<unsigned long long*>(&ws.stats->n_evals),
+        reinterpret_cast<unsigned long long*>(&ws.stats->n_items), t->status, split);
     return cudaGetLastError();
 }
 
