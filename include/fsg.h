@@ -65,12 +65,18 @@ extern "C" {
 /* Arithmetic of the kernel evaluations. */
 #define FSG_PREC_AUTO 0         /* FP32 for d <= 16; tensor-core form for large d */
 #define FSG_PREC_FP32 1         /* FP32 direct differences + ex2 on every d       */
-#define FSG_PREC_SPLIT_BF16 2   /* d <= 64: centred tiles, 3-part BF16           */
-                                /* split, six tcgen05 products, FP32 accumulate; */
-                                /* use with fsg_spatial_order (the leaf phase    */
-                                /* too for d in 17..64; FP32 for d <= 16); the   */
-                                /* only form with the approximate bin pass       */
-                                /* (fsg_params.kde_eps)                          */
+#define FSG_PREC_SPLIT_BF16 2   /* FP32 data as 3-part BF16, six tcgen05        */
+                                /* products per coordinate, FP32 accumulate.     */
+                                /* d <= 64: tiles centred at their mean; use     */
+                                /* with fsg_spatial_order (the leaf phase too    */
+                                /* for d in 17..64; FP32 for d <= 16); the only  */
+                                /* form with the approximate bin pass            */
+                                /* (fsg_params.kde_eps).  d > 64: uncentred      */
+                                /* ||x||^2 + ||y||^2 - 2 x.y (norms from FP64    */
+                                /* sums) on the tensor-core bin pass and leaf    */
+                                /* kernel; a value is within relative            */
+                                /* gamma (6 dpad / 16 + 1) 2^-22 (|x|^2 + |y|^2) */
+                                /* + 2^-22 (dpad = d rounded up to 64)           */
 #define FSG_PREC_EXACT_INT 3    /* tcgen05 BF16 on data that are k/255 exactly    */
 /* Kernel family (Sec. 2.1): the exponent of k(x, y) is minus the scale times
  * the squared Euclidean distance (Gaussian, scale gamma of scale_conv), the
@@ -366,6 +372,43 @@ int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_
                     int32_t edge_mode, int32_t* d_src, int32_t* d_dst, void* d_w, int64_t cap,
                     int64_t* d_m_out, double* d_deg, int32_t* d_samples, uint8_t* d_flags,
                     fsg_stats* d_stats, void* stream);
+
+/*
+ * Algorithm 2 in steps over ranges of query points, for long runs that are
+ * checkpointed and resumed (the paper has no counterpart; Sec. 4.1's
+ * descents are independent per query given the KDE values and the draws).
+ * fsg_graph_begin validates the call exactly as fsg_build_graph does, runs
+ * the bin pass for every query and keeps its sums in the tree; each
+ * fsg_graph_step samples the queries at tree positions [q_begin, q_end)
+ * (tree position = original index under the identity order; fsg_tree_perm
+ * gives the map otherwise): degrees, descents, bucketing, leaf finish and,
+ * with params->resolve, the re-decision, overwriting that range's sampling
+ * state in the tree.  A step reads only the bin sums and its queries' own
+ * draws, so steps may come in any order, be repeated (after a failed
+ * fsg_sync, say) and be resumed from any position: the device-resident
+ * state of the other ranges is the checkpoint, fsg_graph_cursor the first
+ * position not yet stepped.  fsg_graph_end forms the edge list and the
+ * optional outputs (arguments as in fsg_build_graph) once every position
+ * has been stepped.  For any split into steps the results are bit for bit
+ * those of fsg_build_graph with the same arguments (with params->resolve:
+ * while each call's flagged samples fit the re-decision's batched scratch,
+ * max(65,536, n L / 64); beyond it the per-sample fallback sums in another
+ * order); statistics count the work done (a repeated step counts twice).  Any other call on the tree
+ * (fsg_build_graph, fsg_degrees, fsg_tree_update, ...) ends the run.
+ * Fused schedule only.
+ *   q_begin, q_end : 0 <= q_begin < q_end <= n.
+ *   cursor         : host int64: smallest position not yet stepped (n when
+ *                    every position was).
+ * Errors: INVALID_ARG (no run begun, bad range, end before every position
+ * was stepped), UNSUPPORTED (levelwise schedules), and those of
+ * fsg_build_graph.
+ */
+int fsg_graph_begin(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_t seed, void* stream);
+int fsg_graph_step(fsg_tree* tree, int64_t q_begin, int64_t q_end, void* stream);
+int fsg_graph_cursor(const fsg_tree* tree, int64_t* cursor);
+int fsg_graph_end(fsg_tree* tree, int32_t edge_mode, int32_t* d_src, int32_t* d_dst, void* d_w, int64_t cap,
+                  int64_t* d_m_out, double* d_deg, int32_t* d_samples, uint8_t* d_flags, fsg_stats* d_stats,
+                  void* stream);
 
 /*
  * Per-phase timing with CUDA events recorded on the call's stream (not part

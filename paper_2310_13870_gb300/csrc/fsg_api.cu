@@ -1,5 +1,6 @@
 // C ABI entry points (include/fsg.h): argument checks, the tree object and
 // its workspace, and the fixed launch sequence of each call.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -97,8 +98,11 @@ struct PhaseScope {
     }
 };
 
+// Every call on a tree starts here; it ends a stepped build in progress
+// (the call reuses the workspace that holds the run's state).
 void begin_call(fsg_tree* t) {
     for (int k = 0; k < FSG_NUM_PHASES; ++k) t->ev_used[k] = false;
+    t->run.active = false;
 }
 
 // Bin pass: the symmetric kernel (each pair once) when bins hold 61..128 points.
@@ -758,14 +762,27 @@ static int64_t bin_evals(const fsg_tree* t, const fsg_params* p) {
 }
 
 // Statistics known on the host: samples run, bin-pass evaluations.
+// (keep_resolved: n_resolved was accumulated by the steps of a stepped build)
 __global__ static void stats_finish_kernel(fsg_stats* st, int64_t n_samples, int64_t bin_evals,
-                                           const int32_t* status, const int32_t* n_resolved, fsg_stats* out) {
+                                           const int32_t* status, const int32_t* n_resolved, fsg_stats* out,
+                                           int keep_resolved = 0) {
     st->n_samples = n_samples;
     st->n_evals += bin_evals;       // the split pass for d <= 64 counts its own on the device
     st->n_bin_evals += bin_evals;
     st->status = status[0];
-    st->n_resolved = n_resolved ? *n_resolved : 0;
+    if (!keep_resolved) st->n_resolved = n_resolved ? *n_resolved : 0;
     if (out) *out = *st;
+}
+
+// A stepped build: the samples one step re-decided, added to the statistics.
+__global__ static void add_resolved_kernel(fsg_stats* st, const int32_t* cnt) { st->n_resolved += cnt[0]; }
+
+// A stepped build: every position's FP32 degree to the caller's array in
+// original index order (the value descend_top writes in a whole build).
+__global__ static void degrees_out_kernel(const float* __restrict__ degf, const int32_t* __restrict__ perm,
+                                          int64_t n, double* __restrict__ d_deg) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        d_deg[perm[q]] = (double)degf[q];
 }
 
 int fsg_degrees(fsg_tree* t, const fsg_params* p, double* d_deg, void* stream) {
@@ -829,6 +846,129 @@ int fsg_build_graph(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, 
                     uint8_t* d_flags, fsg_stats* d_stats, void* stream) {
     return fsg::build_graph_internal(t, p, L, seed, edge_mode, d_src, d_dst, d_w, cap, d_m_out, d_deg, d_samples,
                                      d_flags, d_stats, (cudaStream_t)stream, false);
+}
+
+// Stepped build: the bin pass of every query, kept in the tree's workspace.
+int fsg_graph_begin(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t seed, void* stream) {
+    if (!t || L < 1 || L > kMaxL) return FSG_ERR_INVALID_ARG;
+    int rc = check_params(p);
+    if (rc != FSG_OK) return rc;
+    if ((rc = check_path(t, p)) != FSG_OK) return rc;
+    if (p->schedule != FSG_SCHED_FUSED) return FSG_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_workspace(t, L, s)) != FSG_OK) return rc;
+    if ((rc = ensure_split(t, p, s)) != FSG_OK) return rc;
+    if (p->resolve && (rc = ensure_resolve(t, L, s)) != FSG_OK) return rc;
+    const KernelParams kp = make_kernel_params(p, L, seed);
+    begin_call(t);  // ends any earlier run
+    cudaError_t e = cudaMemsetAsync(t->ws.stats, 0, sizeof(fsg_stats), s);
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_KDE_BINS, s);
+        e = run_kde_bins(t, kp, s);
+        t->launches += 1;
+    }
+    if (e != cudaSuccess) return status_of(e);
+    t->run.p = *p;
+    t->run.L = L;
+    t->run.seed = seed;
+    t->run.done.clear();
+    t->run.active = true;
+    return FSG_OK;
+}
+
+// Stepped build: sampling of the queries at tree positions [q0, q1).
+int fsg_graph_step(fsg_tree* t, int64_t q0, int64_t q1, void* stream) {
+    if (!t || !t->run.active || q0 < 0 || q1 > t->n || q0 >= q1) return FSG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const fsg_params& p = t->run.p;
+    const KernelParams kp = make_kernel_params(&p, t->run.L, t->run.seed);
+    Workspace& ws = t->ws;
+    cudaError_t e = cudaMemsetAsync(ws.bin_count, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.bin_cursor, 0, sizeof(int32_t) * t->nb * kBinSlots, s);
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_DESCEND_TOP, s);
+        e = launch_descend_top(t, kp, nullptr, 1, s, q0, q1);
+        t->launches += 1;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_BUCKET, s);
+        e = launch_bucket(t, kp, s, q0, q1);
+        t->launches += 2;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_LEAF, s);
+        e = run_leaf_phase(t, kp, s);
+    }
+    if (e == cudaSuccess && kp.resolve) {
+        PhaseScope ph(t, FSG_PHASE_RESOLVE, s);
+        e = launch_resolve(t, kp, s, q0, q1);
+        if (e == cudaSuccess) {
+            add_resolved_kernel<<<1, 1, 0, s>>>(ws.stats, t->rs.cnt);
+            e = cudaGetLastError();
+        }
+        t->launches += 9;
+    }
+    if (e != cudaSuccess) return status_of(e);
+    // record [q0, q1) among the stepped ranges (sorted, merged)
+    auto& done = t->run.done;
+    done.emplace_back(q0, q1);
+    std::sort(done.begin(), done.end());
+    std::vector<std::pair<int64_t, int64_t>> merged;
+    for (const auto& r : done) {
+        if (!merged.empty() && r.first <= merged.back().second)
+            merged.back().second = std::max(merged.back().second, r.second);
+        else
+            merged.push_back(r);
+    }
+    done.swap(merged);
+    return FSG_OK;
+}
+
+int fsg_graph_cursor(const fsg_tree* t, int64_t* cursor) {
+    if (!t || !cursor || !t->run.active) return FSG_ERR_INVALID_ARG;
+    const auto& done = t->run.done;
+    *cursor = (done.empty() || done[0].first > 0) ? 0 : done[0].second;
+    return FSG_OK;
+}
+
+// Stepped build: the edge list and outputs once every position was stepped.
+int fsg_graph_end(fsg_tree* t, int32_t edge_mode, int32_t* d_src, int32_t* d_dst, void* d_w, int64_t cap,
+                  int64_t* d_m_out, double* d_deg, int32_t* d_samples, uint8_t* d_flags, fsg_stats* d_stats,
+                  void* stream) {
+    if (!t || !t->run.active || !d_src || !d_dst || !d_w || !d_m_out) return FSG_ERR_INVALID_ARG;
+    if (edge_mode != FSG_EDGES_SET && edge_mode != FSG_EDGES_MULTI) return FSG_ERR_INVALID_ARG;
+    const int32_t L = t->run.L;
+    if (cap < t->n * (int64_t)L) return FSG_ERR_CAPACITY;
+    const auto& done = t->run.done;
+    if (done.size() != 1 || done[0].first != 0 || done[0].second != t->n) return FSG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const fsg_params& p = t->run.p;
+    const KernelParams kp = make_kernel_params(&p, L, t->run.seed);
+    cudaError_t e;
+    {
+        PhaseScope ph(t, FSG_PHASE_EDGES, s);
+        e = launch_edges(t, kp, edge_mode, d_src, d_dst, d_w, cap, d_m_out, s);
+        t->launches += edge_mode == FSG_EDGES_SET ? 6 : 5;
+    }
+    if (e == cudaSuccess) {
+        PhaseScope ph(t, FSG_PHASE_OUTPUTS, s);
+        e = launch_outputs(t, kp, d_samples, d_flags, d_stats, s);
+        if (e == cudaSuccess && d_deg) {
+            int64_t blocks = (t->n + 255) / 256;
+            if (blocks > 152 * 8) blocks = 152 * 8;
+            degrees_out_kernel<<<(int)blocks, 256, 0, s>>>(t->ws.degf, t->perm, t->n, d_deg);
+            e = cudaGetLastError();
+            t->launches += 1;
+        }
+        if (e == cudaSuccess) {
+            stats_finish_kernel<<<1, 1, 0, s>>>(t->ws.stats, t->n * L, bin_evals(t, &p), t->status, nullptr, d_stats,
+                                                1);
+            e = cudaGetLastError();
+        }
+        t->launches += 2;
+    }
+    if (e == cudaSuccess) t->run.active = false;
+    return status_of(e);
 }
 
 }  // extern "C"

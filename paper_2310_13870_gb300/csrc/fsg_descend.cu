@@ -29,8 +29,9 @@ __device__ __forceinline__ int k_of(int r, uint32_t b0, uint32_t b1, uint32_t be
 // decisions of each of the query's L samples, and the compact list of the
 // distinct bins its samples reached with the mask of samples at each.
 __global__ void __launch_bounds__(256)
-descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, const int32_t* __restrict__ perm,
-                   KernelParams kp, int with_samples, double* __restrict__ d_deg, float* __restrict__ degf,
+descend_top_kernel(const float* __restrict__ binsum, int n, int q_lo, int q_hi, int nb, int s0,
+                   const int32_t* __restrict__ perm, KernelParams kp, int with_samples, double* __restrict__ d_deg,
+                   float* __restrict__ degf,
                    uint8_t* __restrict__ flags, int32_t* __restrict__ leaf_pos, float* __restrict__ ksmp,
                    int32_t* __restrict__ bin_count, int32_t* __restrict__ qitem_bin,
                    uint64_t* __restrict__ qitem_mask, int32_t* __restrict__ qitem_cnt, uint16_t* __restrict__ flev) {
@@ -52,14 +53,14 @@ descend_top_kernel(const float* __restrict__ binsum, int n, int nb, int s0, cons
         for (int k = 0; k < 8; ++k)
             if (k < nv) v[k] = __ldcs(r4 + k * 32 + lane);
     };
-    if (vec && blockIdx.x * warps + w < n) load_row(blockIdx.x * warps + w);
-    for (int q = blockIdx.x * warps + w; q < n; q += qstride) {
+    if (vec && q_lo + (int)blockIdx.x * warps + w < q_hi) load_row(q_lo + blockIdx.x * warps + w);
+    for (int q = q_lo + blockIdx.x * warps + w; q < q_hi; q += qstride) {
         if (vec) {
             float4* t4 = reinterpret_cast<float4*>(tree + nb);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (k < nv) t4[k * 32 + lane] = v[k];
-            if (q + qstride < n) load_row(q + qstride);
+            if (q + qstride < q_hi) load_row(q + qstride);
         } else {
             const float* row = binsum + (size_t)q * nb;
             for (int b = lane; b < nb; b += 32) tree[nb + b] = row[b];
@@ -190,12 +191,12 @@ scan_bins_kernel(const int32_t* __restrict__ bin_count, int nb, int32_t* __restr
 // Items of every query into their bin's segment [bin_off[b], bin_off[b+1]).
 __global__ void __launch_bounds__(128)
 scatter_items_kernel(const int32_t* __restrict__ qitem_bin, const uint64_t* __restrict__ qitem_mask,
-                     const int32_t* __restrict__ qitem_cnt, int n, int L, const int32_t* __restrict__ bin_off,
-                     int32_t* __restrict__ bin_cursor, int32_t* __restrict__ items_q,
-                     uint64_t* __restrict__ items_mask, long long max_items) {
+                     const int32_t* __restrict__ qitem_cnt, int q_lo, int q_hi, int L,
+                     const int32_t* __restrict__ bin_off, int32_t* __restrict__ bin_cursor,
+                     int32_t* __restrict__ items_q, uint64_t* __restrict__ items_mask, long long max_items) {
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = blockIdx.x * warps + w; q < n; q += gridDim.x * warps) {
+    for (int q = q_lo + blockIdx.x * warps + w; q < q_hi; q += gridDim.x * warps) {
         const int cnt = qitem_cnt[q];
         for (int k = lane; k < cnt; k += 32) {
             const int b = qitem_bin[(size_t)q * L + k] * kBinSlots + (q & (kBinSlots - 1));
@@ -896,7 +897,8 @@ int leaf_queries_per_tile(const fsg_tree* t) {
 }
 
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
-                               cudaStream_t s) {
+                               cudaStream_t s, int64_t q_lo, int64_t q_hi) {
+    if (q_hi < 0) q_hi = t->n;
     int warps = 8;
     while (warps > 1 && (size_t)warps * 8 * t->nb > 96 * 1024) warps >>= 1;
     const size_t smem = (size_t)warps * 8 * t->nb;  // per warp: 2 nb tree nodes (later nb bin masks)
@@ -904,10 +906,12 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
         const cudaError_t e = set_smem_limit(descend_top_kernel, smem < 48 * 1024 ? 48 * 1024 : smem);
         if (e != cudaSuccess) return e;
     }
-    int64_t blocks = (t->n + warps - 1) / warps;
+    int64_t blocks = (q_hi - q_lo + warps - 1) / warps;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) return cudaSuccess;
     const auto& ws = t->ws;
-    descend_top_kernel<<<(int)blocks, warps * 32, smem, s>>>(ws.binsum, (int)t->n, t->nb, t->s0, t->perm, kp,
+    descend_top_kernel<<<(int)blocks, warps * 32, smem, s>>>(ws.binsum, (int)t->n, (int)q_lo, (int)q_hi, t->nb,
+                                                            t->s0, t->perm, kp,
                                                             with_samples, d_deg, ws.degf, ws.flags, ws.leaf_pos,
                                                             ws.ksmp, ws.bin_count, ws.qitem_bin, ws.qitem_mask,
                                                             ws.qitem_cnt,
@@ -915,16 +919,19 @@ cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s, int64_t q_lo, int64_t q_hi) {
+    if (q_hi < 0) q_hi = t->n;
     const auto& ws = t->ws;
     scan_bins_kernel<<<1, 1024, 0, s>>>(ws.bin_count, t->nb * kBinSlots, ws.bin_off);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    int64_t blocks = (t->n + 3) / 4;
+    int64_t blocks = (q_hi - q_lo + 3) / 4;
     if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) return cudaSuccess;
     const long long max_items = t->n * (long long)(ws.cap_L < t->nb ? ws.cap_L : t->nb);
-    scatter_items_kernel<<<(int)blocks, 128, 0, s>>>(ws.qitem_bin, ws.qitem_mask, ws.qitem_cnt, (int)t->n, kp.L,
-                                                     ws.bin_off, ws.bin_cursor, ws.items_q, ws.items_mask, max_items);
+    scatter_items_kernel<<<(int)blocks, 128, 0, s>>>(ws.qitem_bin, ws.qitem_mask, ws.qitem_cnt, (int)q_lo,
+                                                     (int)q_hi, kp.L, ws.bin_off, ws.bin_cursor, ws.items_q,
+                                                     ws.items_mask, max_items);
     return cudaGetLastError();
 }
 

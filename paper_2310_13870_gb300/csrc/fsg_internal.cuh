@@ -7,6 +7,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+#include <vector>
+
 #include "fsg.h"
 
 namespace fsg {
@@ -135,6 +138,16 @@ struct fsg_tree {
     alignas(64) unsigned char tmap_sp[128] = {};
     fsg::Workspace ws;
     fsg::ResolveWs rs;
+    // stepped graph build (fsg_graph_begin / step / end): the call's
+    // parameters and the stepped position ranges (sorted, disjoint, merged);
+    // any other call on the tree ends it
+    struct GraphRun {
+        bool active = false;
+        fsg_params p{};
+        int32_t L = 0;
+        uint64_t seed = 0;
+        std::vector<std::pair<int64_t, int64_t>> done;
+    } run;
     fsg::LaunchTuning tune;
     // per-phase timing (fsg_profile) and kernel-launch count
     bool profiling = false;
@@ -218,9 +231,12 @@ int build_graph_internal(fsg_tree* t, const fsg_params* p, int32_t L, uint64_t s
                          int32_t* d_samples, uint8_t* d_flags, fsg_stats* d_stats, cudaStream_t s, bool skip_bins);
 bool kde_bins_sym_supported(const fsg_tree* t);
 int64_t kde_bins_sym_evals(const fsg_tree* t);
+// The descent above the bins and the bucketing for the queries at tree
+// positions [q_lo, q_hi) (q_hi < 0: every query).
 cudaError_t launch_descend_top(const fsg_tree* t, const KernelParams& kp, double* d_deg, int with_samples,
-                               cudaStream_t s);
-cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+                               cudaStream_t s, int64_t q_lo = 0, int64_t q_hi = -1);
+cudaError_t launch_bucket(const fsg_tree* t, const KernelParams& kp, cudaStream_t s, int64_t q_lo = 0,
+                          int64_t q_hi = -1);
 cudaError_t launch_leaf_finish(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
 int leaf_queries_per_tile(const fsg_tree* t);
 int64_t leaf_default_splits(const fsg_tree* t, int L);
@@ -232,7 +248,10 @@ cudaError_t launch_edges(const fsg_tree* t, const KernelParams& kp, int edge_mod
 // ensure_resolve before the call's first launch).
 bool resolve_supported(const fsg_tree* t);
 int ensure_resolve(fsg_tree* t, int L, cudaStream_t s);
-cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);
+// Re-decides the flagged samples of the queries at tree positions
+// [q_lo, q_hi) (q_hi < 0: every query).
+cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, cudaStream_t s, int64_t q_lo = 0,
+                           int64_t q_hi = -1);
 cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d_samples, uint8_t* d_flags,
                            fsg_stats* d_stats, cudaStream_t s);
 cudaError_t launch_kde_bins_generic(const fsg_tree* t, const KernelParams& kp, cudaStream_t s);

@@ -72,10 +72,12 @@ __device__ __forceinline__ void node_range(int h, int n, int& a, int& c) {
     }
 }
 
+// Samples e in [e_lo, e_hi) (positions q_lo..q_hi - 1 times L) that are flagged.
 __global__ void rs_compact_kernel(const uint8_t* __restrict__ flags, const uint8_t* __restrict__ lflags,
-                                  const int32_t* __restrict__ leaf_pos, int64_t total, int32_t* __restrict__ list,
-                                  int32_t* __restrict__ cnt) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+                                  const int32_t* __restrict__ leaf_pos, int64_t e_lo, int64_t e_hi, int64_t total,
+                                  int32_t* __restrict__ list, int32_t* __restrict__ cnt) {
+    for (int64_t e = e_lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e_hi;
+         e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t pos = leaf_pos[e];
         if (pos >= 0 && ((flags[e] | lflags[e]) & 1)) {
             const int slot = atomicAdd(&cnt[0], 1);
@@ -617,17 +619,22 @@ int ensure_resolve(fsg_tree* t, int L, cudaStream_t s) {
     return FSG_OK;
 }
 
-cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
+cudaError_t launch_resolve(const fsg_tree* t, const KernelParams& kp, cudaStream_t s, int64_t q_lo,
+                           int64_t q_hi) {
     const auto& ws = t->ws;
     const ResolveWs& rs = t->rs;
     const int64_t total = t->n * (int64_t)kp.L;
+    if (q_hi < 0) q_hi = t->n;
+    const int64_t e_lo = q_lo * kp.L, e_hi = q_hi * kp.L;
     cudaError_t e = cudaMemsetAsync(rs.cnt, 0, sizeof(int32_t) * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(rs.node_cnt, 0, sizeof(int32_t) * (size_t)t->nb, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(rs.node_cur, 0, sizeof(int32_t) * (size_t)t->nb, s);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (total + 255) / 256;
+    int64_t blocks = (e_hi - e_lo + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    rs_compact_kernel<<<(int)blocks, 256, 0, s>>>(ws.flags, ws.lflags, ws.leaf_pos, total, rs.list, rs.cnt);
+    if (blocks < 1) blocks = 1;
+    rs_compact_kernel<<<(int)blocks, 256, 0, s>>>(ws.flags, ws.lflags, ws.leaf_pos, e_lo, e_hi, total, rs.list,
+                                                  rs.cnt);
     const int fb = (rs.fcap + 255) / 256 < 152 * 8 ? (rs.fcap + 255) / 256 : 152 * 8;
     rs_jobs_kernel<<<fb, 256, 0, s>>>(rs.list, ws.leaf_pos, rs.flev, t->bnd, t->nb, t->s0, rs.fcap, t->dp, rs.sbin,
                                       rs.node_cnt, rs.cnt);

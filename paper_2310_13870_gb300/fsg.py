@@ -49,6 +49,7 @@ EXPORTED = [
     "fsg_batch_create", "fsg_batch_run", "fsg_batch_destroy",
     "fsg_server_create", "fsg_server_submit", "fsg_server_poll", "fsg_server_cancel", "fsg_server_info",
     "fsg_server_destroy", "fsg_selftest_wait_timeout", "fsg_bounds_error",
+    "fsg_graph_begin", "fsg_graph_step", "fsg_graph_cursor", "fsg_graph_end",
 ]
 FSG_NUM_PHASES = 8
 PHASES = ["tree", "kde_bins", "descend_top", "bucket", "leaf_finish", "edges", "outputs", "resolve"]
@@ -159,6 +160,10 @@ def load(path: str = LIB_PATH):
     lib.fsg_tree_perm.argtypes = [P, P, P]
     lib.fsg_selftest_wait_timeout.argtypes = [ctypes.c_int64, P]
     lib.fsg_bounds_error.argtypes = [P]
+    lib.fsg_graph_begin.argtypes = [P, P, I32, U64, P]
+    lib.fsg_graph_step.argtypes = [P, I64, I64, P]
+    lib.fsg_graph_cursor.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.fsg_graph_end.argtypes = [P, I32, P, P, P, I64, P, P, P, P, P, P]
     for name in EXPORTED:
         if name not in ("fsg_version", "fsg_error_string", "fsg_free_tree", "fsg_batch_destroy", "fsg_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -380,6 +385,34 @@ def fsg_build_graph(tree: Tree, p: fsg_params, L: int, seed: int, edge_mode: int
                                   _dptr(bufs.src), _dptr(bufs.dst), _dptr(bufs.w), bufs.cap, _dptr(bufs.m),
                                   _dptr(bufs.deg), _dptr(bufs.samples), _dptr(bufs.flags), _dptr(bufs.stats),
                                   _stream_ptr(stream)), "fsg_build_graph")
+    return bufs
+
+
+def fsg_graph_begin(tree: Tree, p: fsg_params, L: int, seed: int, stream=None):
+    """Stepped build: the bin pass of every query (kept in the tree)."""
+    _check(load().fsg_graph_begin(tree.handle, ctypes.byref(p), L, ctypes.c_uint64(seed), _stream_ptr(stream)),
+           "fsg_graph_begin")
+
+
+def fsg_graph_step(tree: Tree, q_begin: int, q_end: int, stream=None):
+    """Stepped build: sampling of the queries at tree positions [q_begin, q_end)."""
+    _check(load().fsg_graph_step(tree.handle, q_begin, q_end, _stream_ptr(stream)), "fsg_graph_step")
+
+
+def fsg_graph_cursor(tree: Tree) -> int:
+    c = ctypes.c_int64()
+    _check(load().fsg_graph_cursor(tree.handle, ctypes.byref(c)), "fsg_graph_cursor")
+    return int(c.value)
+
+
+def fsg_graph_end(tree: Tree, L: int, edge_mode: int = FSG_EDGES_SET, bufs: Optional[GraphBuffers] = None,
+                  weight_f64: bool = False, stream=None) -> GraphBuffers:
+    """Stepped build: edge list and outputs once every position was stepped."""
+    if bufs is None:
+        bufs = GraphBuffers(tree.n, L, weight_f64=weight_f64)
+    _check(load().fsg_graph_end(tree.handle, edge_mode, _dptr(bufs.src), _dptr(bufs.dst), _dptr(bufs.w), bufs.cap,
+                                _dptr(bufs.m), _dptr(bufs.deg), _dptr(bufs.samples), _dptr(bufs.flags),
+                                _dptr(bufs.stats), _stream_ptr(stream)), "fsg_graph_end")
     return bufs
 
 

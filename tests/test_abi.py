@@ -71,6 +71,12 @@ def test_bad_arguments_are_refused_without_gpu(lib):
     assert lib.fsg_tree_tuning(None, None, ctypes.byref(tun)) == fsg.FSG_ERR_INVALID_ARG
     ev = ctypes.c_int64()
     assert lib.fsg_bin_pass_evals(None, ctypes.byref(p), ctypes.byref(ev)) == fsg.FSG_ERR_INVALID_ARG
+    # the stepped build: no tree, no run
+    assert lib.fsg_graph_begin(None, ctypes.byref(p), 8, 0, None) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_graph_step(None, 0, 10, None) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_graph_cursor(None, ctypes.byref(ev)) == fsg.FSG_ERR_INVALID_ARG
+    assert lib.fsg_graph_end(None, 0, fake, fake, fake, 100, fake, None, None, None, None,
+                             None) == fsg.FSG_ERR_INVALID_ARG
     m = ctypes.c_int64()
     buf = (ctypes.c_float * 8)()
     for bad in (fsg.params(0.0), fsg.params(float("nan")), fsg.params(-1.0), fsg.params(0.1, self_mode=3),
