@@ -34,8 +34,11 @@ if ROOT not in sys.path:
 
 METRIC = "sampled graph edges/s & Gkernel-evals/s vs plain FP32 GPU path; p50/p99 latency"
 UNIT = "sampled edges/s"
+OUTPUTS = ("edge list (src, dst, FP32 weight) and FP64 degrees written every step; the optional per-sample "
+           "neighbour and flag arrays are not requested")
 WORKLOAD = dict(workload="gaussian_mixture n=100000 d=10 k=10 box=10 sigma=1.5 L=64 seed=0", n=100_000, d=10,
-                sigma=1.5, L=64, seed=0, edges="SET", self_term="EXCLUDE", l2="flushed (512 MB write) between steps")
+                sigma=1.5, L=64, seed=0, edges="SET", self_term="EXCLUDE", l2="flushed (512 MB write) between steps",
+                outputs=OUTPUTS)
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
@@ -54,7 +57,7 @@ def alu_peak_evals(d: int, mhz: float = SM_MAX_MHZ, ops: int = 0) -> float:
 
 DIGITS = dict(workload="digit_like n=70000 d=784 (10 prototypes, 8-bit) sigma=median/2 L=64 seed=0", n=70_000,
               d=784, sigma=None, L=64, seed=0, edges="SET", self_term="EXCLUDE",
-              l2="flushed (512 MB write) between steps")
+              l2="flushed (512 MB write) between steps", outputs=OUTPUTS)
 
 
 def make_points(rank: int = 0):

@@ -147,3 +147,28 @@ def test_split_large_d_refusals(fsg):
             fsg.fsg_degrees(tree, fsg.params(2.0, precision=fsg.FSG_PREC_SPLIT_BF16, **kw))
         assert e.value.status == fsg.FSG_ERR_UNSUPPORTED
     tree.close()
+
+
+@pytest.mark.parametrize("n,d", [(1, 100), (2, 100), (3, 65), (77, 300), (129, 128), (300, 4096)])
+def test_split_large_d_small_and_wide(fsg, n, d):
+    # one point (no other mass: every sample empty), two points (each the
+    # other's only neighbour, weight k), a single bin under one tile, a
+    # ragged tile, and the widest d the library takes
+    X = jittered_digits(n, d, 40 + n)
+    sigma = 6.0 if d < 1000 else 15.0
+    g = run(fsg, X, sigma, 8, 3, fsg.FSG_PREC_SPLIT_BF16)
+    assert g["stats"]["status"] == 0
+    gam = ora.gamma(sigma)
+    want = ora.degrees(X, gam)
+    if n == 1:
+        assert g["deg"][0] == 0.0 and (g["samples"] == -1).all() and g["src"].size == 0
+        return
+    kv = np.exp(-gam * cdist(X.astype(np.float64), X.astype(np.float64), "sqeuclidean"))
+    np.fill_diagonal(kv, 0.0)
+    q = np.arange(n)
+    assert (np.abs(g["deg"] - want) <= degree_bound(X, gam, q, kv) + n * TINY).all()
+    smp, _, _ = ora.sample(X, gam, 8, 3)
+    assert not ((g["samples"] != smp) & (g["flags"] == 0)).any()
+    if n == 2:
+        assert (g["samples"] == np.array([[1], [0]])).all()
+        np.testing.assert_allclose(g["w"], kv[0, 1], rtol=W_RTOL)
