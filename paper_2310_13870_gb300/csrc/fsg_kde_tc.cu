@@ -301,22 +301,33 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 if (SYM && mirror) {  // warp-uniform
                     // column sums through a transposed 32 x 32 tile: row = lane
                     // written as 16-byte pieces (row stride 36 floats: no bank
-                    // conflict either way), then lane = column adds its rows in
-                    // order, those of the warp's first bin and the rest apart
+                    // conflict either way); then lanes l and l + 16 take the
+                    // column pair 2 (l % 16), 2 (l % 16) + 1 as FP32x2 values,
+                    // rows 0..15 and 16..31 in order, those of the warp's first
+                    // bin and the rest apart, and the two halves are added
                     float* tw = ctile + (warp - 2) * 32 * 36;
                     __syncwarp();  // the previous chunk's reads are done
 #pragma unroll
                     for (int j = 0; j < 32; j += 4)
                         *reinterpret_cast<float4*>(tw + lane * 36 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                     __syncwarp();
-                    float sa = 0.f, sb = 0.f;
+                    const int hrow = (lane >> 4) * 16, c2 = 2 * (lane & 15);
+                    uint64_t sa = f2_pack(0.f, 0.f), sb = sa;
 #pragma unroll
-                    for (int rr = 0; rr < 32; ++rr) {
-                        const float x = tw[rr * 36 + lane];
-                        if (rr < w_split) sa += x; else sb += x;
+                    for (int rr = 0; rr < 16; ++rr) {
+                        const uint64_t x = *reinterpret_cast<const uint64_t*>(tw + (hrow + rr) * 36 + c2);
+                        if (hrow + rr < w_split) sa = f2_add(sa, x); else sb = f2_add(sb, x);
                     }
-                    cp[2 * (cc + lane)] = sa;
-                    cp[2 * (cc + lane) + 1] = sb;
+                    sa = f2_add(sa, __shfl_xor_sync(0xffffffffu, sa, 16));
+                    sb = f2_add(sb, __shfl_xor_sync(0xffffffffu, sb, 16));
+                    if (lane < 16) {  // rows 0..15 + rows 16..31; colpart is 4-byte aligned: scalar stores
+                        const float2 a = f2_unpack(sa), b = f2_unpack(sb);
+                        float* o = cp + 2 * (cc + c2);
+                        o[0] = a.x;
+                        o[1] = b.x;
+                        o[2] = a.y;
+                        o[3] = b.y;
+                    }
                 }
                 tc_row_bins(v, c0 + cc, acc, bin, next_b, bnd_s, nbc, orow);
             }
