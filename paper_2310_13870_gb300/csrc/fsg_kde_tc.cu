@@ -662,13 +662,17 @@ cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaSt
 // summed once per item (and their tree above), deeper nodes are sums over
 // their points' values, with the same Philox draws and decision rule as
 // every other level; it writes the sampled position, kernel value and flags.
-// With bins of up to 160 points two CTAs share an SM, so one CTA's epilogue
-// and descents overlap the other's copies and MMAs.
+// Several CTAs share an SM (three with a 2-stage ring for bins of up to 80
+// points, else two), so one CTA's epilogue and descents overlap the others'
+// copies and MMAs.
 // ---------------------------------------------------------------------------
 namespace fsg {
 namespace {
 
-constexpr int kLvStages = 3;
+// Stages of the K ring (template parameter ST): 2 where the value rows fit
+// two stages and three CTAs fit an SM (bins of up to 80 points: one CTA's
+// epilogue and descents then overlap two others' copies and MMAs), else 3
+// with two CTAs per SM.
 constexpr int kLvThreads = 256;  // two threads per item row (TMEM lane): warps w and w + 4
 constexpr int kLvBox = 16;  // point rows per TMA box
 
@@ -682,23 +686,26 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
 struct LvLayout {
     uint32_t kB, stage, bars, rowpos, qmask, prefix, pnorm, bnd4, btree, total;
     bool tree_in_stages;
-    __host__ __device__ explicit LvLayout(int nmax) {
+    bool rows_fit;  // the [128][nmax + 1] value rows fit the stages
+    __host__ __device__ LvLayout(int nmax, int nst) {
         kB = (uint32_t)nmax * 128u;
         stage = 128u * 128u + kB;
-        bars = kLvStages * stage;                        // done[3], full[3], accf, fin
-        rowpos = bars + 8 * (2 * kLvStages + 2) + 16;    // + TMEM slot
+        bars = (uint32_t)nst * stage;                    // done[nst], full[nst], accf, fin
+        rowpos = bars + 8 * (2 * nst + 2) + 16;          // + TMEM slot
         qmask = rowpos + 128 * 4;                        // [128] sample masks of the chunk's items
         prefix = qmask + 128 * 8;                        // [129] samples before each item (+ 3 words)
         pnorm = prefix + 132 * 4;
         bnd4 = pnorm + (uint32_t)nmax * 4;
         const uint32_t after = bnd4 + 17 * 4 + 12;
-        tree_in_stages = (size_t)128 * (nmax + 1 + 33) * 4 <= (size_t)kLvStages * stage;
+        rows_fit = (size_t)128 * (nmax + 1) * 4 <= (size_t)nst * stage;
+        tree_in_stages = (size_t)128 * (nmax + 1 + 33) * 4 <= (size_t)nst * stage;
         btree = tree_in_stages ? 128u * (uint32_t)(nmax + 1) * 4u : ((after + 15u) & ~15u);
         total = tree_in_stages ? after : btree + 128 * 33 * 4;
     }
 };
 
-__global__ void __launch_bounds__(kLvThreads, 2)
+template <int ST>
+__global__ void __launch_bounds__(kLvThreads, ST == 2 ? 3 : 2)
 leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat16* __restrict__ Xb,
                       const float* __restrict__ norms, int dpad, int nmax, const int32_t* __restrict__ bnd,
                       const int32_t* __restrict__ bin_off, const int32_t* __restrict__ items_q,
@@ -719,14 +726,14 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     uint32_t tcols = 32;
     while ((int)tcols < N) tcols <<= 1;
     const uint32_t idesc = idesc_bf16(128, N);
-    const LvLayout ly(nmax);
+    const LvLayout ly(nmax, ST);
     const uint32_t kA = 128u * 128u;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     uint64_t* done = reinterpret_cast<uint64_t*>(base + ly.bars);  // MMAs reading a stage are done
-    uint64_t* full = done + kLvStages;                              // a stage's point rows landed
-    uint64_t* accf = full + kLvStages;                              // accumulator complete
+    uint64_t* full = done + ST;                              // a stage's point rows landed
+    uint64_t* accf = full + ST;                              // accumulator complete
     uint64_t* fin = accf + 1;                                       // teardown
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
     int32_t* rowpos = reinterpret_cast<int32_t*>(base + ly.rowpos);  // [128] item query positions
@@ -745,7 +752,7 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     const int kv = split ? 6 * kchunks : kchunks;    // K chunks of one accumulation
     const size_t rstride = split ? 3 * (size_t)dpad : (size_t)dpad;  // BF16 values per point row
     if (tid == 0) {
-        for (int s = 0; s < kLvStages; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&done[s], 1);
             mbar_init(&full[s], 1);
         }
@@ -765,7 +772,7 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    int g = 0;      // stage uses issued so far (stage g % kLvStages, its use number g / kLvStages)
+    int g = 0;      // stage uses issued so far (stage g % ST, its use number g / ST)
     int tiles = 0;  // accumulator tiles completed
     bool mma_issued = false;
     bool ok = true;
@@ -793,11 +800,11 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
             ++nfill;
         }
     };
-    // waits until the MMAs of stage use g2 - kLvStages are done
+    // waits until the MMAs of stage use g2 - ST are done
     auto stage_free = [&](int g2) -> bool {
-        const int use = g2 / kLvStages;
+        const int use = g2 / ST;
         if (use == 0) return true;
-        return mbar_wait_bounded(&done[g2 % kLvStages], (uint32_t)(use - 1) & 1u, status);
+        return mbar_wait_bounded(&done[g2 % ST], (uint32_t)(use - 1) & 1u, status);
     };
     for (int chunk = blockIdx.y; chunk < nchunks; chunk += gridDim.y) {
         const int it0 = chunk * 128;
@@ -814,24 +821,24 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
             gsrc[i] = Xb + (size_t)(pos >= 0 ? pos : 0) * rstride + (tid & 7) * 8;
             gbytes |= (pos >= 0 ? 1u : 0u) << i;
         }
-        const int pre = min(kLvStages - 1, kv);
+        const int pre = min(ST - 1, kv);
         for (int kc = 0; kc < pre; ++kc) {
             if (ok) ok = stage_free(g + kc);
-            if (ok) fill(kc, (g + kc) % kLvStages);
+            if (ok) fill(kc, (g + kc) % ST);
         }
         for (int kc = 0; kc < kv; ++kc) {
-            const int gs = g + kc, s = gs % kLvStages;
+            const int gs = g + kc, s = gs % ST;
             if (kc + pre < kv) {
                 if (ok) ok = stage_free(g + kc + pre);
-                if (ok) fill(kc + pre, (g + kc + pre) % kLvStages);
-                asm volatile("cp.async.wait_group %0;" ::"n"(kLvStages - 1) : "memory");
+                if (ok) fill(kc + pre, (g + kc + pre) % ST);
+                asm volatile("cp.async.wait_group %0;" ::"n"(ST - 1) : "memory");
             } else {
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             if (__syncthreads_or(!ok)) { ok = false; break; }
             if (tid == 0) {
-                ok = mbar_wait_bounded(&full[s], (uint32_t)(gs / kLvStages) & 1u, status);
+                ok = mbar_wait_bounded(&full[s], (uint32_t)(gs / ST) & 1u, status);
                 if (ok) {
                     ++ncons;
                     tc_fence_after();
@@ -956,7 +963,7 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
     if (tid == 0) {
         // point rows still in flight (an aborted chunk): let them land
         for (int gs = ncons; gs < nfill; ++gs)
-            mbar_wait_bounded(&full[gs % kLvStages], (uint32_t)(gs / kLvStages) & 1u, status);
+            mbar_wait_bounded(&full[gs % ST], (uint32_t)(gs / ST) & 1u, status);
         if (mma_issued) {
             umma_commit(fin);
             mbar_wait_bounded(fin, 0u, status);
@@ -975,9 +982,14 @@ leaf_values_tc_kernel(const __grid_constant__ CUtensorMap tmP, const __nv_bfloat
 cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const int nmax = (t->mmax + 15) & ~15;  // point rows of the largest bin, rounded to the TMA box
     if (nmax > 256) return cudaErrorInvalidValue;
-    const size_t smem = 1024 + LvLayout(nmax).total;
+    // two stages when the value rows fit them and three CTAs fit the SM's
+    // 228 KB (1 KB reserved per CTA); three stages always hold the rows
+    const LvLayout l2(nmax, 2);
+    const bool two = l2.rows_fit && 3 * (2048 + (size_t)l2.total) <= 228 * 1024;
+    const size_t smem = 1024 + (size_t)(two ? l2.total : LvLayout(nmax, 3).total);
+    auto kern = two ? leaf_values_tc_kernel<2> : leaf_values_tc_kernel<3>;
     {
-        const cudaError_t e = set_smem_limit(leaf_values_tc_kernel, 227 * 1024);
+        const cudaError_t e = set_smem_limit(kern, 227 * 1024);
         if (e != cudaSuccess) return e;
     }
     const int64_t items_est = t->n * (int64_t)(kp.L < t->nb ? kp.L : t->nb);
@@ -991,7 +1003,7 @@ cudaError_t launch_leaf_values_tc(const fsg_tree* t, const KernelParams& kp, cud
     const auto& ws = t->ws;
     const int split = kp.precision == FSG_PREC_SPLIT_BF16 ? 1 : 0;
     if (split && !t->Xs) return cudaErrorInvalidValue;
-    leaf_values_tc_kernel<<<grid, kLvThreads, smem, s>>>(
+    kern<<<grid, kLvThreads, smem, s>>>(
         *reinterpret_cast<const CUtensorMap*>(split ? t->tmap_sp : t->tmap_p),
         reinterpret_cast<const __nv_bfloat16*>(split ? t->Xs : t->Xb), split ? t->snorms : t->norms, t->dpad, nmax,
         t->bnd, ws.bin_off, ws.items_q, ws.items_mask, t->perm, kp, tc_neg_c(kp), t->s0, ws.leaf_pos, ws.ksmp,
