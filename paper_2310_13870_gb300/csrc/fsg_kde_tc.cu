@@ -85,12 +85,12 @@ __device__ __forceinline__ void split_cols(int v, int kchunks, bool split, int& 
 // per (point, bin) and CTA goes into bin sums zeroed beforehand.  A bin meets at most two row
 // tiles, so every such sum receives at most two additions onto zero, whose
 // result does not depend on their order.
-template <int EW, int ST, bool SYM, bool EXPD>
+template <int EW, int ST, bool SYM, bool EXPD, bool SPLIT>
 __global__ void __launch_bounds__(64 + 32 * EW, 1)
 kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int n, int kchunks, const int32_t* __restrict__ bnd, int nb,
                    int bpc, int nchunk, float neg_c, int self_exclude, float* __restrict__ binsum,
-                   int32_t* __restrict__ status, int split) {
+                   int32_t* __restrict__ status) {
     extern __shared__ unsigned char smem_raw[];
     constexpr uint32_t kStage = kABytes + kBBytes;
     constexpr int kCols = kTcN / (EW / 4);  // columns of each epilogue warp per tile
@@ -106,7 +106,9 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     int32_t* winfo = flags + 2;                                   // [4] warp's first bin, [4] rows in it
     int32_t* bnd_s = winfo + 8;                                   // bpc + 1 (column bins)
     int32_t* rbnd_s = bnd_s + ((bpc + 1 + 3) & ~3);                // bpc + 1 (row bins, SYM)
-    float* pnorm = reinterpret_cast<float*>(rbnd_s + ((bpc + 1 + 3) & ~3));  // [epilogue warp][kCols]
+    // [epilogue warp][kCols], 16-byte aligned (float4 broadcast reads)
+    float* pnorm = reinterpret_cast<float*>(rbnd_s + ((bpc + 1 + 3) & ~3));
+    pnorm += ((16u - (smem_u32(pnorm) & 15u)) & 15u) / 4u;
     float* outs = pnorm + EW * kCols;                              // [EW/4 parts][128][bpc]
     float* colpart = outs + (EW / 4) * kTcM * bpc;                 // SYM: [2][EW/4][4][kCols][2]
     // SYM: [EW][32][36] transposed tiles, 16-byte aligned (float4 stores)
@@ -175,7 +177,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const uint32_t tmem = *tmem_slot;
     const int pa = bnd_s[0], pe = bnd_s[nbc];
     const int ntile = (pe - pa + kTcN - 1) / kTcN;
-    const int kv = split ? 6 * kchunks : kchunks;  // K chunks of one tile
+    const int kv = SPLIT ? 6 * kchunks : kchunks;  // K chunks of one tile
     const int total = ntile * kv;
     volatile int32_t* abort_flag = flags;
     volatile int32_t* consumed = flags + 1;
@@ -184,7 +186,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     // The 8-bit form needs exact 8-bit values (checked when the tree is built
     // or updated); the split form takes any FP32 data.
-    const bool inexact = !split && status[1] != 0;
+    const bool inexact = !SPLIT && status[1] != 0;
 
     if (!inexact && warp == 0 && lane == 0) {
         // ---- TMA producer
@@ -196,7 +198,7 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             }
             const int tile = it / kv, kc = it - tile * kv;
             int xa, xb;
-            split_cols(kc, kchunks, split != 0, xa, xb);
+            split_cols(kc, kchunks, SPLIT, xa, xb);
             unsigned char* st = base + s * kStage;
             mbar_arrive_expect_tx(&full[s], kStage);
             tma_load_2d(st, &tmA, xa, q0, &full[s]);
@@ -291,9 +293,9 @@ kde_bins_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 if (cc + 32 < kCols) tmem_issue32(tcol + (uint32_t)(cc + 32), rb[cur ^ 1]);
                 float v[32];
                 if (check)
-                    tc_values32<true, EXPD>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
+                    tc_values32<true, EXPD, SPLIT>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
                 else
-                    tc_values32<false, EXPD>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
+                    tc_values32<false, EXPD, SPLIT>(rb[cur], pn + cc, c0 + cc, nq, neg_c, q, pe, self_exclude, v);
                 if (SYM && !rvalid) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = 0.f;
@@ -539,7 +541,7 @@ constexpr int kTcSymMaxBins = 16;  // bins per chunk of the symmetric pass
 size_t tc_bins_smem(int ew, int bpc, int st, bool sym) {
     const int kcols = kTcN / (ew / 4);
     return 1024 + (size_t)st * kStageBytes + 8 * (2 * st + 7) + 16 + 8 * 4 + 2 * (size_t)((bpc + 1 + 3) & ~3) * 4 +
-           (size_t)ew * kcols * 4 + (size_t)(ew / 4) * kTcM * bpc * 4 +
+           16 + (size_t)ew * kcols * 4 + (size_t)(ew / 4) * kTcM * bpc * 4 +
            (sym ? (size_t)2 * (ew / 4) * 4 * kcols * 2 * 4 + 16 + (size_t)ew * 32 * 36 * 4 : 0);
 }
 
@@ -595,10 +597,10 @@ static float tc_neg_c(const KernelParams& kp) {
     return kp.family == kFamExp ? kp.neg_c / 255.f : kp.neg_c / (255.f * 255.f);
 }
 
-template <bool EXPD>
+template <bool EXPD, bool SPLIT>
 cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
     const float nc = tc_neg_c(kp);
-    const int split = kp.precision == FSG_PREC_SPLIT_BF16 ? 1 : 0;
+    const bool split = SPLIT;
     if (split && !t->Xs) return cudaErrorInvalidValue;
     const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(split ? t->tmap_sa : t->tmap_a);
     const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(split ? t->tmap_sb : t->tmap_b);
@@ -608,7 +610,7 @@ cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cuda
         const int nchunk = (t->nb + G - 1) / G;
         const int tmax = (int)((((int64_t)G * t->mmax) + kTcM - 1) / kTcM);
         const size_t smem = tc_bins_smem(kTcEpiWarps, G, kTcSymStages, true);
-        auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcSymStages, true, EXPD>;
+        auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcSymStages, true, EXPD, SPLIT>;
         cudaError_t e = set_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
         // the sums that the mirrored values reach are accumulated onto zero
@@ -616,7 +618,7 @@ cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cuda
         if (e != cudaSuccess) return e;
         dim3 grid(tmax, nchunk * (nchunk + 1) / 2);
         kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, G,
-                                                       nchunk, nc, kp.self_exclude, t->ws.binsum, t->status, split);
+                                                       nchunk, nc, kp.self_exclude, t->ws.binsum, t->status);
         return cudaGetLastError();
     }
     const int qblocks = (int)((t->n + kTcM - 1) / kTcM);
@@ -628,19 +630,22 @@ cudaError_t launch_kde_bins_tc_f(const fsg_tree* t, const KernelParams& kp, cuda
     if (t->tune.tc_bins > 0 && t->tune.tc_bins < bpc) bpc = t->tune.tc_bins;
     chunks = (t->nb + bpc - 1) / bpc;
     const size_t smem = tc_bins_smem(kTcEpiWarps, bpc, kTcStages, false);
-    auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcStages, false, EXPD>;
+    auto kern = kde_bins_tc_kernel<kTcEpiWarps, kTcStages, false, EXPD, SPLIT>;
     {
         const cudaError_t e = set_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid(qblocks, chunks);
     kern<<<grid, 64 + 32 * kTcEpiWarps, smem, s>>>(ta, tb, norms, (int)t->n, t->dpad / kTcK, t->bnd, t->nb, bpc,
-                                                   chunks, nc, kp.self_exclude, t->ws.binsum, t->status, split);
+                                                   chunks, nc, kp.self_exclude, t->ws.binsum, t->status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_kde_bins_tc(const fsg_tree* t, const KernelParams& kp, cudaStream_t s) {
-    return kp.family == kFamExp ? launch_kde_bins_tc_f<true>(t, kp, s) : launch_kde_bins_tc_f<false>(t, kp, s);
+    // the split form is Gaussian only (the path checks refuse the others)
+    if (kp.precision == FSG_PREC_SPLIT_BF16) return launch_kde_bins_tc_f<false, true>(t, kp, s);
+    return kp.family == kFamExp ? launch_kde_bins_tc_f<true, false>(t, kp, s)
+                                : launch_kde_bins_tc_f<false, false>(t, kp, s);
 }
 
 }  // namespace fsg

@@ -116,32 +116,42 @@ __device__ __forceinline__ float tree_sum32(float (&x)[32]) {
 }
 
 // Kernel values v[0..31] of 32 columns of one row from its 32 dot products.
+// pn: the 32 columns' norms, 16-byte aligned (read as float4 broadcasts).
 // CHECK: test for the ragged end (p >= pe) and the query's own position.
 // EXPD: the exponential kernel (Sec. 2.1), whose exponent scales the
 // Euclidean distance, the square root of the exact integer squared distance.
-template <bool CHECK, bool EXPD = false>
+// CLAMP: clamp the squared distance at zero (the split form, whose expansion
+// can round below zero; on 8-bit data it is an exact non-negative integer
+// while the norms stay below 2^24, and otherwise off by the norms' rounding
+// on either side of zero).
+template <bool CHECK, bool EXPD = false, bool CLAMP = true>
 __device__ __forceinline__ void tc_values32(const uint32_t (&r)[32], const float* __restrict__ pn, int pc, float nq,
                                             float neg_c, int q, int pe, int self_exclude, float (&v)[32]) {
     const uint64_t nq2 = f2_pack(nq, nq), m2 = f2_pack(-2.f, -2.f), nc2 = f2_pack(neg_c, neg_c);
 #pragma unroll
-    for (int j = 0; j < 32; j += 2) {
-        // integer units: exact while the sums stay below 2^24
-        const uint64_t arg = f2_fma(m2, f2_pack(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
-                                    f2_add(nq2, f2_pack(pn[j], pn[j + 1])));
-        const float2 a = f2_unpack(arg);
-        float x0 = fmaxf(a.x, 0.f), x1 = fmaxf(a.y, 0.f);
-        if (EXPD) {
-            x0 = sqrt_approx(x0);
-            x1 = sqrt_approx(x1);
+    for (int j4 = 0; j4 < 32; j4 += 4) {
+        const float4 p4 = *reinterpret_cast<const float4*>(pn + j4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = j4 + 2 * h;
+            // integer units: exact while the sums stay below 2^24
+            const uint64_t arg = f2_fma(m2, f2_pack(__uint_as_float(r[j]), __uint_as_float(r[j + 1])),
+                                        f2_add(nq2, h ? f2_pack(p4.z, p4.w) : f2_pack(p4.x, p4.y)));
+            const float2 a = f2_unpack(arg);
+            float x0 = CLAMP ? fmaxf(a.x, 0.f) : a.x, x1 = CLAMP ? fmaxf(a.y, 0.f) : a.y;
+            if (EXPD) {
+                x0 = sqrt_approx(x0);
+                x1 = sqrt_approx(x1);
+            }
+            const float2 e = f2_unpack(f2_mul(f2_pack(x0, x1), nc2));
+            float k0 = ex2_approx(e.x), k1 = ex2_approx(e.y);
+            if (CHECK) {
+                if (pc + j >= pe || (self_exclude && pc + j == q)) k0 = 0.f;
+                if (pc + j + 1 >= pe || (self_exclude && pc + j + 1 == q)) k1 = 0.f;
+            }
+            v[j] = k0;
+            v[j + 1] = k1;
         }
-        const float2 e = f2_unpack(f2_mul(f2_pack(x0, x1), nc2));
-        float k0 = ex2_approx(e.x), k1 = ex2_approx(e.y);
-        if (CHECK) {
-            if (pc + j >= pe || (self_exclude && pc + j == q)) k0 = 0.f;
-            if (pc + j + 1 >= pe || (self_exclude && pc + j + 1 == q)) k1 = 0.f;
-        }
-        v[j] = k0;
-        v[j + 1] = k1;
     }
 }
 

@@ -5,7 +5,9 @@ access.  The test builds that library beside the normal one and runs graph
 builds through it on every path it instruments (the symmetric FP32 and
 plain bin passes, descend_top and the item scatter, the 128-point and
 generic leaf kernels, the symmetric tensor-core pass, the high-precision
-re-decision), each against the FP64 oracle, with no check failing."""
+re-decision, the split form at d > 64 and a stepped build over uneven
+ranges), each against the FP64 oracle or the whole build, with no check
+failing."""
 import os
 import subprocess
 import sys
@@ -44,6 +46,29 @@ for X, sigma, L, extra in cases:
     smp, _, _ = ora.sample(X, ora.gamma(sigma), L, 5, queries=q)
     assert not ((b.samples.cpu().numpy()[q] != smp) & (b.flags.cpu().numpy()[q] == 0)).any()
     tree.close()
+# the split form at d > 64 (three-part operands on the tensor-core kernels)
+X = inputs.digit_like(n=1800, d=200, seed=5)
+tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
+b = fsg.fsg_build_graph(tree, fsg.params(3.0, precision=fsg.FSG_PREC_SPLIT_BF16), 16, 5)
+assert fsg.fsg_sync(tree) == 0
+out = (__import__("ctypes").c_int64 * 4)()
+assert lib.fsg_bounds_error(out) == 0 and list(out) == [0, 0, 0, 0], list(out)
+want = ora.degrees(X, ora.gamma(3.0))
+assert (np.abs(b.deg.cpu().numpy() - want) <= 1e-4 * want).all()
+tree.close()
+# a stepped build over uneven ranges (descent and bucketing by range)
+X = inputs.gaussian_mixture(n=7001, d=10, seed=6)
+tree = fsg.fsg_build_tree(torch.from_numpy(X).cuda())
+p = fsg.params(1.5, resolve=True)
+whole = fsg.fsg_build_graph(tree, p, 32, 7)
+fsg.fsg_graph_begin(tree, p, 32, 7)
+for a, c in ((5000, 7001), (0, 1), (1, 5000)):
+    fsg.fsg_graph_step(tree, a, c)
+st = fsg.fsg_graph_end(tree, 32)
+assert fsg.fsg_sync(tree) == 0
+assert lib.fsg_bounds_error(out) == 0 and list(out) == [0, 0, 0, 0], list(out)
+assert (st.samples.cpu().numpy() == whole.samples.cpu().numpy()).all()
+tree.close()
 print("bounds build ok")
 '''
 
