@@ -272,6 +272,8 @@ constexpr int kSymThreads = kSymWarps * 32;
 constexpr int kSymMaxBin = 128;     // points per bin (one shared-memory stage)
 constexpr int kSymMinBin = 61;      // a bin covers >= 16 lanes
 constexpr int kSymNodes = 16;       // bins per block at most
+constexpr int kSymMRow = kSymNodes + 1;  // mirror row stride: odd, so the B lanes that add to
+                                         // B consecutive rows hit B distinct banks
 constexpr int kSymStages = 3;
 // points per mirror reduce-scatter (fewer for large d, to stay within 128 registers)
 template <int D>
@@ -372,14 +374,14 @@ __device__ __forceinline__ void sym_batch(const float* __restrict__ tp, int pb, 
         float eh = reduce_scatter_half<B>(colE, lane);
         if (sw.nseg < 3) eh += __shfl_xor_sync(0xffffffffu, eh, 16);
         if (FULL || pl < nbat) {
-            if (lane < B) atomicAdd(&mrow[(pb + pl) * kSymNodes + sw.rf], eh);
+            if (lane < B) atomicAdd(&mrow[(pb + pl) * kSymMRow + sw.rf], eh);
             else if (sw.nseg == 3 && lane >= 16 && lane < 16 + B)
-                atomicAdd(&mrow[(pb + pl) * kSymNodes + sw.rf + 2], eh);
+                atomicAdd(&mrow[(pb + pl) * kSymMRow + sw.rf + 2], eh);
         }
         if (sw.nseg > 1) {
             float mh = reduce_scatter_half<B>(colM, lane);
             mh += __shfl_xor_sync(0xffffffffu, mh, 16);
-            if ((FULL || pl < nbat) && lane < B) atomicAdd(&mrow[(pb + pl) * kSymNodes + sw.rf + 1], mh);
+            if ((FULL || pl < nbat) && lane < B) atomicAdd(&mrow[(pb + pl) * kSymMRow + sw.rf + 1], mh);
         }
     }
 }
@@ -403,7 +405,7 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
             return false;
         }
         const float* tp = pts + s * STAGE_FLOATS;
-        float* mrow = mir + (b & 1) * kSymMaxBin * kSymNodes;
+        float* mrow = mir + (b & 1) * kSymMaxBin * kSymMRow;
         const int t0 = pbn[b], cnt = pbn[b + 1] - t0;
         uint64_t acc[2] = {0ull, 0ull};
         constexpr int B = SymBatch<D>::B;
@@ -430,8 +432,8 @@ __device__ __forceinline__ bool sym_bins(float* pts, float* mir, uint64_t* bars,
             for (int e = tid; e < cnt * nq; e += kSymThreads) {
                 const int r = e / nq, c = e - r * nq;
                 if (FSG_INB((size_t)(t0 + r) * nb + qn0 + c, bins_lim, kSiteSymMirror))
-                    binsum[(size_t)(t0 + r) * nb + qn0 + c] = mrow[r * kSymNodes + c];
-                mrow[r * kSymNodes + c] = 0.f;
+                    binsum[(size_t)(t0 + r) * nb + qn0 + c] = mrow[r * kSymMRow + c];
+                mrow[r * kSymMRow + c] = 0.f;
             }
         }
     }
@@ -454,8 +456,8 @@ __device__ __forceinline__ void sym_block_pair(const float* __restrict__ Xdup, c
     const long long bins_lim = 0;
 #endif
     float* pts = reinterpret_cast<float*>(smem_raw);                       // [stages][128][DP][2]
-    float* mir = pts + kSymStages * STAGE_FLOATS;                          // [2][128][kSymNodes]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(mir + 2 * kSymMaxBin * kSymNodes);
+    float* mir = pts + kSymStages * STAGE_FLOATS;                          // [2][128][kSymMRow]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(mir + 2 * kSymMaxBin * kSymMRow);
     int32_t* qb = reinterpret_cast<int32_t*>(bars + kSymStages);           // query bin bounds [G+1]
     int32_t* pbn = qb + kSymNodes + 1;                                     // point bin bounds [G+1]
     int32_t* lb = pbn + kSymNodes + 1;                                     // first lane of each query bin
@@ -465,7 +467,7 @@ __device__ __forceinline__ void sym_block_pair(const float* __restrict__ Xdup, c
     const int nq = min(G, nb - qn0), np = min(G, nb - pn0);
     if (tid <= nq) qb[tid] = bnd[qn0 + tid];
     if (tid <= np) pbn[tid] = bnd[pn0 + tid];
-    for (int i = tid; i < 2 * kSymMaxBin * kSymNodes; i += kSymThreads) mir[i] = 0.f;
+    for (int i = tid; i < 2 * kSymMaxBin * kSymMRow; i += kSymThreads) mir[i] = 0.f;
     if (tid == 0) {
         for (int s = 0; s < kSymStages; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
@@ -581,7 +583,7 @@ cudaError_t launch_sym_d(const fsg_tree* t, const KernelParams& kp, cudaStream_t
     constexpr int DP = (D + 3) & ~3;
     const int G = sym_block_bins(t);
     const int nblk = (t->nb + G - 1) / G;
-    const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymNodes * 4 +
+    const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymMRow * 4 +
                         kSymStages * 8 + 3 * (kSymNodes + 1) * 4;
     {
         const cudaError_t e = set_smem_limit(kde_bins_sym_kernel<D, F>, (int)smem);
@@ -653,7 +655,7 @@ template <int D, int F>
 cudaError_t launch_sym_packed_d(const SymPackDesc* d_descs, const SymPackTable* tab, int count, int total,
                                 cudaStream_t s) {
     constexpr int DP = (D + 3) & ~3;
-    const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymNodes * 4 +
+    const size_t smem = (size_t)kSymStages * kSymMaxBin * DP * 2 * 4 + (size_t)2 * kSymMaxBin * kSymMRow * 4 +
                         kSymStages * 8 + 3 * (kSymNodes + 1) * 4;
     if (tab) {
         const cudaError_t e = set_smem_limit(kde_bins_sym_packed_param_kernel<D, F>, (int)smem);
