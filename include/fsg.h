@@ -394,7 +394,9 @@ int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_
  * while each call's flagged samples fit the re-decision's batched scratch,
  * max(65,536, n L / 64); beyond it the per-sample fallback sums in another
  * order); statistics count the work done (a repeated step counts twice).  Any other call on the tree
- * (fsg_build_graph, fsg_degrees, fsg_tree_update, ...) ends the run.
+ * (fsg_build_graph, fsg_degrees, fsg_tree_update, ...) ends the run.  The
+ * steps share the tree's workspace: issue them one after another on one
+ * stream, or order them with events (steps that overlap on the GPU race).
  * Fused schedule only.
  *   q_begin, q_end : 0 <= q_begin < q_end <= n.
  *   cursor         : host int64: smallest position not yet stepped (n when
