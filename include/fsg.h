@@ -578,8 +578,8 @@ int fsg_bounds_error(int64_t* out);
 
 /*
  * End-to-end entry point on HOST buffers: copies h_points to the device,
- * builds the tree (FSG_ORDER_SPATIAL for FSG_PREC_SPLIT_BF16, identity
- * otherwise), runs fsg_build_graph, and copies the edge list back.  The
+ * builds the tree (FSG_ORDER_SPATIAL for FSG_PREC_SPLIT_BF16 up to d = 64,
+ * identity otherwise), runs fsg_build_graph, and copies the edge list back.  The
  * server builds its trees the same way.
  *   h_src, h_dst (int32 [cap]), h_w (float32 [cap]; params->weight_f64 must
  *   be 0), *h_m_out (edge count).

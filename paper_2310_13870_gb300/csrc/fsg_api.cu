@@ -1114,8 +1114,9 @@ int fsg_build_graph_host(const float* h_points, int64_t n, int32_t d, const fsg_
     }
     e = cudaMemcpyAsync(hc.d_points, h_points, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return status_of(e);
-    // the split form takes the spatial tree order (compact tiles for its centring)
-    const bool spatial = p->precision == FSG_PREC_SPLIT_BF16;
+    // the split form up to d = 64 takes the spatial tree order (compact tiles
+    // for its centring; above d = 64 it centres nothing)
+    const bool spatial = p->precision == FSG_PREC_SPLIT_BF16 && d <= 64;
     fsg_tree* t = hc.tree;
     if (t && t->n == n && t->d == d && (t->ord != nullptr) == spatial) {
         rc = fsg_tree_update(t, hc.d_points, stream);

@@ -52,8 +52,10 @@ struct Slot {
 size_t request_bytes(const fsg_request& r) {
     size_t b = fsg::tree_bytes_estimate(r.n, r.d, r.L) + sizeof(float) * (size_t)r.n * r.d +
                (sizeof(int32_t) * 2 + sizeof(float)) * (size_t)r.n * r.L + 4096;
-    if (r.params.precision == FSG_PREC_SPLIT_BF16)  // bins hold at least 32 points; the order's scratch
+    if (r.params.precision == FSG_PREC_SPLIT_BF16 && r.d <= 64)  // bins hold at least 32 points; the order's scratch
         b += fsg::split_workspace_bytes(r.n, (r.n + 31) / 32, r.d > 16) + fsg::spatial_order_scratch_bytes(r.n, r.d);
+    else if (r.params.precision == FSG_PREC_SPLIT_BF16)  // d > 64: the three-part BF16 image and its norms
+        b += (sizeof(uint16_t) * 3 * (size_t)((r.d + 63) / 64 * 64) + sizeof(float)) * (size_t)(r.n + 256);
     return b;
 }
 
@@ -146,9 +148,11 @@ struct fsg_server {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? FSG_ERR_OOM : FSG_ERR_CUDA;
         }
-        // split-precision requests get the spatial tree order (compact tiles for its centring)
+        // split-precision requests up to d = 64 get the spatial tree order
+        // (compact tiles for its centring; the form above d = 64 centres nothing)
         fsg_tree_opts topts{};
-        topts.order = r.params.precision == FSG_PREC_SPLIT_BF16 ? FSG_ORDER_SPATIAL : FSG_ORDER_IDENTITY;
+        topts.order = r.params.precision == FSG_PREC_SPLIT_BF16 && r.d <= 64 ? FSG_ORDER_SPATIAL
+                                                                             : FSG_ORDER_IDENTITY;
         int rc = fsg::build_tree_internal(s.d_points, r.n, r.d, &topts, s.stream, pool, &s.tree);
         if (rc != FSG_OK) return rc;
         const fsg_params& p = r.params;
