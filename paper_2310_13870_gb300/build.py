@@ -66,7 +66,7 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(nvcc, s, verbose), srcs))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"]  # dlopen: the NVTX tool hook
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -12,6 +12,8 @@
 #include <mutex>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fsg_internal.cuh"
 
 namespace fsg {
@@ -83,11 +85,19 @@ KernelParams make_kernel_params(const fsg_params* p, int L, uint64_t seed) {
 }
 
 // Records the start/end event of a phase when profiling is on.
+// One phase of a call: CUDA events around it when profiling (fsg_profile),
+// and always an NVTX range with the phase's name on the host timeline, for
+// tracing tools such as Nsight Systems (without a tool attached the NVTX
+// calls return at once).
+constexpr const char* kPhaseNames[FSG_NUM_PHASES] = {"fsg:tree",  "fsg:kde_bins", "fsg:descend_top",
+                                                     "fsg:bucket", "fsg:leaf",    "fsg:edges",
+                                                     "fsg:outputs", "fsg:resolve"};
 struct PhaseScope {
     fsg_tree* t;
     int phase;
     cudaStream_t s;
     PhaseScope(fsg_tree* t_, int phase_, cudaStream_t s_) : t(t_), phase(phase_), s(s_) {
+        nvtxRangePushA(kPhaseNames[phase]);
         if (t->profiling) cudaEventRecord(t->ev_start[phase], s);
     }
     ~PhaseScope() {
@@ -95,6 +105,7 @@ struct PhaseScope {
             cudaEventRecord(t->ev_end[phase], s);
             t->ev_used[phase] = true;
         }
+        nvtxRangePop();
     }
 };
 
