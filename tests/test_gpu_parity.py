@@ -155,6 +155,31 @@ def test_dimensions(fsg, d):
     check_samples(g["samples"], g["flags"], o["samples"])
 
 
+@pytest.mark.parametrize("n,d", [(700, 100), (601, 1000), (500, 4096)])
+def test_wide_dimensions(fsg, n, d):
+    # the FP32 generic passes up to the widest d the library takes (FP32
+    # data, so AUTO keeps FP32): many 32-coordinate chunks, ragged n.  The
+    # squared distance sums d rounded terms, so a term with exponent a (log2
+    # units) is within ln2 a (d + 3) 2^-24 relative (plus ex2's 2^-22 and the
+    # sums' roundings); the degrees are checked against that bound over each
+    # query's terms where it exceeds 1e-5.  sigma = sqrt(d) keeps a near 1.5,
+    # where the typical error stays far inside the 2^-13 decision flags.
+    from scipy.spatial.distance import cdist
+    X = inputs.gaussian_mixture(n=n, d=d, k=3, box=2.0, seed=d)
+    sigma = math.sqrt(d)
+    gam = ora.gamma(sigma)
+    g = gpu_graph(fsg, X, sigma, 8, d)
+    o = ora.build_graph(X, gam, 8, d)
+    Xd = X.astype(np.float64)
+    a = gam * math.log2(math.e) * cdist(Xd, Xd, "sqeuclidean")
+    kv = np.exp2(-a)
+    np.fill_diagonal(kv, 0.0)
+    bound = (kv * a).sum(1) * math.log(2) * (d + 3) * 2.0 ** -24 + o["deg"] * (2.0 ** -22 + 96 * 2.0 ** -24)
+    err = np.abs(g["deg"] - o["deg"])
+    assert (err <= np.maximum(bound, DEG_RTOL * o["deg"]) + n * TINY).all(), float((err / o["deg"]).max())
+    check_samples(g["samples"], g["flags"], o["samples"])
+
+
 def test_digit_like_d784(fsg):
     # 784-dimensional 8-bit images, sigma = median pairwise distance / 2.
     X = inputs.digit_like(n=2500, seed=3)
