@@ -74,6 +74,7 @@ def edge_set(src, dst):
     (777, 2, 0.1, 7, 3),       # ragged n, odd L
     (1500, 5, 0.6, 64, 1),     # L = 64 (full sample mask)
     (300, 10, 1.5, 33, 2),     # L just above one warp
+    (1001, 3, 0.3, 1, 4),      # L = 1: one sample per point
 ])
 def test_full_graph_matches_oracle(fsg, n, d, sigma, L, seed):
     if d == 2:
