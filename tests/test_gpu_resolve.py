@@ -64,6 +64,11 @@ CASES = {
     "approx_d10": (lambda: inputs.gaussian_mixture(n=6_000, d=10, seed=7), 1.5, 32, 5,
                    {"precision": 2, "kde_eps": 1.0 / (6.0 * np.log(6000))}, True),
     "digits_tc": (lambda: inputs.digit_like(n=3_000, seed=8), None, 16, 6, {}, False),
+    # the split form above d = 64 on FP32 data (digit images with a jitter
+    # below one grey level); its flagged samples take the per-sample walker
+    "split_d200": (lambda: (inputs.digit_like(n=2_000, d=200, seed=10).astype(np.float64) +
+                            np.random.Generator(np.random.PCG64(10)).uniform(0.0, 1.0 / 255.0, (2_000, 200))
+                            ).astype(np.float32), 3.0, 16, 8, {"precision": 2}, False),
 }
 
 
