@@ -241,6 +241,9 @@ def sub_digits(fsg, stream, flush, steps):
         bufs = fsg.GraphBuffers(n, L, with_aux=False)
         bufs.deg = torch.empty(n, dtype=torch.float64, device="cuda")
 
+    # launch shapes picked by the library's autotuner (untimed), as for the headline workload
+    fsg.fsg_autotune(tree, p, L, seed, reps=3, stream=stream)
+
     def step():
         fsg.fsg_tree_update(tree, pts, stream=stream)
         fsg.fsg_build_graph(tree, p, L, seed, bufs=bufs, stream=stream)
@@ -266,6 +269,7 @@ def sub_digits(fsg, stream, flush, steps):
     # the same input in split precision (three-part BF16 operands, six
     # products per coordinate, the FP32-data form at d > 64)
     ps = fsg.params(sigma, precision=fsg.FSG_PREC_SPLIT_BF16)
+    fsg.fsg_autotune(tree, ps, L, seed, reps=3, stream=stream)  # its own launch shapes (untimed)
 
     def step_split():
         fsg.fsg_tree_update(tree, pts, stream=stream)
