@@ -22,7 +22,8 @@
 //
 // The same kernels serve the split precision (FSG_PREC_SPLIT_BF16) for FP32
 // data at d > 64.  Each coordinate is held as three BF16 parts, x = hi + mid
-// + lo exactly (each part the BF16 rounding of what the previous ones leave),
+// + lo exactly for |x| >= 2^-100 (each part the BF16 rounding of what the
+// previous ones leave; smaller values add nothing at FP32 precision),
 // in one row of 3 dpad values; x.y is accumulated in FP32 in TMEM from six of
 // the nine part products, the small ones first (lo.hi, hi.lo, mid.mid,
 // mid.hi, hi.mid, hi.hi: the three left out lie below 2^-24 of |x||y|), each
