@@ -4,8 +4,11 @@
  * The library computes, on one GPU, the data-parallel core of the algorithm of
  * Macgregor & Sun, "Fast Approximation of Similarity Graphs with Kernel
  * Density Estimation" (NeurIPS 2023):
- *   - Gaussian kernel k(x_i,x_j) = exp(-gamma ||x_i-x_j||^2)          (Sec. 2.1)
- *   - KDE sums g_[a,b](y_i) = sum_{j=a..b} k(y_i,x_j), computed exactly   (Eq. 1)
+ *   - Gaussian kernel k(x_i,x_j) = exp(-gamma ||x_i-x_j||^2), and the
+ *     Laplacian and exponential kernels of the same section       (Sec. 2.1)
+ *   - KDE sums g_[a,b](y_i) = sum_{j=a..b} k(y_i,x_j), computed exactly, or
+ *     within a stated relative bound (approximate KDE, fsg_params.kde_eps)
+ *                                                                      (Eq. 1)
  *   - degrees g_[1,n](x_i)                                          (Algorithm 2)
  *   - L neighbour samples per point by recursive halving of the point set,
  *     moving left with probability g_left/(g_left+g_right)   (Algorithm 1, Sec. 4.1)
@@ -149,8 +152,8 @@ typedef struct {
      * kde_eps * degree of its mass (a one-sided error, before rounding).
      * Decisions on those sums are flagged with the extra tolerance
      * kde_eps * degree, so unflagged samples still equal the exact method's.
-     * Values inside a bin are not approximated.  FSG_PREC_SPLIT_BF16 only
-     * (FSG_ERR_UNSUPPORTED otherwise); negative, non-finite or > 0.5:
+     * Values inside a bin are not approximated.  FSG_PREC_SPLIT_BF16 with
+     * d <= 64 only (FSG_ERR_UNSUPPORTED otherwise); negative, non-finite or > 0.5:
      * FSG_ERR_INVALID_ARG.  The paper's bound for the method is
      * eps <= 1/(6 log n). */
     float kde_eps;
