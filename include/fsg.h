@@ -242,11 +242,14 @@ int fsg_tree_info(const fsg_tree* tree, int64_t* n, int32_t* d, int32_t* depth);
 /*
  * Kernel evaluations k(x_q, x_p) that the bin pass of the fused schedule
  * executes on this tree with these parameters (a diagnostic for roofline
- * accounting; Eq. 1 needs n^2 of them).  n^2 for the plain, generic-d and
- * tensor-core passes; (n^2 + sum_k S_k^2) / 2 for the symmetric FP32 pass,
- * S_k the point counts of its blocks of bins; for the split pass n^2 is an
- * upper bound (it skips tile pairs whose values are all zero in FP32 and
- * counts what it executes in fsg_stats.n_bin_evals).  0 for the levelwise
+ * accounting; Eq. 1 needs n^2 of them).  The symmetric passes evaluate each
+ * pair once off their diagonal blocks: (n^2 + sum_k S_k^2) / 2 for the
+ * d <= 16 FP32 pass and the tensor-core pass (also in the split form above
+ * d = 64), S_k the point counts of their blocks or chunks of bins, and
+ * T (T + 1) / 2 tiles of 128 x 128 for the d > 16 FP32 pass (T = ceil(n /
+ * 128)); n^2 for the two-order forms (other bin sizes); for the d <= 64
+ * split pass n^2 is an upper bound (it skips tile pairs whose values are
+ * all zero in FP32 and counts what it executes in fsg_stats.n_bin_evals).  0 for the levelwise
  * schedules, which count their own evaluations on the device
  * (fsg_stats.n_evals).
  *   evals : host int64, written on success.
@@ -263,7 +266,8 @@ int fsg_bin_pass_evals(const fsg_tree* tree, const fsg_params* params, int64_t* 
  */
 typedef struct {
     int32_t sym_bins;     /* bins per block of the symmetric d <= 16 bin pass   */
-    int32_t tc_bins;      /* bins per chunk of the tensor-core bin pass (<= 24) */
+    int32_t tc_bins;      /* bins per chunk of the tensor-core bin pass (<= 24; */
+                          /* 8..16 in its symmetric form)                      */
     int32_t leaf_splits;  /* CTAs per bin of the leaf finish                   */
     int32_t reserved[5];
 } fsg_tuning;
@@ -396,11 +400,11 @@ int fsg_build_graph(fsg_tree* tree, const fsg_params* params, int32_t L, uint64_
  * those of fsg_build_graph with the same arguments (with params->resolve:
  * while each call's flagged samples fit the re-decision's batched scratch,
  * max(65,536, n L / 64); beyond it the per-sample fallback sums in another
- * order); statistics count the work done (a repeated step counts twice).  Any other call on the tree
- * (fsg_build_graph, fsg_degrees, fsg_tree_update, ...) ends the run.  The
- * steps share the tree's workspace: issue them one after another on one
- * stream, or order them with events (steps that overlap on the GPU race).
- * Fused schedule only.
+ * order); statistics count the work done (a repeated step counts twice).
+ * Any other call on the tree (fsg_build_graph, fsg_degrees,
+ * fsg_tree_update, ...) ends the run.  The steps share the tree's
+ * workspace: issue them one after another on one stream, or order them with
+ * events (steps that overlap on the GPU race).  Fused schedule only.
  *   q_begin, q_end : 0 <= q_begin < q_end <= n.
  *   cursor         : host int64: smallest position not yet stepped (n when
  *                    every position was).
