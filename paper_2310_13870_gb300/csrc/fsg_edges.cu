@@ -298,19 +298,22 @@ __global__ void outputs_kernel(const int32_t* __restrict__ leaf_pos, const uint8
                                const uint8_t* __restrict__ lflags, const int32_t* __restrict__ perm, int n, int L,
                                int32_t* __restrict__ d_samples,
                                uint8_t* __restrict__ d_flags, fsg_stats* __restrict__ stats) {
-    const int64_t total = (int64_t)n * L;
+    // one warp per query position q, lanes over its L samples
     unsigned long long fl = 0, sf = 0, em = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int q = (int)(e / L);
-        const int l = (int)(e - (int64_t)q * L);
-        const int32_t pos = leaf_pos[e];
-        const uint8_t f = flags[e] | (pos >= 0 ? lflags[e] : (uint8_t)0);
-        const size_t o = (size_t)perm[q] * L + l;
-        if (d_samples) d_samples[o] = pos >= 0 ? perm[pos] : -1;
-        if (d_flags) d_flags[o] = f;
-        fl += f != 0;
-        sf += pos == q;
-        em += pos < 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < n; q += warps) {
+        const size_t orow = (size_t)perm[q] * L;
+        for (int l = lane; l < L; l += 32) {
+            const size_t e = (size_t)q * L + l;
+            const int32_t pos = leaf_pos[e];
+            const uint8_t f = flags[e] | (pos >= 0 ? lflags[e] : (uint8_t)0);
+            if (d_samples) d_samples[orow + l] = pos >= 0 ? perm[pos] : -1;
+            if (d_flags) d_flags[orow + l] = f;
+            fl += f != 0;
+            sf += pos == q;
+            em += pos < 0;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -367,7 +370,7 @@ cudaError_t launch_outputs(const fsg_tree* t, const KernelParams& kp, int32_t* d
                            fsg_stats* d_stats, cudaStream_t s) {
     (void)d_stats;
     const auto& ws = t->ws;
-    outputs_kernel<<<grid_for(t->n * kp.L, 256), 256, 0, s>>>(ws.leaf_pos, ws.flags, ws.lflags, t->perm, (int)t->n,
+    outputs_kernel<<<grid_for(t->n * 32, 256), 256, 0, s>>>(ws.leaf_pos, ws.flags, ws.lflags, t->perm, (int)t->n,
                                                               kp.L, d_samples, d_flags, ws.stats);
     return cudaGetLastError();
 }
